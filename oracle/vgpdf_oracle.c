@@ -1,0 +1,1079 @@
+/*
+ * vgpdf_oracle.c -- plain, slow, FP64 CPU oracle for batched local-GP distance fields.
+ *
+ * TEST INFRASTRUCTURE ONLY.  Only the test suite, the package's smoke check and the
+ * benchmark's CPU-baseline leg load this library.  It shares no code, header, table or
+ * constant with the CUDA path, and the CUDA path never calls it.
+ *
+ * What it computes, in the paper's order (Wu, Le Gentil, Vidal-Calleja, "VDB-GPDF",
+ * arXiv 2407.09649):
+ *   - voxelisation into 8^3-voxel leaves, voxel centres as training points (Sec. IV-A);
+ *   - one GP per leaf / per query neighbourhood, SE kernel k = exp(-r^2 / (2 l^2))
+ *     (Sec. III-A), A = K + sigma^2 I factorised by a textbook Cholesky, alpha = A^-1 1
+ *     (Eq. 1);
+ *   - latent mean o = k^T alpha (Eq. 1), latent variance u = 1 - k^T A^-1 k (Eq. 2 with
+ *     the sign read as the standard GP posterior), gradient of o (Eq. 5);
+ *   - reverting d = sqrt(-2 l^2 log o) (Eq. 3), distance variance v = Lambda^2 u with
+ *     Lambda = -l / (o sqrt(-2 log o)) = -l^2 / (o d) (Eq. 4), chain-rule gradient
+ *     grad d = -l^2 grad o / (o d);
+ *   - closest-node selection of the L-GPDF GP for each testing voxel (Sec. IV-B);
+ *   - probabilistic fusion, inverse-variance (Eqs. 7-8) or TSDF-style weights (Eq. 9);
+ *   - G-GPDF queries against the GP of the query's 27-leaf neighbourhood (Sec. IV-D,
+ *     with the neighbourhood search done on the leaf lattice instead of a kd-tree);
+ *   - the backward pass of the distance w.r.t. query and surface points, derived from
+ *     Eq. 1 by differentiating alpha = A^-1 1.
+ *
+ * The paper leaves the following open; this file takes these readings:
+ *   - voxel index ijk = floor(p / vs + 1/2) in IEEE FP64 (p widened from float32);
+ *     |ijk| < 2^20 - 64, else the point is dropped / the query is invalid;
+ *   - voxel bit inside a leaf = x + 8 y + 64 z of the in-leaf offset; training points
+ *     of a leaf in ascending bit order; when a leaf holds n > cap occupied voxels it
+ *     keeps indices floor(k n / cap), k = 0..cap-1;
+ *   - the capped occupancy of Eq. 3-4: o >= 1 gives d = 0 with zero gradient;
+ *     o <= 0 or log o below -d_max^2 / (2 l^2) gives d = d_max, status 2; Lambda uses
+ *     max(d, d_var_floor) and o = 1 when o >= 1;
+ *   - closest L-GPDF node: the voxel's own leaf if it holds a GP, else the neighbour leaf
+ *     with the smallest squared centre distance in half-voxel integer units, ties to the
+ *     first in (dz, dy, dx) order from -1 to 1;
+ *   - G-GPDF instance of a query leaf M: the points of the 27 leaves around M; if those
+ *     are empty, the 27 leaves around the nearest occupied leaf F within Chebyshev radius
+ *     max_leaf_search (nearest by integer leaf distance, ties to the smaller key); none ->
+ *     status 1.  When an instance has more than max_pts_group points it keeps those
+ *     nearest to the centre leaf's centre (FP64 squared distance, ties to the lower
+ *     point index); instance points are kept in ascending point index.
+ *
+ * Parity status: every exported function is pinned by the CPU tests against closed forms,
+ * brute force, exact rational arithmetic or invariants.
+ *
+ * Build: gcc -O2 -fPIC -shared -ffp-contract=off -fopenmp (no FMA contraction, so the
+ * voxel-key and selection arithmetic is the plain IEEE sequence written here).
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+typedef struct {
+    double voxel_size;      /* metres per voxel edge */
+    double lengthscale;     /* SE kernel length scale l (m) */
+    double sigma_occ;       /* latent occupancy noise std; sigma^2 is added to diag(K) */
+    double d_max;           /* distance cap (m) -> log-occupancy floor */
+    double d_var_floor;     /* lower bound on d inside Lambda (m) */
+    int32_t max_pts_leaf;   /* per-leaf training cap (L-GPDF) */
+    int32_t max_pts_group;  /* per-neighbourhood cap (G-GPDF) */
+    int32_t max_leaf_search;/* Chebyshev leaf radius of the fallback search */
+    int32_t fusion;         /* 0: inverse variance (Eqs. 7-8); 1: TSDF weights (Eq. 9) */
+} or_params;
+
+enum { ST_OK = 0, ST_NO_SUPPORT = 1, ST_CLAMPED = 2, ST_BAD_INPUT = 3, ST_FACTOR_FAIL = 4 };
+
+#define KEY_BIAS (1LL << 20)
+#define IJK_LIMIT 1048512.0 /* 2^20 - 64 */
+
+/* ------------------------------------------------------------------------------------ */
+/* indexing                                                                             */
+/* ------------------------------------------------------------------------------------ */
+static int64_t floor_div8(int64_t v) { return v >= 0 ? v / 8 : -((-v + 7) / 8); }
+
+static uint64_t pack_key(int64_t x, int64_t y, int64_t z) {
+    return ((uint64_t)(x + KEY_BIAS) << 42) | ((uint64_t)(y + KEY_BIAS) << 21) |
+           (uint64_t)(z + KEY_BIAS);
+}
+
+static void unpack_key(uint64_t k, int64_t out[3]) {
+    out[0] = (int64_t)((k >> 42) & 0x1FFFFF) - KEY_BIAS;
+    out[1] = (int64_t)((k >> 21) & 0x1FFFFF) - KEY_BIAS;
+    out[2] = (int64_t)(k & 0x1FFFFF) - KEY_BIAS;
+}
+
+/* voxel index of one point (Sec. IV-A: points are grouped by the voxel they fall in). */
+static int voxel_ijk(const double p[3], double vs, int64_t ijk[3]) {
+    for (int a = 0; a < 3; ++a) {
+        if (!isfinite(p[a])) return 0;
+        double t = p[a] / vs;
+        double u = t + 0.5;
+        double f = floor(u);
+        if (!(f > -IJK_LIMIT && f < IJK_LIMIT)) return 0;
+        ijk[a] = (int64_t)f;
+    }
+    return 1;
+}
+
+static void leaf_of(const int64_t ijk[3], int64_t leaf[3], int32_t* bit) {
+    for (int a = 0; a < 3; ++a) leaf[a] = floor_div8(ijk[a]);
+    *bit = (int32_t)((ijk[0] - 8 * leaf[0]) + 8 * (ijk[1] - 8 * leaf[1]) + 64 * (ijk[2] - 8 * leaf[2]));
+}
+
+static int cmp_u64(const void* a, const void* b) {
+    uint64_t x = *(const uint64_t*)a, y = *(const uint64_t*)b;
+    return (x > y) - (x < y);
+}
+
+static int64_t find_key(const uint64_t* keys, int64_t n, uint64_t k) {
+    int64_t lo = 0, hi = n;
+    while (lo < hi) {
+        int64_t mid = lo + (hi - lo) / 2;
+        if (keys[mid] < k) lo = mid + 1; else hi = mid;
+    }
+    return (lo < n && keys[lo] == k) ? lo : -1;
+}
+
+void or_index_points(const or_params* P, const float* pts, int64_t n, int64_t* ijk_out,
+                     uint64_t* vkey, uint64_t* lkey, int32_t* bit_out, uint8_t* ok) {
+    for (int64_t i = 0; i < n; ++i) {
+        double p[3] = {(double)pts[3 * i], (double)pts[3 * i + 1], (double)pts[3 * i + 2]};
+        int64_t ijk[3] = {0, 0, 0}, leaf[3] = {0, 0, 0};
+        int32_t bit = 0;
+        int good = voxel_ijk(p, P->voxel_size, ijk);
+        if (good) leaf_of(ijk, leaf, &bit);
+        if (ijk_out) for (int a = 0; a < 3; ++a) ijk_out[3 * i + a] = good ? ijk[a] : 0;
+        if (vkey) vkey[i] = good ? pack_key(ijk[0], ijk[1], ijk[2]) : 0;
+        if (lkey) lkey[i] = good ? pack_key(leaf[0], leaf[1], leaf[2]) : 0;
+        if (bit_out) bit_out[i] = good ? bit : -1;
+        if (ok) ok[i] = (uint8_t)good;
+    }
+}
+
+/* ------------------------------------------------------------------------------------ */
+/* dense GP algebra on one instance (Eqs. 1, 2, 5), packed lower triangle, row major     */
+/* ------------------------------------------------------------------------------------ */
+#define PK(i, j) ((int64_t)(i) * ((i) + 1) / 2 + (j))
+
+/* Cholesky-Banachiewicz, row by row: A = L L^T, L overwrites the lower triangle. */
+static int cholesky_packed(double* A, int N) {
+    for (int i = 0; i < N; ++i) {
+        for (int j = 0; j <= i; ++j) {
+            double s = A[PK(i, j)];
+            for (int k = 0; k < j; ++k) s -= A[PK(i, k)] * A[PK(j, k)];
+            if (i == j) {
+                if (!(s > 0.0)) return 0;
+                A[PK(i, i)] = sqrt(s);
+            } else {
+                A[PK(i, j)] = s / A[PK(j, j)];
+            }
+        }
+    }
+    return 1;
+}
+
+/* L z = b (forward substitution) */
+static void forward_subst(const double* L, int N, const double* b, double* z) {
+    for (int i = 0; i < N; ++i) {
+        double s = b[i];
+        for (int k = 0; k < i; ++k) s -= L[PK(i, k)] * z[k];
+        z[i] = s / L[PK(i, i)];
+    }
+}
+
+/* L^T x = z (back substitution) */
+static void back_subst(const double* L, int N, const double* z, double* x) {
+    for (int i = N - 1; i >= 0; --i) {
+        double s = z[i];
+        for (int k = i + 1; k < N; ++k) s -= L[PK(k, i)] * x[k];
+        x[i] = s / L[PK(i, i)];
+    }
+}
+
+static double se_kernel(const double* a, const double* b, double l) {
+    double dx = a[0] - b[0], dy = a[1] - b[1], dz = a[2] - b[2];
+    double r2 = dx * dx + dy * dy + dz * dz;
+    return exp(-r2 / (2.0 * l * l));
+}
+
+/* Train one GP: L = chol(K + sigma^2 I), alpha = (K + sigma^2 I)^-1 1 (Eq. 1). */
+int or_gp_fit(const double* X, int N, const or_params* P, double* L, double* alpha) {
+    double s2 = P->sigma_occ * P->sigma_occ;
+    for (int i = 0; i < N; ++i) {
+        for (int j = 0; j < i; ++j) L[PK(i, j)] = se_kernel(X + 3 * i, X + 3 * j, P->lengthscale);
+        L[PK(i, i)] = 1.0 + s2;
+    }
+    if (!cholesky_packed(L, N)) return 0;
+    double* ones = (double*)malloc(sizeof(double) * (N > 0 ? N : 1));
+    double* z = (double*)malloc(sizeof(double) * (N > 0 ? N : 1));
+    for (int i = 0; i < N; ++i) ones[i] = 1.0;
+    forward_subst(L, N, ones, z);
+    back_subst(L, N, z, alpha);
+    free(ones);
+    free(z);
+    return 1;
+}
+
+typedef struct {
+    double o, go[3], u, d, gd[3], v;
+    int status;
+} or_eval;
+
+/* Reverting function (Eq. 3), its variance (Eq. 4) and the chain-rule gradient. */
+static void revert(const or_params* P, or_eval* r) {
+    double l = P->lengthscale, l2 = l * l;
+    double log_floor = -(P->d_max * P->d_max) / (2.0 * l2);
+    if (!(r->o > 0.0)) {
+        r->status = ST_CLAMPED; r->d = P->d_max; r->gd[0] = r->gd[1] = r->gd[2] = 0.0;
+        r->v = INFINITY;
+        return;
+    }
+    double lo = log(r->o);
+    if (lo < log_floor) {
+        r->status = ST_CLAMPED; r->d = P->d_max; r->gd[0] = r->gd[1] = r->gd[2] = 0.0;
+        r->v = INFINITY;
+        return;
+    }
+    r->status = ST_OK;
+    if (lo >= 0.0) {
+        double lam = -l2 / (1.0 * P->d_var_floor);
+        r->d = 0.0; r->gd[0] = r->gd[1] = r->gd[2] = 0.0;
+        r->v = lam * lam * r->u;
+        return;
+    }
+    r->d = sqrt(-2.0 * l2 * lo);
+    for (int a = 0; a < 3; ++a) r->gd[a] = -l2 * r->go[a] / (r->o * r->d);
+    double dv = r->d > P->d_var_floor ? r->d : P->d_var_floor;
+    double lam = -l2 / (r->o * dv);
+    r->v = lam * lam * r->u;
+}
+
+/* Latent mean (Eq. 1), its gradient (Eq. 5), latent variance (Eq. 2), then reverting. */
+static void gp_eval(const double* X, int N, const double* L, const double* alpha,
+                    const double xs[3], const or_params* P, int want_var, double* kbuf,
+                    double* vbuf, or_eval* r) {
+    double l = P->lengthscale;
+    double o = 0.0, g[3] = {0.0, 0.0, 0.0};
+    for (int j = 0; j < N; ++j) {
+        double k = se_kernel(xs, X + 3 * j, l);
+        if (kbuf) kbuf[j] = k;
+        o += alpha[j] * k;
+        for (int a = 0; a < 3; ++a) g[a] += alpha[j] * k * (X[3 * j + a] - xs[a]);
+    }
+    r->o = o;
+    for (int a = 0; a < 3; ++a) r->go[a] = g[a] / (l * l);
+    r->u = NAN;
+    if (want_var) {
+        forward_subst(L, N, kbuf, vbuf);
+        double s = 0.0;
+        for (int j = 0; j < N; ++j) s += vbuf[j] * vbuf[j];
+        double u = 1.0 - s;
+        r->u = u > 0.0 ? u : 0.0;
+    }
+    revert(P, r);
+    if (!want_var) r->v = NAN;
+}
+
+static void eval_invalid(or_eval* r, int status) {
+    r->o = NAN; r->u = NAN;
+    r->go[0] = r->go[1] = r->go[2] = 0.0;
+    r->d = INFINITY; r->gd[0] = r->gd[1] = r->gd[2] = 0.0; r->v = INFINITY;
+    r->status = status;
+}
+
+/* ------------------------------------------------------------------------------------ */
+/* batched independent instances                                                         */
+/* ------------------------------------------------------------------------------------ */
+int or_gp_batch(const or_params* P, int64_t n_inst, const int64_t* inst_off, const double* X,
+                const int64_t* q_off, const double* Q, int want_var, double* d, double* grad,
+                double* var, uint8_t* status, double* occ, double* grad_occ, double* u_out,
+                double* alpha_out) {
+    int err = 0;
+#pragma omp parallel for schedule(dynamic, 1) reduction(| : err)
+    for (int64_t I = 0; I < n_inst; ++I) {
+        int N = (int)(inst_off[I + 1] - inst_off[I]);
+        const double* XI = X + 3 * inst_off[I];
+        double* L = (double*)malloc(sizeof(double) * ((int64_t)N * (N + 1) / 2 + 1));
+        double* al = (double*)malloc(sizeof(double) * (N + 1));
+        double* kb = (double*)malloc(sizeof(double) * (N + 1));
+        double* vb = (double*)malloc(sizeof(double) * (N + 1));
+        if (!L || !al || !kb || !vb) { err = 1; free(L); free(al); free(kb); free(vb); continue; }
+        int ok = N > 0 && or_gp_fit(XI, N, P, L, al);
+        if (alpha_out) for (int j = 0; j < N; ++j) alpha_out[inst_off[I] + j] = ok ? al[j] : NAN;
+        for (int64_t q = q_off[I]; q < q_off[I + 1]; ++q) {
+            or_eval r;
+            const double* xs = Q + 3 * q;
+            if (!(isfinite(xs[0]) && isfinite(xs[1]) && isfinite(xs[2]))) eval_invalid(&r, ST_BAD_INPUT);
+            else if (N == 0) eval_invalid(&r, ST_NO_SUPPORT);
+            else if (!ok) eval_invalid(&r, ST_FACTOR_FAIL);
+            else gp_eval(XI, N, L, al, xs, P, want_var, kb, vb, &r);
+            if (d) d[q] = r.d;
+            if (grad) for (int a = 0; a < 3; ++a) grad[3 * q + a] = r.gd[a];
+            if (var) var[q] = r.v;
+            if (status) status[q] = (uint8_t)r.status;
+            if (occ) occ[q] = r.o;
+            if (grad_occ) for (int a = 0; a < 3; ++a) grad_occ[3 * q + a] = r.go[a];
+            if (u_out) u_out[q] = r.u;
+        }
+        free(L); free(al); free(kb); free(vb);
+    }
+    return err ? -1 : 0;
+}
+
+/* ------------------------------------------------------------------------------------ */
+/* L-GPDF frame: voxelise, one GP per leaf, testing voxels, closest-node inference       */
+/* ------------------------------------------------------------------------------------ */
+typedef struct {
+    uint64_t lkey;
+    int32_t bit;
+    int32_t pad;
+} vox_rec;
+
+static int cmp_vox(const void* a, const void* b) {
+    const vox_rec* x = (const vox_rec*)a;
+    const vox_rec* y = (const vox_rec*)b;
+    if (x->lkey != y->lkey) return x->lkey < y->lkey ? -1 : 1;
+    return (x->bit > y->bit) - (x->bit < y->bit);
+}
+
+typedef struct {
+    or_params P;
+    int64_t n_leaves;
+    uint64_t* leaf_key;   /* sorted */
+    int32_t* leaf_nocc;   /* occupied voxels before the cap */
+    int64_t* inst_off;    /* [n_leaves + 1] */
+    double* X;            /* training voxel centres, global FP64 */
+    int64_t* L_off;       /* packed factor offsets */
+    double* L;
+    double* alpha;
+    uint8_t* fit_ok;
+    int64_t n_test;
+    uint64_t* test_key;
+    uint64_t* test_inst_key;
+    double* test_d;
+    double* test_v;
+    double* test_grad;
+    uint8_t* test_status;
+} or_frame;
+
+static void voxel_of_bit(const int64_t leaf[3], int bit, int64_t ijk[3]) {
+    ijk[0] = 8 * leaf[0] + (bit & 7);
+    ijk[1] = 8 * leaf[1] + ((bit >> 3) & 7);
+    ijk[2] = 8 * leaf[2] + (bit >> 6);
+}
+
+void or_frame_free(or_frame* F) {
+    if (!F) return;
+    free(F->leaf_key); free(F->leaf_nocc); free(F->inst_off); free(F->X); free(F->L_off);
+    free(F->L); free(F->alpha); free(F->fit_ok); free(F->test_key); free(F->test_inst_key);
+    free(F->test_d); free(F->test_v); free(F->test_grad); free(F->test_status);
+    free(F);
+}
+
+or_frame* or_frame_build(const or_params* P, const float* pts, int64_t n) {
+    or_frame* F = (or_frame*)calloc(1, sizeof(or_frame));
+    if (!F) return NULL;
+    F->P = *P;
+    double vs = P->voxel_size;
+    /* 1. voxelise: (leaf key, bit) of every valid point, then unique */
+    vox_rec* R = (vox_rec*)malloc(sizeof(vox_rec) * (n > 0 ? n : 1));
+    int64_t m = 0;
+    for (int64_t i = 0; i < n; ++i) {
+        double p[3] = {(double)pts[3 * i], (double)pts[3 * i + 1], (double)pts[3 * i + 2]};
+        int64_t ijk[3], leaf[3];
+        int32_t bit;
+        if (!voxel_ijk(p, vs, ijk)) continue;
+        leaf_of(ijk, leaf, &bit);
+        R[m].lkey = pack_key(leaf[0], leaf[1], leaf[2]);
+        R[m].bit = bit;
+        R[m].pad = 0;
+        ++m;
+    }
+    qsort(R, (size_t)m, sizeof(vox_rec), cmp_vox);
+    int64_t u = 0;
+    for (int64_t i = 0; i < m; ++i)
+        if (u == 0 || R[i].lkey != R[u - 1].lkey || R[i].bit != R[u - 1].bit) R[u++] = R[i];
+    /* 2. leaves, occupied counts, capped training sets */
+    int64_t nl = 0;
+    for (int64_t i = 0; i < u; ++i) if (i == 0 || R[i].lkey != R[i - 1].lkey) ++nl;
+    F->n_leaves = nl;
+    F->leaf_key = (uint64_t*)malloc(sizeof(uint64_t) * (nl + 1));
+    F->leaf_nocc = (int32_t*)malloc(sizeof(int32_t) * (nl + 1));
+    F->inst_off = (int64_t*)malloc(sizeof(int64_t) * (nl + 1));
+    int64_t* run_start = (int64_t*)malloc(sizeof(int64_t) * (nl + 1));
+    {
+        int64_t li = -1;
+        for (int64_t i = 0; i < u; ++i) {
+            if (i == 0 || R[i].lkey != R[i - 1].lkey) {
+                ++li;
+                F->leaf_key[li] = R[i].lkey;
+                F->leaf_nocc[li] = 0;
+                run_start[li] = i;
+            }
+            F->leaf_nocc[li]++;
+        }
+    }
+    int cap = P->max_pts_leaf;
+    F->inst_off[0] = 0;
+    for (int64_t l = 0; l < nl; ++l) {
+        int64_t N = F->leaf_nocc[l] > cap ? cap : F->leaf_nocc[l];
+        F->inst_off[l + 1] = F->inst_off[l] + N;
+    }
+    int64_t T = F->inst_off[nl];
+    F->X = (double*)malloc(sizeof(double) * 3 * (T + 1));
+    F->L_off = (int64_t*)malloc(sizeof(int64_t) * (nl + 1));
+    F->L_off[0] = 0;
+    for (int64_t l = 0; l < nl; ++l) {
+        int64_t N = F->inst_off[l + 1] - F->inst_off[l];
+        F->L_off[l + 1] = F->L_off[l] + N * (N + 1) / 2;
+    }
+    F->L = (double*)malloc(sizeof(double) * (F->L_off[nl] + 1));
+    F->alpha = (double*)malloc(sizeof(double) * (T + 1));
+    F->fit_ok = (uint8_t*)malloc(nl + 1);
+#pragma omp parallel for schedule(dynamic, 4)
+    for (int64_t l = 0; l < nl; ++l) {
+        int64_t nocc = F->leaf_nocc[l];
+        int64_t N = F->inst_off[l + 1] - F->inst_off[l];
+        int64_t leaf[3];
+        unpack_key(F->leaf_key[l], leaf);
+        for (int64_t k = 0; k < N; ++k) {
+            int64_t pick = nocc > cap ? (k * nocc) / cap : k;
+            int64_t ijk[3];
+            voxel_of_bit(leaf, R[run_start[l] + pick].bit, ijk);
+            for (int a = 0; a < 3; ++a) F->X[3 * (F->inst_off[l] + k) + a] = (double)ijk[a] * vs;
+        }
+        F->fit_ok[l] = (uint8_t)or_gp_fit(F->X + 3 * F->inst_off[l], (int)N, P, F->L + F->L_off[l],
+                                          F->alpha + F->inst_off[l]);
+    }
+    free(run_start);
+    free(R);
+    /* 3. testing voxels: every voxel of every GP leaf and of its 26 neighbours */
+    uint64_t* tl = (uint64_t*)malloc(sizeof(uint64_t) * (27 * nl + 1));
+    int64_t ntl = 0;
+    for (int64_t l = 0; l < nl; ++l) {
+        int64_t leaf[3];
+        unpack_key(F->leaf_key[l], leaf);
+        for (int dz = -1; dz <= 1; ++dz)
+            for (int dy = -1; dy <= 1; ++dy)
+                for (int dx = -1; dx <= 1; ++dx) tl[ntl++] = pack_key(leaf[0] + dx, leaf[1] + dy, leaf[2] + dz);
+    }
+    qsort(tl, (size_t)ntl, sizeof(uint64_t), cmp_u64);
+    int64_t nt = 0;
+    for (int64_t i = 0; i < ntl; ++i) if (nt == 0 || tl[i] != tl[nt - 1]) tl[nt++] = tl[i];
+    F->n_test = nt * 512;
+    F->test_key = (uint64_t*)malloc(sizeof(uint64_t) * (F->n_test + 1));
+    F->test_inst_key = (uint64_t*)malloc(sizeof(uint64_t) * (F->n_test + 1));
+    F->test_d = (double*)malloc(sizeof(double) * (F->n_test + 1));
+    F->test_v = (double*)malloc(sizeof(double) * (F->n_test + 1));
+    F->test_grad = (double*)malloc(sizeof(double) * 3 * (F->n_test + 1));
+    F->test_status = (uint8_t*)malloc(F->n_test + 1);
+    int Nmax = 1;
+    for (int64_t l = 0; l < nl; ++l) {
+        int64_t N = F->inst_off[l + 1] - F->inst_off[l];
+        if (N > Nmax) Nmax = (int)N;
+    }
+#pragma omp parallel
+    {
+        double* kb = (double*)malloc(sizeof(double) * Nmax);
+        double* vb = (double*)malloc(sizeof(double) * Nmax);
+#pragma omp for schedule(dynamic, 4)
+        for (int64_t t = 0; t < nt; ++t) {
+            int64_t M[3];
+            unpack_key(tl[t], M);
+            int64_t own = find_key(F->leaf_key, nl, tl[t]);
+            for (int b = 0; b < 512; ++b) {
+                int64_t ijk[3];
+                voxel_of_bit(M, b, ijk);
+                int64_t inst = own;
+                if (inst < 0) {
+                    int64_t best_d2 = INT64_MAX;
+                    for (int dz = -1; dz <= 1; ++dz)
+                        for (int dy = -1; dy <= 1; ++dy)
+                            for (int dx = -1; dx <= 1; ++dx) {
+                                if (!dx && !dy && !dz) continue;
+                                int64_t Fl[3] = {M[0] + dx, M[1] + dy, M[2] + dz};
+                                int64_t f = find_key(F->leaf_key, nl, pack_key(Fl[0], Fl[1], Fl[2]));
+                                if (f < 0) continue;
+                                int64_t d2 = 0;
+                                for (int a = 0; a < 3; ++a) {
+                                    int64_t e = 2 * ijk[a] - (16 * Fl[a] + 7);
+                                    d2 += e * e;
+                                }
+                                if (d2 < best_d2) { best_d2 = d2; inst = f; }
+                            }
+                }
+                int64_t o = t * 512 + b;
+                F->test_key[o] = pack_key(ijk[0], ijk[1], ijk[2]);
+                or_eval r;
+                double xs[3] = {(double)ijk[0] * vs, (double)ijk[1] * vs, (double)ijk[2] * vs};
+                if (inst < 0) {
+                    eval_invalid(&r, ST_NO_SUPPORT);
+                    F->test_inst_key[o] = 0;
+                } else {
+                    F->test_inst_key[o] = F->leaf_key[inst];
+                    int N = (int)(F->inst_off[inst + 1] - F->inst_off[inst]);
+                    if (!F->fit_ok[inst]) eval_invalid(&r, ST_FACTOR_FAIL);
+                    else gp_eval(F->X + 3 * F->inst_off[inst], N, F->L + F->L_off[inst],
+                                 F->alpha + F->inst_off[inst], xs, P, 1, kb, vb, &r);
+                }
+                F->test_d[o] = r.d;
+                F->test_v[o] = r.v;
+                for (int a = 0; a < 3; ++a) F->test_grad[3 * o + a] = r.gd[a];
+                F->test_status[o] = (uint8_t)r.status;
+            }
+        }
+        free(kb);
+        free(vb);
+    }
+    free(tl);
+    return F;
+}
+
+int64_t or_frame_count(const or_frame* F, int what) {
+    if (what == 0) return F->n_leaves;
+    if (what == 1) return F->inst_off[F->n_leaves];
+    if (what == 2) return F->n_test;
+    return -1;
+}
+
+void or_frame_leaves(const or_frame* F, uint64_t* key, int32_t* nocc, int64_t* inst_off,
+                     double* X, double* alpha) {
+    int64_t nl = F->n_leaves, T = F->inst_off[nl];
+    if (key) memcpy(key, F->leaf_key, sizeof(uint64_t) * nl);
+    if (nocc) memcpy(nocc, F->leaf_nocc, sizeof(int32_t) * nl);
+    if (inst_off) memcpy(inst_off, F->inst_off, sizeof(int64_t) * (nl + 1));
+    if (X) memcpy(X, F->X, sizeof(double) * 3 * T);
+    if (alpha) memcpy(alpha, F->alpha, sizeof(double) * T);
+}
+
+void or_frame_tests(const or_frame* F, uint64_t* key, uint64_t* inst_key, double* d, double* v,
+                    double* grad, uint8_t* status) {
+    int64_t n = F->n_test;
+    if (key) memcpy(key, F->test_key, sizeof(uint64_t) * n);
+    if (inst_key) memcpy(inst_key, F->test_inst_key, sizeof(uint64_t) * n);
+    if (d) memcpy(d, F->test_d, sizeof(double) * n);
+    if (v) memcpy(v, F->test_v, sizeof(double) * n);
+    if (grad) memcpy(grad, F->test_grad, sizeof(double) * 3 * n);
+    if (status) memcpy(status, F->test_status, n);
+}
+
+/* ------------------------------------------------------------------------------------ */
+/* global grid + probabilistic fusion (Eqs. 7-9)                                        */
+/* ------------------------------------------------------------------------------------ */
+typedef struct {
+    uint64_t key;
+    double D, V;
+} gvox;
+
+typedef struct {
+    int64_t n;
+    gvox* v;       /* sorted by key */
+    int64_t nl;
+    uint64_t* lkey; /* sorted */
+    uint8_t* lflag; /* bit0: touched by the latest fuse; bit1: ever touched */
+} or_grid;
+
+or_grid* or_grid_new(void) { return (or_grid*)calloc(1, sizeof(or_grid)); }
+
+void or_grid_free(or_grid* g) {
+    if (!g) return;
+    free(g->v); free(g->lkey); free(g->lflag); free(g);
+}
+
+typedef struct {
+    uint64_t key;
+    double d, v;
+    int64_t order;
+} fin;
+
+static int cmp_fin(const void* a, const void* b) {
+    const fin* x = (const fin*)a;
+    const fin* y = (const fin*)b;
+    if (x->key != y->key) return x->key < y->key ? -1 : 1;
+    return (x->order > y->order) - (x->order < y->order);
+}
+
+static uint64_t leaf_key_of_voxel_key(uint64_t vk) {
+    int64_t ijk[3];
+    unpack_key(vk, ijk);
+    return pack_key(floor_div8(ijk[0]), floor_div8(ijk[1]), floor_div8(ijk[2]));
+}
+
+/* one fusion step of a stored voxel (D, V) with a new estimate (d, v) */
+static void fuse_one(int mode, double* D, double* V, double d, double v) {
+    if (mode == 0) { /* Eqs. 7-8 */
+        double Vp = *V;
+        double a = Vp / (Vp + v);
+        double b = v / (Vp + v);
+        *D = a * d + b * (*D);
+        *V = 1.0 / (1.0 / Vp + 1.0 / v);
+    } else { /* Eq. 9: V is the accumulated weight, the new weight is 1 - v */
+        double Vp = *V, w = 1.0 - v;
+        double a = w / (Vp + w);
+        double b = Vp / (Vp + w);
+        *D = a * d + b * (*D);
+        *V = Vp + w;
+    }
+}
+
+int or_grid_fuse(or_grid* g, int mode, const uint64_t* key, const double* d, const double* v,
+                 const uint8_t* status, int64_t n) {
+    fin* in = (fin*)malloc(sizeof(fin) * (n > 0 ? n : 1));
+    int64_t m = 0;
+    for (int64_t i = 0; i < n; ++i) {
+        if (status[i] != ST_OK || !isfinite(d[i]) || !isfinite(v[i]) || !(v[i] > 0.0)) continue;
+        if (mode == 1 && !(v[i] < 1.0)) continue;
+        in[m].key = key[i]; in[m].d = d[i]; in[m].v = v[i]; in[m].order = i;
+        ++m;
+    }
+    qsort(in, (size_t)m, sizeof(fin), cmp_fin);
+    gvox* out = (gvox*)malloc(sizeof(gvox) * (g->n + m + 1));
+    int64_t a = 0, b = 0, o = 0;
+    while (a < g->n || b < m) {
+        if (b >= m || (a < g->n && g->v[a].key < in[b].key)) { out[o++] = g->v[a++]; continue; }
+        gvox cur;
+        if (a < g->n && g->v[a].key == in[b].key) cur = g->v[a++];
+        else {
+            cur.key = in[b].key;
+            cur.D = in[b].d;
+            cur.V = mode == 0 ? in[b].v : 1.0 - in[b].v;
+            ++b;
+        }
+        while (b < m && in[b].key == cur.key) { fuse_one(mode, &cur.D, &cur.V, in[b].d, in[b].v); ++b; }
+        out[o++] = cur;
+    }
+    free(g->v);
+    g->v = out;
+    g->n = o;
+    /* leaf flags */
+    for (int64_t i = 0; i < g->nl; ++i) g->lflag[i] &= (uint8_t)~1u;
+    uint64_t* tk = (uint64_t*)malloc(sizeof(uint64_t) * (m + 1));
+    int64_t nt = 0;
+    for (int64_t i = 0; i < m; ++i) tk[nt++] = leaf_key_of_voxel_key(in[i].key);
+    qsort(tk, (size_t)nt, sizeof(uint64_t), cmp_u64);
+    int64_t ut = 0;
+    for (int64_t i = 0; i < nt; ++i) if (ut == 0 || tk[i] != tk[ut - 1]) tk[ut++] = tk[i];
+    uint64_t* nk = (uint64_t*)malloc(sizeof(uint64_t) * (g->nl + ut + 1));
+    uint8_t* nf = (uint8_t*)malloc(g->nl + ut + 1);
+    a = 0; b = 0; o = 0;
+    while (a < g->nl || b < ut) {
+        if (b >= ut || (a < g->nl && g->lkey[a] < tk[b])) { nk[o] = g->lkey[a]; nf[o++] = g->lflag[a++]; continue; }
+        uint8_t f = 0;
+        if (a < g->nl && g->lkey[a] == tk[b]) f = g->lflag[a++];
+        nk[o] = tk[b++];
+        nf[o++] = (uint8_t)(f | 3u);
+    }
+    free(g->lkey); free(g->lflag);
+    g->lkey = nk; g->lflag = nf; g->nl = o;
+    free(tk);
+    free(in);
+    return 0;
+}
+
+int64_t or_grid_size(const or_grid* g) { return g->n; }
+
+void or_grid_export(const or_grid* g, uint64_t* key, double* D, double* V, uint8_t* flags) {
+    for (int64_t i = 0; i < g->n; ++i) {
+        if (key) key[i] = g->v[i].key;
+        if (D) D[i] = g->v[i].D;
+        if (V) V[i] = g->v[i].V;
+        if (flags) {
+            int64_t l = find_key(g->lkey, g->nl, leaf_key_of_voxel_key(g->v[i].key));
+            flags[i] = l >= 0 ? g->lflag[l] : 0;
+        }
+    }
+}
+
+/* ------------------------------------------------------------------------------------ */
+/* G-GPDF: surface points binned by leaf; per-neighbourhood GPs for arbitrary queries    */
+/* ------------------------------------------------------------------------------------ */
+typedef struct {
+    or_params P;
+    int64_t n_pts;
+    double* pts;      /* widened input, n_pts*3 */
+    int64_t nl;
+    uint64_t* lkey;   /* sorted occupied leaves */
+    int64_t* off;     /* [nl + 1] */
+    int64_t* idx;     /* point indices, ascending within a leaf */
+} or_surface;
+
+typedef struct {
+    uint64_t k;
+    int64_t i;
+} kidx;
+
+static int cmp_kidx(const void* a, const void* b) {
+    const kidx* x = (const kidx*)a;
+    const kidx* y = (const kidx*)b;
+    if (x->k != y->k) return x->k < y->k ? -1 : 1;
+    return (x->i > y->i) - (x->i < y->i);
+}
+
+void or_surface_free(or_surface* S) {
+    if (!S) return;
+    free(S->pts); free(S->lkey); free(S->off); free(S->idx); free(S);
+}
+
+or_surface* or_surface_new(const or_params* P, const float* pts, int64_t n) {
+    or_surface* S = (or_surface*)calloc(1, sizeof(or_surface));
+    S->P = *P;
+    S->n_pts = n;
+    S->pts = (double*)malloc(sizeof(double) * 3 * (n + 1));
+    kidx* R = (kidx*)malloc(sizeof(kidx) * (n + 1));
+    int64_t m = 0;
+    for (int64_t i = 0; i < n; ++i) {
+        for (int a = 0; a < 3; ++a) S->pts[3 * i + a] = (double)pts[3 * i + a];
+        int64_t ijk[3], leaf[3];
+        int32_t bit;
+        if (!voxel_ijk(S->pts + 3 * i, P->voxel_size, ijk)) continue;
+        leaf_of(ijk, leaf, &bit);
+        R[m].k = pack_key(leaf[0], leaf[1], leaf[2]);
+        R[m].i = i;
+        ++m;
+    }
+    qsort(R, (size_t)m, sizeof(kidx), cmp_kidx);
+    int64_t nl = 0;
+    for (int64_t i = 0; i < m; ++i) if (i == 0 || R[i].k != R[i - 1].k) ++nl;
+    S->nl = nl;
+    S->lkey = (uint64_t*)malloc(sizeof(uint64_t) * (nl + 1));
+    S->off = (int64_t*)malloc(sizeof(int64_t) * (nl + 1));
+    S->idx = (int64_t*)malloc(sizeof(int64_t) * (m + 1));
+    int64_t l = -1;
+    for (int64_t i = 0; i < m; ++i) {
+        if (i == 0 || R[i].k != R[i - 1].k) { ++l; S->lkey[l] = R[i].k; S->off[l] = i; }
+        S->idx[i] = R[i].i;
+    }
+    S->off[nl] = m;
+    free(R);
+    return S;
+}
+
+int64_t or_surface_leaves(const or_surface* S, uint64_t* key, int64_t* off, int64_t* idx) {
+    if (key) memcpy(key, S->lkey, sizeof(uint64_t) * S->nl);
+    if (off) memcpy(off, S->off, sizeof(int64_t) * (S->nl + 1));
+    if (idx) memcpy(idx, S->idx, sizeof(int64_t) * S->off[S->nl]);
+    return S->nl;
+}
+
+/* Centre leaf of the instance that serves query leaf M, or -1 (status 1). */
+static int centre_leaf(const or_surface* S, const int64_t M[3], int64_t C[3]) {
+    for (int dz = -1; dz <= 1; ++dz)
+        for (int dy = -1; dy <= 1; ++dy)
+            for (int dx = -1; dx <= 1; ++dx)
+                if (find_key(S->lkey, S->nl, pack_key(M[0] + dx, M[1] + dy, M[2] + dz)) >= 0) {
+                    C[0] = M[0]; C[1] = M[1]; C[2] = M[2];
+                    return 1;
+                }
+    int R = S->P.max_leaf_search;
+    int64_t best_d2 = INT64_MAX;
+    uint64_t best_key = 0;
+    int found = 0;
+    for (int dz = -R; dz <= R; ++dz)
+        for (int dy = -R; dy <= R; ++dy)
+            for (int dx = -R; dx <= R; ++dx) {
+                uint64_t k = pack_key(M[0] + dx, M[1] + dy, M[2] + dz);
+                if (find_key(S->lkey, S->nl, k) < 0) continue;
+                int64_t d2 = (int64_t)dx * dx + (int64_t)dy * dy + (int64_t)dz * dz;
+                if (!found || d2 < best_d2 || (d2 == best_d2 && k < best_key)) {
+                    found = 1; best_d2 = d2; best_key = k;
+                }
+            }
+    if (!found) return 0;
+    unpack_key(best_key, C);
+    return 1;
+}
+
+typedef struct {
+    double d2;
+    int64_t i;
+} didx;
+
+static int cmp_didx(const void* a, const void* b) {
+    const didx* x = (const didx*)a;
+    const didx* y = (const didx*)b;
+    if (x->d2 != y->d2) return x->d2 < y->d2 ? -1 : 1;
+    return (x->i > y->i) - (x->i < y->i);
+}
+
+/* Point indices of the instance centred on leaf C (27 leaves, capped, ascending index). */
+int64_t or_surface_instance(const or_surface* S, uint64_t ckey, int64_t* out_idx) {
+    int64_t C[3];
+    unpack_key(ckey, C);
+    int64_t cnt = 0;
+    for (int dz = -1; dz <= 1; ++dz)
+        for (int dy = -1; dy <= 1; ++dy)
+            for (int dx = -1; dx <= 1; ++dx) {
+                int64_t l = find_key(S->lkey, S->nl, pack_key(C[0] + dx, C[1] + dy, C[2] + dz));
+                if (l >= 0) cnt += S->off[l + 1] - S->off[l];
+            }
+    didx* cand = (didx*)malloc(sizeof(didx) * (cnt + 1));
+    int64_t m = 0;
+    double vs = S->P.voxel_size;
+    double c[3];
+    for (int a = 0; a < 3; ++a) c[a] = ((double)(8 * C[a]) + 3.5) * vs;
+    for (int dz = -1; dz <= 1; ++dz)
+        for (int dy = -1; dy <= 1; ++dy)
+            for (int dx = -1; dx <= 1; ++dx) {
+                int64_t l = find_key(S->lkey, S->nl, pack_key(C[0] + dx, C[1] + dy, C[2] + dz));
+                if (l < 0) continue;
+                for (int64_t t = S->off[l]; t < S->off[l + 1]; ++t) {
+                    int64_t i = S->idx[t];
+                    const double* x = S->pts + 3 * i;
+                    double ex = x[0] - c[0], ey = x[1] - c[1], ez = x[2] - c[2];
+                    cand[m].d2 = (ex * ex + ey * ey) + ez * ez;
+                    cand[m].i = i;
+                    ++m;
+                }
+            }
+    int64_t cap = S->P.max_pts_group;
+    if (m > cap) {
+        qsort(cand, (size_t)m, sizeof(didx), cmp_didx);
+        m = cap;
+    }
+    int64_t* ids = (int64_t*)malloc(sizeof(int64_t) * (m + 1));
+    for (int64_t t = 0; t < m; ++t) ids[t] = cand[t].i;
+    /* ascending point index */
+    for (int64_t t = 1; t < m; ++t) {
+        int64_t v = ids[t], s = t - 1;
+        while (s >= 0 && ids[s] > v) { ids[s + 1] = ids[s]; --s; }
+        ids[s + 1] = v;
+    }
+    if (out_idx) memcpy(out_idx, ids, sizeof(int64_t) * m);
+    free(ids);
+    free(cand);
+    return m;
+}
+
+/* shared set-up of a query batch: query -> instance id, instance list */
+typedef struct {
+    int64_t nq;
+    int64_t* q_inst;     /* -1: bad input (3) or no support (1) */
+    uint8_t* q_status0;
+    int64_t ni;
+    uint64_t* ikey;      /* centre leaf key per instance (sorted) */
+    int64_t* ioff;       /* [ni + 1] offsets into iidx */
+    int64_t* iidx;       /* point indices per instance */
+} qplan;
+
+static void qplan_free(qplan* Q) {
+    free(Q->q_inst); free(Q->q_status0); free(Q->ikey); free(Q->ioff); free(Q->iidx);
+}
+
+static void qplan_build(const or_surface* S, const float* q, int64_t n, qplan* Q) {
+    memset(Q, 0, sizeof(*Q));
+    Q->nq = n;
+    Q->q_inst = (int64_t*)malloc(sizeof(int64_t) * (n + 1));
+    Q->q_status0 = (uint8_t*)malloc(n + 1);
+    uint64_t* qleaf = (uint64_t*)malloc(sizeof(uint64_t) * (n + 1));
+    kidx* R = (kidx*)malloc(sizeof(kidx) * (n + 1));
+    int64_t m = 0;
+    for (int64_t i = 0; i < n; ++i) {
+        double p[3] = {(double)q[3 * i], (double)q[3 * i + 1], (double)q[3 * i + 2]};
+        int64_t ijk[3], leaf[3];
+        int32_t bit;
+        Q->q_inst[i] = -1;
+        if (!voxel_ijk(p, S->P.voxel_size, ijk)) { Q->q_status0[i] = ST_BAD_INPUT; qleaf[i] = 0; continue; }
+        leaf_of(ijk, leaf, &bit);
+        qleaf[i] = pack_key(leaf[0], leaf[1], leaf[2]);
+        Q->q_status0[i] = ST_OK;
+        R[m].k = qleaf[i]; R[m].i = i; ++m;
+    }
+    qsort(R, (size_t)m, sizeof(kidx), cmp_kidx);
+    /* unique query leaves -> centre leaf */
+    int64_t ng = 0;
+    for (int64_t i = 0; i < m; ++i) if (i == 0 || R[i].k != R[i - 1].k) ++ng;
+    uint64_t* gkey = (uint64_t*)malloc(sizeof(uint64_t) * (ng + 1));
+    uint64_t* gcen = (uint64_t*)malloc(sizeof(uint64_t) * (ng + 1));
+    uint8_t* gok = (uint8_t*)malloc(ng + 1);
+    ng = 0;
+    for (int64_t i = 0; i < m; ++i) if (i == 0 || R[i].k != R[i - 1].k) gkey[ng++] = R[i].k;
+#pragma omp parallel for schedule(dynamic, 16)
+    for (int64_t g = 0; g < ng; ++g) {
+        int64_t M[3], C[3];
+        unpack_key(gkey[g], M);
+        gok[g] = (uint8_t)centre_leaf(S, M, C);
+        gcen[g] = gok[g] ? pack_key(C[0], C[1], C[2]) : 0;
+    }
+    /* unique centres -> instances */
+    uint64_t* ck = (uint64_t*)malloc(sizeof(uint64_t) * (ng + 1));
+    int64_t nc = 0;
+    for (int64_t g = 0; g < ng; ++g) if (gok[g]) ck[nc++] = gcen[g];
+    qsort(ck, (size_t)nc, sizeof(uint64_t), cmp_u64);
+    int64_t ni = 0;
+    for (int64_t i = 0; i < nc; ++i) if (ni == 0 || ck[i] != ck[ni - 1]) ck[ni++] = ck[i];
+    Q->ni = ni;
+    Q->ikey = ck;
+    Q->ioff = (int64_t*)malloc(sizeof(int64_t) * (ni + 1));
+    int64_t* cnt = (int64_t*)malloc(sizeof(int64_t) * (ni + 1));
+#pragma omp parallel for schedule(dynamic, 16)
+    for (int64_t I = 0; I < ni; ++I) cnt[I] = or_surface_instance(S, ck[I], NULL);
+    Q->ioff[0] = 0;
+    for (int64_t I = 0; I < ni; ++I) Q->ioff[I + 1] = Q->ioff[I] + cnt[I];
+    Q->iidx = (int64_t*)malloc(sizeof(int64_t) * (Q->ioff[ni] + 1));
+#pragma omp parallel for schedule(dynamic, 16)
+    for (int64_t I = 0; I < ni; ++I) or_surface_instance(S, ck[I], Q->iidx + Q->ioff[I]);
+    free(cnt);
+    /* query -> instance */
+    for (int64_t i = 0; i < n; ++i) {
+        if (Q->q_status0[i] != ST_OK) continue;
+        int64_t g = find_key(gkey, ng, qleaf[i]);
+        if (!gok[g]) { Q->q_status0[i] = ST_NO_SUPPORT; continue; }
+        Q->q_inst[i] = find_key(Q->ikey, ni, gcen[g]);
+    }
+    free(gkey); free(gcen); free(gok); free(R); free(qleaf);
+}
+
+/* per-instance fitted state */
+typedef struct {
+    int N;
+    double* X;
+    double* L;
+    double* alpha;
+    int ok;
+} ifit;
+
+static void ifit_make(const or_surface* S, const qplan* Q, int64_t I, ifit* f) {
+    f->N = (int)(Q->ioff[I + 1] - Q->ioff[I]);
+    f->X = (double*)malloc(sizeof(double) * 3 * (f->N + 1));
+    for (int j = 0; j < f->N; ++j)
+        for (int a = 0; a < 3; ++a) f->X[3 * j + a] = S->pts[3 * Q->iidx[Q->ioff[I] + j] + a];
+    f->L = (double*)malloc(sizeof(double) * ((int64_t)f->N * (f->N + 1) / 2 + 1));
+    f->alpha = (double*)malloc(sizeof(double) * (f->N + 1));
+    f->ok = or_gp_fit(f->X, f->N, &S->P, f->L, f->alpha);
+}
+
+static void ifit_free(ifit* f) { free(f->X); free(f->L); free(f->alpha); }
+
+int or_query(const or_surface* S, const float* q, int64_t n, int want_var, double* d, double* grad,
+             double* var, uint8_t* status, uint64_t* inst_key, int32_t* inst_n) {
+    qplan Q;
+    qplan_build(S, q, n, &Q);
+    /* queries grouped by instance */
+    int64_t* qo = (int64_t*)calloc((size_t)(Q.ni + 1), sizeof(int64_t));
+    int64_t* ql = (int64_t*)malloc(sizeof(int64_t) * (n + 1));
+    for (int64_t i = 0; i < n; ++i) if (Q.q_inst[i] >= 0) qo[Q.q_inst[i] + 1]++;
+    for (int64_t I = 0; I < Q.ni; ++I) qo[I + 1] += qo[I];
+    {
+        int64_t* fill = (int64_t*)malloc(sizeof(int64_t) * (Q.ni + 1));
+        memcpy(fill, qo, sizeof(int64_t) * (Q.ni + 1));
+        for (int64_t i = 0; i < n; ++i) if (Q.q_inst[i] >= 0) ql[fill[Q.q_inst[i]]++] = i;
+        free(fill);
+    }
+    for (int64_t i = 0; i < n; ++i) {
+        if (Q.q_inst[i] >= 0) continue;
+        or_eval r;
+        eval_invalid(&r, Q.q_status0[i]);
+        if (d) d[i] = r.d;
+        if (grad) for (int a = 0; a < 3; ++a) grad[3 * i + a] = 0.0;
+        if (var) var[i] = r.v;
+        if (status) status[i] = (uint8_t)r.status;
+        if (inst_key) inst_key[i] = 0;
+        if (inst_n) inst_n[i] = 0;
+    }
+#pragma omp parallel for schedule(dynamic, 1)
+    for (int64_t I = 0; I < Q.ni; ++I) {
+        ifit f;
+        ifit_make(S, &Q, I, &f);
+        double* kb = (double*)malloc(sizeof(double) * (f.N + 1));
+        double* vb = (double*)malloc(sizeof(double) * (f.N + 1));
+        for (int64_t t = qo[I]; t < qo[I + 1]; ++t) {
+            int64_t i = ql[t];
+            double xs[3] = {(double)q[3 * i], (double)q[3 * i + 1], (double)q[3 * i + 2]};
+            or_eval r;
+            if (!f.ok) eval_invalid(&r, ST_FACTOR_FAIL);
+            else gp_eval(f.X, f.N, f.L, f.alpha, xs, &S->P, want_var, kb, vb, &r);
+            if (d) d[i] = r.d;
+            if (grad) for (int a = 0; a < 3; ++a) grad[3 * i + a] = r.gd[a];
+            if (var) var[i] = r.v;
+            if (status) status[i] = (uint8_t)r.status;
+            if (inst_key) inst_key[i] = Q.ikey[I];
+            if (inst_n) inst_n[i] = f.N;
+        }
+        free(kb); free(vb);
+        ifit_free(&f);
+    }
+    free(qo); free(ql);
+    qplan_free(&Q);
+    return 0;
+}
+
+/*
+ * Backward pass of L = sum_q f(d_q) given dL/dd_q (derived from Eq. 1 and Eq. 3):
+ *   dL/dx*_q = dL/dd_q * grad d_q;
+ *   with obar_q = dL/dd_q * dd/do_q = dL/dd_q * (-l^2 / (o_q d_q)), per instance
+ *   abar = sum_q obar_q k_q, lambda = A^-1 abar, and for training point j
+ *   dL/dx_j = sum_q obar_q alpha_j k_qj (x*_q - x_j) / l^2
+ *             - sum_i (lambda_i alpha_j + lambda_j alpha_i) k_ij (x_i - x_j) / l^2.
+ * The contributions of every instance that holds point j are summed into dL/dX[j]
+ * in instance order.  Clamped or invalid results contribute zero.
+ */
+int or_query_backward(const or_surface* S, const float* q, int64_t n, const double* dL_dd,
+                      double* dL_dq, double* dL_dX) {
+    qplan Q;
+    qplan_build(S, q, n, &Q);
+    int64_t* qo = (int64_t*)calloc((size_t)(Q.ni + 1), sizeof(int64_t));
+    int64_t* ql = (int64_t*)malloc(sizeof(int64_t) * (n + 1));
+    for (int64_t i = 0; i < n; ++i) if (Q.q_inst[i] >= 0) qo[Q.q_inst[i] + 1]++;
+    for (int64_t I = 0; I < Q.ni; ++I) qo[I + 1] += qo[I];
+    {
+        int64_t* fill = (int64_t*)malloc(sizeof(int64_t) * (Q.ni + 1));
+        memcpy(fill, qo, sizeof(int64_t) * (Q.ni + 1));
+        for (int64_t i = 0; i < n; ++i) if (Q.q_inst[i] >= 0) ql[fill[Q.q_inst[i]]++] = i;
+        free(fill);
+    }
+    if (dL_dq) for (int64_t i = 0; i < 3 * n; ++i) dL_dq[i] = 0.0;
+    double* contrib = (double*)calloc((size_t)(3 * Q.ioff[Q.ni] + 1), sizeof(double));
+    double l = S->P.lengthscale, l2 = l * l;
+#pragma omp parallel for schedule(dynamic, 1)
+    for (int64_t I = 0; I < Q.ni; ++I) {
+        ifit f;
+        ifit_make(S, &Q, I, &f);
+        int N = f.N;
+        double* kb = (double*)malloc(sizeof(double) * (N + 1));
+        double* abar = (double*)calloc((size_t)(N + 1), sizeof(double));
+        double* lam = (double*)malloc(sizeof(double) * (N + 1));
+        double* z = (double*)malloc(sizeof(double) * (N + 1));
+        double* g = contrib + 3 * Q.ioff[I];
+        if (f.ok) {
+            for (int64_t t = qo[I]; t < qo[I + 1]; ++t) {
+                int64_t i = ql[t];
+                double xs[3] = {(double)q[3 * i], (double)q[3 * i + 1], (double)q[3 * i + 2]};
+                or_eval r;
+                gp_eval(f.X, N, f.L, f.alpha, xs, &S->P, 0, kb, NULL, &r);
+                if (dL_dq) for (int a = 0; a < 3; ++a) dL_dq[3 * i + a] = dL_dd[i] * r.gd[a];
+                int smooth = r.status == ST_OK && r.d > 0.0 && r.o < 1.0;
+                if (!smooth) continue;
+                double obar = dL_dd[i] * (-l2 / (r.o * r.d));
+                for (int j = 0; j < N; ++j) {
+                    abar[j] += obar * kb[j];
+                    for (int a = 0; a < 3; ++a)
+                        g[3 * j + a] += obar * f.alpha[j] * kb[j] * (xs[a] - f.X[3 * j + a]) / l2;
+                }
+            }
+            forward_subst(f.L, N, abar, z);
+            back_subst(f.L, N, z, lam);
+            for (int j = 0; j < N; ++j)
+                for (int i2 = 0; i2 < N; ++i2) {
+                    if (i2 == j) continue;
+                    double kij = se_kernel(f.X + 3 * i2, f.X + 3 * j, l);
+                    double c = (lam[i2] * f.alpha[j] + lam[j] * f.alpha[i2]) * kij;
+                    for (int a = 0; a < 3; ++a) g[3 * j + a] -= c * (f.X[3 * i2 + a] - f.X[3 * j + a]) / l2;
+                }
+        }
+        free(kb); free(abar); free(lam); free(z);
+        ifit_free(&f);
+    }
+    if (dL_dX) {
+        for (int64_t i = 0; i < 3 * S->n_pts; ++i) dL_dX[i] = 0.0;
+        for (int64_t I = 0; I < Q.ni; ++I)
+            for (int64_t t = Q.ioff[I]; t < Q.ioff[I + 1]; ++t)
+                for (int a = 0; a < 3; ++a) dL_dX[3 * Q.iidx[t] + a] += contrib[3 * t + a];
+    }
+    free(contrib); free(qo); free(ql);
+    qplan_free(&Q);
+    return 0;
+}
+
+/* ------------------------------------------------------------------------------------ */
+void or_set_threads(int n) {
+#ifdef _OPENMP
+    if (n > 0) omp_set_num_threads(n);
+#else
+    (void)n;
+#endif
+}
+
+int or_get_threads(void) {
+#ifdef _OPENMP
+    return omp_get_max_threads();
+#else
+    return 1;
+#endif
+}
