@@ -1,0 +1,282 @@
+/*
+ * vgpdf.h -- C ABI of the GB300 library for batched local Gaussian-process distance fields
+ * (the data-parallel hot path of VDB-GPDF, Wu, Le Gentil and Vidal-Calleja, arXiv 2407.09649).
+ *
+ * The library keeps a sparse voxel map on one GPU: a hash of 8^3-voxel leaves replacing the
+ * paper's OpenVDB trees (Sec. III-B).  Three entry points carry the method:
+ *
+ *   vgp_build_frame              L-GPDF of one frame (Sec. IV-A/B): voxelise the points,
+ *                                one GP per occupied leaf trained on voxel centres, distance
+ *                                and variance inferred at every testing voxel;
+ *   vgp_fuse                     probabilistic fusion of a frame into the global grid
+ *                                (Sec. IV-C, Eqs. 7-8, or Eq. 9);
+ *   vgp_query_distance_gradient  G-GPDF queries (Sec. IV-D): per query leaf a GP over the
+ *                                surface points of its 27-leaf neighbourhood, trained lazily
+ *                                for the leaves that queries touch; distance, gradient and
+ *                                variance at arbitrary points.
+ *
+ * plus vgp_query_backward (derivatives of the distance w.r.t. query and surface points),
+ * vgp_gp_batch (independent GP instances given directly) and grid export/import.
+ *
+ * Every GP uses the unscaled SE kernel k(x, x') = exp(-|x - x'|^2 / (2 l^2)) (Sec. III-A),
+ * A = K + sigma^2 I, alpha = A^-1 1 (Eq. 1), latent variance u = 1 - k^T A^-1 k (Eq. 2, read
+ * as the standard GP posterior), latent gradient (Eq. 5), reverting d = sqrt(-2 l^2 log o)
+ * (Eq. 3), distance variance v = Lambda^2 u, Lambda = -l^2 / (o d) (Eq. 4), and the
+ * chain-rule distance gradient grad d = -l^2 grad o / (o d).
+ *
+ * Conventions, for every function below:
+ *   - Pointers named *_dev are device memory on the map's GPU, owned by the caller, which
+ *     must keep them alive until the stream has passed the call.  Host pointers are named
+ *     without that suffix.  The library owns vgp_map and vgp_frame and their device memory.
+ *   - Point arrays are float32, row-major [n][3] (x, y, z in metres, world frame).
+ *   - Calls enqueue work on `stream` (a cudaStream_t; NULL is the legacy default stream)
+ *     and return once it is enqueued.  Some calls read a few sizes back from the GPU and so
+ *     synchronise the stream part-way (noted per call).  Read outputs after a stream sync
+ *     or vgp_sync().
+ *   - Return value: VGP_OK (0) or a negative VGP_ERR_* code; vgp_last_error() then gives a
+ *     thread-local message.  On error, outputs are unspecified and the map stays usable
+ *     unless the code is VGP_ERR_CUDA.
+ *   - A map and its frames may be used from one host thread at a time.
+ *   - Per-query status: VGP_ST_OK, VGP_ST_NO_SUPPORT (no surface point within the leaf
+ *     search radius), VGP_ST_CLAMPED (o <= 0 or log o below the floor: d = d_max),
+ *     VGP_ST_BAD_INPUT (non-finite or out-of-range coordinate), VGP_ST_FACTOR_FAIL
+ *     (non-positive Cholesky pivot).  For NO_SUPPORT, BAD_INPUT and FACTOR_FAIL:
+ *     d = +inf, grad = 0, var = +inf.  For CLAMPED: d = d_max, grad = 0, var = +inf.
+ *     For o >= 1 (on or inside the surface): status OK, d = 0, grad = 0.
+ */
+#ifndef VGPDF_H
+#define VGPDF_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct vgp_map vgp_map;
+typedef struct vgp_frame vgp_frame;
+typedef void* vgp_stream; /* cudaStream_t */
+
+enum {
+    VGP_OK = 0,
+    VGP_ERR_ARG = -1,        /* invalid argument or unsupported size */
+    VGP_ERR_OOM = -2,        /* device or host allocation failed */
+    VGP_ERR_CUDA = -3,       /* a CUDA call failed (message has the CUDA error) */
+    VGP_ERR_TABLE_FULL = -4, /* a hash table ran out of slots (bounded probe) */
+    VGP_ERR_TIMEOUT = -5,    /* a bounded device-side loop hit its limit */
+    VGP_ERR_STATE = -6       /* call out of order (e.g. query before set_surface) */
+};
+
+enum { VGP_FP64 = 0, VGP_MIXED = 1 };          /* precision */
+enum { VGP_FUSE_INVVAR = 0, VGP_FUSE_TSDF = 1 }; /* fusion rule: Eq. 8 or Eq. 9 */
+enum {
+    VGP_ST_OK = 0,
+    VGP_ST_NO_SUPPORT = 1,
+    VGP_ST_CLAMPED = 2,
+    VGP_ST_BAD_INPUT = 3,
+    VGP_ST_FACTOR_FAIL = 4
+};
+
+/*
+ * Map parameters.  Defaults (vgp_default_params): voxel 0.1 m, l = 0.3 m (about three
+ * voxels, Sec. V: l spanning 2-4 voxels), sigma_occ = 0.01 (std of the latent occupancy
+ * noise; sigma^2 is added to diag K, Eq. 1), d_max = 10 m, d_var_floor = 1e-3 m,
+ * max_pts_leaf = 64, max_pts_group = 1024, max_leaf_search = 8, fusion = VGP_FUSE_INVVAR,
+ * precision = VGP_MIXED.
+ *
+ *   voxel_size       voxel edge (m); leaves are 8^3 voxels (Sec. III-B).
+ *   lengthscale      SE kernel length scale l (m).
+ *   sigma_occ        latent noise std (unitless occupancy).
+ *   d_max            distance cap: log o is floored at -d_max^2 / (2 l^2) (footnote of
+ *                    Sec. III-A: the occupancy is capped; the cap value is ours).
+ *   d_var_floor      lower bound on d inside Lambda (m).
+ *   max_pts_leaf     L-GPDF training cap per leaf: a leaf with n > cap occupied voxels keeps
+ *                    the voxels of rank floor(k n / cap), k = 0..cap-1, in bit order
+ *                    (bit = x + 8 y + 64 z of the in-leaf offset).  1..512.
+ *   max_pts_group    G-GPDF cap per neighbourhood: keeps the points nearest to the centre
+ *                    leaf's centre (FP64 squared distance, ties to the lower point index).
+ *                    1..1024.
+ *   max_leaf_search  Chebyshev radius (in leaves) of the fallback search when a query's
+ *                    27-leaf neighbourhood is empty.  0..16.
+ *   fusion           VGP_FUSE_INVVAR (Eqs. 7-8) or VGP_FUSE_TSDF (Eq. 9, weight 1 - v).
+ *   precision        VGP_FP64: every step in FP64.  VGP_MIXED: kernel values, latent mean
+ *                    and gradient in FP32 (shifted by the nearest training point so they
+ *                    cannot underflow); Cholesky, triangular solves, variance and the
+ *                    reverting log in FP64.
+ *   profile          0 (default) or 1: record CUDA events around the GP solve kernels and
+ *                    report their time in vgp_stats.t_solve_ms (adds one stream sync per call).
+ */
+typedef struct {
+    double voxel_size;
+    double lengthscale;
+    double sigma_occ;
+    double d_max;
+    double d_var_floor;
+    int32_t max_pts_leaf;
+    int32_t max_pts_group;
+    int32_t max_leaf_search;
+    int32_t fusion;
+    int32_t precision;
+    int32_t profile;     /* nonzero: time the solve kernels with CUDA events (vgp_stats) */
+    int32_t reserved[2]; /* must be zero */
+} vgp_params;
+
+/* Counters of the most recent call on a map (host copy; informational). */
+typedef struct {
+    int64_t n_points;     /* valid input points (frame or surface) */
+    int64_t n_leaves;     /* occupied leaves (frame) or surface leaves */
+    int64_t n_instances;  /* GP instances solved */
+    int64_t n_train;      /* sum of N over instances */
+    int64_t n_queries;    /* queries or testing voxels evaluated */
+    int64_t n_groups;     /* distinct query leaves (G-GPDF) */
+    int64_t bucket_count[5]; /* instances per size bucket: N<=32, <=64, <=128, <=256, >256 */
+    double sum_n3;        /* sum of N^3 over instances */
+    double sum_n2;        /* sum of N^2 over instances */
+    double t_solve_ms;    /* GP solve kernels (factorise + evaluate), if params.profile */
+    int64_t grid_leaves;  /* leaves in the global grid */
+    int64_t grid_capacity_leaves;
+} vgp_stats;
+
+/* Fill *p with the defaults listed above. */
+void vgp_default_params(vgp_params* p);
+
+/* Create a map on the current CUDA device.  Validates *p (VGP_ERR_ARG on a bad value). */
+int vgp_create(const vgp_params* p, vgp_map** out);
+
+/* Destroy a map (synchronises its device work first).  NULL is a no-op. */
+int vgp_destroy(vgp_map* m);
+
+/*
+ * L-GPDF of one frame (Sec. IV-A, IV-B; Eqs. 1-4).
+ *   pts_dev  [n][3] float32 world-frame points (device).  Non-finite points and points with
+ *            |p / voxel_size| >= 2^20 - 64 are ignored.  n >= 0 (n == 0 gives an empty frame).
+ * Voxelises with ijk = floor(p / voxel_size + 1/2) (IEEE FP64), builds one GP per occupied
+ * leaf on its (capped) voxel centres, and infers distance d and variance v at every voxel of
+ * every occupied leaf and of its 26 neighbour leaves (the testing voxels), each voxel using
+ * the GP of its own leaf if that leaf holds one, else of the neighbour leaf whose centre is
+ * nearest (ties to the first in (dz, dy, dx) order from -1 to 1).
+ * On success *out receives a new frame (free with vgp_frame_destroy).  Synchronises the
+ * stream several times to size its buffers.
+ */
+int vgp_build_frame(vgp_map* m, const float* pts_dev, int64_t n, vgp_stream stream,
+                    vgp_frame** out);
+
+/*
+ * Views of a frame's testing-voxel results (device pointers, owned by the frame, valid until
+ * vgp_frame_destroy).  Arrays have *n_test entries in one common (unspecified) order:
+ *   keys    voxel key: ((i + 2^20) << 42) | ((j + 2^20) << 21) | (k + 2^20)
+ *   d, v    distance (m) and distance variance (m^2), FP64
+ *   grad    [n_test][3] distance gradient, FP64
+ *   status  VGP_ST_*
+ * Any output pointer may be NULL.
+ */
+int vgp_frame_results(const vgp_frame* f, int64_t* n_test, const uint64_t** keys,
+                      const double** d, const double** v, const double** grad,
+                      const uint8_t** status);
+
+/*
+ * Views of a frame's GP instances (device pointers, owned by the frame), one per occupied
+ * leaf, in an unspecified common order:
+ *   leaf_key  packed leaf key (as voxel keys, of the leaf coordinates floor(ijk / 8))
+ *   n_occ     occupied voxels of the leaf before the cap
+ *   inst_off  [n_leaves + 1] int64 offsets into X / alpha
+ *   X         [n_train][3] FP64 training voxel centres, world frame, in bit order
+ *   alpha     [n_train] FP64 (K + sigma^2 I)^-1 1 of each leaf's GP (Eq. 1)
+ * Any output pointer may be NULL.
+ */
+int vgp_frame_instances(const vgp_frame* f, int64_t* n_leaves, int64_t* n_train,
+                        const uint64_t** leaf_key, const int32_t** n_occ,
+                        const int64_t** inst_off, const double** X, const double** alpha);
+
+/* Free a frame (waits for its stream).  NULL is a no-op. */
+int vgp_frame_destroy(vgp_frame* f);
+
+/*
+ * Fuse a frame into the map's global grid (Sec. IV-C).  For each testing voxel with status
+ * OK, finite d and finite v > 0 (and v < 1 for Eq. 9): a first visit stores D = d, V = v
+ * (Eq. 9: V = 1 - v); later visits apply Eqs. 7-8 (D = a d + b D, a = V / (V + v),
+ * b = v / (V + v), V = (1/V + 1/v)^-1) or Eq. 9.  Leaves that receive a voxel are marked
+ * active (flag bit 0: touched by this fuse, bit 1: ever touched).  Grows the grid as needed
+ * (may synchronise the stream).  The frame must come from the same map.
+ */
+int vgp_fuse(vgp_map* m, vgp_frame* f, vgp_stream stream);
+
+/*
+ * Copy the global grid to host arrays sorted by voxel key: keys, D, V, and the flags of
+ * the voxel's leaf.  Call with keys == NULL to get the count in *n; otherwise *n is the
+ * capacity of the arrays on input and the count on output (VGP_ERR_ARG if too small).
+ * Synchronises the stream.
+ */
+int vgp_export_grid(vgp_map* m, int64_t* n, uint64_t* keys, double* D, double* V,
+                    uint8_t* flags, vgp_stream stream);
+
+/* Replace the global grid by host arrays in the export format (checkpoint / resume). */
+int vgp_import_grid(vgp_map* m, int64_t n, const uint64_t* keys, const double* D,
+                    const double* V, const uint8_t* flags, vgp_stream stream);
+
+/*
+ * G-GPDF training set (Sec. IV-D): bin surface points by leaf.  The map keeps its own copy
+ * (float32) so pts_dev may be freed after the call.  Replaces any previous surface.
+ * Synchronises the stream.
+ */
+int vgp_set_surface(vgp_map* m, const float* pts_dev, int64_t n, vgp_stream stream);
+
+/*
+ * G-GPDF query (Sec. IV-D; Eqs. 1-5).  For each query point q_dev[i] (float32 [n][3]):
+ * the query leaf M = floor(ijk / 8); the GP instance is the set of surface points in the
+ * 27 leaves around M (or, if those are empty, around the nearest occupied leaf within
+ * max_leaf_search: smallest integer leaf distance, ties to the smaller key), capped at
+ * max_pts_group.  Outputs (device, caller-owned, each may be NULL except d_dev):
+ *   d_dev      [n] FP64 distance (m)
+ *   grad_dev   [n][3] FP64 distance gradient
+ *   var_dev    [n] FP64 distance variance (m^2); computing it adds an FP64 triangular solve
+ *              per query (NULL skips it)
+ *   status_dev [n] VGP_ST_*
+ * VGP_ERR_STATE before vgp_set_surface.  Synchronises the stream several times.
+ */
+int vgp_query_distance_gradient(vgp_map* m, const float* q_dev, int64_t n, double* d_dev,
+                                double* grad_dev, double* var_dev, uint8_t* status_dev,
+                                vgp_stream stream);
+
+/*
+ * Backward pass of a scalar loss L through vgp_query_distance_gradient, with the discrete
+ * choices (instances, caps) of the forward pass.  Given dL_dd_dev [n] FP64:
+ *   dL_dq_dev  [n][3] FP64: dL/dd_i * grad d_i (may be NULL)
+ *   dL_dX_dev  [n_surface][3] FP64, overwritten: derivative w.r.t. each surface point of the
+ *              last vgp_set_surface, from differentiating alpha = A^-1 1 (Eq. 1) and k
+ *              (may be NULL).
+ * The factorisation and alpha are recomputed, not stored.  Results where the forward
+ * output was clamped or invalid contribute zero.  Synchronises the stream.
+ */
+int vgp_query_backward(vgp_map* m, const float* q_dev, int64_t n, const double* dL_dd_dev,
+                       double* dL_dq_dev, double* dL_dX_dev, vgp_stream stream);
+
+/*
+ * Independent GP instances given directly (no grid): instance I trains on
+ * X_dev[inst_off[I] .. inst_off[I+1]) and answers Q_dev[q_off[I] .. q_off[I+1]).
+ *   inst_off_dev, q_off_dev  [n_inst + 1] int64 device offsets (non-decreasing, from 0)
+ *   X_dev, Q_dev             float32 [.][3] device points
+ *   outputs as for vgp_query_distance_gradient, indexed like Q_dev (var_dev may be NULL).
+ * Instances with N > 1024 are rejected (VGP_ERR_ARG).  Uses the map's parameters and
+ * device arena.  Synchronises the stream.
+ */
+int vgp_gp_batch(vgp_map* m, int64_t n_inst, const int64_t* inst_off_dev, const float* X_dev,
+                 const int64_t* q_off_dev, const float* Q_dev, double* d_dev, double* grad_dev,
+                 double* var_dev, uint8_t* status_dev, vgp_stream stream);
+
+/* Counters of the most recent build_frame / set_surface / query / batch call. */
+int vgp_get_stats(const vgp_map* m, vgp_stats* out);
+
+/* Number of CUDA kernels this library has launched in the process so far (diagnostic). */
+int64_t vgp_launch_count(void);
+
+/* Wait for all device work of the map. */
+int vgp_sync(vgp_map* m);
+
+/* Message of the last error on this thread ("" if none).  Never NULL. */
+const char* vgp_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* VGPDF_H */

@@ -1,0 +1,227 @@
+"""Thin Python binding of the C ABI (``include/vgpdf.h``) over torch CUDA tensors.
+
+Argument marshalling only: every step of the path runs in the CUDA library.  PyTorch
+provides device memory and the current stream.
+"""
+from __future__ import annotations
+
+import ctypes as C
+
+import numpy as np
+import torch
+
+from . import _lib as L
+
+
+class _CudaView:
+    """Zero-copy view of library-owned device memory for ``torch.as_tensor``."""
+
+    def __init__(self, ptr: int, shape, typestr: str):
+        self.__cuda_array_interface__ = {"shape": tuple(shape), "typestr": typestr,
+                                         "data": (int(ptr), False), "version": 3, "strides": None}
+
+
+def _view(ptr, shape, typestr, dtype):
+    n = int(np.prod(shape)) if len(shape) else 1
+    if n == 0 or not ptr:
+        return torch.empty(shape, dtype=dtype, device="cuda")
+    return torch.as_tensor(_CudaView(ptr, shape, typestr), device="cuda").clone()
+
+
+def _stream():
+    return C.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+
+def _dev_f32(x, name: str) -> torch.Tensor:
+    if isinstance(x, np.ndarray):
+        x = torch.from_numpy(np.ascontiguousarray(x, dtype=np.float32))
+    if not isinstance(x, torch.Tensor):
+        raise TypeError(f"{name}: expected a torch tensor or numpy array")
+    x = x.to(device="cuda", dtype=torch.float32).contiguous()
+    if x.dim() != 2 or x.shape[1] != 3:
+        raise ValueError(f"{name}: expected shape [n, 3], got {tuple(x.shape)}")
+    return x
+
+
+def _ptr(t):
+    return None if t is None else C.c_void_p(t.data_ptr())
+
+
+def make_params(**kw) -> L.VgpParams:
+    lib = L.load()
+    p = L.VgpParams()
+    lib.vgp_default_params(C.byref(p))
+    for k, v in kw.items():
+        if k == "precision" and isinstance(v, str):
+            v = {"fp64": L.VGP_FP64, "mixed": L.VGP_MIXED}[v]
+        if k == "fusion" and isinstance(v, str):
+            v = {"invvar": L.VGP_FUSE_INVVAR, "tsdf": L.VGP_FUSE_TSDF}[v]
+        if not hasattr(p, k):
+            raise KeyError(f"unknown parameter {k}")
+        setattr(p, k, v)
+    return p
+
+
+class Frame:
+    """An L-GPDF frame: leaf GPs and testing-voxel results (library-owned)."""
+
+    def __init__(self, gmap: "Map", handle):
+        self._map = gmap
+        self._h = handle
+
+    def results(self) -> dict:
+        lib = L.load()
+        n = C.c_int64()
+        k, d, v, g, s = (C.c_void_p() for _ in range(5))
+        L.check(lib.vgp_frame_results(self._h, C.byref(n), C.byref(k), C.byref(d), C.byref(v), C.byref(g),
+                                      C.byref(s)))
+        torch.cuda.current_stream().synchronize()
+        n = n.value
+        return dict(keys=_view(k.value, (n,), "<u8", torch.uint64), d=_view(d.value, (n,), "<f8", torch.float64),
+                    v=_view(v.value, (n,), "<f8", torch.float64),
+                    grad=_view(g.value, (n, 3), "<f8", torch.float64),
+                    status=_view(s.value, (n,), "|u1", torch.uint8))
+
+    def instances(self) -> dict:
+        lib = L.load()
+        nl, T = C.c_int64(), C.c_int64()
+        lk, no, off, X, al = (C.c_void_p() for _ in range(5))
+        L.check(lib.vgp_frame_instances(self._h, C.byref(nl), C.byref(T), C.byref(lk), C.byref(no), C.byref(off),
+                                        C.byref(X), C.byref(al)))
+        torch.cuda.current_stream().synchronize()
+        nl, T = nl.value, T.value
+        return dict(leaf_key=_view(lk.value, (nl,), "<u8", torch.uint64),
+                    n_occ=_view(no.value, (nl,), "<i4", torch.int32),
+                    inst_off=_view(off.value, (nl + 1,), "<i8", torch.int64),
+                    X=_view(X.value, (T, 3), "<f8", torch.float64), alpha=_view(al.value, (T,), "<f8", torch.float64))
+
+    @property
+    def n_test(self) -> int:
+        n = C.c_int64()
+        L.check(L.load().vgp_frame_results(self._h, C.byref(n), None, None, None, None, None))
+        return n.value
+
+    def close(self):
+        if self._h:
+            L.load().vgp_frame_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Map:
+    """A GP distance-field map on the current CUDA device (see ``include/vgpdf.h``)."""
+
+    def __init__(self, **params):
+        lib = L.load()
+        self.params = make_params(**params)
+        h = C.c_void_p()
+        L.check(lib.vgp_create(C.byref(self.params), C.byref(h)))
+        self._h = h
+        self._surface = None
+        self._surface_key = None
+
+    # -- L-GPDF ----------------------------------------------------------------------
+    def build_frame(self, pts) -> Frame:
+        pts = _dev_f32(pts, "pts")
+        h = C.c_void_p()
+        L.check(L.load().vgp_build_frame(self._h, _ptr(pts), pts.shape[0], _stream(), C.byref(h)))
+        return Frame(self, h)
+
+    def fuse(self, frame: Frame) -> None:
+        L.check(L.load().vgp_fuse(self._h, frame._h, _stream()))
+
+    def export_grid(self):
+        lib = L.load()
+        n = C.c_int64(0)
+        L.check(lib.vgp_export_grid(self._h, C.byref(n), None, None, None, None, _stream()))
+        k = np.zeros(n.value, np.uint64)
+        D = np.zeros(n.value)
+        V = np.zeros(n.value)
+        fl = np.zeros(n.value, np.uint8)
+        if n.value:
+            L.check(lib.vgp_export_grid(self._h, C.byref(n), k.ctypes.data_as(C.c_void_p),
+                                        D.ctypes.data_as(C.c_void_p), V.ctypes.data_as(C.c_void_p),
+                                        fl.ctypes.data_as(C.c_void_p), _stream()))
+        return k[:n.value], D[:n.value], V[:n.value], fl[:n.value]
+
+    def import_grid(self, keys, D, V, flags) -> None:
+        keys = np.ascontiguousarray(keys, np.uint64)
+        D = np.ascontiguousarray(D, np.float64)
+        V = np.ascontiguousarray(V, np.float64)
+        flags = np.ascontiguousarray(flags, np.uint8)
+        L.check(L.load().vgp_import_grid(self._h, len(keys), keys.ctypes.data_as(C.c_void_p),
+                                         D.ctypes.data_as(C.c_void_p), V.ctypes.data_as(C.c_void_p),
+                                         flags.ctypes.data_as(C.c_void_p), _stream()))
+
+    # -- G-GPDF ----------------------------------------------------------------------
+    def set_surface(self, pts) -> None:
+        pts = _dev_f32(pts, "pts")
+        L.check(L.load().vgp_set_surface(self._h, _ptr(pts), pts.shape[0], _stream()))
+        self._surface = pts
+        self._surface_key = (pts.data_ptr(), tuple(pts.shape), pts._version)
+
+    def surface_is(self, pts: torch.Tensor) -> bool:
+        return self._surface_key == (pts.data_ptr(), tuple(pts.shape), pts._version)
+
+    def query(self, q, grad: bool = True, var: bool = False, out: dict | None = None) -> dict:
+        q = _dev_f32(q, "q")
+        n = q.shape[0]
+        out = out or {}
+        d = out.get("d") if out.get("d") is not None else torch.empty(n, dtype=torch.float64, device="cuda")
+        g = (out.get("grad") if out.get("grad") is not None else torch.empty((n, 3), dtype=torch.float64, device="cuda")) if grad else None
+        v = (out.get("var") if out.get("var") is not None else torch.empty(n, dtype=torch.float64, device="cuda")) if var else None
+        s = out.get("status") if out.get("status") is not None else torch.empty(n, dtype=torch.uint8, device="cuda")
+        L.check(L.load().vgp_query_distance_gradient(self._h, _ptr(q), n, _ptr(d), _ptr(g), _ptr(v), _ptr(s),
+                                                     _stream()))
+        return dict(d=d, grad=g, var=v, status=s)
+
+    def query_backward(self, q, dL_dd, want_dq: bool = True, want_dX: bool = True):
+        q = _dev_f32(q, "q")
+        n = q.shape[0]
+        dL_dd = dL_dd.to(device="cuda", dtype=torch.float64).contiguous()
+        dq = torch.empty((n, 3), dtype=torch.float64, device="cuda") if want_dq else None
+        m = self._surface.shape[0] if self._surface is not None else 0
+        dX = torch.empty((m, 3), dtype=torch.float64, device="cuda") if want_dX else None
+        L.check(L.load().vgp_query_backward(self._h, _ptr(q), n, _ptr(dL_dd), _ptr(dq), _ptr(dX), _stream()))
+        return dq, dX
+
+    # -- independent instances ---------------------------------------------------------
+    def gp_batch(self, inst_off, X, q_off, Q, var: bool = True) -> dict:
+        inst_off = torch.as_tensor(inst_off, dtype=torch.int64).to("cuda").contiguous()
+        q_off = torch.as_tensor(q_off, dtype=torch.int64).to("cuda").contiguous()
+        X = _dev_f32(X, "X")
+        Q = _dev_f32(Q, "Q")
+        n = Q.shape[0]
+        d = torch.empty(n, dtype=torch.float64, device="cuda")
+        g = torch.empty((n, 3), dtype=torch.float64, device="cuda")
+        v = torch.empty(n, dtype=torch.float64, device="cuda") if var else None
+        s = torch.empty(n, dtype=torch.uint8, device="cuda")
+        L.check(L.load().vgp_gp_batch(self._h, inst_off.shape[0] - 1, _ptr(inst_off), _ptr(X), _ptr(q_off), _ptr(Q),
+                                      _ptr(d), _ptr(g), _ptr(v), _ptr(s), _stream()))
+        return dict(d=d, grad=g, var=v, status=s)
+
+    def stats(self) -> dict:
+        st = L.VgpStats()
+        L.check(L.load().vgp_get_stats(self._h, C.byref(st)))
+        out = {k: getattr(st, k) for k, _ in L.VgpStats._fields_}
+        out["bucket_count"] = list(st.bucket_count)
+        return out
+
+    def sync(self):
+        L.check(L.load().vgp_sync(self._h))
+
+    def close(self):
+        if getattr(self, "_h", None):
+            L.load().vgp_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,920 @@
+// api.cu -- the C ABI (include/vgpdf.h): map and frame handles, device memory, and the
+// orchestration of the L-GPDF frame (Sec. IV-A/B), fusion (Sec. IV-C) and G-GPDF queries
+// (Sec. IV-D) over the kernels of grid.cu and solve.cu.
+#include <algorithm>
+#include <atomic>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "grid.h"
+
+using namespace vgp;
+
+// --------------------------------------------------------------------------------------
+// errors
+// --------------------------------------------------------------------------------------
+static thread_local std::string g_last_error;
+static std::atomic<int64_t> g_launches{0};
+
+namespace vgp {
+void note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+}  // namespace vgp
+
+static int fail(int code, const char* fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof(buf), fmt, ap);
+    va_end(ap);
+    g_last_error = buf;
+    return code;
+}
+
+#define CUDA_TRY(expr)                                                                            \
+    do {                                                                                          \
+        cudaError_t e_ = (expr);                                                                  \
+        if (e_ != cudaSuccess) return fail(VGP_ERR_CUDA, "%s: %s (%s:%d)", #expr, cudaGetErrorString(e_), __FILE__, __LINE__); \
+    } while (0)
+
+// --------------------------------------------------------------------------------------
+// arena
+// --------------------------------------------------------------------------------------
+namespace vgp {
+void* Arena::get(Slot s, size_t bytes, cudaStream_t st) {
+    bytes = std::max<size_t>(bytes, 256);
+    if (size_[s] >= bytes) return ptr_[s];
+    if (ptr_[s]) cudaFreeAsync(ptr_[s], st);
+    size_t want = std::max(bytes, size_[s] + size_[s] / 2);
+    void* p = nullptr;
+    if (cudaMallocAsync(&p, want, st) != cudaSuccess) {
+        cudaGetLastError();
+        if (cudaMallocAsync(&p, bytes, st) != cudaSuccess) {
+            ptr_[s] = nullptr;
+            size_[s] = 0;
+            return nullptr;
+        }
+        want = bytes;
+    }
+    ptr_[s] = p;
+    size_[s] = want;
+    return p;
+}
+void Arena::release_all(cudaStream_t st) {
+    for (int i = 0; i < kNumSlots; ++i) {
+        if (ptr_[i]) cudaFreeAsync(ptr_[i], st);
+        ptr_[i] = nullptr;
+        size_[i] = 0;
+    }
+}
+Arena::~Arena() {
+    for (int i = 0; i < kNumSlots; ++i)
+        if (ptr_[i]) cudaFree(ptr_[i]);
+}
+}  // namespace vgp
+
+static uint32_t pow2_at_least(int64_t n) {
+    uint64_t c = 64;
+    while ((int64_t)c < n) c <<= 1;
+    if (c > (1ull << 31)) c = 1ull << 31;
+    return (uint32_t)c;
+}
+
+// --------------------------------------------------------------------------------------
+// handles
+// --------------------------------------------------------------------------------------
+struct vgp_map {
+    vgp_params prm{};
+    DevParams P{};
+    int device = 0;
+    Arena ar;
+    int* dev_words = nullptr;  // [0] err, [1] n_valid, [2] count, [3] pool_count, [4] orphan
+    int* host_words = nullptr; // pinned mirror
+    // global grid
+    Table g;
+    int32_t* g_slot2pool = nullptr;
+    int pool_cap = 0;
+    unsigned long long* g_known = nullptr;
+    double* g_D = nullptr;
+    double* g_V = nullptr;
+    int32_t* g_flags = nullptr;
+    int g_leaves = 0;
+    // surface
+    float* s_pts = nullptr;
+    int64_t s_n = 0, s_pts_cap = 0;
+    Table s_tab;
+    int32_t* s_slot2leaf = nullptr;
+    int s_nl = 0;
+    int64_t* s_off = nullptr;
+    int32_t* s_idx = nullptr;
+    int64_t s_idx_cap = 0, s_off_cap = 0;
+    bool has_surface = false;
+    vgp_stats stats{};
+};
+
+struct vgp_frame {
+    vgp_map* m = nullptr;
+    cudaStream_t st = nullptr;
+    int64_t nl = 0, T = 0, ntest = 0;
+    uint64_t* leaf_key = nullptr;
+    int32_t* nocc = nullptr;
+    int64_t* inst_off = nullptr;
+    double* X = nullptr;
+    double* Xl = nullptr;
+    float* Xf = nullptr;
+    double* centre = nullptr;
+    double* alpha = nullptr;
+    uint64_t* tkey = nullptr;
+    double* d = nullptr;
+    double* v = nullptr;
+    double* grad = nullptr;
+    uint8_t* status = nullptr;
+    std::vector<void*> owned;
+    template <typename T_>
+    T_* alloc(int64_t n, cudaStream_t s) {
+        void* p = nullptr;
+        if (cudaMallocAsync(&p, std::max<int64_t>(n, 1) * sizeof(T_), s) != cudaSuccess) return nullptr;
+        owned.push_back(p);
+        return (T_*)p;
+    }
+};
+
+static DevParams expand(const vgp_params& p) {
+    DevParams P{};
+    P.vs = p.voxel_size;
+    P.l = p.lengthscale;
+    P.l2 = p.lengthscale * p.lengthscale;
+    P.inv2l2 = 1.0 / (2.0 * P.l2);
+    P.s2 = p.sigma_occ * p.sigma_occ;
+    P.d_max = p.d_max;
+    P.log_floor = -(p.d_max * p.d_max) / (2.0 * P.l2);
+    P.d_var_floor = p.d_var_floor;
+    P.inv2l2_log2e = (float)(1.4426950408889634 / (2.0 * P.l2));
+    P.cap_leaf = p.max_pts_leaf;
+    P.cap_group = p.max_pts_group;
+    P.search_r = p.max_leaf_search;
+    P.fusion = p.fusion;
+    P.precision = p.precision;
+    return P;
+}
+
+static int read_words(vgp_map* m, cudaStream_t st) {
+    CUDA_TRY(cudaMemcpyAsync(m->host_words, m->dev_words, sizeof(int) * 8, cudaMemcpyDeviceToHost, st));
+    CUDA_TRY(cudaStreamSynchronize(st));
+    return VGP_OK;
+}
+
+static int check_err(vgp_map* m, const char* where) {
+    int e = m->host_words[0];
+    if (e & kErrTableFull) return fail(VGP_ERR_TABLE_FULL, "%s: hash table full", where);
+    if (e & kErrTimeout) return fail(VGP_ERR_TIMEOUT, "%s: device loop limit reached", where);
+    if (e & kErrCapacity) return fail(VGP_ERR_OOM, "%s: internal buffer bound exceeded", where);
+    return VGP_OK;
+}
+
+#define TRY(expr)                 \
+    do {                          \
+        int rc_ = (expr);         \
+        if (rc_ != VGP_OK) return rc_; \
+    } while (0)
+
+#define ARENA(var, type, slot, count)                                                       \
+    type* var = (type*)m->ar.get(Arena::slot, sizeof(type) * (size_t)std::max<int64_t>((count), 1), st); \
+    if (!var) return fail(VGP_ERR_OOM, "device allocation of %s failed", #var)
+
+// --------------------------------------------------------------------------------------
+// C ABI
+// --------------------------------------------------------------------------------------
+extern "C" {
+
+const char* vgp_last_error(void) { return g_last_error.c_str(); }
+
+int64_t vgp_launch_count(void) { return g_launches.load(); }
+
+void vgp_default_params(vgp_params* p) {
+    if (!p) return;
+    std::memset(p, 0, sizeof(*p));
+    p->voxel_size = 0.1;
+    p->lengthscale = 0.3;
+    p->sigma_occ = 0.01;
+    p->d_max = 10.0;
+    p->d_var_floor = 1e-3;
+    p->max_pts_leaf = 64;
+    p->max_pts_group = 1024;
+    p->max_leaf_search = 8;
+    p->fusion = VGP_FUSE_INVVAR;
+    p->precision = VGP_MIXED;
+}
+
+int vgp_create(const vgp_params* p, vgp_map** out) {
+    if (!p || !out) return fail(VGP_ERR_ARG, "vgp_create: null argument");
+    *out = nullptr;
+    if (!(p->voxel_size > 0) || !std::isfinite(p->voxel_size)) return fail(VGP_ERR_ARG, "voxel_size must be > 0");
+    if (!(p->lengthscale > 0) || !std::isfinite(p->lengthscale)) return fail(VGP_ERR_ARG, "lengthscale must be > 0");
+    if (!(p->sigma_occ > 0) || !std::isfinite(p->sigma_occ)) return fail(VGP_ERR_ARG, "sigma_occ must be > 0");
+    if (!(p->d_max > 0) || !(p->d_var_floor > 0)) return fail(VGP_ERR_ARG, "d_max and d_var_floor must be > 0");
+    if (p->max_pts_leaf < 1 || p->max_pts_leaf > 512) return fail(VGP_ERR_ARG, "max_pts_leaf must be in [1, 512]");
+    if (p->max_pts_group < 1 || p->max_pts_group > 1024) return fail(VGP_ERR_ARG, "max_pts_group must be in [1, 1024]");
+    if (p->max_leaf_search < 0 || p->max_leaf_search > 16) return fail(VGP_ERR_ARG, "max_leaf_search must be in [0, 16]");
+    if (p->fusion != VGP_FUSE_INVVAR && p->fusion != VGP_FUSE_TSDF) return fail(VGP_ERR_ARG, "unknown fusion rule");
+    if (p->precision != VGP_FP64 && p->precision != VGP_MIXED) return fail(VGP_ERR_ARG, "unknown precision");
+    if (p->reserved[0] || p->reserved[1]) return fail(VGP_ERR_ARG, "reserved fields must be zero");
+    if (p->profile != 0 && p->profile != 1) return fail(VGP_ERR_ARG, "profile must be 0 or 1");
+    vgp_map* m = new (std::nothrow) vgp_map();
+    if (!m) return fail(VGP_ERR_OOM, "host allocation failed");
+    m->prm = *p;
+    m->P = expand(*p);
+    cudaGetDevice(&m->device);
+    if (cudaMalloc(&m->dev_words, sizeof(int) * 8) != cudaSuccess ||
+        cudaMallocHost(&m->host_words, sizeof(int) * 8) != cudaSuccess) {
+        cudaGetLastError();
+        delete m;
+        return fail(VGP_ERR_CUDA, "vgp_create: device allocation failed (is a CUDA device present?)");
+    }
+    cudaMemset(m->dev_words, 0, sizeof(int) * 8);
+    *out = m;
+    return VGP_OK;
+}
+
+int vgp_destroy(vgp_map* m) {
+    if (!m) return VGP_OK;
+    cudaDeviceSynchronize();
+    cudaFree(m->dev_words);
+    cudaFreeHost(m->host_words);
+    cudaFree(m->g.keys);
+    cudaFree(m->g_slot2pool);
+    cudaFree(m->g_known);
+    cudaFree(m->g_D);
+    cudaFree(m->g_V);
+    cudaFree(m->g_flags);
+    cudaFree(m->s_pts);
+    cudaFree(m->s_tab.keys);
+    cudaFree(m->s_slot2leaf);
+    cudaFree(m->s_off);
+    cudaFree(m->s_idx);
+    delete m;
+    return VGP_OK;
+}
+
+int vgp_sync(vgp_map* m) {
+    if (!m) return fail(VGP_ERR_ARG, "null map");
+    CUDA_TRY(cudaDeviceSynchronize());
+    return VGP_OK;
+}
+
+int vgp_get_stats(const vgp_map* m, vgp_stats* out) {
+    if (!m || !out) return fail(VGP_ERR_ARG, "null argument");
+    *out = m->stats;
+    return VGP_OK;
+}
+
+// ---------------------------------- frame ----------------------------------------------
+int vgp_build_frame(vgp_map* m, const float* pts, int64_t n, vgp_stream stream, vgp_frame** out) {
+    if (!m || !out || n < 0 || (n > 0 && !pts)) return fail(VGP_ERR_ARG, "vgp_build_frame: bad argument");
+    if (n > (1ll << 30)) return fail(VGP_ERR_ARG, "vgp_build_frame: n too large");
+    *out = nullptr;
+    cudaStream_t st = (cudaStream_t)stream;
+    const DevParams& P = m->P;
+    vgp_stats S{};
+    CUDA_TRY(cudaMemsetAsync(m->dev_words, 0, sizeof(int) * 8, st));
+    // 1. voxelise into the frame's leaf table
+    Table ft;
+    uint32_t Cf = pow2_at_least(2 * std::max<int64_t>(n, 1));
+    ft.mask = Cf - 1;
+    ARENA(fkeys, uint64_t, kTmp0, Cf);
+    ARENA(fmasks, unsigned long long, kTmp1, (int64_t)Cf * 8);
+    ARENA(fslot2leaf, int32_t, kTmp2, Cf);
+    ARENA(flist, int32_t, kTmp3, Cf);
+    ARENA(flkeys, uint64_t, kTmp4, Cf);
+    ft.keys = fkeys;
+    CUDA_TRY(cudaMemsetAsync(fkeys, 0xFF, sizeof(uint64_t) * Cf, st));
+    CUDA_TRY(cudaMemsetAsync(fmasks, 0, sizeof(unsigned long long) * Cf * 8, st));
+    frame_voxelise(pts, n, P, ft, fmasks, m->dev_words + 1, m->dev_words, st);
+    collect_table(ft, fslot2leaf, flist, flkeys, m->dev_words + 2, Cf, m->dev_words, st);
+    TRY(read_words(m, st));
+    TRY(check_err(m, "vgp_build_frame"));
+    const int nl = m->host_words[2];
+    S.n_points = m->host_words[1];
+    vgp_frame* f = new (std::nothrow) vgp_frame();
+    if (!f) return fail(VGP_ERR_OOM, "host allocation failed");
+    f->m = m;
+    f->st = st;
+    f->nl = nl;
+    auto bail = [&](int code, const char* what) {
+        vgp_frame_destroy(f);
+        return fail(code, "vgp_build_frame: %s", what);
+    };
+    f->leaf_key = f->alloc<uint64_t>(nl, st);
+    f->nocc = f->alloc<int32_t>(nl, st);
+    f->inst_off = f->alloc<int64_t>(nl + 1, st);
+    int64_t* ninst = (int64_t*)m->ar.get(Arena::kTmp5, sizeof(int64_t) * (nl + 1), st);
+    if (!f->leaf_key || !f->nocc || !f->inst_off || !ninst) return bail(VGP_ERR_OOM, "allocation failed");
+    if (nl > 0) cudaMemcpyAsync(f->leaf_key, flkeys, sizeof(uint64_t) * nl, cudaMemcpyDeviceToDevice, st);
+    // 2. per-leaf counts, capped training sets
+    frame_leaf_counts(flist, nl, fmasks, P.cap_leaf, f->nocc, ninst, st);
+    exclusive_scan_i64(ninst, f->inst_off, nl, st, m->ar);
+    int64_t T = 0;
+    cudaMemcpyAsync(&T, f->inst_off + nl, sizeof(int64_t), cudaMemcpyDeviceToHost, st);
+    if (cudaStreamSynchronize(st) != cudaSuccess) return bail(VGP_ERR_CUDA, cudaGetErrorString(cudaGetLastError()));
+    f->T = T;
+    f->X = f->alloc<double>(3 * T, st);
+    f->Xl = f->alloc<double>(3 * T, st);
+    f->Xf = f->alloc<float>(3 * T, st);
+    f->alpha = f->alloc<double>(T, st);
+    f->centre = f->alloc<double>(3 * (int64_t)nl, st);
+    if (!f->X || !f->Xl || !f->Xf || !f->alpha || !f->centre) return bail(VGP_ERR_OOM, "allocation failed");
+    frame_leaf_points(flist, flkeys, nl, fmasks, f->nocc, f->inst_off, P, f->X, f->Xl, f->Xf, f->centre, st);
+    // 3. testing leaves: occupied leaves and their 26 neighbours
+    Table tt;
+    uint32_t Ct = pow2_at_least(2 * 27 * (int64_t)std::max(nl, 1));
+    tt.mask = Ct - 1;
+    tt.keys = (uint64_t*)m->ar.get(Arena::kTmp6, sizeof(uint64_t) * Ct, st);
+    uint64_t* tl_keys = (uint64_t*)m->ar.get(Arena::kTmp7, sizeof(uint64_t) * Ct, st);
+    if (!tt.keys || !tl_keys) return bail(VGP_ERR_OOM, "allocation failed");
+    cudaMemsetAsync(tt.keys, 0xFF, sizeof(uint64_t) * Ct, st);
+    frame_dilate(f->leaf_key, nl, tt, m->dev_words, st);
+    collect_table(tt, nullptr, nullptr, tl_keys, m->dev_words + 2, Ct, m->dev_words, st);
+    if (read_words(m, st) != VGP_OK) return bail(VGP_ERR_CUDA, "sync failed");
+    if (check_err(m, "vgp_build_frame") != VGP_OK) {
+        std::string msg = g_last_error;
+        vgp_frame_destroy(f);
+        g_last_error = msg;
+        return VGP_ERR_TABLE_FULL;
+    }
+    const int ntl = m->host_words[2];
+    // 4. closest-node choice per testing voxel; group voxels by instance
+    int64_t* inst_cnt = (int64_t*)m->ar.get(Arena::kTmp8, sizeof(int64_t) * (nl + 1), st);
+    int64_t* q_off = (int64_t*)m->ar.get(Arena::kTmp9, sizeof(int64_t) * (nl + 1), st);
+    int64_t* cursor = (int64_t*)m->ar.get(Arena::kTmp10, sizeof(int64_t) * (nl + 1), st);
+    if (!inst_cnt || !q_off || !cursor) return bail(VGP_ERR_OOM, "allocation failed");
+    cudaMemsetAsync(inst_cnt, 0, sizeof(int64_t) * (nl + 1), st);
+    cudaMemsetAsync(cursor, 0, sizeof(int64_t) * (nl + 1), st);
+    frame_assign_tests(tl_keys, ntl, ft, fslot2leaf, inst_cnt, m->dev_words + 4, st);
+    exclusive_scan_i64(inst_cnt, q_off, nl, st, m->ar);
+    const int64_t ntest = (int64_t)ntl * 512;
+    f->ntest = ntest;
+    f->tkey = f->alloc<uint64_t>(ntest, st);
+    f->d = f->alloc<double>(ntest, st);
+    f->v = f->alloc<double>(ntest, st);
+    f->grad = f->alloc<double>(3 * ntest, st);
+    f->status = f->alloc<uint8_t>(ntest, st);
+    if (!f->tkey || !f->d || !f->v || !f->grad || !f->status) return bail(VGP_ERR_OOM, "allocation failed");
+    frame_scatter_tests(tl_keys, ntl, ft, fslot2leaf, q_off, cursor, f->tkey, st);
+    // 5. factorise every leaf GP and infer at its testing voxels
+    SolveBatch b;
+    b.n_inst = nl;
+    b.inst_off = f->inst_off;
+    b.Xl = f->Xl;
+    b.Xf = f->Xf;
+    b.centre = f->centre;
+    b.q_off = q_off;
+    b.qkey = f->tkey;
+    b.d = f->d;
+    b.grad = f->grad;
+    b.var = f->v;
+    b.status = f->status;
+    b.alpha_out = f->alpha;
+    b.want_var = 1;
+    SolveStats ss;
+    solve_batch(b, P, m->dev_words, st, m->ar, &ss, nullptr, m->prm.profile != 0);
+    if (read_words(m, st) != VGP_OK) return bail(VGP_ERR_CUDA, "sync failed");
+    if (m->host_words[4] != 0) return bail(VGP_ERR_STATE, "testing voxel without a neighbouring GP leaf");
+    cudaError_t ce = cudaGetLastError();
+    if (ce != cudaSuccess) return bail(VGP_ERR_CUDA, cudaGetErrorString(ce));
+    S.n_leaves = nl;
+    S.n_instances = nl;
+    S.n_train = T;
+    S.n_queries = ntest;
+    for (int i = 0; i < 5; ++i) S.bucket_count[i] = ss.bucket_count[i];
+    S.sum_n3 = ss.sum_n3;
+    S.sum_n2 = ss.sum_n2;
+    S.t_solve_ms = ss.t_solve_ms;
+    S.grid_leaves = m->g_leaves;
+    S.grid_capacity_leaves = m->pool_cap;
+    m->stats = S;
+    *out = f;
+    return VGP_OK;
+}
+
+int vgp_frame_results(const vgp_frame* f, int64_t* n_test, const uint64_t** keys, const double** d,
+                      const double** v, const double** grad, const uint8_t** status) {
+    if (!f) return fail(VGP_ERR_ARG, "null frame");
+    if (n_test) *n_test = f->ntest;
+    if (keys) *keys = f->tkey;
+    if (d) *d = f->d;
+    if (v) *v = f->v;
+    if (grad) *grad = f->grad;
+    if (status) *status = f->status;
+    return VGP_OK;
+}
+
+int vgp_frame_instances(const vgp_frame* f, int64_t* n_leaves, int64_t* n_train, const uint64_t** leaf_key,
+                        const int32_t** n_occ, const int64_t** inst_off, const double** X, const double** alpha) {
+    if (!f) return fail(VGP_ERR_ARG, "null frame");
+    if (n_leaves) *n_leaves = f->nl;
+    if (n_train) *n_train = f->T;
+    if (leaf_key) *leaf_key = f->leaf_key;
+    if (n_occ) *n_occ = f->nocc;
+    if (inst_off) *inst_off = f->inst_off;
+    if (X) *X = f->X;
+    if (alpha) *alpha = f->alpha;
+    return VGP_OK;
+}
+
+int vgp_frame_destroy(vgp_frame* f) {
+    if (!f) return VGP_OK;
+    for (void* p : f->owned) cudaFreeAsync(p, f->st);
+    cudaStreamSynchronize(f->st);
+    delete f;
+    return VGP_OK;
+}
+
+// ---------------------------------- fusion ---------------------------------------------
+static int grid_reserve(vgp_map* m, int64_t extra_leaves, cudaStream_t st) {
+    const int64_t need = m->g_leaves + extra_leaves;
+    if (need > (1ll << 30)) return fail(VGP_ERR_OOM, "grid too large");
+    // payload pool
+    if (need > m->pool_cap) {
+        int64_t nc = std::max<int64_t>(need, std::max<int64_t>(1024, (int64_t)m->pool_cap * 2));
+        unsigned long long* known = nullptr;
+        double *D = nullptr, *V = nullptr;
+        int32_t* flags = nullptr;
+        if (cudaMalloc(&known, sizeof(unsigned long long) * 8 * nc) != cudaSuccess ||
+            cudaMalloc(&D, sizeof(double) * 512 * nc) != cudaSuccess ||
+            cudaMalloc(&V, sizeof(double) * 512 * nc) != cudaSuccess ||
+            cudaMalloc(&flags, sizeof(int32_t) * nc) != cudaSuccess) {
+            cudaGetLastError();
+            cudaFree(known); cudaFree(D); cudaFree(V); cudaFree(flags);
+            return fail(VGP_ERR_OOM, "grid pool allocation failed (%lld leaves)", (long long)nc);
+        }
+        if (m->g_leaves > 0) {
+            cudaMemcpyAsync(known, m->g_known, sizeof(unsigned long long) * 8 * m->g_leaves, cudaMemcpyDeviceToDevice, st);
+            cudaMemcpyAsync(D, m->g_D, sizeof(double) * 512 * m->g_leaves, cudaMemcpyDeviceToDevice, st);
+            cudaMemcpyAsync(V, m->g_V, sizeof(double) * 512 * m->g_leaves, cudaMemcpyDeviceToDevice, st);
+            cudaMemcpyAsync(flags, m->g_flags, sizeof(int32_t) * m->g_leaves, cudaMemcpyDeviceToDevice, st);
+        }
+        CUDA_TRY(cudaStreamSynchronize(st));
+        cudaFree(m->g_known); cudaFree(m->g_D); cudaFree(m->g_V); cudaFree(m->g_flags);
+        m->g_known = known; m->g_D = D; m->g_V = V; m->g_flags = flags;
+        m->pool_cap = (int)nc;
+    }
+    // hash table at load <= 1/2
+    if ((int64_t)m->g.cap() < 2 * need) {
+        Table nt;
+        uint32_t cap = pow2_at_least(std::max<int64_t>(4 * need, 1024));
+        nt.mask = cap - 1;
+        int32_t* ns2p = nullptr;
+        if (cudaMalloc(&nt.keys, sizeof(uint64_t) * cap) != cudaSuccess ||
+            cudaMalloc(&ns2p, sizeof(int32_t) * cap) != cudaSuccess) {
+            cudaGetLastError();
+            cudaFree(nt.keys); cudaFree(ns2p);
+            return fail(VGP_ERR_OOM, "grid table allocation failed");
+        }
+        cudaMemsetAsync(nt.keys, 0xFF, sizeof(uint64_t) * cap, st);
+        cudaMemsetAsync(ns2p, 0xFF, sizeof(int32_t) * cap, st);
+        if (m->g.keys) grid_rehash(m->g, m->g_slot2pool, nt, ns2p, m->dev_words, st);
+        CUDA_TRY(cudaStreamSynchronize(st));
+        cudaFree(m->g.keys); cudaFree(m->g_slot2pool);
+        m->g = nt;
+        m->g_slot2pool = ns2p;
+    }
+    return VGP_OK;
+}
+
+int vgp_fuse(vgp_map* m, vgp_frame* f, vgp_stream stream) {
+    if (!m || !f || f->m != m) return fail(VGP_ERR_ARG, "vgp_fuse: bad argument");
+    cudaStream_t st = (cudaStream_t)stream;
+    CUDA_TRY(cudaMemsetAsync(m->dev_words, 0, sizeof(int) * 3, st));
+    TRY(grid_reserve(m, f->ntest / 512 + 1, st));
+    CUDA_TRY(cudaMemcpyAsync(m->dev_words + 3, &m->g_leaves, sizeof(int), cudaMemcpyHostToDevice, st));
+    fuse_clear_flags(m->g_flags, m->g_leaves, st);
+    fuse_insert(f->tkey, f->d, f->v, f->status, f->ntest, m->prm.fusion, m->g, m->g_slot2pool, m->dev_words, st);
+    fuse_alloc(m->g_slot2pool, m->g, m->dev_words + 3, m->pool_cap, m->g_known, m->g_flags, m->dev_words, st);
+    fuse_update(f->tkey, f->d, f->v, f->status, f->ntest, m->prm.fusion, m->g, m->g_slot2pool, m->g_known, m->g_D,
+                m->g_V, m->g_flags, st);
+    TRY(read_words(m, st));
+    TRY(check_err(m, "vgp_fuse"));
+    CUDA_TRY(cudaGetLastError());
+    m->g_leaves = m->host_words[3];
+    m->stats.grid_leaves = m->g_leaves;
+    m->stats.grid_capacity_leaves = m->pool_cap;
+    return VGP_OK;
+}
+
+int vgp_export_grid(vgp_map* m, int64_t* n, uint64_t* keys, double* D, double* V, uint8_t* flags, vgp_stream stream) {
+    if (!m || !n) return fail(VGP_ERR_ARG, "vgp_export_grid: bad argument");
+    cudaStream_t st = (cudaStream_t)stream;
+    const int64_t cap_out = (int64_t)m->g_leaves * 512;
+    if (m->g_leaves == 0) {
+        *n = 0;
+        return VGP_OK;
+    }
+    ARENA(okey, uint64_t, kTmp0, cap_out);
+    ARENA(oD, double, kTmp1, cap_out);
+    ARENA(oV, double, kTmp2, cap_out);
+    ARENA(ofl, uint8_t, kTmp3, cap_out);
+    grid_export(m->g, m->g_slot2pool, m->g_known, m->g_D, m->g_V, m->g_flags, m->dev_words + 2, okey, oD, oV, ofl, st);
+    TRY(read_words(m, st));
+    const int64_t cnt = m->host_words[2];
+    if (!keys) {
+        *n = cnt;
+        return VGP_OK;
+    }
+    if (*n < cnt) return fail(VGP_ERR_ARG, "vgp_export_grid: arrays hold %lld < %lld", (long long)*n, (long long)cnt);
+    std::vector<uint64_t> hk(cnt);
+    std::vector<double> hD(cnt), hV(cnt);
+    std::vector<uint8_t> hf(cnt);
+    CUDA_TRY(cudaMemcpyAsync(hk.data(), okey, sizeof(uint64_t) * cnt, cudaMemcpyDeviceToHost, st));
+    CUDA_TRY(cudaMemcpyAsync(hD.data(), oD, sizeof(double) * cnt, cudaMemcpyDeviceToHost, st));
+    CUDA_TRY(cudaMemcpyAsync(hV.data(), oV, sizeof(double) * cnt, cudaMemcpyDeviceToHost, st));
+    CUDA_TRY(cudaMemcpyAsync(hf.data(), ofl, cnt, cudaMemcpyDeviceToHost, st));
+    CUDA_TRY(cudaStreamSynchronize(st));
+    std::vector<int64_t> ord(cnt);
+    for (int64_t i = 0; i < cnt; ++i) ord[i] = i;
+    std::sort(ord.begin(), ord.end(), [&](int64_t a, int64_t b) { return hk[a] < hk[b]; });
+    for (int64_t i = 0; i < cnt; ++i) {
+        keys[i] = hk[ord[i]];
+        if (D) D[i] = hD[ord[i]];
+        if (V) V[i] = hV[ord[i]];
+        if (flags) flags[i] = hf[ord[i]];
+    }
+    *n = cnt;
+    return VGP_OK;
+}
+
+int vgp_import_grid(vgp_map* m, int64_t n, const uint64_t* keys, const double* D, const double* V,
+                    const uint8_t* flags, vgp_stream stream) {
+    if (!m || n < 0 || (n > 0 && (!keys || !D || !V || !flags))) return fail(VGP_ERR_ARG, "vgp_import_grid: bad argument");
+    cudaStream_t st = (cudaStream_t)stream;
+    // clear the current grid
+    if (m->g.keys) {
+        CUDA_TRY(cudaMemsetAsync(m->g.keys, 0xFF, sizeof(uint64_t) * m->g.cap(), st));
+        CUDA_TRY(cudaMemsetAsync(m->g_slot2pool, 0xFF, sizeof(int32_t) * m->g.cap(), st));
+    }
+    m->g_leaves = 0;
+    if (n == 0) return VGP_OK;
+    CUDA_TRY(cudaMemsetAsync(m->dev_words, 0, sizeof(int) * 8, st));
+    TRY(grid_reserve(m, n, st));  // at most one leaf per voxel
+    ARENA(ik, uint64_t, kTmp0, n);
+    ARENA(iD, double, kTmp1, n);
+    ARENA(iV, double, kTmp2, n);
+    ARENA(ifl, uint8_t, kTmp3, n);
+    CUDA_TRY(cudaMemcpyAsync(ik, keys, sizeof(uint64_t) * n, cudaMemcpyHostToDevice, st));
+    CUDA_TRY(cudaMemcpyAsync(iD, D, sizeof(double) * n, cudaMemcpyHostToDevice, st));
+    CUDA_TRY(cudaMemcpyAsync(iV, V, sizeof(double) * n, cudaMemcpyHostToDevice, st));
+    CUDA_TRY(cudaMemcpyAsync(ifl, flags, n, cudaMemcpyHostToDevice, st));
+    grid_import(ik, iD, iV, ifl, n, m->g, m->g_slot2pool, m->dev_words + 3, m->pool_cap, m->g_known, m->g_D, m->g_V,
+                m->g_flags, m->dev_words, st);
+    TRY(read_words(m, st));
+    TRY(check_err(m, "vgp_import_grid"));
+    m->g_leaves = m->host_words[3];
+    return VGP_OK;
+}
+
+// ---------------------------------- surface --------------------------------------------
+int vgp_set_surface(vgp_map* m, const float* pts, int64_t n, vgp_stream stream) {
+    if (!m || n < 0 || (n > 0 && !pts)) return fail(VGP_ERR_ARG, "vgp_set_surface: bad argument");
+    if (n >= (1ll << 31)) return fail(VGP_ERR_ARG, "vgp_set_surface: at most 2^31 - 1 points");
+    cudaStream_t st = (cudaStream_t)stream;
+    const DevParams& P = m->P;
+    m->has_surface = false;
+    if (n > m->s_pts_cap) {
+        cudaFree(m->s_pts);
+        m->s_pts = nullptr;
+        if (cudaMalloc(&m->s_pts, sizeof(float) * 3 * n) != cudaSuccess) {
+            cudaGetLastError();
+            m->s_pts_cap = 0;
+            return fail(VGP_ERR_OOM, "surface copy allocation failed");
+        }
+        m->s_pts_cap = n;
+    }
+    if (n > 0) CUDA_TRY(cudaMemcpyAsync(m->s_pts, pts, sizeof(float) * 3 * n, cudaMemcpyDeviceToDevice, st));
+    m->s_n = n;
+    uint32_t Cs = pow2_at_least(2 * std::max<int64_t>(n, 1));
+    if (m->s_tab.cap() != Cs) {
+        cudaFree(m->s_tab.keys);
+        cudaFree(m->s_slot2leaf);
+        m->s_tab.keys = nullptr;
+        m->s_slot2leaf = nullptr;
+        if (cudaMalloc(&m->s_tab.keys, sizeof(uint64_t) * Cs) != cudaSuccess ||
+            cudaMalloc(&m->s_slot2leaf, sizeof(int32_t) * Cs) != cudaSuccess) {
+            cudaGetLastError();
+            return fail(VGP_ERR_OOM, "surface table allocation failed");
+        }
+        m->s_tab.mask = Cs - 1;
+    }
+    CUDA_TRY(cudaMemsetAsync(m->s_tab.keys, 0xFF, sizeof(uint64_t) * Cs, st));
+    CUDA_TRY(cudaMemsetAsync(m->dev_words, 0, sizeof(int) * 8, st));
+    ARENA(pt_slot, int32_t, kTmp0, n);
+    ARENA(slot_cnt, int32_t, kTmp1, Cs);
+    ARENA(list, int32_t, kTmp2, Cs);
+    CUDA_TRY(cudaMemsetAsync(slot_cnt, 0, sizeof(int32_t) * Cs, st));
+    surface_bin(m->s_pts, n, P, m->s_tab, pt_slot, slot_cnt, m->dev_words + 1, m->dev_words, st);
+    collect_table(m->s_tab, m->s_slot2leaf, list, nullptr, m->dev_words + 2, Cs, m->dev_words, st);
+    TRY(read_words(m, st));
+    TRY(check_err(m, "vgp_set_surface"));
+    const int nl = m->host_words[2];
+    m->stats = vgp_stats{};
+    m->stats.n_points = m->host_words[1];
+    m->stats.n_leaves = nl;
+    if (nl + 1 > m->s_off_cap) {
+        cudaFree(m->s_off);
+        if (cudaMalloc(&m->s_off, sizeof(int64_t) * (nl + 1)) != cudaSuccess) {
+            cudaGetLastError();
+            m->s_off = nullptr;
+            m->s_off_cap = 0;
+            return fail(VGP_ERR_OOM, "surface offsets allocation failed");
+        }
+        m->s_off_cap = nl + 1;
+    }
+    const int64_t nv = m->host_words[1];
+    if (nv > m->s_idx_cap) {
+        cudaFree(m->s_idx);
+        if (cudaMalloc(&m->s_idx, sizeof(int32_t) * std::max<int64_t>(nv, 1)) != cudaSuccess) {
+            cudaGetLastError();
+            m->s_idx = nullptr;
+            m->s_idx_cap = 0;
+            return fail(VGP_ERR_OOM, "surface index allocation failed");
+        }
+        m->s_idx_cap = nv;
+    }
+    ARENA(cnt, int64_t, kTmp3, nl + 1);
+    ARENA(cursor, int32_t, kTmp4, nl + 1);
+    surface_leaf_counts(list, nl, slot_cnt, cnt, st);
+    exclusive_scan_i64(cnt, m->s_off, nl, st, m->ar);
+    CUDA_TRY(cudaMemsetAsync(cursor, 0, sizeof(int32_t) * (nl + 1), st));
+    surface_scatter(pt_slot, n, m->s_slot2leaf, m->s_off, cursor, m->s_idx, nl, st);
+    CUDA_TRY(cudaStreamSynchronize(st));
+    CUDA_TRY(cudaGetLastError());
+    m->s_nl = nl;
+    m->has_surface = true;
+    return VGP_OK;
+}
+
+// ---------------------------------- queries --------------------------------------------
+struct QueryPlan {
+    int64_t n = 0;
+    int ni = 0, ng = 0;
+    int64_t T = 0;
+    int64_t* inst_off = nullptr;
+    double* Xl = nullptr;
+    float* Xf = nullptr;
+    double* centre = nullptr;
+    int64_t* gidx = nullptr;
+    int64_t* q_off = nullptr;
+    int64_t* qidx = nullptr;
+};
+
+static int plan_queries(vgp_map* m, const float* q, int64_t n, double* d, double* grad, double* var, uint8_t* status,
+                        cudaStream_t st, QueryPlan& Q) {
+    const DevParams& P = m->P;
+    Q.n = n;
+    CUDA_TRY(cudaMemsetAsync(m->dev_words, 0, sizeof(int) * 8, st));
+    // query leaves (groups)
+    Table qt;
+    uint32_t Cq = pow2_at_least(2 * std::min<int64_t>(std::max<int64_t>(n, 1), 1ll << 21));
+    ARENA(q_slot, int32_t, kTmp0, n);
+    for (int attempt = 0;; ++attempt) {
+        qt.mask = Cq - 1;
+        qt.keys = (uint64_t*)m->ar.get(Arena::kTmp1, sizeof(uint64_t) * Cq, st);
+        if (!qt.keys) return fail(VGP_ERR_OOM, "query table allocation failed");
+        CUDA_TRY(cudaMemsetAsync(qt.keys, 0xFF, sizeof(uint64_t) * Cq, st));
+        CUDA_TRY(cudaMemsetAsync(m->dev_words, 0, sizeof(int), st));
+        query_leaf(q, n, P, qt, q_slot, m->dev_words, st);
+        TRY(read_words(m, st));
+        if (!(m->host_words[0] & kErrTableFull)) break;
+        if (attempt >= 6 || Cq >= (1u << 31)) return fail(VGP_ERR_TABLE_FULL, "query leaf table full");
+        Cq <<= 2;
+    }
+    ARENA(slot2group, int32_t, kTmp2, Cq);
+    ARENA(gkeys, uint64_t, kTmp3, Cq);
+    collect_table(qt, slot2group, nullptr, gkeys, m->dev_words + 2, Cq, m->dev_words, st);
+    TRY(read_words(m, st));
+    TRY(check_err(m, "query"));
+    const int ng = m->host_words[2];
+    Q.ng = ng;
+    ARENA(gcen, uint64_t, kTmp4, ng);
+    group_centre(gkeys, ng, m->s_tab, P.search_r, gcen, st);
+    // unique centres -> instances
+    Table it;
+    uint32_t Ci = pow2_at_least(2 * (int64_t)std::max(ng, 1));
+    it.mask = Ci - 1;
+    it.keys = (uint64_t*)m->ar.get(Arena::kTmp5, sizeof(uint64_t) * Ci, st);
+    ARENA(islot2inst, int32_t, kTmp6, Ci);
+    ARENA(ikeys, uint64_t, kTmp7, Ci);
+    if (!it.keys) return fail(VGP_ERR_OOM, "instance table allocation failed");
+    CUDA_TRY(cudaMemsetAsync(it.keys, 0xFF, sizeof(uint64_t) * Ci, st));
+    insert_centres(gcen, ng, it, m->dev_words, st);
+    collect_table(it, islot2inst, nullptr, ikeys, m->dev_words + 2, Ci, m->dev_words, st);
+    TRY(read_words(m, st));
+    TRY(check_err(m, "query"));
+    const int ni = m->host_words[2];
+    Q.ni = ni;
+    ARENA(ncand, int64_t, kTmp8, ni + 1);
+    ARENA(ninst, int64_t, kTmp9, ni + 1);
+    ARENA(inst_off, int64_t, kTmp10, ni + 1);
+    inst_count(ikeys, ni, m->s_tab, m->s_slot2leaf, m->s_off, P.cap_group, ncand, ninst, st);
+    exclusive_scan_i64(ninst, inst_off, ni, st, m->ar);
+    int64_t T = 0;
+    CUDA_TRY(cudaMemcpyAsync(&T, inst_off + ni, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+    CUDA_TRY(cudaStreamSynchronize(st));
+    Q.T = T;
+    ARENA(Xl, double, kTmp11, 3 * T);
+    ARENA(Xf, float, kTmp12, 3 * T);
+    ARENA(gidx, int64_t, kTmp13, T);
+    ARENA(centre, double, kTmp14, 3 * (int64_t)ni);
+    inst_gather(ikeys, ni, m->s_tab, m->s_slot2leaf, m->s_off, m->s_idx, m->s_pts, ncand, inst_off, P, Xl, Xf, gidx,
+                centre, st);
+    // route queries to instances
+    ARENA(q_inst, int32_t, kTmp15, n);
+    ARENA(inst_qcnt, int64_t, kTmp16, ni + 1);
+    ARENA(q_off, int64_t, kTmp17, ni + 1);
+    CUDA_TRY(cudaMemsetAsync(inst_qcnt, 0, sizeof(int64_t) * (ni + 1), st));
+    query_route(q_slot, n, slot2group, gcen, it, islot2inst, q_inst, inst_qcnt, st);
+    exclusive_scan_i64(inst_qcnt, q_off, ni, st, m->ar);
+    CUDA_TRY(cudaMemsetAsync(inst_qcnt, 0, sizeof(int64_t) * (ni + 1), st));  // reused as cursor
+    int64_t* qidx = (int64_t*)m->ar.get(Arena::kWs2, sizeof(int64_t) * std::max<int64_t>(n, 1), st);
+    if (!qidx) return fail(VGP_ERR_OOM, "query index allocation failed");
+    query_scatter(q_inst, n, q_off, inst_qcnt, qidx, d, grad, var, status, st);
+    Q.inst_off = inst_off;
+    Q.Xl = Xl;
+    Q.Xf = Xf;
+    Q.centre = centre;
+    Q.gidx = gidx;
+    Q.q_off = q_off;
+    Q.qidx = qidx;
+    return VGP_OK;
+}
+
+int vgp_query_distance_gradient(vgp_map* m, const float* q, int64_t n, double* d, double* grad, double* var,
+                                uint8_t* status, vgp_stream stream) {
+    if (!m || n < 0 || (n > 0 && (!q || !d))) return fail(VGP_ERR_ARG, "vgp_query_distance_gradient: bad argument");
+    if (!m->has_surface) return fail(VGP_ERR_STATE, "vgp_query_distance_gradient before vgp_set_surface");
+    if (n >= (1ll << 31)) return fail(VGP_ERR_ARG, "at most 2^31 - 1 queries per call");
+    if (n == 0) return VGP_OK;
+    cudaStream_t st = (cudaStream_t)stream;
+    QueryPlan Q;
+    TRY(plan_queries(m, q, n, d, grad, var, status, st, Q));
+    SolveBatch b;
+    b.n_inst = Q.ni;
+    b.inst_off = Q.inst_off;
+    b.Xl = Q.Xl;
+    b.Xf = Q.Xf;
+    b.centre = Q.centre;
+    b.q_off = Q.q_off;
+    b.qidx = Q.qidx;
+    b.qxyz = q;
+    b.d = d;
+    b.grad = grad;
+    b.var = var;
+    b.status = status;
+    b.want_var = var != nullptr;
+    SolveStats ss;
+    solve_batch(b, m->P, m->dev_words, st, m->ar, &ss, nullptr, m->prm.profile != 0);
+    CUDA_TRY(cudaGetLastError());
+    vgp_stats S{};
+    S.n_points = m->s_n;
+    S.n_leaves = m->s_nl;
+    S.n_instances = Q.ni;
+    S.n_train = Q.T;
+    S.n_queries = n;
+    S.n_groups = Q.ng;
+    for (int i = 0; i < 5; ++i) S.bucket_count[i] = ss.bucket_count[i];
+    S.sum_n3 = ss.sum_n3;
+    S.sum_n2 = ss.sum_n2;
+    S.t_solve_ms = ss.t_solve_ms;
+    S.grid_leaves = m->g_leaves;
+    S.grid_capacity_leaves = m->pool_cap;
+    m->stats = S;
+    return VGP_OK;
+}
+
+int vgp_query_backward(vgp_map* m, const float* q, int64_t n, const double* dL_dd, double* dL_dq, double* dL_dX,
+                       vgp_stream stream) {
+    if (!m || n < 0 || (n > 0 && (!q || !dL_dd))) return fail(VGP_ERR_ARG, "vgp_query_backward: bad argument");
+    if (!m->has_surface) return fail(VGP_ERR_STATE, "vgp_query_backward before vgp_set_surface");
+    if (n >= (1ll << 31)) return fail(VGP_ERR_ARG, "at most 2^31 - 1 queries per call");
+    cudaStream_t st = (cudaStream_t)stream;
+    if (dL_dq && n > 0) CUDA_TRY(cudaMemsetAsync(dL_dq, 0, sizeof(double) * 3 * n, st));
+    if (dL_dX && m->s_n > 0) CUDA_TRY(cudaMemsetAsync(dL_dX, 0, sizeof(double) * 3 * m->s_n, st));
+    if (n == 0) return VGP_OK;
+    double* dtmp = (double*)m->ar.get(Arena::kBw0, sizeof(double) * n, st);
+    if (!dtmp) return fail(VGP_ERR_OOM, "allocation failed");
+    QueryPlan Q;
+    TRY(plan_queries(m, q, n, dtmp, nullptr, nullptr, nullptr, st, Q));
+    double* obar = (double*)m->ar.get(Arena::kBw1, sizeof(double) * n, st);
+    if (!obar) return fail(VGP_ERR_OOM, "allocation failed");
+    SolveBatch b;
+    b.n_inst = Q.ni;
+    b.inst_off = Q.inst_off;
+    b.Xl = Q.Xl;
+    b.Xf = Q.Xf;
+    b.centre = Q.centre;
+    b.q_off = Q.q_off;
+    b.qidx = Q.qidx;
+    b.qxyz = q;
+    b.d = dtmp;
+    BackwardBatch bw;
+    bw.gidx = Q.gidx;
+    bw.dL_dd = dL_dd;
+    bw.dL_dq = dL_dq;
+    bw.dL_dX = dL_dX;
+    bw.obar = obar;
+    solve_batch(b, m->P, m->dev_words, st, m->ar, nullptr, &bw);
+    CUDA_TRY(cudaStreamSynchronize(st));
+    CUDA_TRY(cudaGetLastError());
+    return VGP_OK;
+}
+
+}  // extern "C"
+
+// ---------------------------------- independent instances ------------------------------
+namespace {
+// Warp per instance: bounds check, bounding-box centre, local coordinates.
+__global__ void k_batch_prep(const int64_t* inst_off, int64_t n_inst, const float* X, double* Xl, float* Xf,
+                             double* centre, int* err) {
+    int64_t I = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    int lane = threadIdx.x & 31;
+    if (I >= n_inst) return;
+    const int64_t b = inst_off[I], e = inst_off[I + 1];
+    if (e - b > 1024 || e < b) {
+        if (lane == 0) atomicOr(err, kErrCapacity);
+        return;
+    }
+    float lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
+    for (int64_t j = b + lane; j < e; j += 32)
+        for (int a = 0; a < 3; ++a) {
+            float v = X[3 * j + a];
+            lo[a] = fminf(lo[a], v);
+            hi[a] = fmaxf(hi[a], v);
+        }
+    double c[3];
+    for (int a = 0; a < 3; ++a) {
+        for (int o = 16; o > 0; o >>= 1) {
+            lo[a] = fminf(lo[a], __shfl_xor_sync(0xffffffffu, lo[a], o));
+            hi[a] = fmaxf(hi[a], __shfl_xor_sync(0xffffffffu, hi[a], o));
+        }
+        c[a] = (e > b && isfinite(lo[a]) && isfinite(hi[a])) ? 0.5 * ((double)lo[a] + (double)hi[a]) : 0.0;
+    }
+    if (lane < 3) centre[3 * I + lane] = c[lane];
+    for (int64_t j = b + lane; j < e; j += 32)
+        for (int a = 0; a < 3; ++a) {
+            double v = (double)X[3 * j + a] - c[a];
+            Xl[3 * j + a] = v;
+            Xf[3 * j + a] = (float)v;
+        }
+}
+}  // namespace
+
+extern "C" int vgp_gp_batch(vgp_map* m, int64_t n_inst, const int64_t* inst_off, const float* X, const int64_t* q_off,
+                            const float* Q, double* d, double* grad, double* var, uint8_t* status, vgp_stream stream) {
+    if (!m || n_inst < 0 || (n_inst > 0 && (!inst_off || !q_off || !d)))
+        return fail(VGP_ERR_ARG, "vgp_gp_batch: bad argument");
+    if (n_inst == 0) return VGP_OK;
+    if (n_inst >= (1ll << 31)) return fail(VGP_ERR_ARG, "vgp_gp_batch: too many instances");
+    cudaStream_t st = (cudaStream_t)stream;
+    int64_t T = 0, NQ = 0;
+    CUDA_TRY(cudaMemcpyAsync(&T, inst_off + n_inst, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+    CUDA_TRY(cudaMemcpyAsync(&NQ, q_off + n_inst, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+    CUDA_TRY(cudaStreamSynchronize(st));
+    if (T < 0 || NQ < 0) return fail(VGP_ERR_ARG, "vgp_gp_batch: negative totals");
+    CUDA_TRY(cudaMemsetAsync(m->dev_words, 0, sizeof(int) * 8, st));
+    ARENA(Xl, double, kTmp11, 3 * T);
+    ARENA(Xf, float, kTmp12, 3 * T);
+    ARENA(centre, double, kTmp14, 3 * n_inst);
+    k_batch_prep<<<(unsigned)((n_inst * 32 + 255) / 256), 256, 0, st>>>(inst_off, n_inst, X, Xl, Xf, centre,
+                                                                         m->dev_words);
+    note_launch();
+    TRY(read_words(m, st));
+    if (m->host_words[0] & kErrCapacity) return fail(VGP_ERR_ARG, "vgp_gp_batch: an instance has more than 1024 points");
+    SolveBatch b;
+    b.n_inst = n_inst;
+    b.inst_off = inst_off;
+    b.Xl = Xl;
+    b.Xf = Xf;
+    b.centre = centre;
+    b.q_off = q_off;
+    b.qidx = nullptr;
+    b.qxyz = Q;
+    b.d = d;
+    b.grad = grad;
+    b.var = var;
+    b.status = status;
+    b.want_var = var != nullptr;
+    SolveStats ss;
+    solve_batch(b, m->P, m->dev_words, st, m->ar, &ss, nullptr, m->prm.profile != 0);
+    CUDA_TRY(cudaGetLastError());
+    vgp_stats S{};
+    S.n_instances = n_inst;
+    S.n_train = T;
+    S.n_queries = NQ;
+    for (int i = 0; i < 5; ++i) S.bucket_count[i] = ss.bucket_count[i];
+    S.sum_n3 = ss.sum_n3;
+    S.sum_n2 = ss.sum_n2;
+    S.t_solve_ms = ss.t_solve_ms;
+    m->stats = S;
+    return VGP_OK;
+}

@@ -1,0 +1,71 @@
+// grid.h -- launchers of grid.cu (sparse leaf tables, instance construction, fusion).
+#pragma once
+
+#include "internal.h"
+
+namespace vgp {
+
+struct Table {
+    uint64_t* keys = nullptr;
+    uint32_t mask = 0;
+    size_t cap() const { return keys ? (size_t)mask + 1 : 0; }
+};
+
+void collect_table(const Table& t, int32_t* slot2idx, int32_t* list, uint64_t* keys_out, int* count_dev,
+                   int64_t list_cap, int* err, cudaStream_t st);
+
+// frame (L-GPDF)
+void frame_voxelise(const float* pts, int64_t n, const DevParams& P, const Table& t, unsigned long long* masks,
+                    int* n_valid, int* err, cudaStream_t st);
+void frame_leaf_counts(const int32_t* list, int nl, const unsigned long long* masks, int cap, int32_t* nocc,
+                       int64_t* ninst, cudaStream_t st);
+void frame_leaf_points(const int32_t* list, const uint64_t* lkeys, int nl, const unsigned long long* masks,
+                       const int32_t* nocc, const int64_t* inst_off, const DevParams& P, double* X, double* Xl,
+                       float* Xf, double* centre, cudaStream_t st);
+void frame_dilate(const uint64_t* lkeys, int nl, const Table& t, int* err, cudaStream_t st);
+void frame_assign_tests(const uint64_t* tl_keys, int ntl, const Table& ft, const int32_t* slot2leaf,
+                        int64_t* inst_cnt, int* n_orphan, cudaStream_t st);
+void frame_scatter_tests(const uint64_t* tl_keys, int ntl, const Table& ft, const int32_t* slot2leaf,
+                         const int64_t* q_off, int64_t* cursor, uint64_t* tkey, cudaStream_t st);
+
+// surface (G-GPDF)
+void surface_bin(const float* pts, int64_t n, const DevParams& P, const Table& t, int32_t* pt_slot, int32_t* slot_cnt,
+                 int* n_valid, int* err, cudaStream_t st);
+void surface_leaf_counts(const int32_t* list, int nl, const int32_t* slot_cnt, int64_t* cnt, cudaStream_t st);
+void surface_scatter(const int32_t* pt_slot, int64_t n, const int32_t* slot2leaf, const int64_t* off, int32_t* cursor,
+                     int32_t* idx, int nl, cudaStream_t st);
+
+// queries
+void query_leaf(const float* q, int64_t n, const DevParams& P, const Table& t, int32_t* q_slot, int* err,
+                cudaStream_t st);
+void group_centre(const uint64_t* gkeys, int ng, const Table& s, int R, uint64_t* gcen, cudaStream_t st);
+void insert_centres(const uint64_t* gcen, int ng, const Table& it, int* err, cudaStream_t st);
+void inst_count(const uint64_t* ikey, int ni, const Table& s, const int32_t* sslot2leaf, const int64_t* soff, int cap,
+                int64_t* ncand, int64_t* ninst, cudaStream_t st);
+void inst_gather(const uint64_t* ikey, int ni, const Table& s, const int32_t* sslot2leaf, const int64_t* soff,
+                 const int32_t* sidx, const float* spts, const int64_t* ncand, const int64_t* inst_off,
+                 const DevParams& P, double* Xl, float* Xf, int64_t* gidx, double* centre, cudaStream_t st);
+void query_route(const int32_t* q_slot, int64_t n, const int32_t* slot2group, const uint64_t* gcen, const Table& it,
+                 const int32_t* islot2inst, int32_t* q_inst, int64_t* inst_qcnt, cudaStream_t st);
+void query_scatter(const int32_t* q_inst, int64_t n, const int64_t* q_off, int64_t* cursor, int64_t* qidx, double* d,
+                   double* grad, double* var, uint8_t* status, cudaStream_t st);
+
+// fusion, export, import
+void fuse_clear_flags(int32_t* flags, int n, cudaStream_t st);
+void fuse_insert(const uint64_t* vkey, const double* d, const double* v, const uint8_t* s, int64_t n, int mode,
+                 const Table& g, int32_t* slot2pool, int* err, cudaStream_t st);
+void fuse_alloc(int32_t* slot2pool, const Table& g, int* pool_count, int pool_cap, unsigned long long* known,
+                int32_t* flags, int* err, cudaStream_t st);
+void fuse_update(const uint64_t* vkey, const double* d, const double* v, const uint8_t* s, int64_t n, int mode,
+                 const Table& g, const int32_t* slot2pool, unsigned long long* known, double* D, double* V,
+                 int32_t* flags, cudaStream_t st);
+void grid_export(const Table& g, const int32_t* slot2pool, const unsigned long long* known, const double* D,
+                 const double* V, const int32_t* flags, int* count, uint64_t* okey, double* oD, double* oV,
+                 uint8_t* ofl, cudaStream_t st);
+void grid_import(const uint64_t* vkey, const double* iD, const double* iV, const uint8_t* ifl, int64_t n, const Table& g,
+                 int32_t* slot2pool, int* pool_count, int pool_cap, unsigned long long* known, double* D, double* V,
+                 int32_t* flags, int* err, cudaStream_t st);
+void grid_rehash(const Table& o, const int32_t* oslot2pool, const Table& nt, int32_t* nslot2pool, int* err,
+                 cudaStream_t st);
+
+}  // namespace vgp

@@ -1,0 +1,81 @@
+// internal.h -- host-side declarations shared by the library's translation units.
+#pragma once
+
+#include <cstddef>
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include <cuda_runtime.h>
+
+#include "common.cuh"
+
+namespace vgp {
+
+// Stream-ordered scratch buffers that grow on demand (cudaMallocAsync on the call's stream).
+class Arena {
+public:
+    enum Slot {
+        kScan0, kScan1, kScan2, kHist, kOrder, kTmp0, kTmp1, kTmp2, kTmp3, kTmp4, kTmp5, kTmp6,
+        kTmp7, kTmp8, kTmp9, kTmp10, kTmp11, kTmp12, kTmp13, kTmp14, kTmp15, kTmp16, kTmp17,
+        kWs0, kWs1, kWs2, kBw0, kBw1, kCounters, kNumSlots
+    };
+    void* get(Slot s, size_t bytes, cudaStream_t st);
+    void release_all(cudaStream_t st);
+    ~Arena();
+
+private:
+    void* ptr_[kNumSlots] = {};
+    size_t size_[kNumSlots] = {};
+};
+
+// Instances to solve (one GP each) with the queries that each must answer.
+struct SolveBatch {
+    int64_t n_inst = 0;
+    const int64_t* inst_off = nullptr;  // [n_inst + 1] offsets into Xl / Xf
+    const double* Xl = nullptr;         // [T][3] FP64 coordinates relative to the centre
+    const float* Xf = nullptr;          // [T][3] FP32 copy of Xl
+    const double* centre = nullptr;     // [n_inst][3] FP64 world-frame centre
+    const int64_t* q_off = nullptr;     // [n_inst + 1] offsets into the position list
+    const int64_t* qidx = nullptr;      // position -> query id (nullptr: identity)
+    const float* qxyz = nullptr;        // world-frame query points (by query id)
+    const uint64_t* qkey = nullptr;     // voxel-key queries (by position), if qxyz is null
+    double* d = nullptr;                // outputs by query id
+    double* grad = nullptr;
+    double* var = nullptr;
+    uint8_t* status = nullptr;
+    double* alpha_out = nullptr;        // [T] optional
+    int want_var = 0;
+};
+
+// Backward-pass extras (G-GPDF only).
+struct BackwardBatch {
+    const int64_t* gidx = nullptr;  // [T] global surface index of each instance point
+    const double* dL_dd = nullptr;  // [n_queries] by query id
+    double* dL_dq = nullptr;        // [n_queries][3]
+    double* dL_dX = nullptr;        // [n_surface][3] accumulated with atomics
+    double* obar = nullptr;         // [n_positions] scratch
+};
+
+struct SolveStats {
+    int64_t bucket_count[5] = {0, 0, 0, 0, 0};
+    double sum_n3 = 0;
+    double sum_n2 = 0;
+    double t_solve_ms = 0;  // filled when profiling
+};
+
+// Process-wide count of kernel launches (each launch site calls this once).
+void note_launch();
+
+// scan.cu / grid kernels
+void exclusive_scan_i64(const int64_t* in, int64_t* out, int64_t n, cudaStream_t st, Arena& ar);
+void fill_i64(int64_t* p, int64_t v, int64_t n, cudaStream_t st);
+void fill_u64(uint64_t* p, uint64_t v, int64_t n, cudaStream_t st);
+void fill_i32(int32_t* p, int32_t v, int64_t n, cudaStream_t st);
+
+// Solve every instance of the batch (factorise, alpha, evaluate its queries).  Returns
+// error bits through *err_dev.  Synchronises once to read the size histogram.
+void solve_batch(const SolveBatch& b, const DevParams& P, int* err_dev, cudaStream_t st,
+                 Arena& ar, SolveStats* stats, const BackwardBatch* bw = nullptr, bool profile = false);
+
+}  // namespace vgp

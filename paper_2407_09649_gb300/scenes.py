@@ -241,11 +241,36 @@ class City:
         self.f_n = np.array([f[3] for f in faces])
         self.f_area = np.linalg.norm(np.cross(self.f_e1, self.f_e2), axis=1)
 
+    def _cell_table(self):
+        # boxes overlapping each 1 m ground cell, padded with -1
+        if getattr(self, "_cells", None) is None:
+            nx, ny = int(np.ceil(self.extent[0])), int(np.ceil(self.extent[1]))
+            lists = [[] for _ in range(nx * ny)]
+            for b, (lo, hi) in enumerate(zip(self.box_lo, self.box_hi)):
+                for ix in range(max(int(np.floor(lo[0])) - 1, 0), min(int(np.floor(hi[0])) + 2, nx)):
+                    for iy in range(max(int(np.floor(lo[1])) - 1, 0), min(int(np.floor(hi[1])) + 2, ny)):
+                        lists[ix * ny + iy].append(b)
+            k = max(1, max(len(x) for x in lists))
+            tab = np.full((nx * ny, k), -1, dtype=np.int64)
+            for c, x in enumerate(lists):
+                tab[c, :len(x)] = x
+            self._cells = (nx, ny, tab)
+        return self._cells
+
     def inside_box(self, P, margin=0.0):
         P = np.asarray(P, dtype=np.float64)
+        nx, ny, tab = self._cell_table()
+        ix = np.clip(np.floor(P[:, 0]).astype(np.int64), 0, nx - 1)
+        iy = np.clip(np.floor(P[:, 1]).astype(np.int64), 0, ny - 1)
+        cand = tab[ix * ny + iy]
         inside = np.zeros(len(P), dtype=bool)
-        for lo, hi in zip(self.box_lo, self.box_hi):
-            inside |= np.all((P > lo + margin) & (P < hi - margin), axis=1)
+        for j in range(cand.shape[1]):
+            b = cand[:, j]
+            has = b >= 0
+            bb = np.where(has, b, 0)
+            lo = self.box_lo[bb] + margin
+            hi = self.box_hi[bb] - margin
+            inside |= has & np.all((P > lo) & (P < hi), axis=1)
         return inside
 
     def _sample_faces(self, rng, n):

@@ -1,0 +1,284 @@
+"""CUDA path vs the FP64 oracle, element by element, through the C ABI.
+
+Tolerances: FP64 path |dd| <= 1e-4 m and gradient angle <= 0.1 deg (the contract), with a
+tighter typical-error check; mixed path |dd| <= 1e-3 m.  Leaf/voxel keys, training sets,
+testing-voxel sets and statuses are compared bit for bit.
+"""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+pytestmark = pytest.mark.gpu
+
+D_TOL = 1e-4
+ANG_TOL_DEG = 0.1
+D_TOL_MIXED = 1e-3
+
+
+@pytest.fixture(scope="module")
+def vg():
+    import paper_2407_09649_gb300 as P
+    P.build()
+    from paper_2407_09649_gb300 import api
+    assert torch.cuda.is_available(), "GPU tests need CUDA"
+    return api
+
+
+def _angle_deg(a, b):
+    na = np.linalg.norm(a, axis=1)
+    nb = np.linalg.norm(b, axis=1)
+    c = np.sum(a * b, 1) / np.maximum(na * nb, 1e-300)
+    return np.degrees(np.arccos(np.clip(c, -1, 1)))
+
+
+def _frame_gpu(vg, pts, **kw):
+    m = vg.Map(**kw)
+    f = m.build_frame(torch.from_numpy(pts).cuda())
+    r = {k: v.cpu().numpy() for k, v in f.results().items()}
+    inst = {k: v.cpu().numpy() for k, v in f.instances().items()}
+    return m, f, r, inst
+
+
+def _sort_by_key(keys, *arrs):
+    o = np.argsort(keys, kind="stable")
+    return (keys[o],) + tuple(a[o] for a in arrs)
+
+
+def _small_scene(seed=0, n=3000):
+    from paper_2407_09649_gb300 import scenes
+    return scenes.sphere_plane_frame(seed, n_sphere=n, n_plane=n)
+
+
+# ----------------------------------------------------------------------------------
+# L-GPDF frame
+# ----------------------------------------------------------------------------------
+@pytest.mark.parametrize("cap", [64, 16])
+def test_frame_indexing_and_training_sets_bitexact(vg, orc, cap):
+    pts = _small_scene(1)
+    P = orc.params(max_pts_leaf=cap)
+    ref = orc.frame(pts, P)
+    m, f, r, inst = _frame_gpu(vg, pts, precision="fp64", max_pts_leaf=cap)
+    lk = inst["leaf_key"]
+    o = np.argsort(lk)
+    assert np.array_equal(lk[o], ref.leaf_key)
+    assert np.array_equal(inst["n_occ"][o], ref.leaf_nocc)
+    off = inst["inst_off"]
+    for gi, ri in zip(o, range(len(ref.leaf_key))):
+        a = inst["X"][off[gi]:off[gi + 1]]
+        b = ref.X[ref.inst_off[ri]:ref.inst_off[ri + 1]]
+        assert np.array_equal(a, b)
+        np.testing.assert_allclose(inst["alpha"][off[gi]:off[gi + 1]], ref.alpha[ref.inst_off[ri]:ref.inst_off[ri + 1]],
+                                   rtol=1e-8, atol=1e-9 * np.abs(ref.alpha).max())
+    k, st = _sort_by_key(r["keys"], r["status"])
+    assert np.array_equal(k, np.sort(ref.test_key))
+    assert np.array_equal(st, ref.status[np.argsort(ref.test_key, kind="stable")])
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_frame_values(vg, orc, precision):
+    pts = _small_scene(2)
+    ref = orc.frame(pts, orc.params())
+    m, f, r, _ = _frame_gpu(vg, pts, precision=precision)
+    k, d, v, g, s = _sort_by_key(r["keys"], r["d"], r["v"], r["grad"], r["status"])
+    ro = np.argsort(ref.test_key, kind="stable")
+    rd, rv, rg, rs = ref.d[ro], ref.v[ro], ref.grad[ro], ref.status[ro]
+    assert np.array_equal(k, ref.test_key[ro])
+    ok = rs == 0
+    if precision == "fp64":
+        assert np.array_equal(s, rs)
+        err = np.abs(d[ok] - rd[ok])
+        assert err.max() <= D_TOL and np.median(err) < 1e-9
+        big = ok & (np.linalg.norm(rg, axis=1) > 0.1)
+        assert _angle_deg(g[big], rg[big]).max() <= ANG_TOL_DEG
+        np.testing.assert_allclose(v[ok], rv[ok], rtol=1e-5, atol=1e-12)
+    else:
+        mid = ok & (rd > 2e-3)
+        assert np.array_equal(s[mid], rs[mid])
+        assert np.abs(d[mid] - rd[mid]).max() <= D_TOL_MIXED
+        big = mid & (np.linalg.norm(rg, axis=1) > 0.5)
+        assert np.percentile(_angle_deg(g[big], rg[big]), 99) <= 1.0
+        np.testing.assert_allclose(v[mid], rv[mid], rtol=1e-4, atol=1e-12)
+
+
+def test_frame_edge_cases(vg):
+    m = vg.Map()
+    f = m.build_frame(torch.zeros((0, 3), device="cuda"))
+    assert f.n_test == 0
+    bad = torch.tensor([[float("nan"), 0, 0], [1e9, 0, 0], [0, float("inf"), 1]], device="cuda")
+    f = m.build_frame(bad)
+    assert f.n_test == 0
+    one = torch.tensor([[0.31, -0.42, 0.05]], device="cuda")
+    f = m.build_frame(one)
+    r = f.results()
+    assert f.n_test == 27 * 512 and int((r["status"] == 0).sum()) == 27 * 512
+
+
+# ----------------------------------------------------------------------------------
+# fusion
+# ----------------------------------------------------------------------------------
+@pytest.mark.parametrize("fusion", ["invvar", "tsdf"])
+def test_fusion_parity(vg, orc, fusion):
+    mode = 0 if fusion == "invvar" else 1
+    P = orc.params(fusion=mode)
+    g_ref = orc.Grid(fusion=mode)
+    m = vg.Map(precision="fp64", fusion=fusion)
+    rng = np.random.default_rng(3)
+    base = _small_scene(4, n=1500)
+    for t in range(3):
+        pts = (base + rng.normal(0, 0.02, base.shape) + np.array([0.05 * t, 0, 0])).astype(np.float32)
+        ref = orc.frame(pts, P)
+        g_ref.fuse_frame(ref)
+        m.fuse(m.build_frame(torch.from_numpy(pts).cuda()))
+    k, D, V, fl = m.export_grid()
+    rk, rD, rV, rfl = g_ref.export()
+    assert np.array_equal(k, rk)
+    assert np.array_equal(fl, rfl)
+    np.testing.assert_allclose(D, rD, rtol=1e-6, atol=D_TOL * 1e-2)
+    np.testing.assert_allclose(V, rV, rtol=1e-5, atol=1e-12)
+    # checkpoint / resume round trip is exact
+    m2 = vg.Map(precision="fp64", fusion=fusion)
+    m2.import_grid(k, D, V, fl)
+    k2, D2, V2, fl2 = m2.export_grid()
+    assert np.array_equal(k2, k) and np.array_equal(D2, D) and np.array_equal(V2, V) and np.array_equal(fl2, fl)
+
+
+# ----------------------------------------------------------------------------------
+# G-GPDF queries
+# ----------------------------------------------------------------------------------
+def _query_scene(seed=5):
+    from paper_2407_09649_gb300 import scenes
+    rng = np.random.default_rng(seed)
+    surf = scenes.sphere_plane_frame(seed, n_sphere=6000, n_plane=6000)
+    # a dense blob so that some neighbourhoods exceed the 1024 cap
+    blob = rng.normal([1.2, -1.5, -1.0], 0.15, (2500, 3)).astype(np.float32)
+    surf = np.vstack([surf, blob]).astype(np.float32)
+    q = scenes.uniform_queries(seed, n=3000, lo=(-4.5, -4.5, -4.5), hi=(4.5, 4.5, 4.5))
+    near = surf[rng.choice(len(surf), 1500)] + rng.normal(0, 0.1, (1500, 3)).astype(np.float32)
+    q = np.vstack([q, near, [[np.nan, 0, 0]], [[40.0, 40.0, 40.0]]]).astype(np.float32)
+    return surf, q
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_query_parity(vg, orc, precision):
+    surf, q = _query_scene()
+    S = orc.Surface(surf, orc.params())
+    ref = S.query(q, want_var=True)
+    assert (ref["inst_n"] == 1024).any()  # the cap selection is exercised
+    m = vg.Map(precision=precision)
+    m.set_surface(torch.from_numpy(surf).cuda())
+    out = m.query(torch.from_numpy(q).cuda(), grad=True, var=True)
+    d, g, v, s = (out[k].cpu().numpy() for k in ("d", "grad", "var", "status"))
+    rd, rg, rv, rs = ref["d"], ref["grad"], ref["var"], ref["status"]
+    ok = rs == 0
+    assert s[-2] == 3 and s[-1] == 1
+    if precision == "fp64":
+        assert np.array_equal(s, rs)
+        err = np.abs(d[ok] - rd[ok])
+        assert err.max() <= D_TOL and np.median(err) < 1e-9
+        big = ok & (np.linalg.norm(rg, axis=1) > 0.1)
+        assert _angle_deg(g[big], rg[big]).max() <= ANG_TOL_DEG
+        fin = ok & np.isfinite(rv)
+        np.testing.assert_allclose(v[fin], rv[fin], rtol=1e-5, atol=1e-12)
+    else:
+        mid = ok & (rd > 2e-3) & (rd < 9.0)
+        assert np.array_equal(s[mid], rs[mid])
+        assert np.abs(d[mid] - rd[mid]).max() <= D_TOL_MIXED
+        big = mid & (np.linalg.norm(rg, axis=1) > 0.5)
+        assert np.percentile(_angle_deg(g[big], rg[big]), 99) <= 1.0
+
+
+def test_query_errors(vg):
+    from paper_2407_09649_gb300 import _lib
+    m = vg.Map()
+    with pytest.raises(_lib.VgpError) as e:
+        m.query(torch.zeros((4, 3), device="cuda"))
+    assert e.value.code == -6
+    with pytest.raises(ValueError):
+        m.set_surface(torch.zeros((4, 2), device="cuda"))
+    with pytest.raises(_lib.VgpError):
+        vg.Map(max_pts_group=2000)
+
+
+# ----------------------------------------------------------------------------------
+# independent instances: every size bucket and the bucket edges
+# ----------------------------------------------------------------------------------
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_gp_batch_parity(vg, orc, precision):
+    from paper_2407_09649_gb300 import scenes
+    inst_off, X, q_off, Q = scenes.patch_sweep(n_inst=40, seed=11, q_per_inst=64)
+    # force sizes on the bucket edges
+    sizes = [1, 2, 31, 32, 33, 64, 65, 128, 129, 224, 225, 256, 257, 700, 1024]
+    rng = np.random.default_rng(12)
+    Xs, Qs = [], []
+    for N in sizes:
+        c = rng.uniform(-20, 20, 3)
+        Xs.append(c + rng.uniform(-0.05, 0.05, (N, 3)) * np.sqrt(N))
+        Qs.append(c + rng.uniform(-1, 1, (50, 3)))
+    X2 = np.vstack([X.astype(np.float64)] + Xs).astype(np.float32)
+    Q2 = np.vstack([Q.astype(np.float64)] + Qs).astype(np.float32)
+    io2 = np.concatenate([inst_off, inst_off[-1] + np.cumsum(sizes)])
+    qo2 = np.concatenate([q_off, q_off[-1] + 50 * np.arange(1, len(sizes) + 1)])
+    ref = orc.gp_batch(io2, X2.astype(np.float64), qo2, Q2.astype(np.float64), orc.params())
+    m = vg.Map(precision=precision)
+    out = m.gp_batch(io2, X2, qo2, Q2, var=True)
+    d, g, v, s = (out[k].cpu().numpy() for k in ("d", "grad", "var", "status"))
+    ok = ref.status == 0
+    if precision == "fp64":
+        assert np.array_equal(s, ref.status)
+        assert np.abs(d[ok] - ref.d[ok]).max() <= D_TOL
+        big = ok & (np.linalg.norm(ref.grad, axis=1) > 0.1)
+        assert _angle_deg(g[big], ref.grad[big]).max() <= ANG_TOL_DEG
+        fin = ok & np.isfinite(ref.var)
+        np.testing.assert_allclose(v[fin], ref.var[fin], rtol=1e-5, atol=1e-12)
+    else:
+        mid = ok & (ref.d > 2e-3) & (ref.d < 9.0)
+        assert np.abs(d[mid] - ref.d[mid]).max() <= D_TOL_MIXED
+
+
+def test_gp_batch_rejects_oversize(vg):
+    from paper_2407_09649_gb300 import _lib
+    m = vg.Map()
+    X = np.zeros((1025, 3), np.float32)
+    with pytest.raises(_lib.VgpError) as e:
+        m.gp_batch([0, 1025], X, [0, 1], np.zeros((1, 3), np.float32))
+    assert e.value.code == -1
+
+
+# ----------------------------------------------------------------------------------
+# backward
+# ----------------------------------------------------------------------------------
+def test_backward_parity(vg, orc):
+    rng = np.random.default_rng(21)
+    g = (np.arange(30) - 14.5) * 0.1
+    surf = np.array([[x, y, 0.1 * np.sin(2 * x) * np.cos(y)] for x in g for y in g])
+    surf = (surf + rng.normal(0, 0.01, surf.shape)).astype(np.float32)
+    q = rng.uniform([-1.2, -1.2, 0.05], [1.2, 1.2, 0.9], (400, 3)).astype(np.float32)
+    w = rng.uniform(0.5, 1.5, len(q))
+    S = orc.Surface(surf, orc.params())
+    rdq, rdX = S.backward(q, w)
+    m = vg.Map(precision="fp64")
+    m.set_surface(torch.from_numpy(surf).cuda())
+    dq, dX = m.query_backward(torch.from_numpy(q).cuda(), torch.from_numpy(w).cuda())
+    dq, dX = dq.cpu().numpy(), dX.cpu().numpy()
+    np.testing.assert_allclose(dq, rdq, rtol=1e-7, atol=1e-9)
+    np.testing.assert_allclose(dX, rdX, rtol=1e-6, atol=1e-8 * np.abs(rdX).max())
+
+
+def test_autograd_function(vg, orc):
+    from paper_2407_09649_gb300.autograd import gpdf_distance
+    rng = np.random.default_rng(22)
+    g = (np.arange(20) - 9.5) * 0.1
+    surf = np.array([[x, y, 0.0] for x in g for y in g]) + rng.normal(0, 0.01, (400, 3))
+    surf = torch.tensor(surf, dtype=torch.float32, device="cuda", requires_grad=True)
+    q = torch.tensor(rng.uniform([-0.7, -0.7, 0.1], [0.7, 0.7, 0.8], (64, 3)), dtype=torch.float32,
+                     device="cuda", requires_grad=True)
+    m = vg.Map(precision="fp64")
+    d = gpdf_distance(q, surf, m)
+    loss = torch.nn.functional.softplus(0.5 - d).sum()
+    loss.backward()
+    w = (-torch.sigmoid(0.5 - d)).detach().double().cpu().numpy()
+    S = orc.Surface(surf.detach().cpu().numpy(), orc.params())
+    rdq, rdX = S.backward(q.detach().cpu().numpy(), w)
+    np.testing.assert_allclose(q.grad.cpu().numpy(), rdq, rtol=1e-4, atol=1e-6)
+    np.testing.assert_allclose(surf.grad.cpu().numpy(), rdX, rtol=1e-4, atol=1e-6)
