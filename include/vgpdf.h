@@ -267,6 +267,12 @@ int vgp_gp_batch(vgp_map* m, int64_t n_inst, const int64_t* inst_off_dev, const 
 /* Counters of the most recent build_frame / set_surface / query / batch call. */
 int vgp_get_stats(const vgp_map* m, vgp_stats* out);
 
+/*
+ * Diagnostic: out_dev[i] = e^(y_dev[i]) computed by the FP64 table-driven exponential that the
+ * mixed path uses for kernel-matrix entries (y <= 0; 0 below -700).  Device arrays of n doubles.
+ */
+int vgp_debug_exp_neg(const vgp_map* m, const double* y_dev, double* out_dev, int64_t n, vgp_stream stream);
+
 /* Number of CUDA kernels this library has launched in the process so far (diagnostic). */
 int64_t vgp_launch_count(void);
 

@@ -53,6 +53,7 @@ SIGNATURES = [
     ("vgp_get_stats", _i32, [_vp, C.POINTER(VgpStats)]),
     ("vgp_sync", _i32, [_vp]),
     ("vgp_launch_count", C.c_int64, []),
+    ("vgp_debug_exp_neg", _i32, [_vp, _vp, _vp, _i64, _vp]),
     ("vgp_last_error", C.c_char_p, []),
 ]
 

@@ -92,6 +92,8 @@ struct vgp_map {
     int device = 0;
     Arena ar;
     int* dev_words = nullptr;  // [0] err, [1] n_valid, [2] count, [3] pool_count, [4] orphan
+    double* tables = nullptr;  // exp_neg table (256) + lattice kernel table (kLatticeTable), FP64
+    float* tables_f = nullptr; // lattice kernel table in FP32
     int* host_words = nullptr; // pinned mirror
     // global grid
     Table g;
@@ -125,6 +127,7 @@ struct vgp_frame {
     double* X = nullptr;
     double* Xl = nullptr;
     float* Xf = nullptr;
+    char4* Xi = nullptr;
     double* centre = nullptr;
     double* alpha = nullptr;
     uint64_t* tkey = nullptr;
@@ -235,6 +238,31 @@ int vgp_create(const vgp_params* p, vgp_map** out) {
         return fail(VGP_ERR_CUDA, "vgp_create: device allocation failed (is a CUDA device present?)");
     }
     cudaMemset(m->dev_words, 0, sizeof(int) * 8);
+    // constant tables, computed on the host in extended precision and rounded once:
+    // 2^(j/256) for the FP64 exponential, exp(-m vs^2 / (2 l^2)) for voxel-lattice distances
+    std::vector<double> tab(256 + kLatticeTable);
+    std::vector<float> tabf(kLatticeTable);
+    for (int j = 0; j < 256; ++j) tab[j] = (double)exp2l((long double)j / 256.0L);
+    const long double vs = p->voxel_size, l = p->lengthscale;
+    for (int m2 = 0; m2 < kLatticeTable; ++m2) {
+        const long double v = expl(-(long double)m2 * vs * vs / (2.0L * l * l));
+        tab[256 + m2] = (double)v;
+        tabf[m2] = (float)v;
+    }
+    if (cudaMalloc(&m->tables, sizeof(double) * tab.size()) != cudaSuccess ||
+        cudaMalloc(&m->tables_f, sizeof(float) * tabf.size()) != cudaSuccess) {
+        cudaGetLastError();
+        cudaFree(m->dev_words);
+        cudaFreeHost(m->host_words);
+        cudaFree(m->tables);
+        delete m;
+        return fail(VGP_ERR_OOM, "vgp_create: table allocation failed");
+    }
+    cudaMemcpy(m->tables, tab.data(), sizeof(double) * tab.size(), cudaMemcpyHostToDevice);
+    cudaMemcpy(m->tables_f, tabf.data(), sizeof(float) * tabf.size(), cudaMemcpyHostToDevice);
+    m->P.exp_tab = m->tables;
+    m->P.lat_tab = m->tables + 256;
+    m->P.lat_tab_f = m->tables_f;
     *out = m;
     return VGP_OK;
 }
@@ -244,6 +272,8 @@ int vgp_destroy(vgp_map* m) {
     cudaDeviceSynchronize();
     cudaFree(m->dev_words);
     cudaFreeHost(m->host_words);
+    cudaFree(m->tables);
+    cudaFree(m->tables_f);
     cudaFree(m->g.keys);
     cudaFree(m->g_slot2pool);
     cudaFree(m->g_known);
@@ -323,10 +353,11 @@ int vgp_build_frame(vgp_map* m, const float* pts, int64_t n, vgp_stream stream, 
     f->X = f->alloc<double>(3 * T, st);
     f->Xl = f->alloc<double>(3 * T, st);
     f->Xf = f->alloc<float>(3 * T, st);
+    f->Xi = f->alloc<char4>(T, st);
     f->alpha = f->alloc<double>(T, st);
     f->centre = f->alloc<double>(3 * (int64_t)nl, st);
-    if (!f->X || !f->Xl || !f->Xf || !f->alpha || !f->centre) return bail(VGP_ERR_OOM, "allocation failed");
-    frame_leaf_points(flist, flkeys, nl, fmasks, f->nocc, f->inst_off, P, f->X, f->Xl, f->Xf, f->centre, st);
+    if (!f->X || !f->Xl || !f->Xf || !f->Xi || !f->alpha || !f->centre) return bail(VGP_ERR_OOM, "allocation failed");
+    frame_leaf_points(flist, flkeys, nl, fmasks, f->nocc, f->inst_off, P, f->X, f->Xl, f->Xf, f->Xi, f->centre, st);
     // 3. testing leaves: occupied leaves and their 26 neighbours
     Table tt;
     uint32_t Ct = pow2_at_least(2 * 27 * (int64_t)std::max(nl, 1));
@@ -369,6 +400,8 @@ int vgp_build_frame(vgp_map* m, const float* pts, int64_t n, vgp_stream stream, 
     b.inst_off = f->inst_off;
     b.Xl = f->Xl;
     b.Xf = f->Xf;
+    b.Xi = f->Xi;
+    b.inst_key = f->leaf_key;
     b.centre = f->centre;
     b.q_off = q_off;
     b.qkey = f->tkey;
@@ -868,6 +901,22 @@ __global__ void k_batch_prep(const int64_t* inst_off, int64_t n_inst, const floa
         }
 }
 }  // namespace
+
+namespace {
+__global__ void k_exp_probe(const double* y, double* out, int64_t n, const double* tab) {
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i < n) out[i] = exp_neg(y[i], tab);
+}
+}  // namespace
+
+extern "C" int vgp_debug_exp_neg(const vgp_map* m, const double* y, double* out, int64_t n, vgp_stream stream) {
+    if (!m || n < 0 || (n > 0 && (!y || !out))) return fail(VGP_ERR_ARG, "vgp_debug_exp_neg: bad argument");
+    if (n == 0) return VGP_OK;
+    k_exp_probe<<<(unsigned)((n + 255) / 256), 256, 0, (cudaStream_t)stream>>>(y, out, n, m->P.exp_tab);
+    note_launch();
+    CUDA_TRY(cudaGetLastError());
+    return VGP_OK;
+}
 
 extern "C" int vgp_gp_batch(vgp_map* m, int64_t n_inst, const int64_t* inst_off, const float* X, const int64_t* q_off,
                             const float* Q, double* d, double* grad, double* var, uint8_t* status, vgp_stream stream) {

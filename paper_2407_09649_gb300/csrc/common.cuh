@@ -33,9 +33,34 @@ struct DevParams {
     double log_floor;   // -d_max^2 / (2 l^2)
     double d_var_floor;
     float inv2l2_log2e; // log2(e) / (2 l^2), for exp2f of the FP32 path
-    float pad0;
+    float vs_f;         // voxel size in FP32
     int cap_leaf, cap_group, search_r, fusion, precision, pad1;
+    const double* exp_tab;   // 2^(j/256), j = 0..255 (FP64), for exp_neg
+    const double* lat_tab;   // exp(-m vs^2 / (2 l^2)), m = 0..kLatticeTable-1 (FP64)
+    const float* lat_tab_f;  // the same in FP32
 };
+
+constexpr int kLatticeTable = 1024;  // squared integer offsets up to 3 * 15^2 = 675 occur
+
+// e^y for y <= 0 in FP64, table-driven (Tang, "Table-driven implementation of the exponential
+// function in IEEE floating-point arithmetic", 1989): y = (256 m + j) ln2/256 + r with
+// |r| <= ln2/512, e^y = 2^m * 2^(j/256) * e^r, e^r by its degree-4 Taylor polynomial
+// (remainder below 4e-17 relative).  tab[j] = 2^(j/256).  Returns 0 for y < -700.
+__device__ __forceinline__ double exp_neg(double y, const double* tab) {
+    if (!(y >= -700.0)) return 0.0;
+    const double big = 6755399441055744.0;  // 1.5 * 2^52: y * 256/ln2 rounded to an integer
+    const double tm = fma(y, 369.3299304675746, big);
+    const int ni = __double2loint(tm);
+    const double n = tm - big;
+    double r = fma(-n, 0x1.62e42fef80000p-9, y);  // ln2/256, high 35 bits (n * hi is exact)
+    r = fma(-n, 0x1.1cf79abc9e3b4p-44, r);        // ln2/256, the rest
+    double p = fma(r, 1.0 / 24.0, 1.0 / 6.0);
+    p = fma(p, r, 0.5);
+    p = fma(p, r, 1.0);
+    p = fma(p, r, 1.0);
+    const double s = tab[ni & 255] * p;
+    return __longlong_as_double(__double_as_longlong(s) + ((long long)(ni >> 8) << 52));
+}
 
 __host__ __device__ inline uint64_t pack_key(int64_t x, int64_t y, int64_t z) {
     return ((uint64_t)(x + kKeyBias) << 42) | ((uint64_t)(y + kKeyBias) << 21) |

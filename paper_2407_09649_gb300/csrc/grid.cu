@@ -193,7 +193,7 @@ __global__ void k_leaf_counts(const int32_t* list, int nl, const unsigned long l
 // One warp per leaf: training voxel centres in bit order with the stride cap.
 __global__ void k_leaf_points(const int32_t* list, const uint64_t* lkeys, int nl, const unsigned long long* masks,
                               const int32_t* nocc, const int64_t* inst_off, DevParams P, double* X, double* Xl,
-                              float* Xf, double* centre) {
+                              float* Xf, char4* Xi, double* centre) {
     int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
     if (warp >= nl) return;
     int s = list[warp];
@@ -223,6 +223,7 @@ __global__ void k_leaf_points(const int32_t* list, const uint64_t* lkeys, int nl
         int b = r < clo ? (int)__fns(lo, 0, r + 1) : 32 + (int)__fns(hi, 0, r - clo + 1);
         int bit = w * 64 + b;
         int ijk[3] = {8 * lx + (bit & 7), 8 * ly + ((bit >> 3) & 7), 8 * lz + (bit >> 6)};
+        Xi[b0 + k] = make_char4((char)(bit & 7), (char)((bit >> 3) & 7), (char)(bit >> 6), 0);
         for (int a = 0; a < 3; ++a) {
             double g = __dmul_rn((double)ijk[a], P.vs);
             double loc = __dsub_rn(g, c[a]);
@@ -331,9 +332,9 @@ void frame_leaf_counts(const int32_t* list, int nl, const unsigned long long* ma
 
 void frame_leaf_points(const int32_t* list, const uint64_t* lkeys, int nl, const unsigned long long* masks,
                        const int32_t* nocc, const int64_t* inst_off, const DevParams& P, double* X, double* Xl,
-                       float* Xf, double* centre, cudaStream_t st) {
+                       float* Xf, char4* Xi, double* centre, cudaStream_t st) {
     if (nl > 0) {
-        k_leaf_points<<<nblk((int64_t)nl * 32), TB, 0, st>>>(list, lkeys, nl, masks, nocc, inst_off, P, X, Xl, Xf, centre);
+        k_leaf_points<<<nblk((int64_t)nl * 32), TB, 0, st>>>(list, lkeys, nl, masks, nocc, inst_off, P, X, Xl, Xf, Xi, centre);
         note_launch();
     }
 }

@@ -21,7 +21,7 @@ void frame_leaf_counts(const int32_t* list, int nl, const unsigned long long* ma
                        int64_t* ninst, cudaStream_t st);
 void frame_leaf_points(const int32_t* list, const uint64_t* lkeys, int nl, const unsigned long long* masks,
                        const int32_t* nocc, const int64_t* inst_off, const DevParams& P, double* X, double* Xl,
-                       float* Xf, double* centre, cudaStream_t st);
+                       float* Xf, char4* Xi, double* centre, cudaStream_t st);
 void frame_dilate(const uint64_t* lkeys, int nl, const Table& t, int* err, cudaStream_t st);
 void frame_assign_tests(const uint64_t* tl_keys, int ntl, const Table& ft, const int32_t* slot2leaf,
                         int64_t* inst_cnt, int* n_orphan, cudaStream_t st);

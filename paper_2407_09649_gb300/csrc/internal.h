@@ -36,6 +36,8 @@ struct SolveBatch {
     const double* Xl = nullptr;         // [T][3] FP64 coordinates relative to the centre
     const float* Xf = nullptr;          // [T][3] FP32 copy of Xl
     const double* centre = nullptr;     // [n_inst][3] FP64 world-frame centre
+    const char4* Xi = nullptr;          // lattice instances: in-leaf voxel offsets (0..7) per point
+    const uint64_t* inst_key = nullptr; // lattice instances: leaf key of each instance
     const int64_t* q_off = nullptr;     // [n_inst + 1] offsets into the position list
     const int64_t* qidx = nullptr;      // position -> query id (nullptr: identity)
     const float* qxyz = nullptr;        // world-frame query points (by query id)

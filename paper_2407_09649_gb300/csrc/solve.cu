@@ -2,10 +2,13 @@
 // evaluation of every query of the instance (latent mean Eq. 1, variance Eq. 2, gradient
 // Eq. 5, reverting Eq. 3 and distance variance Eq. 4), plus the backward pass.
 //
-// One CTA owns one instance at a time and pulls instances from a list sorted by
-// decreasing size (a persistent launch per size bucket, longest-first).  The packed lower
-// triangle of A = K + sigma^2 I lives in shared memory when it fits, else in a per-CTA
-// global workspace.
+// One CTA owns one instance at a time and pulls instances from a list sorted by decreasing
+// size (a persistent launch per size bucket, longest first).  A = K + sigma^2 I is stored as
+// the lower triangle of 8x8 tiles (64 contiguous doubles per tile, tiles in packed row
+// order), in shared memory when it fits, else in a per-CTA global workspace.  The Cholesky
+// factorisation is right-looking by 8-column panels; the panel solve and the trailing
+// update run on the FP64 tensor path (mma.sync m8n8k4 f64), the 8x8 diagonal blocks on the
+// FP64 pipe.
 #include <algorithm>
 #include <cstdio>
 #include <vector>
@@ -16,7 +19,25 @@ namespace vgp {
 
 namespace {
 
-__host__ __device__ __forceinline__ int64_t pk(int i, int j) { return (int64_t)i * (i + 1) / 2 + j; }
+// offset of tile (it, jt), jt <= it, in the tile-packed lower triangle
+__host__ __device__ __forceinline__ int64_t tix(int it, int jt) { return ((int64_t)it * (it + 1) / 2 + jt) * 64; }
+__host__ __device__ __forceinline__ int64_t n_tiles(int nt) { return (int64_t)nt * (nt + 1) / 2; }
+
+// row index of packed-triangle entry p (0 <= col <= row)
+__device__ __forceinline__ int tri_row(int p) {
+    int r = (int)((sqrtf(8.0f * (float)p + 1.0f) - 1.0f) * 0.5f);
+    while ((r + 1) * (r + 2) / 2 <= p) ++r;
+    while (r * (r + 1) / 2 > p) --r;
+    return r;
+}
+
+// D(8x8) += A(8x4) B(4x8) on the FP64 tensor path.  Fragments: a = A[g][t],
+// b = B[t][g], c = D[g][2t .. 2t+1] with g = lane / 4, t = lane % 4.
+__device__ __forceinline__ void dmma(double& c0, double& c1, double a, double b) {
+    asm volatile("mma.sync.aligned.m8n8k4.row.col.f64.f64.f64.f64 {%0,%1}, {%2}, {%3}, {%0,%1};\n"
+                 : "+d"(c0), "+d"(c1)
+                 : "d"(a), "d"(b));
+}
 
 struct SolveCtx {
     SolveBatch b;
@@ -25,122 +46,233 @@ struct SolveCtx {
     int* counter;
     const int32_t* order;  // instance ids, decreasing N
     int n_work;
-    int nmax;              // largest N in this launch
+    int npad;              // largest N in this launch, rounded up to 8
     int a_in_smem;
-    double* ws_a;          // per-CTA packed A when not in shared memory
+    double* ws_a;          // per-CTA tile-packed A when not in shared memory
     int64_t ws_a_stride;
-    double* ws_v;          // per-CTA variance columns [nmax][blockDim]
+    double* ws_v;          // per-CTA variance columns [npad][blockDim]
     int64_t ws_v_stride;
     BackwardBatch bw;
-    int backward;
 };
 
 struct Shared {
     double* X;      // [N][3] local FP64
-    double* alpha;  // [N]
-    double* invd;   // [N] 1 / L_ii
-    double* y;      // [N] scratch
-    double* z;      // [N] scratch
-    double* A;      // packed lower triangle
+    double* alpha;  // [npad]
+    double* invd;   // [npad] 1 / L_ii
+    double* z;      // [npad] scratch
+    double* w;      // [npad] scratch
+    double* Tinv;   // [64] inverse of the current diagonal tile
+    double* T256;   // [256] 2^(j/256) for exp_neg
+    double* A;      // tile-packed lower triangle
     float* Xf;      // [N][3]
-    float* alf;     // [N]
+    float* alf;     // [npad] alpha rounded to FP32
+    float* alf_lo;  // [npad] alpha - alf, rounded to FP32
+    int* xi;        // [npad] lattice offsets x | y << 8 | z << 16 (lattice instances)
 };
 
-__device__ Shared carve(double* sm, int nmax, int a_in_smem, double* ws_a) {
+__device__ Shared carve(double* sm, int npad, int a_in_smem, double* ws_a) {
     Shared s;
     s.X = sm;
-    s.alpha = s.X + 3 * nmax;
-    s.invd = s.alpha + nmax;
-    s.y = s.invd + nmax;
-    s.z = s.y + nmax;
-    double* end = s.z + nmax;
+    s.alpha = s.X + 3 * npad;
+    s.invd = s.alpha + npad;
+    s.z = s.invd + npad;
+    s.w = s.z + npad;
+    s.Tinv = s.w + npad;
+    s.T256 = s.Tinv + 64;
+    double* end = s.T256 + 256;
     if (a_in_smem) {
         s.A = end;
-        end += pk(nmax, 0);
+        end += n_tiles(npad / 8) * 64;
     } else {
         s.A = ws_a;
     }
     s.Xf = reinterpret_cast<float*>(end);
-    s.alf = s.Xf + 3 * nmax;
+    s.alf = s.Xf + 3 * npad;
+    s.alf_lo = s.alf + npad;
+    s.xi = reinterpret_cast<int*>(s.alf_lo + npad);
     return s;
 }
 
-__host__ size_t smem_bytes(int nmax, int a_in_smem) {
-    size_t d = (size_t)7 * nmax + (a_in_smem ? (size_t)pk(nmax, 0) : 0);
-    return d * sizeof(double) + (size_t)4 * nmax * sizeof(float);
+__host__ size_t smem_bytes(int npad, int a_in_smem) {
+    size_t d = (size_t)7 * npad + 64 + 256 + (a_in_smem ? (size_t)n_tiles(npad / 8) * 64 : 0);
+    return d * sizeof(double) + (size_t)5 * npad * sizeof(float) + (size_t)npad * sizeof(int);
+}
+
+__device__ __forceinline__ int lat_m(int a, int b) {
+    const int dx = (a & 255) - (b & 255), dy = ((a >> 8) & 255) - ((b >> 8) & 255), dz = ((a >> 16) & 255) - ((b >> 16) & 255);
+    return dx * dx + dy * dy + dz * dz;
+}
+
+// SE kernel value of a pair of training points (Sec. III-A), FP64: from the exact lattice
+// table for voxel-centre instances, else exp_neg (mixed) or the library exp (plain).
+__device__ __forceinline__ double kval_pair(const DevParams& P, const Shared& s, bool lattice, int i, int j) {
+    if (lattice) return P.lat_tab[lat_m(s.xi[i], s.xi[j])];
+    double dx = s.X[3 * i] - s.X[3 * j], dy = s.X[3 * i + 1] - s.X[3 * j + 1], dz = s.X[3 * i + 2] - s.X[3 * j + 2];
+    const double y = -(dx * dx + dy * dy + dz * dz) * P.inv2l2;
+    return P.precision == VGP_MIXED ? exp_neg(y, s.T256) : exp(y);
+}
+
+// Solve (L L^T) x = rhs in place on s.z (x written to out), L tile-packed; rows >= N of rhs
+// must be zero.  Right-looking by 8-row blocks on each side.
+__device__ void chol_solve(const Shared& s, const double* A, int Nt, double* out) {
+    const int tid = threadIdx.x, nt = blockDim.x;
+    const int Np = Nt * 8;
+    double* z = s.z;
+    for (int kt = 0; kt < Nt; ++kt) {
+        if (tid == 0) {
+            const double* D = A + tix(kt, kt);
+            for (int r = 0; r < 8; ++r) {
+                double v = z[8 * kt + r];
+                for (int c2 = 0; c2 < r; ++c2) v -= D[r * 8 + c2] * z[8 * kt + c2];
+                z[8 * kt + r] = v * s.invd[8 * kt + r];
+            }
+        }
+        __syncthreads();
+        for (int i = 8 * (kt + 1) + tid; i < Np; i += nt) {
+            const double* T = A + tix(i >> 3, kt) + (i & 7) * 8;
+            double v = z[i];
+#pragma unroll
+            for (int c2 = 0; c2 < 8; ++c2) v -= T[c2] * z[8 * kt + c2];
+            z[i] = v;
+        }
+        __syncthreads();
+    }
+    for (int kt = Nt - 1; kt >= 0; --kt) {
+        if (tid == 0) {
+            const double* D = A + tix(kt, kt);
+            for (int r = 7; r >= 0; --r) {
+                double v = z[8 * kt + r];
+                for (int c2 = r + 1; c2 < 8; ++c2) v -= D[c2 * 8 + r] * out[8 * kt + c2];
+                out[8 * kt + r] = v * s.invd[8 * kt + r];
+            }
+        }
+        __syncthreads();
+        for (int j = tid; j < 8 * kt; j += nt) {
+            const double* T = A + tix(kt, j >> 3) + (j & 7);
+            double v = z[j];
+#pragma unroll
+            for (int c2 = 0; c2 < 8; ++c2) v -= T[c2 * 8] * out[8 * kt + c2];
+            z[j] = v;
+        }
+        __syncthreads();
+    }
 }
 
 // Assemble A, factorise, solve alpha.  Returns false if a pivot was not positive.
-__device__ bool fit_instance(const SolveCtx& c, const Shared& s, int I, int N, int64_t base) {
+__device__ bool fit_instance(const SolveCtx& c, const Shared& s, int N, int64_t base) {
     const int tid = threadIdx.x, nt = blockDim.x;
+    const int lane = tid & 31, warp = tid >> 5, nwarps = nt >> 5;
+    const int g = lane >> 2, t = lane & 3;
     __shared__ int s_fail;
-    for (int t = tid; t < 3 * N; t += nt) {
-        double v = c.b.Xl[3 * base + t];
-        s.X[t] = v;
-        s.Xf[t] = (float)v;
+    const int Np = (N + 7) & ~7, Nt = Np >> 3;
+    const bool lattice = c.b.Xi != nullptr;
+    for (int e = tid; e < 3 * N; e += nt) {
+        double v = c.b.Xl[3 * base + e];
+        s.X[e] = v;
+        s.Xf[e] = (float)v;
     }
+    if (lattice)
+        for (int e = tid; e < N; e += nt) {
+            const char4 q = c.b.Xi[base + e];
+            s.xi[e] = ((int)q.x + 16) | (((int)q.y + 16) << 8) | (((int)q.z + 16) << 16);
+        }
     if (tid == 0) s_fail = 0;
     __syncthreads();
     double* A = s.A;
-    // K + sigma^2 I, lower triangle (Sec. III-A kernel, Eq. 1 noise term)
-    const int TX = 16, TY = nt / 16;
-    const int tx = tid % TX, ty = tid / TX;
-    for (int i = ty; i < N; i += TY) {
-        const double xi = s.X[3 * i], yi = s.X[3 * i + 1], zi = s.X[3 * i + 2];
-        for (int j = tx; j <= i; j += TX) {
+    // A = K + sigma^2 I in 8x8 tiles (Sec. III-A kernel, Eq. 1 noise term); padding rows and
+    // columns are the identity so the padded factor is block-diagonal.
+    const int64_t ntl = n_tiles(Nt);
+    for (int64_t tl = warp; tl < ntl; tl += nwarps) {
+        const int it = tri_row((int)tl), jt = (int)tl - it * (it + 1) / 2;
+        for (int e = lane; e < 64; e += 32) {
+            const int i = 8 * it + (e >> 3), j = 8 * jt + (e & 7);
             double v;
-            if (j == i) {
-                v = 1.0 + c.P.s2;
-            } else {
-                double dx = xi - s.X[3 * j], dy = yi - s.X[3 * j + 1], dz = zi - s.X[3 * j + 2];
-                double r2 = dx * dx + dy * dy + dz * dz;
-                v = exp(-r2 * c.P.inv2l2);
-            }
-            A[pk(i, j)] = v;
+            if (i >= N || j >= N) v = (i == j) ? 1.0 : 0.0;
+            else if (j > i) v = 0.0;
+            else if (j == i) v = 1.0 + c.P.s2;
+            else v = kval_pair(c.P, s, lattice, i, j);
+            A[tl * 64 + e] = v;
         }
     }
     __syncthreads();
-    // right-looking Cholesky, column by column
-    for (int k = 0; k < N; ++k) {
+    for (int kt = 0; kt < Nt; ++kt) {
+        // diagonal tile: 8x8 Cholesky and the inverse of its factor (FP64 pipe)
         if (tid == 0) {
-            double a = A[pk(k, k)];
-            if (!(a > 0.0)) {
+            double* D = A + tix(kt, kt);
+            double* W = s.Tinv;
+            bool bad = false;
+            for (int j = 0; j < 8 && !bad; ++j) {
+                double v = D[j * 8 + j];
+                for (int k = 0; k < j; ++k) v -= D[j * 8 + k] * D[j * 8 + k];
+                if (!(v > 0.0)) {
+                    bad = true;
+                    break;
+                }
+                const double d = sqrt(v), inv = 1.0 / d;
+                D[j * 8 + j] = d;
+                s.invd[8 * kt + j] = inv;
+                for (int i = j + 1; i < 8; ++i) {
+                    double u = D[i * 8 + j];
+                    for (int k = 0; k < j; ++k) u -= D[i * 8 + k] * D[j * 8 + k];
+                    D[i * 8 + j] = u * inv;
+                }
+            }
+            if (bad) {
                 s_fail = 1;
             } else {
-                double r = sqrt(a);
-                A[pk(k, k)] = r;
-                s.invd[k] = 1.0 / r;
+                for (int j = 0; j < 8; ++j) {
+                    for (int i = 0; i < j; ++i) W[i * 8 + j] = 0.0;
+                    W[j * 8 + j] = s.invd[8 * kt + j];
+                    for (int i = j + 1; i < 8; ++i) {
+                        double u = 0.0;
+                        for (int k = j; k < i; ++k) u += D[i * 8 + k] * W[k * 8 + j];
+                        W[i * 8 + j] = -u * s.invd[8 * kt + i];
+                    }
+                }
             }
         }
         __syncthreads();
         if (s_fail) break;
-        const double ik = s.invd[k];
-        for (int i = k + 1 + tid; i < N; i += nt) A[pk(i, k)] *= ik;
+        // panel: L_it,kt = A_it,kt * Tinv^T
+        for (int it = kt + 1 + warp; it < Nt; it += nwarps) {
+            double* T = A + tix(it, kt);
+            const double a0 = T[g * 8 + t], a1 = T[g * 8 + 4 + t];
+            const double b0 = s.Tinv[g * 8 + t], b1 = s.Tinv[g * 8 + 4 + t];
+            double c0 = 0.0, c1 = 0.0;
+            dmma(c0, c1, a0, b0);
+            dmma(c0, c1, a1, b1);
+            __syncwarp();
+            T[g * 8 + 2 * t] = c0;
+            T[g * 8 + 2 * t + 1] = c1;
+        }
         __syncthreads();
-        for (int i = k + 1 + ty; i < N; i += TY) {
-            const double lik = A[pk(i, k)];
-            for (int j = k + 1 + tx; j <= i; j += TX) A[pk(i, j)] -= lik * A[pk(j, k)];
+        // trailing update: A_it,jt -= L_it,kt L_jt,kt^T for kt < jt <= it
+        const int M = Nt - kt - 1;
+        const int P = M * (M + 1) / 2;
+        for (int p = warp; p < P; p += nwarps) {
+            const int ii = tri_row(p), jj = p - ii * (ii + 1) / 2;
+            const int it = kt + 1 + ii, jt = kt + 1 + jj;
+            const double* Li = A + tix(it, kt);
+            const double* Lj = A + tix(jt, kt);
+            double* C = A + tix(it, jt);
+            double c0 = C[g * 8 + 2 * t], c1 = C[g * 8 + 2 * t + 1];
+            dmma(c0, c1, -Li[g * 8 + t], Lj[g * 8 + t]);
+            dmma(c0, c1, -Li[g * 8 + 4 + t], Lj[g * 8 + 4 + t]);
+            C[g * 8 + 2 * t] = c0;
+            C[g * 8 + 2 * t + 1] = c1;
         }
         __syncthreads();
     }
     if (s_fail) return false;
-    // alpha = L^-T L^-1 1 (Eq. 1)
-    for (int i = tid; i < N; i += nt) s.z[i] = 1.0;
+    // alpha = A^-1 1 (Eq. 1)
+    for (int i = tid; i < Np; i += nt) s.z[i] = i < N ? 1.0 : 0.0;
     __syncthreads();
-    for (int j = 0; j < N; ++j) {
-        const double yj = s.z[j] * s.invd[j];
-        for (int i = j + 1 + tid; i < N; i += nt) s.z[i] -= A[pk(i, j)] * yj;
-        if (tid == 0) s.y[j] = yj;
-        __syncthreads();
+    chol_solve(s, A, Nt, s.alpha);
+    for (int j = tid; j < Np; j += nt) {
+        const float hi = (float)s.alpha[j];
+        s.alf[j] = hi;
+        s.alf_lo[j] = (float)(s.alpha[j] - (double)hi);
     }
-    for (int j = N - 1; j >= 0; --j) {
-        const double aj = s.y[j] * s.invd[j];
-        for (int i = tid; i < j; i += nt) s.y[i] -= A[pk(j, i)] * aj;
-        __syncthreads();
-        if (tid == 0) s.alpha[j] = aj;
-        __syncthreads();
-    }
-    for (int j = tid; j < N; j += nt) s.alf[j] = (float)s.alpha[j];
     __syncthreads();
     return true;
 }
@@ -152,8 +284,8 @@ struct EvalOut {
 
 // Reverting (Eq. 3), distance variance (Eq. 4), chain-rule gradient, with the caps of the
 // occupancy: lo = log o, gro = grad o / o.
-__device__ __forceinline__ void revert(const DevParams& P, double lo, const double gro[3], double u,
-                                       bool want_var, EvalOut& r) {
+__device__ __forceinline__ void revert(const DevParams& P, double lo, const double gro[3], double u, bool want_var,
+                                       EvalOut& r) {
     if (!(lo >= P.log_floor)) {  // also catches NaN (o <= 0)
         r.status = VGP_ST_CLAMPED;
         r.d = P.d_max;
@@ -192,11 +324,18 @@ __device__ __forceinline__ void write_out(const SolveBatch& b, int64_t qid, cons
     if (b.status) b.status[qid] = (uint8_t)r.status;
 }
 
-__device__ __forceinline__ void query_local(const SolveCtx& c, int I, int64_t p, int64_t qid, double xl[3]) {
+__device__ __forceinline__ void query_local(const SolveCtx& c, int I, int64_t p, int64_t qid, double xl[3],
+                                            int* qi = nullptr) {
     double xg[3];
     if (c.b.qkey) {
         int i, j, k;
         unpack_key(c.b.qkey[p], i, j, k);
+        if (qi && c.b.inst_key) {
+            int lx, ly, lz;
+            unpack_key(c.b.inst_key[I], lx, ly, lz);
+            // offsets relative to the instance leaf origin, biased by 16 into 0..255
+            *qi = (i - 8 * lx + 16) | ((j - 8 * ly + 16) << 8) | ((k - 8 * lz + 16) << 16);
+        }
         xg[0] = (double)i * c.P.vs;
         xg[1] = (double)j * c.P.vs;
         xg[2] = (double)k * c.P.vs;
@@ -209,33 +348,51 @@ __device__ __forceinline__ void query_local(const SolveCtx& c, int I, int64_t p,
 }
 
 // Latent mean and gradient at one query; returns lo = log o and gro = grad o / o.
-__device__ __forceinline__ void latent_mean(const SolveCtx& c, const Shared& s, int N, const double xl[3],
-                                            double& lo, double gro[3]) {
-    if (c.P.precision == VGP_MIXED) {
-        // FP32 with the nearest training point as the shift: exp(-(r^2 - r0^2) / 2l^2) <= 1
+// qi: biased lattice offsets of the query (lattice instances only).
+__device__ __forceinline__ void latent_mean(const DevParams& P, const Shared& s, int N, bool lattice, int qi,
+                                            const double xl[3], double& lo, double gro[3]) {
+    if (P.precision == VGP_MIXED) {
+        // FP32 kernel values and FP32 accumulation.  Off the lattice, the nearest training point
+        // shifts the exponent (exp(-(r^2 - r0^2) / 2l^2) <= 1, no underflow).  The sum is
+        // compensated: alpha is carried as two floats and the rounding error of every product
+        // and addition is accumulated separately (Neumaier), all on the FP32 pipe.
         const float qx = (float)xl[0], qy = (float)xl[1], qz = (float)xl[2];
-        float r0 = INFINITY;
-        for (int j = 0; j < N; ++j) {
-            float dx = s.Xf[3 * j] - qx, dy = s.Xf[3 * j + 1] - qy, dz = s.Xf[3 * j + 2] - qz;
-            r0 = fminf(r0, fmaf(dx, dx, fmaf(dy, dy, dz * dz)));
+        float r0 = 0.f;
+        if (!lattice) {
+            r0 = INFINITY;
+            for (int j = 0; j < N; ++j) {
+                float dx = s.Xf[3 * j] - qx, dy = s.Xf[3 * j + 1] - qy, dz = s.Xf[3 * j + 2] - qz;
+                r0 = fminf(r0, fmaf(dx, dx, fmaf(dy, dy, dz * dz)));
+            }
         }
-        float sum = 0.f, gx = 0.f, gy = 0.f, gz = 0.f;
+        float sum = 0.f, comp = 0.f, gx = 0.f, gy = 0.f, gz = 0.f;
         for (int j = 0; j < N; ++j) {
             float dx = s.Xf[3 * j] - qx, dy = s.Xf[3 * j + 1] - qy, dz = s.Xf[3 * j + 2] - qz;
-            float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-            float w = s.alf[j] * exp2f((r0 - r2) * c.P.inv2l2_log2e);
-            sum += w;
+            float e;
+            if (lattice) {
+                e = P.lat_tab_f[lat_m(s.xi[j], qi)];
+            } else {
+                float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+                e = exp2f((r0 - r2) * P.inv2l2_log2e);
+            }
+            const float ah = s.alf[j];
+            const float w = ah * e;
+            comp += fmaf(ah, e, -w) + s.alf_lo[j] * e;
+            const float t2 = sum + w;
+            comp += fabsf(sum) >= fabsf(w) ? (sum - t2) + w : (w - t2) + sum;
+            sum = t2;
             gx = fmaf(w, dx, gx);
             gy = fmaf(w, dy, gy);
             gz = fmaf(w, dz, gz);
         }
-        if (!(sum > 0.f)) {
+        const double tot = (double)sum + (double)comp;
+        if (!(tot > 0.0)) {
             lo = NAN;
             gro[0] = gro[1] = gro[2] = 0.0;
             return;
         }
-        lo = -(double)r0 * c.P.inv2l2 + log((double)sum);
-        const double inv = 1.0 / ((double)sum * c.P.l2);
+        lo = -(double)r0 * P.inv2l2 + log(tot);
+        const double inv = 1.0 / (tot * P.l2);
         gro[0] = (double)gx * inv;
         gro[1] = (double)gy * inv;
         gro[2] = (double)gz * inv;
@@ -243,8 +400,10 @@ __device__ __forceinline__ void latent_mean(const SolveCtx& c, const Shared& s, 
         double o = 0.0, gx = 0.0, gy = 0.0, gz = 0.0;
         for (int j = 0; j < N; ++j) {
             double dx = s.X[3 * j] - xl[0], dy = s.X[3 * j + 1] - xl[1], dz = s.X[3 * j + 2] - xl[2];
-            double r2 = dx * dx + dy * dy + dz * dz;
-            double w = s.alpha[j] * exp(-r2 * c.P.inv2l2);
+            double k;
+            if (lattice) k = P.lat_tab[lat_m(s.xi[j], qi)];
+            else k = exp(-(dx * dx + dy * dy + dz * dz) * P.inv2l2);
+            const double w = s.alpha[j] * k;
             o += w;
             gx += w * dx;
             gy += w * dy;
@@ -256,22 +415,36 @@ __device__ __forceinline__ void latent_mean(const SolveCtx& c, const Shared& s, 
             return;
         }
         lo = log(o);
-        const double inv = 1.0 / (o * c.P.l2);
+        const double inv = 1.0 / (o * P.l2);
         gro[0] = gx * inv;
         gro[1] = gy * inv;
         gro[2] = gz * inv;
     }
 }
 
-// u = 1 - |L^-1 k|^2 (Eq. 2), the thread's own column of V in global workspace.
-__device__ __forceinline__ double latent_var(const SolveCtx& c, const Shared& s, int N, const double xl[3],
-                                             double* V, int stride) {
+// u = 1 - |L^-1 k|^2 (Eq. 2) with FP64 kernel values; the thread's own column of V lives in
+// global workspace.
+__device__ __forceinline__ double latent_var(const DevParams& P, const Shared& s, int N, bool lattice, int qi,
+                                             const double xl[3], double* V, int stride) {
+    const double* A = s.A;
     double acc = 0.0;
     for (int i = 0; i < N; ++i) {
-        double dx = s.X[3 * i] - xl[0], dy = s.X[3 * i + 1] - xl[1], dz = s.X[3 * i + 2] - xl[2];
-        double sum = exp(-(dx * dx + dy * dy + dz * dz) * c.P.inv2l2);
-        const double* Li = s.A + pk(i, 0);
-        for (int j = 0; j < i; ++j) sum -= Li[j] * V[(int64_t)j * stride];
+        double sum;
+        if (lattice) {
+            sum = P.lat_tab[lat_m(s.xi[i], qi)];
+        } else {
+            double dx = s.X[3 * i] - xl[0], dy = s.X[3 * i + 1] - xl[1], dz = s.X[3 * i + 2] - xl[2];
+            const double y = -(dx * dx + dy * dy + dz * dz) * P.inv2l2;
+            sum = P.precision == VGP_MIXED ? exp_neg(y, s.T256) : exp(y);
+        }
+        const int it = i >> 3, r = i & 7;
+        for (int jt = 0; jt < it; ++jt) {
+            const double* T = A + tix(it, jt) + r * 8;
+#pragma unroll
+            for (int c2 = 0; c2 < 8; ++c2) sum -= T[c2] * V[(int64_t)(8 * jt + c2) * stride];
+        }
+        const double* T = A + tix(it, it) + r * 8;
+        for (int c2 = 0; c2 < r; ++c2) sum -= T[c2] * V[(int64_t)(8 * it + c2) * stride];
         const double vi = sum * s.invd[i];
         V[(int64_t)i * stride] = vi;
         acc += vi * vi;
@@ -279,13 +452,22 @@ __device__ __forceinline__ double latent_var(const SolveCtx& c, const Shared& s,
     return fmax(0.0, 1.0 - acc);
 }
 
+__device__ __forceinline__ void invalid(EvalOut& r, int status) {
+    r.status = status;
+    r.d = INFINITY;
+    r.g[0] = r.g[1] = r.g[2] = 0.0;
+    r.v = INFINITY;
+}
+
 __global__ void k_solve(SolveCtx c) {
     extern __shared__ double sm[];
     __shared__ int s_w;
     const int tid = threadIdx.x, nt = blockDim.x;
     double* ws_a = c.a_in_smem ? nullptr : c.ws_a + (int64_t)blockIdx.x * c.ws_a_stride;
-    Shared s = carve(sm, c.nmax, c.a_in_smem, ws_a);
-    double* V = c.ws_v + (int64_t)blockIdx.x * c.ws_v_stride + tid;
+    Shared s = carve(sm, c.npad, c.a_in_smem, ws_a);
+    double* V = c.ws_v ? c.ws_v + (int64_t)blockIdx.x * c.ws_v_stride + tid : nullptr;
+    const bool lattice = c.b.Xi != nullptr;
+    for (int j = tid; j < 256; j += nt) s.T256[j] = c.P.exp_tab[j];
     for (;;) {
         if (tid == 0) s_w = atomicAdd(c.counter, 1);
         __syncthreads();
@@ -296,28 +478,23 @@ __global__ void k_solve(SolveCtx c) {
         const int64_t base = c.b.inst_off[I];
         const int N = (int)(c.b.inst_off[I + 1] - base);
         const int64_t q0 = c.b.q_off[I], q1 = c.b.q_off[I + 1];
-        const bool ok = N > 0 && fit_instance(c, s, I, N, base);
+        const bool ok = N > 0 && fit_instance(c, s, N, base);
         if (c.b.alpha_out)
             for (int j = tid; j < N; j += nt) c.b.alpha_out[base + j] = ok ? s.alpha[j] : NAN;
         for (int64_t p = q0 + tid; p < q1; p += nt) {
             const int64_t qid = c.b.qidx ? c.b.qidx[p] : p;
             EvalOut r;
             if (!ok) {
-                r.status = N > 0 ? VGP_ST_FACTOR_FAIL : VGP_ST_NO_SUPPORT;
-                r.d = INFINITY;
-                r.g[0] = r.g[1] = r.g[2] = 0.0;
-                r.v = INFINITY;
+                invalid(r, N > 0 ? VGP_ST_FACTOR_FAIL : VGP_ST_NO_SUPPORT);
             } else {
                 double xl[3], lo, gro[3];
-                query_local(c, I, p, qid, xl);
+                int qi = 0;
+                query_local(c, I, p, qid, xl, &qi);
                 if (!(isfinite(xl[0]) && isfinite(xl[1]) && isfinite(xl[2]))) {
-                    r.status = VGP_ST_BAD_INPUT;
-                    r.d = INFINITY;
-                    r.g[0] = r.g[1] = r.g[2] = 0.0;
-                    r.v = INFINITY;
+                    invalid(r, VGP_ST_BAD_INPUT);
                 } else {
-                    latent_mean(c, s, N, xl, lo, gro);
-                    double u = c.b.want_var ? latent_var(c, s, N, xl, V, nt) : 0.0;
+                    latent_mean(c.P, s, N, lattice, qi, xl, lo, gro);
+                    const double u = c.b.want_var ? latent_var(c.P, s, N, lattice, qi, xl, V, nt) : 0.0;
                     revert(c.P, lo, gro, u, c.b.want_var != 0, r);
                 }
             }
@@ -332,14 +509,17 @@ __global__ void k_solve(SolveCtx c) {
 //   obar_q = dL/dd_q * dd/do_q, abar = sum_q obar_q k_q, lambda = A^-1 abar,
 //   dL/dx_j = sum_q obar_q alpha_j k_qj (x*_q - x_j) / l^2
 //             - sum_i (lambda_i alpha_j + lambda_j alpha_i) k_ij (x_i - x_j) / l^2,
-// and dL/dx*_q = dL/dd_q grad d_q.  FP64 throughout.
+// and dL/dx*_q = dL/dd_q grad d_q.  FP64 throughout; alpha is recomputed, not stored.
 __global__ void k_backward(SolveCtx c) {
     extern __shared__ double sm[];
     __shared__ int s_w;
     const int tid = threadIdx.x, nt = blockDim.x;
     double* ws_a = c.a_in_smem ? nullptr : c.ws_a + (int64_t)blockIdx.x * c.ws_a_stride;
-    Shared s = carve(sm, c.nmax, c.a_in_smem, ws_a);
+    Shared s = carve(sm, c.npad, c.a_in_smem, ws_a);
     const double l2 = c.P.l2;
+    SolveCtx cc = c;
+    cc.P.precision = VGP_FP64;
+    for (int j = tid; j < 256; j += nt) s.T256[j] = c.P.exp_tab[j];
     for (;;) {
         if (tid == 0) s_w = atomicAdd(c.counter, 1);
         __syncthreads();
@@ -349,23 +529,21 @@ __global__ void k_backward(SolveCtx c) {
         const int I = c.order[w];
         const int64_t base = c.b.inst_off[I];
         const int N = (int)(c.b.inst_off[I + 1] - base);
+        const int Nt = (N + 7) >> 3;
         const int64_t q0 = c.b.q_off[I], q1 = c.b.q_off[I + 1];
-        SolveCtx cc = c;
-        cc.P.precision = VGP_FP64;
-        const bool ok = N > 0 && fit_instance(cc, s, I, N, base);
-        // per query: obar and dL/dq
+        const bool ok = N > 0 && fit_instance(cc, s, N, base);
         for (int64_t p = q0 + tid; p < q1; p += nt) {
             const int64_t qid = c.b.qidx ? c.b.qidx[p] : p;
             double ob = 0.0, gq[3] = {0.0, 0.0, 0.0};
             if (ok) {
                 double xl[3], lo, gro[3];
                 query_local(cc, I, p, qid, xl);
-                latent_mean(cc, s, N, xl, lo, gro);
+                latent_mean(cc.P, s, N, false, 0, xl, lo, gro);
                 EvalOut r;
                 revert(cc.P, lo, gro, 0.0, false, r);
-                const double g = c.bw.dL_dd[qid];
-                for (int a = 0; a < 3; ++a) gq[a] = g * r.g[a];
-                if (r.status == VGP_ST_OK && r.d > 0.0 && lo < 0.0) ob = g * (-l2 / (exp(lo) * r.d));
+                const double gd = c.bw.dL_dd[qid];
+                for (int a = 0; a < 3; ++a) gq[a] = gd * r.g[a];
+                if (r.status == VGP_ST_OK && r.d > 0.0 && lo < 0.0) ob = gd * (-l2 / (exp(lo) * r.d));
             }
             c.bw.obar[p] = ob;
             if (c.bw.dL_dq)
@@ -374,7 +552,11 @@ __global__ void k_backward(SolveCtx c) {
         __syncthreads();
         if (ok && c.bw.dL_dX) {
             // abar_j and the direct term, thread per training point
-            for (int j = tid; j < N; j += nt) {
+            for (int j = tid; j < 8 * Nt; j += nt) {
+                if (j >= N) {
+                    s.z[j] = 0.0;
+                    continue;
+                }
                 double ab = 0.0, g1[3] = {0.0, 0.0, 0.0};
                 for (int64_t p = q0; p < q1; ++p) {
                     const double ob = c.bw.obar[p];
@@ -390,36 +572,21 @@ __global__ void k_backward(SolveCtx c) {
                     g1[2] += ob * k * dz;
                 }
                 s.z[j] = ab;
-                s.y[j] = 0.0;
                 for (int a = 0; a < 3; ++a) g1[a] *= s.alpha[j] / l2;
                 const int64_t gi = c.bw.gidx[base + j];
                 for (int a = 0; a < 3; ++a) atomicAdd(&c.bw.dL_dX[3 * gi + a], g1[a]);
             }
             __syncthreads();
-            // lambda = A^-1 abar (two triangular solves, in place in z -> y)
-            const double* A = s.A;
-            for (int j = 0; j < N; ++j) {
-                const double yj = s.z[j] * s.invd[j];
-                for (int i = j + 1 + tid; i < N; i += nt) s.z[i] -= A[pk(i, j)] * yj;
-                if (tid == 0) s.y[j] = yj;
-                __syncthreads();
-            }
-            for (int j = N - 1; j >= 0; --j) {
-                const double lj = s.y[j] * s.invd[j];
-                for (int i = tid; i < j; i += nt) s.y[i] -= A[pk(j, i)] * lj;
-                __syncthreads();
-                if (tid == 0) s.z[j] = lj;  // z now holds lambda
-                __syncthreads();
-            }
+            chol_solve(s, s.A, Nt, s.w);  // lambda = A^-1 abar -> s.w
             for (int j = tid; j < N; j += nt) {
                 double g2[3] = {0.0, 0.0, 0.0};
-                const double lj = s.z[j], aj = s.alpha[j];
+                const double lj = s.w[j], aj = s.alpha[j];
                 for (int i = 0; i < N; ++i) {
                     if (i == j) continue;
                     double dx = s.X[3 * i] - s.X[3 * j], dy = s.X[3 * i + 1] - s.X[3 * j + 1],
                            dz = s.X[3 * i + 2] - s.X[3 * j + 2];
                     double k = exp(-(dx * dx + dy * dy + dz * dz) * c.P.inv2l2);
-                    double cf = (s.z[i] * aj + lj * s.alpha[i]) * k;
+                    double cf = (s.w[i] * aj + lj * s.alpha[i]) * k;
                     g2[0] -= cf * dx;
                     g2[1] -= cf * dy;
                     g2[2] -= cf * dz;
@@ -439,8 +606,7 @@ __global__ void k_hist_n(const int64_t* inst_off, int64_t n, int* hist) {
     atomicAdd(&hist[min(N, 1024)], 1);
 }
 
-// order[] sorted by increasing N via the prefix of the histogram; the kernels walk it from
-// the end (largest first) through `rev`.
+// order[] sorted by increasing N via the prefix of the histogram
 __global__ void k_order_n(const int64_t* inst_off, int64_t n, int* cursor, int32_t* order) {
     int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (i >= n) return;
@@ -456,8 +622,8 @@ __global__ void k_reverse_i32(const int32_t* in, int32_t* out, int n) {
 
 }  // namespace
 
-void solve_batch(const SolveBatch& b, const DevParams& P, int* err_dev, cudaStream_t st, Arena& ar,
-                 SolveStats* stats, const BackwardBatch* bw, bool profile) {
+void solve_batch(const SolveBatch& b, const DevParams& P, int* err_dev, cudaStream_t st, Arena& ar, SolveStats* stats,
+                 const BackwardBatch* bw, bool profile) {
     const int64_t n = b.n_inst;
     if (n <= 0) return;
     // size histogram and decreasing-size order
@@ -493,10 +659,12 @@ void solve_batch(const SolveBatch& b, const DevParams& P, int* err_dev, cudaStre
         cudaEventCreate(&ev1);
         cudaEventRecord(ev0, st);
     }
-    // buckets (descending): [225, 1024] global A; [129, 224], [65, 128], [33, 64], [0, 32] smem A
-    struct Bucket { int lo, hi, smem_a, threads; };
-    const Bucket buckets[] = {{225, 1024, 0, 256}, {129, 224, 1, 256}, {65, 128, 1, 256},
-                              {33, 64, 1, 128}, {0, 32, 1, 64}};
+    // size buckets, largest first: A in global workspace above 224, in shared memory below
+    struct Bucket {
+        int lo, hi, smem_a, threads;
+    };
+    const Bucket buckets[] = {{225, 1024, 0, 512}, {129, 224, 1, 512}, {65, 128, 1, 256},
+                              {33, 64, 1, 128},    {0, 32, 1, 64}};
     int dev = 0, n_sm = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev);
@@ -510,7 +678,10 @@ void solve_batch(const SolveBatch& b, const DevParams& P, int* err_dev, cudaStre
             cnt += h[N];
             if (h[N]) nmax = N;
         }
-        if (cnt == 0) { ++bi; continue; }
+        if (cnt == 0) {
+            ++bi;
+            continue;
+        }
         SolveCtx c;
         c.b = b;
         c.P = P;
@@ -518,23 +689,21 @@ void solve_batch(const SolveBatch& b, const DevParams& P, int* err_dev, cudaStre
         c.counter = counters + bi;
         c.order = order + done;
         c.n_work = cnt;
-        c.nmax = std::max(nmax, 1);
+        c.npad = std::max((nmax + 7) & ~7, 8);
         c.a_in_smem = bk.smem_a;
-        c.backward = bw != nullptr;
         if (bw) c.bw = *bw;
-        size_t shm = smem_bytes(c.nmax, c.a_in_smem);
+        const size_t shm = smem_bytes(c.npad, c.a_in_smem);
         auto kern = bw ? k_backward : k_solve;
         cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm);
         int per_sm = 0;
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, bk.threads, shm);
         per_sm = std::max(per_sm, 1);
-        int grid = (int)std::min<int64_t>(cnt, (int64_t)n_sm * per_sm);
-        c.ws_a_stride = c.a_in_smem ? 0 : pk(c.nmax, 0);
-        c.ws_a = c.a_in_smem ? nullptr
-                             : (double*)ar.get(Arena::kWs0, sizeof(double) * c.ws_a_stride * grid, st);
-        c.ws_v_stride = (int64_t)c.nmax * bk.threads;
-        c.ws_v = (b.want_var && !bw) ? (double*)ar.get(Arena::kWs1, sizeof(double) * c.ws_v_stride * grid, st)
-                                     : nullptr;
+        if (!c.a_in_smem) per_sm = 1;  // keep the global working set near L2 size
+        const int grid = (int)std::min<int64_t>(cnt, (int64_t)n_sm * per_sm);
+        c.ws_a_stride = c.a_in_smem ? 0 : n_tiles(c.npad / 8) * 64;
+        c.ws_a = c.a_in_smem ? nullptr : (double*)ar.get(Arena::kWs0, sizeof(double) * c.ws_a_stride * grid, st);
+        c.ws_v_stride = (int64_t)c.npad * bk.threads;
+        c.ws_v = (b.want_var && !bw) ? (double*)ar.get(Arena::kWs1, sizeof(double) * c.ws_v_stride * grid, st) : nullptr;
         kern<<<grid, bk.threads, shm, st>>>(c);
         note_launch();
         done += cnt;
