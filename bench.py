@@ -35,10 +35,8 @@ WORKLOAD = "city G-GPDF: 2M surface pts, 10M queries (70% free space, 30% <=0.5 
 
 
 def _dist_env():
-    ws = int(os.environ.get("WORLD_SIZE", "1"))
-    rank = int(os.environ.get("RANK", "0"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
-    return ws, rank, local
+    from paper_2407_09649_gb300 import replicas
+    return replicas.rank_env()
 
 
 def _scene(rank: int, n_surface: int, n_query: int):
@@ -159,12 +157,10 @@ def run_ours(args):
         torch.cuda.synchronize()
     ms = ev0.elapsed_time(ev1)
     launches = int(lib.vgp_launch_count() - l0)
-    if ws > 1:
-        t = torch.tensor([ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    from paper_2407_09649_gb300 import replicas
+    value, sec = replicas.aggregate(nq * args.steps, ms / 1e3, ws, device=dev)
+    ms = sec * 1e3
     ms_step = ms / args.steps
-    value = ws * nq * args.steps / (ms / 1e3)
     st = m.stats()
 
     # the dominant kernel (GP solve: Cholesky + alpha + evaluation), timed with events
@@ -177,28 +173,8 @@ def run_ours(args):
     achieved = fp64_flops / (solve_ms / 1e3) / 1e12
 
     extra = {}
-    if not args.quick:
-        # variance on (extra FP64 triangular solve per query)
-        outv = dict(out, var=torch.empty(nq, dtype=torch.float64, device=dev))
-        torch.cuda.synchronize()
-        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        a.record()
-        m.set_surface(S)
-        m.query(Q, grad=True, var=True, out=outv)
-        b.record()
-        torch.cuda.synchronize()
-        extra["variance_on_queries_per_s"] = nq / (a.elapsed_time(b) / 1e3)
-        # plain FP64 (batched)
-        m64 = Map(precision="fp64")
-        m64.set_surface(S)
-        m64.query(Q, grad=True, var=False, out=out)
-        torch.cuda.synchronize()
-        a.record()
-        m64.set_surface(S)
-        m64.query(Q, grad=True, var=False, out=out)
-        b.record()
-        torch.cuda.synchronize()
-        extra["fp64_batched_queries_per_s"] = nq / (a.elapsed_time(b) / 1e3)
+    if not args.quick and rank == 0:
+        extra = comparisons(S, Q, S_h, args)
 
     # end to end through the C ABI: pinned host inputs in, results out, every step
     S_pin = torch.from_numpy(S_h).pin_memory()
@@ -225,11 +201,7 @@ def run_ours(args):
         e2e_step()
     b.record()
     torch.cuda.synchronize()
-    e_ms = a.elapsed_time(b) / e_steps
-    if ws > 1:
-        t = torch.tensor([e_ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e_ms = float(t.item())
+    e_value, _ = replicas.aggregate(nq * e_steps, a.elapsed_time(b) / 1e3, ws, device=dev)
 
     cpu = None
     if rank == 0 and not args.no_cpu:
@@ -247,7 +219,7 @@ def run_ours(args):
                        "parallelism": f"replicas x{ws}" if ws > 1 else "single GPU",
                        "instances": st["n_instances"], "query_leaves": st["n_groups"],
                        "bucket_count": st["bucket_count"]},
-            "e2e": {"value": ws * nq / (e_ms / 1e3), "unit": UNIT,
+            "e2e": {"value": e_value, "unit": UNIT,
                     "h2d_bytes_per_step": int(S_h.nbytes + Q_h.nbytes), "d2h_bytes_per_step": int(nq * 32)},
             "gpu_launches": launches,
             "roofline": {"kernel": "k_solve (K assembly, FP64 Cholesky, alpha, fused eval)", "bound": "alu",
@@ -265,6 +237,81 @@ def run_ours(args):
     if ws > 1:
         dist.barrier()
         dist.destroy_process_group()
+
+
+def _timed(fn, reps=1):
+    import torch
+    fn()
+    torch.cuda.synchronize()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record()
+    for _ in range(reps):
+        fn()
+    b.record()
+    torch.cuda.synchronize()
+    return a.elapsed_time(b) / reps / 1e3
+
+
+def comparisons(S, Q, S_h, args):
+    """Secondary lines, each timed once with CUDA events after a warm-up call: variance on,
+    the all-FP64 batched form and the plain FP64 per-instance form on a query subset, the
+    L-GPDF room sequence (voxels/s) and the independent-instance sweep."""
+    import torch
+    from paper_2407_09649_gb300 import scenes
+    from paper_2407_09649_gb300.api import Map
+    out = {}
+    nsub = min(args.n_sub, Q.shape[0])
+    Qs = Q[:nsub].contiguous()
+
+    res = {}
+    for name, kw, var in (("mixed", dict(precision="mixed"), False), ("mixed_var", dict(precision="mixed"), True),
+                          ("fp64", dict(precision="fp64"), False), ("fp64_var", dict(precision="fp64"), True)):
+        m = Map(**kw)
+        t = _timed(lambda: (m.set_surface(S), m.query(Qs, grad=True, var=var)))
+        res[name] = nsub / t
+    out["subset_queries"] = nsub
+    out["subset_queries_per_s"] = res
+    # plain FP64 per-instance launches (the comparison form), on a smaller subset
+    npi = min(args.n_per_instance, Q.shape[0])
+    Qp = Q[:npi].contiguous()
+    mp = Map(precision="fp64", launch="per_instance")
+    mb = Map(precision="mixed")
+    tp = _timed(lambda: (mp.set_surface(S), mp.query(Qp, grad=True, var=False)))
+    tb = _timed(lambda: (mb.set_surface(S), mb.query(Qp, grad=True, var=False)))
+    out["per_instance_fp64"] = {"queries": npi, "queries_per_s": npi / tp, "instances": mp.stats()["n_instances"],
+                                "batched_mixed_same_queries_per_s": npi / tb, "speedup_batched_mixed": tp / tb}
+    # L-GPDF: room sequence, one frame = build (voxelise, leaf GPs, testing voxels) + fuse
+    room = scenes.Room(0)
+    frames = [torch.from_numpy(room.frame(k, seed=0)).cuda() for k in range(args.room_frames)]
+    for prec in ("mixed", "fp64"):
+        mr = Map(precision=prec, max_pts_leaf=512)
+        f0 = mr.build_frame(frames[0])
+        mr.fuse(f0)
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        nvox = 0
+        a.record()
+        for fr in frames:
+            f = mr.build_frame(fr)
+            nvox += f.n_test
+            mr.fuse(f)
+        b.record()
+        torch.cuda.synchronize()
+        sec = a.elapsed_time(b) / 1e3
+        out.setdefault("lgpdf_room", {})[prec] = {"voxels_per_s": nvox / sec, "frames": len(frames),
+                                                 "ms_per_frame": 1e3 * sec / len(frames),
+                                                 "testing_voxels_per_frame": nvox / len(frames)}
+    # independent-instance sweep (N log-uniform in [4, 1024], 512 queries each)
+    io, X, qo, Qw = scenes.patch_sweep(n_inst=args.sweep_inst, seed=4)
+    io_d = torch.from_numpy(io).cuda()
+    qo_d = torch.from_numpy(qo).cuda()
+    X_d = torch.from_numpy(X).cuda()
+    Q_d = torch.from_numpy(Qw).cuda()
+    for prec in ("mixed", "fp64"):
+        mw = Map(precision=prec)
+        t = _timed(lambda: mw.gp_batch(io_d, X_d, qo_d, Q_d, var=False))
+        out.setdefault("sweep", {})[prec] = {"instances": args.sweep_inst, "queries_per_s": Qw.shape[0] / t}
+    return out
 
 
 def cpu_baseline(S_h, Q_h, n_sample):
@@ -317,14 +364,18 @@ def run_reference(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--n-surface", type=int, default=2_000_000)
     ap.add_argument("--n-query", type=int, default=10_000_000)
     ap.add_argument("--cpu-sample", type=int, default=2000)
     ap.add_argument("--ref-sample", type=int, default=1000)
-    ap.add_argument("--quick", action="store_true", help="skip the variance-on and FP64 comparison lines")
+    ap.add_argument("--quick", action="store_true", help="skip the comparison lines")
+    ap.add_argument("--n-sub", type=int, default=1_000_000, help="queries of the precision comparison subset")
+    ap.add_argument("--n-per-instance", type=int, default=50_000, help="queries of the per-instance comparison")
+    ap.add_argument("--room-frames", type=int, default=10)
+    ap.add_argument("--sweep-inst", type=int, default=20_000)
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     args = ap.parse_args()
     if args.warmup < 3:

@@ -69,6 +69,7 @@ enum {
 
 enum { VGP_FP64 = 0, VGP_MIXED = 1 };          /* precision */
 enum { VGP_FUSE_INVVAR = 0, VGP_FUSE_TSDF = 1 }; /* fusion rule: Eq. 8 or Eq. 9 */
+enum { VGP_LAUNCH_BATCHED = 0, VGP_LAUNCH_PER_INSTANCE = 1 };
 enum {
     VGP_ST_OK = 0,
     VGP_ST_NO_SUPPORT = 1,
@@ -105,6 +106,10 @@ enum {
  *                    reverting log in FP64.
  *   profile          0 (default) or 1: record CUDA events around the GP solve kernels and
  *                    report their time in vgp_stats.t_solve_ms (adds one stream sync per call).
+ *   launch           VGP_LAUNCH_BATCHED (default): all GP instances of a call run in a few
+ *                    persistent launches, one per size bucket, largest first.
+ *                    VGP_LAUNCH_PER_INSTANCE: one kernel launch per instance, in instance
+ *                    order (the plain comparison form; same arithmetic, no batching).
  */
 typedef struct {
     double voxel_size;
@@ -118,7 +123,8 @@ typedef struct {
     int32_t fusion;
     int32_t precision;
     int32_t profile;     /* nonzero: time the solve kernels with CUDA events (vgp_stats) */
-    int32_t reserved[2]; /* must be zero */
+    int32_t launch;      /* VGP_LAUNCH_BATCHED (0) or VGP_LAUNCH_PER_INSTANCE (1) */
+    int32_t reserved;    /* must be zero */
 } vgp_params;
 
 /* Counters of the most recent call on a map (host copy; informational). */

@@ -15,6 +15,7 @@ ERRORS = {-1: "VGP_ERR_ARG", -2: "VGP_ERR_OOM", -3: "VGP_ERR_CUDA", -4: "VGP_ERR
           -5: "VGP_ERR_TIMEOUT", -6: "VGP_ERR_STATE"}
 VGP_FP64, VGP_MIXED = 0, 1
 VGP_FUSE_INVVAR, VGP_FUSE_TSDF = 0, 1
+VGP_LAUNCH_BATCHED, VGP_LAUNCH_PER_INSTANCE = 0, 1
 ST_OK, ST_NO_SUPPORT, ST_CLAMPED, ST_BAD_INPUT, ST_FACTOR_FAIL = 0, 1, 2, 3, 4
 
 
@@ -22,7 +23,7 @@ class VgpParams(C.Structure):
     _fields_ = [("voxel_size", C.c_double), ("lengthscale", C.c_double), ("sigma_occ", C.c_double),
                 ("d_max", C.c_double), ("d_var_floor", C.c_double), ("max_pts_leaf", C.c_int32),
                 ("max_pts_group", C.c_int32), ("max_leaf_search", C.c_int32), ("fusion", C.c_int32),
-                ("precision", C.c_int32), ("profile", C.c_int32), ("reserved", C.c_int32 * 2)]
+                ("precision", C.c_int32), ("profile", C.c_int32), ("launch", C.c_int32), ("reserved", C.c_int32)]
 
 
 class VgpStats(C.Structure):

@@ -22,6 +22,7 @@ static std::atomic<int64_t> g_launches{0};
 
 namespace vgp {
 void note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+void set_last_error(const char* msg) { g_last_error = msg; }
 }  // namespace vgp
 
 static int fail(int code, const char* fmt, ...) {
@@ -224,7 +225,8 @@ int vgp_create(const vgp_params* p, vgp_map** out) {
     if (p->max_leaf_search < 0 || p->max_leaf_search > 16) return fail(VGP_ERR_ARG, "max_leaf_search must be in [0, 16]");
     if (p->fusion != VGP_FUSE_INVVAR && p->fusion != VGP_FUSE_TSDF) return fail(VGP_ERR_ARG, "unknown fusion rule");
     if (p->precision != VGP_FP64 && p->precision != VGP_MIXED) return fail(VGP_ERR_ARG, "unknown precision");
-    if (p->reserved[0] || p->reserved[1]) return fail(VGP_ERR_ARG, "reserved fields must be zero");
+    if (p->reserved) return fail(VGP_ERR_ARG, "reserved fields must be zero");
+    if (p->launch != VGP_LAUNCH_BATCHED && p->launch != VGP_LAUNCH_PER_INSTANCE) return fail(VGP_ERR_ARG, "unknown launch mode");
     if (p->profile != 0 && p->profile != 1) return fail(VGP_ERR_ARG, "profile must be 0 or 1");
     vgp_map* m = new (std::nothrow) vgp_map();
     if (!m) return fail(VGP_ERR_OOM, "host allocation failed");
@@ -412,7 +414,7 @@ int vgp_build_frame(vgp_map* m, const float* pts, int64_t n, vgp_stream stream, 
     b.alpha_out = f->alpha;
     b.want_var = 1;
     SolveStats ss;
-    solve_batch(b, P, m->dev_words, st, m->ar, &ss, nullptr, m->prm.profile != 0);
+    solve_batch(b, P, m->dev_words, st, m->ar, &ss, nullptr, m->prm.profile != 0, m->prm.launch);
     if (read_words(m, st) != VGP_OK) return bail(VGP_ERR_CUDA, "sync failed");
     if (m->host_words[4] != 0) return bail(VGP_ERR_STATE, "testing voxel without a neighbouring GP leaf");
     cudaError_t ce = cudaGetLastError();
@@ -806,7 +808,7 @@ int vgp_query_distance_gradient(vgp_map* m, const float* q, int64_t n, double* d
     b.status = status;
     b.want_var = var != nullptr;
     SolveStats ss;
-    solve_batch(b, m->P, m->dev_words, st, m->ar, &ss, nullptr, m->prm.profile != 0);
+    solve_batch(b, m->P, m->dev_words, st, m->ar, &ss, nullptr, m->prm.profile != 0, m->prm.launch);
     CUDA_TRY(cudaGetLastError());
     vgp_stats S{};
     S.n_points = m->s_n;
@@ -954,7 +956,7 @@ extern "C" int vgp_gp_batch(vgp_map* m, int64_t n_inst, const int64_t* inst_off,
     b.status = status;
     b.want_var = var != nullptr;
     SolveStats ss;
-    solve_batch(b, m->P, m->dev_words, st, m->ar, &ss, nullptr, m->prm.profile != 0);
+    solve_batch(b, m->P, m->dev_words, st, m->ar, &ss, nullptr, m->prm.profile != 0, m->prm.launch);
     CUDA_TRY(cudaGetLastError());
     vgp_stats S{};
     S.n_instances = n_inst;

@@ -78,6 +78,14 @@ void fill_i32(int32_t* p, int32_t v, int64_t n, cudaStream_t st);
 // Solve every instance of the batch (factorise, alpha, evaluate its queries).  Returns
 // error bits through *err_dev.  Synchronises once to read the size histogram.
 void solve_batch(const SolveBatch& b, const DevParams& P, int* err_dev, cudaStream_t st,
-                 Arena& ar, SolveStats* stats, const BackwardBatch* bw = nullptr, bool profile = false);
+                 Arena& ar, SolveStats* stats, const BackwardBatch* bw = nullptr, bool profile = false,
+                 int launch = 0);
+
+// Set the thread-local message returned by vgp_last_error().
+void set_last_error(const char* msg);
+
+// k_solve with caller-provided scratch and no allocation (see noalloc.cu); 0 on success.
+int solve_launch_static(const SolveBatch& b, const DevParams& P, int* err_dev, int npad, int threads, int max_grid,
+                        int* counter, const int32_t* order, double* ws_v, cudaStream_t st);
 
 }  // namespace vgp

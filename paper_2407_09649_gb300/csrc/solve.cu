@@ -31,6 +31,10 @@ __device__ __forceinline__ int tri_row(int p) {
     return r;
 }
 
+__device__ __forceinline__ double neg(double x) {  // sign flip on the integer pipe
+    return __longlong_as_double(__double_as_longlong(x) ^ (long long)0x8000000000000000ull);
+}
+
 // D(8x8) += A(8x4) B(4x8) on the FP64 tensor path.  Fragments: a = A[g][t],
 // b = B[t][g], c = D[g][2t .. 2t+1] with g = lane / 4, t = lane % 4.
 __device__ __forceinline__ void dmma(double& c0, double& c1, double a, double b) {
@@ -44,7 +48,8 @@ struct SolveCtx {
     DevParams P;
     int* err;
     int* counter;
-    const int32_t* order;  // instance ids, decreasing N
+    const int32_t* order;  // instance ids, decreasing N (null: inst_base + work index)
+    int inst_base;
     int n_work;
     int npad;              // largest N in this launch, rounded up to 8
     int a_in_smem;
@@ -64,6 +69,7 @@ struct Shared {
     double* Tinv;   // [64] inverse of the current diagonal tile
     double* T256;   // [256] 2^(j/256) for exp_neg
     double* A;      // tile-packed lower triangle
+    double* panel;  // [npad/8 - 1][64] current panel column when A is in global memory
     float* Xf;      // [N][3]
     float* alf;     // [npad] alpha rounded to FP32
     float* alf_lo;  // [npad] alpha - alf, rounded to FP32
@@ -83,8 +89,11 @@ __device__ Shared carve(double* sm, int npad, int a_in_smem, double* ws_a) {
     if (a_in_smem) {
         s.A = end;
         end += n_tiles(npad / 8) * 64;
+        s.panel = nullptr;
     } else {
         s.A = ws_a;
+        s.panel = end;
+        end += (int64_t)(npad / 8) * 64;
     }
     s.Xf = reinterpret_cast<float*>(end);
     s.alf = s.Xf + 3 * npad;
@@ -94,7 +103,7 @@ __device__ Shared carve(double* sm, int npad, int a_in_smem, double* ws_a) {
 }
 
 __host__ size_t smem_bytes(int npad, int a_in_smem) {
-    size_t d = (size_t)7 * npad + 64 + 256 + (a_in_smem ? (size_t)n_tiles(npad / 8) * 64 : 0);
+    size_t d = (size_t)7 * npad + 64 + 256 + (a_in_smem ? (size_t)n_tiles(npad / 8) * 64 : (size_t)(npad / 8) * 64);
     return d * sizeof(double) + (size_t)5 * npad * sizeof(float) + (size_t)npad * sizeof(int);
 }
 
@@ -233,7 +242,7 @@ __device__ bool fit_instance(const SolveCtx& c, const Shared& s, int N, int64_t 
         }
         __syncthreads();
         if (s_fail) break;
-        // panel: L_it,kt = A_it,kt * Tinv^T
+        // panel: L_it,kt = A_it,kt * Tinv^T (kept in shared memory too when A is global)
         for (int it = kt + 1 + warp; it < Nt; it += nwarps) {
             double* T = A + tix(it, kt);
             const double a0 = T[g * 8 + t], a1 = T[g * 8 + 4 + t];
@@ -244,22 +253,63 @@ __device__ bool fit_instance(const SolveCtx& c, const Shared& s, int N, int64_t 
             __syncwarp();
             T[g * 8 + 2 * t] = c0;
             T[g * 8 + 2 * t + 1] = c1;
+            if (s.panel) {
+                double* Pt = s.panel + (it - kt - 1) * 64;
+                Pt[g * 8 + 2 * t] = c0;
+                Pt[g * 8 + 2 * t + 1] = c1;
+            }
         }
         __syncthreads();
-        // trailing update: A_it,jt -= L_it,kt L_jt,kt^T for kt < jt <= it
+        // trailing update A_it,jt -= L_it,kt L_jt,kt^T (kt < jt <= it) in 2x2 blocks of tiles:
+        // four independent accumulators per warp, fragments from shared memory
         const int M = Nt - kt - 1;
-        const int P = M * (M + 1) / 2;
-        for (int p = warp; p < P; p += nwarps) {
-            const int ii = tri_row(p), jj = p - ii * (ii + 1) / 2;
-            const int it = kt + 1 + ii, jt = kt + 1 + jj;
-            const double* Li = A + tix(it, kt);
-            const double* Lj = A + tix(jt, kt);
-            double* C = A + tix(it, jt);
-            double c0 = C[g * 8 + 2 * t], c1 = C[g * 8 + 2 * t + 1];
-            dmma(c0, c1, -Li[g * 8 + t], Lj[g * 8 + t]);
-            dmma(c0, c1, -Li[g * 8 + 4 + t], Lj[g * 8 + 4 + t]);
-            C[g * 8 + 2 * t] = c0;
-            C[g * 8 + 2 * t + 1] = c1;
+        const int MB = (M + 1) >> 1;
+        const int NB = MB * (MB + 1) / 2;
+        for (int p = warp; p < NB; p += nwarps) {
+            const int bi = tri_row(p), bj = p - bi * (bi + 1) / 2;
+            const int i0 = 2 * bi, j0 = 2 * bj;
+            double na[2][2], bb[2][2];
+#pragma unroll
+            for (int r = 0; r < 2; ++r) {
+                const int ii = i0 + r, jj = j0 + r;
+                const double* Pi = s.panel ? s.panel + ii * 64 : A + tix(kt + 1 + ii, kt);
+                const double* Pj = s.panel ? s.panel + jj * 64 : A + tix(kt + 1 + jj, kt);
+#pragma unroll
+                for (int k = 0; k < 2; ++k) {
+                    na[r][k] = ii < M ? neg(Pi[g * 8 + 4 * k + t]) : 0.0;
+                    bb[r][k] = jj < M ? Pj[g * 8 + 4 * k + t] : 0.0;
+                }
+            }
+            double cc[2][2][2];
+            bool valid[2][2];
+#pragma unroll
+            for (int r = 0; r < 2; ++r)
+#pragma unroll
+                for (int q = 0; q < 2; ++q) {
+                    const int ii = i0 + r, jj = j0 + q;
+                    valid[r][q] = ii < M && jj <= ii;
+                    cc[r][q][0] = cc[r][q][1] = 0.0;
+                    if (valid[r][q]) {
+                        const double* C = A + tix(kt + 1 + ii, kt + 1 + jj);
+                        cc[r][q][0] = C[g * 8 + 2 * t];
+                        cc[r][q][1] = C[g * 8 + 2 * t + 1];
+                    }
+                }
+#pragma unroll
+            for (int k = 0; k < 2; ++k)
+#pragma unroll
+                for (int r = 0; r < 2; ++r)
+#pragma unroll
+                    for (int q = 0; q < 2; ++q) dmma(cc[r][q][0], cc[r][q][1], na[r][k], bb[q][k]);
+#pragma unroll
+            for (int r = 0; r < 2; ++r)
+#pragma unroll
+                for (int q = 0; q < 2; ++q)
+                    if (valid[r][q]) {
+                        double* C = A + tix(kt + 1 + i0 + r, kt + 1 + j0 + q);
+                        C[g * 8 + 2 * t] = cc[r][q][0];
+                        C[g * 8 + 2 * t + 1] = cc[r][q][1];
+                    }
         }
         __syncthreads();
     }
@@ -474,7 +524,7 @@ __global__ void k_solve(SolveCtx c) {
         const int w = s_w;
         __syncthreads();
         if (w >= c.n_work) break;
-        const int I = c.order[w];
+        const int I = c.order ? c.order[w] : c.inst_base + w;
         const int64_t base = c.b.inst_off[I];
         const int N = (int)(c.b.inst_off[I + 1] - base);
         const int64_t q0 = c.b.q_off[I], q1 = c.b.q_off[I + 1];
@@ -622,8 +672,39 @@ __global__ void k_reverse_i32(const int32_t* in, int32_t* out, int n) {
 
 }  // namespace
 
+// One persistent launch of k_solve over instances in the given order with caller-provided
+// scratch (no allocation): A in shared memory (npad <= 224), variance columns in ws_v
+// (max_grid * npad * threads doubles), work counter *counter zeroed by the caller.
+int solve_launch_static(const SolveBatch& b, const DevParams& P, int* err_dev, int npad, int threads, int max_grid,
+                        int* counter, const int32_t* order, double* ws_v, cudaStream_t st) {
+    SolveCtx c;
+    c.b = b;
+    c.P = P;
+    c.err = err_dev;
+    c.counter = counter;
+    c.order = order;
+    c.inst_base = 0;
+    c.n_work = (int)b.n_inst;
+    c.npad = npad;
+    c.a_in_smem = 1;
+    c.ws_a = nullptr;
+    c.ws_a_stride = 0;
+    const size_t shm = smem_bytes(npad, 1);
+    if (cudaFuncSetAttribute(k_solve, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm) != cudaSuccess) return -1;
+    int dev = 0, n_sm = 0, per_sm = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_solve, threads, shm);
+    const int grid = (int)std::min<int64_t>(std::min<int64_t>(b.n_inst, (int64_t)n_sm * std::max(per_sm, 1)), max_grid);
+    c.ws_v_stride = (int64_t)npad * threads;
+    c.ws_v = ws_v;
+    k_solve<<<grid, threads, shm, st>>>(c);
+    note_launch();
+    return cudaGetLastError() == cudaSuccess ? 0 : -1;
+}
+
 void solve_batch(const SolveBatch& b, const DevParams& P, int* err_dev, cudaStream_t st, Arena& ar, SolveStats* stats,
-                 const BackwardBatch* bw, bool profile) {
+                 const BackwardBatch* bw, bool profile, int launch) {
     const int64_t n = b.n_inst;
     if (n <= 0) return;
     // size histogram and decreasing-size order
@@ -668,6 +749,46 @@ void solve_batch(const SolveBatch& b, const DevParams& P, int* err_dev, cudaStre
     int dev = 0, n_sm = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev);
+    if (launch == VGP_LAUNCH_PER_INSTANCE && !bw) {
+        // the plain comparison form: one launch per instance, in instance order, one CTA each
+        int* ctr = (int*)ar.get(Arena::kCounters, sizeof(int) * n, st);
+        cudaMemsetAsync(ctr, 0, sizeof(int) * n, st);
+        std::vector<int64_t> off(n + 1);
+        cudaMemcpyAsync(off.data(), b.inst_off, sizeof(int64_t) * (n + 1), cudaMemcpyDeviceToHost, st);
+        cudaStreamSynchronize(st);
+        for (int64_t I = 0; I < n; ++I) {
+            const int N = (int)(off[I + 1] - off[I]);
+            SolveCtx c;
+            c.b = b;
+            c.P = P;
+            c.err = err_dev;
+            c.counter = ctr + I;
+            c.order = nullptr;
+            c.inst_base = (int)I;
+            c.n_work = 1;
+            c.npad = std::max((N + 7) & ~7, 8);
+            c.a_in_smem = c.npad <= 224;
+            const int threads = c.npad <= 32 ? 64 : c.npad <= 64 ? 128 : c.npad <= 128 ? 256 : 512;
+            const size_t shm = smem_bytes(c.npad, c.a_in_smem);
+            cudaFuncSetAttribute(k_solve, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm);
+            c.ws_a_stride = c.a_in_smem ? 0 : n_tiles(c.npad / 8) * 64;
+            c.ws_a = c.a_in_smem ? nullptr : (double*)ar.get(Arena::kWs0, sizeof(double) * n_tiles(128) * 64, st);
+            c.ws_v_stride = (int64_t)c.npad * threads;
+            c.ws_v = b.want_var ? (double*)ar.get(Arena::kWs1, sizeof(double) * 1024 * 512, st) : nullptr;
+            k_solve<<<1, threads, shm, st>>>(c);
+            note_launch();
+        }
+        if (profile) {
+            cudaEventRecord(ev1, st);
+            cudaEventSynchronize(ev1);
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, ev0, ev1);
+            if (stats) stats->t_solve_ms += ms;
+            cudaEventDestroy(ev0);
+            cudaEventDestroy(ev1);
+        }
+        return;
+    }
     int* counters = (int*)ar.get(Arena::kCounters, sizeof(int) * 8, st);
     cudaMemsetAsync(counters, 0, sizeof(int) * 8, st);
     int done = 0;  // instances already assigned (from the large end)
@@ -688,6 +809,7 @@ void solve_batch(const SolveBatch& b, const DevParams& P, int* err_dev, cudaStre
         c.err = err_dev;
         c.counter = counters + bi;
         c.order = order + done;
+        c.inst_base = 0;
         c.n_work = cnt;
         c.npad = std::max((nmax + 7) & ~7, 8);
         c.a_in_smem = bk.smem_a;
