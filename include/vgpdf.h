@@ -270,6 +270,32 @@ int vgp_gp_batch(vgp_map* m, int64_t n_inst, const int64_t* inst_off_dev, const 
                  const int64_t* q_off_dev, const float* Q_dev, double* d_dev, double* grad_dev,
                  double* var_dev, uint8_t* status_dev, vgp_stream stream);
 
+/*
+ * vgp_gp_batch_static -- vgp_gp_batch for callers that cannot allocate device memory.
+ * The paper has no counterpart; this entry point exists for callers for whom a cudaMalloc
+ * (or a stream-ordered allocation) is not allowed or not possible at call time: code running
+ * under an externally owned memory budget, real-time loops that must never enter the
+ * allocator, or hosts that give the library a fixed footprint.  It needs no vgp_map either.
+ *
+ * Same computation and outputs as vgp_gp_batch with the parameters *p (precision, l, sigma,
+ * d_max, d_var_floor; grid fields unused), on the current device.  All scratch lives in one
+ * statically sized device array of about 31 MiB, compiled into the library: every GPU on which
+ * the library is loaded holds it until the process exits.  Limits (VGP_ERR_ARG beyond them,
+ * before any result is written): at most 65536 instances and 262144 training points per call,
+ * at most 64 points per instance.
+ *
+ * The first call on each device looks up the array's device address and writes a constant
+ * table into it with a synchronous copy: make that first call before any stream capture.
+ * The call reads two words back from the GPU, so it synchronises the stream.  Every call on a
+ * device shares the same array and it keeps the last call's contents; the call clears what
+ * must start at zero.  Calls whose GPU work overlaps (several streams or host threads at once)
+ * race on the array and give wrong results: serialise them.  Outputs are complete once the
+ * stream has passed the call.  Calls no cudaMalloc, cudaFree or allocating library routine.
+ */
+int vgp_gp_batch_static(const vgp_params* p, int64_t n_inst, const int64_t* inst_off_dev, const float* X_dev,
+                        const int64_t* q_off_dev, const float* Q_dev, double* d_dev, double* grad_dev,
+                        double* var_dev, uint8_t* status_dev, vgp_stream stream);
+
 /* Counters of the most recent build_frame / set_surface / query / batch call. */
 int vgp_get_stats(const vgp_map* m, vgp_stats* out);
 

@@ -51,6 +51,7 @@ SIGNATURES = [
     ("vgp_query_distance_gradient", _i32, [_vp, _vp, _i64, _vp, _vp, _vp, _vp, _vp]),
     ("vgp_query_backward", _i32, [_vp, _vp, _i64, _vp, _vp, _vp, _vp]),
     ("vgp_gp_batch", _i32, [_vp, _i64, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp]),
+    ("vgp_gp_batch_static", _i32, [C.POINTER(VgpParams), _i64, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp]),
     ("vgp_get_stats", _i32, [_vp, C.POINTER(VgpStats)]),
     ("vgp_sync", _i32, [_vp]),
     ("vgp_launch_count", C.c_int64, []),
