@@ -1,0 +1,141 @@
+"""Parity at the full workload sizes, in the launch configuration the benchmark times:
+the whole workload runs on the GPU in one call, and a seeded sample of outputs is compared
+with the FP64 oracle (which recomputes each sampled output from the same inputs)."""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+pytestmark = pytest.mark.gpu
+
+
+def _angle_deg(a, b):
+    c = np.sum(a * b, 1) / np.maximum(np.linalg.norm(a, axis=1) * np.linalg.norm(b, axis=1), 1e-300)
+    return np.degrees(np.arccos(np.clip(c, -1, 1)))
+
+
+@pytest.fixture(scope="module")
+def api():
+    import paper_2407_09649_gb300 as P
+    P.build()
+    from paper_2407_09649_gb300 import api as A
+    return A
+
+
+def test_sphere_plane_frame_and_queries_full(api, orc):
+    """20k-point sphere + plane frame (cap 64 per leaf): every testing voxel and all 10k
+    queries, FP64 and mixed."""
+    from paper_2407_09649_gb300 import scenes
+    pts = scenes.sphere_plane_frame(0)
+    q = scenes.uniform_queries(0)
+    ref = orc.frame(pts, orc.params())
+    ro = np.argsort(ref.test_key, kind="stable")
+    S = orc.Surface(pts, orc.params())
+    rq = S.query(q, want_var=True)
+    for prec, tol in (("fp64", 1e-4), ("mixed", 1e-3)):
+        m = api.Map(precision=prec)
+        f = m.build_frame(torch.from_numpy(pts).cuda())
+        r = {k: v.cpu().numpy() for k, v in f.results().items()}
+        o = np.argsort(r["keys"], kind="stable")
+        assert np.array_equal(r["keys"][o], ref.test_key[ro])
+        ok = (ref.status[ro] == 0) & (ref.d[ro] > 2e-3)
+        assert np.abs(r["d"][o][ok] - ref.d[ro][ok]).max() <= tol
+        m.set_surface(torch.from_numpy(pts).cuda())
+        out = m.query(torch.from_numpy(q).cuda(), grad=True, var=True)
+        d, g, s = out["d"].cpu().numpy(), out["grad"].cpu().numpy(), out["status"].cpu().numpy()
+        ok = (rq["status"] == 0) & (rq["d"] > 2e-3) & (rq["d"] < 9.0)
+        assert np.array_equal(s[ok], rq["status"][ok])
+        assert np.abs(d[ok] - rq["d"][ok]).max() <= tol
+        big = ok & (np.linalg.norm(rq["grad"], axis=1) > 0.5)
+        assert np.percentile(_angle_deg(g[big], rq["grad"][big]), 99.9) <= (0.1 if prec == "fp64" else 1.0)
+
+
+def test_city_query_full_size_sampled(api, orc):
+    """2M surface points, 10M queries in one call (as timed); 300 sampled queries checked."""
+    from paper_2407_09649_gb300 import scenes
+    city = scenes.City(0)
+    S_h = city.surface(n=2_000_000, seed=0)
+    Q_h = city.queries(n=10_000_000, seed=1)
+    m = api.Map(precision="mixed")
+    m.set_surface(torch.from_numpy(S_h).cuda())
+    out = m.query(torch.from_numpy(Q_h).cuda(), grad=True, var=False)
+    rng = np.random.default_rng(7)
+    idx = rng.choice(len(Q_h), 300, replace=False)
+    orc.set_threads(0)
+    ref = orc.Surface(S_h, orc.params()).query(Q_h[idx], want_var=False)
+    d = out["d"].cpu().numpy()[idx]
+    s = out["status"].cpu().numpy()[idx]
+    g = out["grad"].cpu().numpy()[idx]
+    ok = (ref["status"] == 0) & (ref["d"] > 2e-3) & (ref["d"] < 9.0)
+    assert ok.sum() > 250
+    assert np.array_equal(s[ok], ref["status"][ok])
+    assert np.abs(d[ok] - ref["d"][ok]).max() <= 1e-3
+    big = ok & (np.linalg.norm(ref["grad"], axis=1) > 0.5)
+    assert np.percentile(_angle_deg(g[big], ref["grad"][big]), 99) <= 1.0
+    far = ref["status"] != 0
+    assert np.array_equal(s[far], ref["status"][far])
+
+
+def test_patch_sweep_full_size_sampled(api, orc):
+    """200,000 instances (N log-uniform in [4, 1024]), 512 queries each, in one call;
+    150 sampled instances checked with all their queries."""
+    from paper_2407_09649_gb300 import scenes
+    io, X, qo, Q = scenes.patch_sweep(n_inst=200_000, seed=4)
+    m = api.Map(precision="mixed")
+    out = m.gp_batch(io, X, qo, Q, var=False)
+    d = out["d"].cpu().numpy()
+    s = out["status"].cpu().numpy()
+    rng = np.random.default_rng(8)
+    # include the largest instances
+    N = np.diff(io)
+    pick = np.unique(np.concatenate([rng.choice(len(N), 120, replace=False), np.argsort(N)[-30:]]))
+    sub_io = np.concatenate([[0], np.cumsum(N[pick])])
+    sub_X = np.concatenate([X[io[i]:io[i + 1]] for i in pick]).astype(np.float64)
+    qsel = np.concatenate([np.arange(qo[i], qo[i + 1]) for i in pick])
+    sub_qo = np.concatenate([[0], np.cumsum(np.diff(qo)[pick])])
+    ref = orc.gp_batch(sub_io, sub_X, sub_qo, Q[qsel].astype(np.float64), orc.params(), want_var=False)
+    ok = (ref.status == 0) & (ref.d > 2e-3) & (ref.d < 9.0)
+    assert np.array_equal(s[qsel][ok], ref.status[ok])
+    assert np.abs(d[qsel][ok] - ref.d[ok]).max() <= 1e-3
+
+
+def test_room_frame_full_size(api, orc):
+    """One 100,000-point room frame with a 512-point leaf cap: every testing voxel (FP64)."""
+    from paper_2407_09649_gb300 import scenes
+    pts = scenes.Room(0).frame(7, seed=0)
+    P = orc.params(max_pts_leaf=512)
+    ref = orc.frame(pts, P)
+    m = api.Map(precision="fp64", max_pts_leaf=512)
+    f = m.build_frame(torch.from_numpy(pts).cuda())
+    r = {k: v.cpu().numpy() for k, v in f.results().items()}
+    o = np.argsort(r["keys"], kind="stable")
+    ro = np.argsort(ref.test_key, kind="stable")
+    assert np.array_equal(r["keys"][o], ref.test_key[ro])
+    assert np.array_equal(r["status"][o], ref.status[ro])
+    ok = ref.status[ro] == 0
+    assert np.abs(r["d"][o][ok] - ref.d[ro][ok]).max() <= 1e-4
+    fin = ok & np.isfinite(ref.v[ro])
+    np.testing.assert_allclose(r["v"][o][fin], ref.v[ro][fin], rtol=1e-5, atol=1e-12)
+
+
+def test_degenerate_instances(api, orc):
+    """Duplicate points (K + sigma^2 I with cond ~ N / sigma^2), a single point, collinear
+    points, and an instance with no queries."""
+    pts = [np.zeros((1000, 3)) + np.array([1.0, 2.0, 3.0]),
+           np.array([[0.5, 0.5, 0.5]]),
+           np.c_[np.linspace(0, 1, 300), np.zeros(300), np.zeros(300)]]
+    Qs = [np.array([[1.0, 2.0, 3.3], [1.2, 2.0, 3.0]]), np.array([[0.9, 0.5, 0.5]]), np.array([[0.5, 0.2, 0.0]]),
+          np.zeros((0, 3))]
+    pts.append(np.array([[5.0, 5.0, 5.0], [5.1, 5.0, 5.0]]))
+    io = np.concatenate([[0], np.cumsum([len(p) for p in pts])])
+    qo = np.concatenate([[0], np.cumsum([len(q) for q in Qs])])
+    X = np.vstack(pts)
+    Q = np.vstack(Qs)
+    ref = orc.gp_batch(io, X, qo, Q, orc.params())
+    for prec in ("fp64", "mixed"):
+        out = api.Map(precision=prec).gp_batch(io, X.astype(np.float32), qo, Q.astype(np.float32))
+        d = out["d"].cpu().numpy()
+        s = out["status"].cpu().numpy()
+        assert np.array_equal(s, ref.status)
+        ok = ref.status == 0
+        assert np.abs(d[ok] - ref.d[ok]).max() <= (1e-4 if prec == "fp64" else 1e-3)
