@@ -83,6 +83,7 @@ def lib():
         L.or_surface_instance.restype = i64
         L.or_query.argtypes = [vp, vp, i64, C.c_int, vp, vp, vp, vp, vp, vp]
         L.or_query_backward.argtypes = [vp, vp, i64, vp, vp, vp]
+        L.or_query_smooth.argtypes = [vp, vp, i64, C.c_int, C.c_double, C.c_int, vp, vp, vp, vp, vp]
         L.or_set_threads.argtypes = [C.c_int]
         L.or_get_threads.restype = C.c_int
         _lib = L
@@ -282,6 +283,19 @@ class Surface:
         iN = np.zeros(n, np.int32)
         lib().or_query(self.h, _p(q), n, int(want_var), _p(d), _p(g), _p(v), _p(st), _p(ik), _p(iN))
         return dict(d=d, grad=g, var=v if want_var else None, status=st, inst_key=ik, inst_n=iN)
+
+    def query_smooth(self, q, n_nodes: int = 8, lam: float = 100.0, want_var: bool = True):
+        """G-GPDF as per-leaf GPs blended by the smooth minimum of Eq. 10."""
+        q = _f32(q)
+        n = len(q)
+        d = np.zeros(n)
+        g = np.zeros((n, 3))
+        v = np.zeros(n)
+        st = np.zeros(n, np.uint8)
+        nn = np.zeros(n, np.int32)
+        lib().or_query_smooth(self.h, _p(q), n, int(n_nodes), float(lam), int(want_var), _p(d), _p(g), _p(v),
+                              _p(st), _p(nn))
+        return dict(d=d, grad=g, var=v if want_var else None, status=st, n_nodes=nn)
 
     def backward(self, q, dL_dd):
         q = _f32(q)

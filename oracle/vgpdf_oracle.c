@@ -1062,6 +1062,185 @@ int or_query_backward(const or_surface* S, const float* q, int64_t n, const doub
 }
 
 /* ------------------------------------------------------------------------------------ */
+/* G-GPDF as blended per-leaf GPs (Sec. IV-D, Eq. 10)                                   */
+/* ------------------------------------------------------------------------------------ */
+/*
+ * Each occupied surface leaf is one GP node, trained on the leaf's points (at most
+ * max_pts_leaf, the ones nearest to the leaf centre, ties to the lower index).  A query uses
+ * the Q nodes nearest to it (FP64 squared distance from the query to the leaf centre, ties
+ * to the smaller key) among the occupied leaves in the 27-leaf neighbourhood of the query
+ * leaf's centre leaf (the same centre rule as the neighbourhood GP).  Eq. 10 is read as a
+ * smooth minimum: d = sum_q d_q w_q / sum_q w_q with w_q = exp(-lambda (d_q - min d)), over the
+ * nodes whose result is valid; the gradient is the plain average of the valid nodes'
+ * gradients ("directly average"), the variance the same weighted average as d.
+ */
+static int64_t leaf_points_capped(const or_surface* S, int64_t l, int cap, int64_t* out) {
+    int64_t n = S->off[l + 1] - S->off[l];
+    int64_t L[3];
+    unpack_key(S->lkey[l], L);
+    double vs = S->P.voxel_size, c[3];
+    for (int a = 0; a < 3; ++a) c[a] = ((double)(8 * L[a]) + 3.5) * vs;
+    didx* cand = (didx*)malloc(sizeof(didx) * (n + 1));
+    for (int64_t t = 0; t < n; ++t) {
+        int64_t i = S->idx[S->off[l] + t];
+        const double* x = S->pts + 3 * i;
+        double ex = x[0] - c[0], ey = x[1] - c[1], ez = x[2] - c[2];
+        cand[t].d2 = (ex * ex + ey * ey) + ez * ez;
+        cand[t].i = i;
+    }
+    int64_t m = n;
+    if (m > cap) {
+        qsort(cand, (size_t)m, sizeof(didx), cmp_didx);
+        m = cap;
+    }
+    for (int64_t t = 0; t < m; ++t) out[t] = cand[t].i;
+    for (int64_t t = 1; t < m; ++t) {
+        int64_t v = out[t], u = t - 1;
+        while (u >= 0 && out[u] > v) { out[u + 1] = out[u]; --u; }
+        out[u + 1] = v;
+    }
+    free(cand);
+    return m;
+}
+
+typedef struct {
+    double d2;
+    uint64_t key;
+    int64_t l;
+} node_c;
+
+static int cmp_node(const void* a, const void* b) {
+    const node_c* x = (const node_c*)a;
+    const node_c* y = (const node_c*)b;
+    if (x->d2 != y->d2) return x->d2 < y->d2 ? -1 : 1;
+    return (x->key > y->key) - (x->key < y->key);
+}
+
+int or_query_smooth(const or_surface* S, const float* q, int64_t n, int Qmax, double lambda, int want_var,
+                    double* d, double* grad, double* var, uint8_t* status, int32_t* n_nodes) {
+    const or_params* P = &S->P;
+    /* fit every occupied leaf lazily, once (cache by leaf index) */
+    ifit* fits = (ifit*)calloc((size_t)(S->nl + 1), sizeof(ifit));
+    uint8_t* have = (uint8_t*)calloc((size_t)(S->nl + 1), 1);
+    int cap = P->max_pts_leaf;
+    /* which leaves are needed: first pass, serial (cheap) */
+    int64_t* need_list = (int64_t*)malloc(sizeof(int64_t) * (S->nl + 1));
+    int64_t n_need = 0;
+    int64_t* q_c = (int64_t*)malloc(sizeof(int64_t) * 3 * (n + 1));
+    uint8_t* q_ok = (uint8_t*)malloc(n + 1);
+    for (int64_t i = 0; i < n; ++i) {
+        double p[3] = {(double)q[3 * i], (double)q[3 * i + 1], (double)q[3 * i + 2]};
+        int64_t ijk[3], M[3], C[3];
+        int32_t bit;
+        q_ok[i] = 0;
+        if (!voxel_ijk(p, P->voxel_size, ijk)) continue;
+        leaf_of(ijk, M, &bit);
+        if (!centre_leaf(S, M, C)) { q_ok[i] = 2; continue; }
+        q_ok[i] = 1;
+        for (int a = 0; a < 3; ++a) q_c[3 * i + a] = C[a];
+        for (int dz = -1; dz <= 1; ++dz)
+            for (int dy = -1; dy <= 1; ++dy)
+                for (int dx = -1; dx <= 1; ++dx) {
+                    int64_t l = find_key(S->lkey, S->nl, pack_key(C[0] + dx, C[1] + dy, C[2] + dz));
+                    if (l >= 0 && !have[l]) { have[l] = 1; need_list[n_need++] = l; }
+                }
+    }
+#pragma omp parallel for schedule(dynamic, 4)
+    for (int64_t t = 0; t < n_need; ++t) {
+        int64_t l = need_list[t];
+        int64_t* ids = (int64_t*)malloc(sizeof(int64_t) * (S->off[l + 1] - S->off[l] + 1));
+        int64_t m = leaf_points_capped(S, l, cap, ids);
+        ifit* f = &fits[l];
+        f->N = (int)m;
+        f->X = (double*)malloc(sizeof(double) * 3 * (m + 1));
+        for (int64_t j = 0; j < m; ++j)
+            for (int a = 0; a < 3; ++a) f->X[3 * j + a] = S->pts[3 * ids[j] + a];
+        f->L = (double*)malloc(sizeof(double) * ((int64_t)m * (m + 1) / 2 + 1));
+        f->alpha = (double*)malloc(sizeof(double) * (m + 1));
+        f->ok = or_gp_fit(f->X, f->N, P, f->L, f->alpha);
+        free(ids);
+    }
+#pragma omp parallel for schedule(dynamic, 64)
+    for (int64_t i = 0; i < n; ++i) {
+        or_eval r0;
+        if (q_ok[i] != 1) {
+            eval_invalid(&r0, q_ok[i] == 0 ? ST_BAD_INPUT : ST_NO_SUPPORT);
+            if (d) d[i] = r0.d;
+            if (grad) for (int a = 0; a < 3; ++a) grad[3 * i + a] = 0.0;
+            if (var) var[i] = r0.v;
+            if (status) status[i] = (uint8_t)r0.status;
+            if (n_nodes) n_nodes[i] = 0;
+            continue;
+        }
+        double xs[3] = {(double)q[3 * i], (double)q[3 * i + 1], (double)q[3 * i + 2]};
+        node_c nc[27];
+        int nn = 0;
+        const int64_t* C = q_c + 3 * i;
+        for (int dz = -1; dz <= 1; ++dz)
+            for (int dy = -1; dy <= 1; ++dy)
+                for (int dx = -1; dx <= 1; ++dx) {
+                    int64_t F[3] = {C[0] + dx, C[1] + dy, C[2] + dz};
+                    uint64_t k = pack_key(F[0], F[1], F[2]);
+                    int64_t l = find_key(S->lkey, S->nl, k);
+                    if (l < 0) continue;
+                    double e2 = 0.0;
+                    for (int a = 0; a < 3; ++a) {
+                        double c = ((double)(8 * F[a]) + 3.5) * P->voxel_size;
+                        double e = xs[a] - c;
+                        e2 += e * e;
+                    }
+                    nc[nn].d2 = e2; nc[nn].key = k; nc[nn].l = l; ++nn;
+                }
+        qsort(nc, (size_t)nn, sizeof(node_c), cmp_node);
+        if (nn > Qmax) nn = Qmax;
+        double dq[27], vq[27], gq[27][3];
+        int stq[27];
+        int n_ok = 0, first_status = ST_NO_SUPPORT;
+        double dmin = INFINITY;
+        for (int t = 0; t < nn; ++t) {
+            ifit* f = &fits[nc[t].l];
+            or_eval r;
+            double* kb = (double*)malloc(sizeof(double) * (f->N + 1));
+            double* vb = (double*)malloc(sizeof(double) * (f->N + 1));
+            if (!f->ok) eval_invalid(&r, ST_FACTOR_FAIL);
+            else gp_eval(f->X, f->N, f->L, f->alpha, xs, P, want_var, kb, vb, &r);
+            free(kb); free(vb);
+            dq[t] = r.d; vq[t] = r.v; stq[t] = r.status;
+            for (int a = 0; a < 3; ++a) gq[t][a] = r.gd[a];
+            if (t == 0) first_status = r.status;
+            if (r.status == ST_OK) { ++n_ok; if (r.d < dmin) dmin = r.d; }
+        }
+        double dd, g[3] = {0.0, 0.0, 0.0}, vv = NAN;
+        int st;
+        if (n_ok == 0) {
+            st = first_status;
+            dd = (st == ST_CLAMPED) ? P->d_max : INFINITY;
+            vv = INFINITY;
+        } else {
+            double sw = 0.0, swd = 0.0, swv = 0.0;
+            for (int t = 0; t < nn; ++t) {
+                if (stq[t] != ST_OK) continue;
+                double w = exp(-lambda * (dq[t] - dmin));
+                sw += w; swd += w * dq[t]; swv += w * vq[t];
+                for (int a = 0; a < 3; ++a) g[a] += gq[t][a];
+            }
+            dd = swd / sw;
+            vv = swv / sw;
+            for (int a = 0; a < 3; ++a) g[a] /= (double)n_ok;
+            st = ST_OK;
+        }
+        if (d) d[i] = dd;
+        if (grad) for (int a = 0; a < 3; ++a) grad[3 * i + a] = g[a];
+        if (var) var[i] = want_var ? vv : NAN;
+        if (status) status[i] = (uint8_t)st;
+        if (n_nodes) n_nodes[i] = nn;
+    }
+    for (int64_t l = 0; l < S->nl; ++l) if (have[l]) ifit_free(&fits[l]);
+    free(fits); free(have); free(need_list); free(q_c); free(q_ok);
+    return 0;
+}
+
+/* ------------------------------------------------------------------------------------ */
 void or_set_threads(int n) {
 #ifdef _OPENMP
     if (n > 0) omp_set_num_threads(n);

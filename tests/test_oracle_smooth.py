@@ -1,0 +1,106 @@
+"""Pins of the oracle's blended per-leaf G-GPDF (Sec. IV-D, Eq. 10 read as a smooth minimum):
+one node reduces to that leaf's GP, two nodes follow the closed-form blend, the node choice
+and the per-leaf cap match brute force, and the blend tends to the minimum / the mean as
+lambda grows / vanishes."""
+import itertools
+
+import numpy as np
+
+
+def _leaf(p, vs=0.1):
+    return tuple(np.floor_divide(np.floor(np.asarray(p, np.float64) / vs + 0.5).astype(np.int64), 8))
+
+
+def test_single_leaf_reduces_to_its_gp(orc):
+    rng = np.random.default_rng(1)
+    pts = rng.uniform(0.0, 0.7, (40, 3)).astype(np.float32)
+    assert len({_leaf(p) for p in pts}) == 1
+    S = orc.Surface(pts, orc.params(max_pts_leaf=64))
+    q = rng.uniform(-0.5, 1.2, (200, 3)).astype(np.float32)
+    r = S.query_smooth(q, n_nodes=8, lam=100.0)
+    ref = orc.gp_single(pts.astype(np.float64), q.astype(np.float64))
+    assert np.all(r["n_nodes"] == 1)
+    assert np.array_equal(r["status"], ref.status)
+    ok = ref.status == 0
+    np.testing.assert_allclose(r["d"][ok], ref.d[ok], rtol=1e-12, atol=1e-14)
+    np.testing.assert_allclose(r["grad"][ok], ref.grad[ok], rtol=1e-10, atol=1e-13)
+    np.testing.assert_allclose(r["var"][ok], ref.var[ok], rtol=1e-10)
+
+
+def _two_leaf_scene(rng):
+    a = rng.uniform([0.0, 0.0, 0.0], [0.7, 0.7, 0.1], (30, 3))
+    b = rng.uniform([0.8, 0.0, 0.3], [1.5, 0.7, 0.45], (25, 3))
+    return a, b
+
+
+def test_two_leaves_closed_form_blend(orc):
+    rng = np.random.default_rng(2)
+    a, b = _two_leaf_scene(rng)
+    pts = np.vstack([a, b]).astype(np.float32)
+    S = orc.Surface(pts, orc.params(max_pts_leaf=64))
+    # query leaves x in {0, 1}: both occupied leaves are in every query's neighbourhood
+    q = rng.uniform([-0.04, -0.2, 0.2], [1.54, 0.9, 1.0], (100, 3)).astype(np.float32)
+    for lam in (100.0, 3.0):
+        r = S.query_smooth(q, n_nodes=8, lam=lam)
+        ra = orc.gp_single(pts[:30].astype(np.float64), q.astype(np.float64))
+        rb = orc.gp_single(pts[30:].astype(np.float64), q.astype(np.float64))
+        both = (ra.status == 0) & (rb.status == 0)
+        assert both.sum() > 50
+        dmin = np.minimum(ra.d, rb.d)
+        wa = np.exp(-lam * (ra.d - dmin))
+        wb = np.exp(-lam * (rb.d - dmin))
+        d = (wa * ra.d + wb * rb.d) / (wa + wb)
+        np.testing.assert_allclose(r["d"][both], d[both], rtol=1e-12, atol=1e-14)
+        np.testing.assert_allclose(r["grad"][both], 0.5 * (ra.grad + rb.grad)[both], rtol=1e-10, atol=1e-13)
+        v = (wa * ra.var + wb * rb.var) / (wa + wb)
+        np.testing.assert_allclose(r["var"][both], v[both], rtol=1e-10)
+    hi = S.query_smooth(q, lam=1e5)
+    lo = S.query_smooth(q, lam=1e-12)
+    np.testing.assert_allclose(hi["d"][both], dmin[both], rtol=0, atol=1e-6)
+    np.testing.assert_allclose(lo["d"][both], 0.5 * (ra.d + rb.d)[both], rtol=1e-9)
+
+
+def test_node_choice_and_leaf_cap_brute_force(orc):
+    rng = np.random.default_rng(3)
+    pts = np.vstack([rng.normal(c, 0.3, (n, 3)) for c, n in (((0, 0, 0), 400), ((1.3, -0.4, 0.2), 150))])
+    pts = pts.astype(np.float32)
+    cap, Q = 25, 3
+    P = orc.params(max_pts_leaf=cap)
+    S = orc.Surface(pts, P)
+    q = rng.uniform(-1.0, 1.8, (60, 3)).astype(np.float32)
+    r = S.query_smooth(q, n_nodes=Q, lam=100.0, want_var=False)
+    leaves = {}
+    for i, p in enumerate(pts):
+        leaves.setdefault(_leaf(p), []).append(i)
+    for i in range(len(q)):
+        M = _leaf(q[i])
+        nb = [(M[0] + a, M[1] + b, M[2] + c) for a, b, c in itertools.product((-1, 0, 1), repeat=3)]
+        if not any(F in leaves for F in nb):
+            continue  # fallback centre: covered by the neighbourhood tests
+        cands = []
+        for F in nb:
+            if F not in leaves:
+                continue
+            cen = (8 * np.array(F, np.float64) + 3.5) * 0.1
+            e = q[i].astype(np.float64) - cen
+            cands.append((float(e @ e), int(orc.pack_key(np.array(F))), F))
+        cands.sort()
+        nodes = [c[2] for c in cands[:Q]]
+        assert r["n_nodes"][i] == len(nodes)
+        ds, gs, ok = [], [], []
+        for F in nodes:
+            ids = leaves[F]
+            cen = (8 * np.array(F, np.float64) + 3.5) * 0.1
+            if len(ids) > cap:
+                dd = [(float(np.sum((pts[j].astype(np.float64) - cen) ** 2)), j) for j in ids]
+                ids = sorted(j for _, j in sorted(dd)[:cap])
+            rr = orc.gp_single(pts[ids].astype(np.float64), q[i:i + 1].astype(np.float64), want_var=False)
+            if rr.status[0] == 0:
+                ds.append(rr.d[0])
+                gs.append(rr.grad[0])
+        if not ds:
+            continue
+        ds = np.array(ds)
+        w = np.exp(-100.0 * (ds - ds.min()))
+        assert abs(r["d"][i] - np.sum(w * ds) / np.sum(w)) <= 1e-12
+        np.testing.assert_allclose(r["grad"][i], np.mean(gs, axis=0), rtol=1e-10, atol=1e-13)
