@@ -143,6 +143,10 @@ def run_ours(args):
         m.set_surface(S)
         m.query(Q, grad=True, var=False, out=out)
 
+    # launch shapes per size bucket from the library's autotuner, on a query subset
+    m.set_surface(S)
+    tuned = m.autotune(Q[: min(nq, args.n_tune)].contiguous())
+
     for _ in range(args.warmup):
         step()
     torch.cuda.synchronize()
@@ -221,7 +225,7 @@ def run_ours(args):
                        "variance": False, "l2": "inputs+outputs (~460 MB) larger than L2",
                        "parallelism": f"replicas x{ws}" if ws > 1 else "single GPU",
                        "instances": st["n_instances"], "query_leaves": st["n_groups"],
-                       "bucket_count": st["bucket_count"]},
+                       "bucket_count": st["bucket_count"], "autotuned_launch": tuned},
             "e2e": {"value": e_value, "unit": UNIT,
                     "h2d_bytes_per_step": int(S_h.nbytes + Q_h.nbytes), "d2h_bytes_per_step": int(nq * 32)},
             "gpu_launches": launches,
@@ -275,6 +279,11 @@ def comparisons(S, Q, S_h, args):
         res[name] = nsub / t
     out["subset_queries"] = nsub
     out["subset_queries_per_s"] = res
+    # G-GPDF as blended per-leaf GPs (Eq. 10, 8 nodes, lambda 100 / m), the full 10M queries
+    msm = Map(precision="mixed", max_pts_leaf=512)
+    t = _timed(lambda: (msm.set_surface(S), msm.query_smooth(Q, n_nodes=8, lam=100.0, grad=True)))
+    out["smooth_min_8_nodes"] = {"queries": int(Q.shape[0]), "queries_per_s": Q.shape[0] / t,
+                                 "leaf_gps": msm.stats()["n_instances"]}
     # plain FP64 per-instance launches (the comparison form), on a smaller subset
     npi = min(args.n_per_instance, Q.shape[0])
     Qp = Q[:npi].contiguous()
@@ -377,8 +386,9 @@ def main():
     ap.add_argument("--ref-sample", type=int, default=1000)
     ap.add_argument("--quick", action="store_true", help="skip the comparison lines")
     ap.add_argument("--n-sub", type=int, default=1_000_000, help="queries of the precision comparison subset")
-    ap.add_argument("--n-per-instance", type=int, default=50_000, help="queries of the per-instance comparison")
+    ap.add_argument("--n-per-instance", type=int, default=5_000, help="queries of the per-instance comparison")
     ap.add_argument("--room-frames", type=int, default=10)
+    ap.add_argument("--n-tune", type=int, default=1_000_000, help="queries the autotuner times")
     ap.add_argument("--sweep-inst", type=int, default=20_000)
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     args = ap.parse_args()

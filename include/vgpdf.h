@@ -139,6 +139,9 @@ typedef struct {
     double sum_n3;        /* sum of N^3 over instances */
     double sum_n2;        /* sum of N^2 over instances */
     double t_solve_ms;    /* GP solve kernels (factorise + evaluate), if params.profile */
+    double t_bucket_ms[5];   /* the same per size bucket */
+    int32_t cfg_threads[5];  /* launch shape used per bucket: threads per CTA ... */
+    int32_t cfg_per_sm[5];   /* ... and cap on CTAs per SM (0: occupancy limit) */
     int64_t grid_leaves;  /* leaves in the global grid */
     int64_t grid_capacity_leaves;
 } vgp_stats;
@@ -243,6 +246,33 @@ int vgp_set_surface(vgp_map* m, const float* pts_dev, int64_t n, vgp_stream stre
 int vgp_query_distance_gradient(vgp_map* m, const float* q_dev, int64_t n, double* d_dev,
                                 double* grad_dev, double* var_dev, uint8_t* status_dev,
                                 vgp_stream stream);
+
+/*
+ * G-GPDF as blended per-leaf GPs (Sec. IV-D, Eq. 10).  Every occupied surface leaf is one GP
+ * node trained on its points (at most max_pts_leaf, those nearest the leaf centre, ties to the
+ * lower index).  For each query, the n_nodes nodes nearest to it (FP64 squared distance to
+ * the leaf centre, ties to the smaller key) among the occupied leaves in the 27-leaf
+ * neighbourhood of its centre leaf (the centre rule of vgp_query_distance_gradient) each give
+ * d_q, grad d_q, v_q (Eqs. 1-5); Eq. 10 is read as a smooth minimum:
+ *   d = sum_q w_q d_q / sum_q w_q,  w_q = exp(-lambda (d_q - min_q d_q)),
+ * over the nodes with status OK; grad d = the plain average of their gradients (the paper
+ * averages the nodes' gradients); var = sum_q w_q v_q / sum_q w_q.  If no node is OK the
+ * status is that of the nearest node.  n_nodes in [1, 27]; lambda > 0 (the paper uses 100
+ * per metre).  Outputs as for vgp_query_distance_gradient (grad_dev, var_dev, status_dev may
+ * be NULL).  Uses n * n_nodes pair buffers in the map's arena.  Synchronises the stream.
+ */
+int vgp_query_smooth(vgp_map* m, const float* q_dev, int64_t n, int32_t n_nodes, double lambda, double* d_dev,
+                     double* grad_dev, double* var_dev, uint8_t* status_dev, vgp_stream stream);
+
+/*
+ * Autotuner of the GP solve launch shapes: plans the given queries against the current
+ * surface (as vgp_query_distance_gradient does), then solves the batch once with each of four
+ * candidate launch shapes (threads per CTA, CTAs per SM) for every size bucket, times each
+ * bucket with CUDA events, and keeps the fastest shape per bucket for later calls on this map
+ * (L-GPDF frames, queries, batches).  Outputs nothing else; the chosen shapes and bucket
+ * times appear in vgp_stats.  VGP_ERR_STATE before vgp_set_surface.  Synchronises the stream.
+ */
+int vgp_autotune(vgp_map* m, const float* q_dev, int64_t n, vgp_stream stream);
 
 /*
  * Backward pass of a scalar loss L through vgp_query_distance_gradient, with the discrete

@@ -30,7 +30,8 @@ class VgpStats(C.Structure):
     _fields_ = [("n_points", C.c_int64), ("n_leaves", C.c_int64), ("n_instances", C.c_int64),
                 ("n_train", C.c_int64), ("n_queries", C.c_int64), ("n_groups", C.c_int64),
                 ("bucket_count", C.c_int64 * 5), ("sum_n3", C.c_double), ("sum_n2", C.c_double),
-                ("t_solve_ms", C.c_double), ("grid_leaves", C.c_int64), ("grid_capacity_leaves", C.c_int64)]
+                ("t_solve_ms", C.c_double), ("t_bucket_ms", C.c_double * 5),
+                ("cfg_threads", C.c_int32 * 5), ("cfg_per_sm", C.c_int32 * 5), ("grid_leaves", C.c_int64), ("grid_capacity_leaves", C.c_int64)]
 
 
 # (name, restype, argtypes)
@@ -50,6 +51,8 @@ SIGNATURES = [
     ("vgp_set_surface", _i32, [_vp, _vp, _i64, _vp]),
     ("vgp_query_distance_gradient", _i32, [_vp, _vp, _i64, _vp, _vp, _vp, _vp, _vp]),
     ("vgp_query_backward", _i32, [_vp, _vp, _i64, _vp, _vp, _vp, _vp]),
+    ("vgp_autotune", _i32, [_vp, _vp, _i64, _vp]),
+    ("vgp_query_smooth", _i32, [_vp, _vp, _i64, C.c_int32, C.c_double, _vp, _vp, _vp, _vp, _vp]),
     ("vgp_gp_batch", _i32, [_vp, _i64, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp]),
     ("vgp_gp_batch_static", _i32, [C.POINTER(VgpParams), _i64, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp]),
     ("vgp_get_stats", _i32, [_vp, C.POINTER(VgpStats)]),

@@ -182,6 +182,26 @@ class Map:
                                                      _stream()))
         return dict(d=d, grad=g, var=v, status=s)
 
+    def query_smooth(self, q, n_nodes: int = 8, lam: float = 100.0, grad: bool = True, var: bool = False) -> dict:
+        """G-GPDF as per-leaf GPs blended by the smooth minimum of Eq. 10 (vgp_query_smooth)."""
+        q = _dev_f32(q, "q")
+        n = q.shape[0]
+        d = torch.empty(n, dtype=torch.float64, device="cuda")
+        g = torch.empty((n, 3), dtype=torch.float64, device="cuda") if grad else None
+        v = torch.empty(n, dtype=torch.float64, device="cuda") if var else None
+        s = torch.empty(n, dtype=torch.uint8, device="cuda")
+        L.check(L.load().vgp_query_smooth(self._h, _ptr(q), n, int(n_nodes), float(lam), _ptr(d), _ptr(g), _ptr(v),
+                                          _ptr(s), _stream()))
+        return dict(d=d, grad=g, var=v, status=s)
+
+    def autotune(self, q) -> dict:
+        """Pick the fastest launch shape per size bucket on these queries (vgp_autotune)."""
+        q = _dev_f32(q, "q")
+        L.check(L.load().vgp_autotune(self._h, _ptr(q), q.shape[0], _stream()))
+        st = self.stats()
+        return {"threads": list(st["cfg_threads"]), "per_sm": list(st["cfg_per_sm"]),
+                "bucket_ms": list(st["t_bucket_ms"])}
+
     def query_backward(self, q, dL_dd, want_dq: bool = True, want_dX: bool = True):
         q = _dev_f32(q, "q")
         n = q.shape[0]
@@ -211,7 +231,8 @@ class Map:
         st = L.VgpStats()
         L.check(L.load().vgp_get_stats(self._h, C.byref(st)))
         out = {k: getattr(st, k) for k, _ in L.VgpStats._fields_}
-        out["bucket_count"] = list(st.bucket_count)
+        for k in ("bucket_count", "t_bucket_ms", "cfg_threads", "cfg_per_sm"):
+            out[k] = list(getattr(st, k))
         return out
 
     def sync(self):

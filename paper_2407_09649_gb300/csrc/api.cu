@@ -116,6 +116,7 @@ struct vgp_map {
     int64_t s_idx_cap = 0, s_off_cap = 0;
     bool has_surface = false;
     vgp_stats stats{};
+    SolveConfig cfg;  // launch shape per size bucket (vgp_autotune)
 };
 
 struct vgp_frame {
@@ -414,7 +415,7 @@ int vgp_build_frame(vgp_map* m, const float* pts, int64_t n, vgp_stream stream, 
     b.alpha_out = f->alpha;
     b.want_var = 1;
     SolveStats ss;
-    solve_batch(b, P, m->dev_words, st, m->ar, &ss, nullptr, m->prm.profile != 0, m->prm.launch);
+    solve_batch(b, P, m->dev_words, st, m->ar, &ss, nullptr, m->prm.profile != 0, m->prm.launch, &m->cfg);
     if (read_words(m, st) != VGP_OK) return bail(VGP_ERR_CUDA, "sync failed");
     if (m->host_words[4] != 0) return bail(VGP_ERR_STATE, "testing voxel without a neighbouring GP leaf");
     cudaError_t ce = cudaGetLastError();
@@ -427,6 +428,11 @@ int vgp_build_frame(vgp_map* m, const float* pts, int64_t n, vgp_stream stream, 
     S.sum_n3 = ss.sum_n3;
     S.sum_n2 = ss.sum_n2;
     S.t_solve_ms = ss.t_solve_ms;
+    for (int i = 0; i < 5; ++i) {
+        S.t_bucket_ms[i] = ss.t_bucket_ms[i];
+        S.cfg_threads[i] = m->cfg.threads[i];
+        S.cfg_per_sm[i] = m->cfg.per_sm[i];
+    }
     S.grid_leaves = m->g_leaves;
     S.grid_capacity_leaves = m->pool_cap;
     m->stats = S;
@@ -703,12 +709,17 @@ struct QueryPlan {
     int64_t* qidx = nullptr;
 };
 
-static int plan_queries(vgp_map* m, const float* q, int64_t n, double* d, double* grad, double* var, uint8_t* status,
-                        cudaStream_t st, QueryPlan& Q) {
+// Query leaves (groups) of a batch and the centre leaf of each group's neighbourhood.
+struct GroupPlan {
+    int ng = 0;
+    int32_t* q_slot = nullptr;      // per query: slot in the query-leaf table, < 0 invalid
+    int32_t* slot2group = nullptr;
+    uint64_t* gcen = nullptr;       // per group: centre leaf key, kEmpty if no support
+};
+
+static int plan_groups(vgp_map* m, const float* q, int64_t n, cudaStream_t st, GroupPlan& G) {
     const DevParams& P = m->P;
-    Q.n = n;
     CUDA_TRY(cudaMemsetAsync(m->dev_words, 0, sizeof(int) * 8, st));
-    // query leaves (groups)
     Table qt;
     uint32_t Cq = pow2_at_least(2 * std::min<int64_t>(std::max<int64_t>(n, 1), 1ll << 21));
     ARENA(q_slot, int32_t, kTmp0, n);
@@ -730,9 +741,26 @@ static int plan_queries(vgp_map* m, const float* q, int64_t n, double* d, double
     TRY(read_words(m, st));
     TRY(check_err(m, "query"));
     const int ng = m->host_words[2];
-    Q.ng = ng;
     ARENA(gcen, uint64_t, kTmp4, ng);
     group_centre(gkeys, ng, m->s_tab, P.search_r, gcen, st);
+    G.ng = ng;
+    G.q_slot = q_slot;
+    G.slot2group = slot2group;
+    G.gcen = gcen;
+    return VGP_OK;
+}
+
+static int plan_queries(vgp_map* m, const float* q, int64_t n, double* d, double* grad, double* var, uint8_t* status,
+                        cudaStream_t st, QueryPlan& Q) {
+    const DevParams& P = m->P;
+    Q.n = n;
+    GroupPlan G;
+    TRY(plan_groups(m, q, n, st, G));
+    const int ng = G.ng;
+    Q.ng = ng;
+    int32_t* q_slot = G.q_slot;
+    int32_t* slot2group = G.slot2group;
+    uint64_t* gcen = G.gcen;
     // unique centres -> instances
     Table it;
     uint32_t Ci = pow2_at_least(2 * (int64_t)std::max(ng, 1));
@@ -808,7 +836,7 @@ int vgp_query_distance_gradient(vgp_map* m, const float* q, int64_t n, double* d
     b.status = status;
     b.want_var = var != nullptr;
     SolveStats ss;
-    solve_batch(b, m->P, m->dev_words, st, m->ar, &ss, nullptr, m->prm.profile != 0, m->prm.launch);
+    solve_batch(b, m->P, m->dev_words, st, m->ar, &ss, nullptr, m->prm.profile != 0, m->prm.launch, &m->cfg);
     CUDA_TRY(cudaGetLastError());
     vgp_stats S{};
     S.n_points = m->s_n;
@@ -821,9 +849,169 @@ int vgp_query_distance_gradient(vgp_map* m, const float* q, int64_t n, double* d
     S.sum_n3 = ss.sum_n3;
     S.sum_n2 = ss.sum_n2;
     S.t_solve_ms = ss.t_solve_ms;
+    for (int i = 0; i < 5; ++i) {
+        S.t_bucket_ms[i] = ss.t_bucket_ms[i];
+        S.cfg_threads[i] = m->cfg.threads[i];
+        S.cfg_per_sm[i] = m->cfg.per_sm[i];
+    }
     S.grid_leaves = m->g_leaves;
     S.grid_capacity_leaves = m->pool_cap;
     m->stats = S;
+    return VGP_OK;
+}
+
+int vgp_query_smooth(vgp_map* m, const float* q, int64_t n, int32_t n_nodes, double lambda, double* d, double* grad,
+                     double* var, uint8_t* status, vgp_stream stream) {
+    if (!m || n < 0 || (n > 0 && (!q || !d))) return fail(VGP_ERR_ARG, "vgp_query_smooth: bad argument");
+    if (n_nodes < 1 || n_nodes > 27) return fail(VGP_ERR_ARG, "vgp_query_smooth: n_nodes must be in [1, 27]");
+    if (!(lambda > 0.0) || !std::isfinite(lambda)) return fail(VGP_ERR_ARG, "vgp_query_smooth: lambda must be > 0");
+    if (!m->has_surface) return fail(VGP_ERR_STATE, "vgp_query_smooth before vgp_set_surface");
+    if (n == 0) return VGP_OK;
+    if (n * n_nodes >= (1ll << 31)) return fail(VGP_ERR_ARG, "vgp_query_smooth: queries x nodes must be < 2^31");
+    cudaStream_t st = (cudaStream_t)stream;
+    const DevParams& P = m->P;
+    GroupPlan G;
+    TRY(plan_groups(m, q, n, st, G));
+    // nodes: every occupied leaf around each group's centre leaf
+    Table it;
+    uint32_t Ci = pow2_at_least(2 * 27 * (int64_t)std::max(G.ng, 1));
+    it.mask = Ci - 1;
+    it.keys = (uint64_t*)m->ar.get(Arena::kTmp5, sizeof(uint64_t) * Ci, st);
+    ARENA(islot2inst, int32_t, kTmp6, Ci);
+    ARENA(ikeys, uint64_t, kTmp7, Ci);
+    if (!it.keys) return fail(VGP_ERR_OOM, "node table allocation failed");
+    CUDA_TRY(cudaMemsetAsync(it.keys, 0xFF, sizeof(uint64_t) * Ci, st));
+    smooth_nodes(G.gcen, G.ng, m->s_tab, it, m->dev_words, st);
+    collect_table(it, islot2inst, nullptr, ikeys, m->dev_words + 2, Ci, m->dev_words, st);
+    TRY(read_words(m, st));
+    TRY(check_err(m, "vgp_query_smooth"));
+    const int ni = m->host_words[2];
+    // one GP per node leaf, capped to the points nearest its centre
+    ARENA(ncand, int64_t, kTmp8, ni + 1);
+    ARENA(ninst, int64_t, kTmp9, ni + 1);
+    ARENA(inst_off, int64_t, kTmp10, ni + 1);
+    inst_count(ikeys, ni, m->s_tab, m->s_slot2leaf, m->s_off, P.cap_leaf, ncand, ninst, st, 1);
+    exclusive_scan_i64(ninst, inst_off, ni, st, m->ar);
+    int64_t T = 0;
+    CUDA_TRY(cudaMemcpyAsync(&T, inst_off + ni, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+    CUDA_TRY(cudaStreamSynchronize(st));
+    ARENA(Xl, double, kTmp11, 3 * T);
+    ARENA(Xf, float, kTmp12, 3 * T);
+    ARENA(gidx, int64_t, kTmp13, T);
+    ARENA(centre, double, kTmp14, 3 * (int64_t)ni);
+    inst_gather(ikeys, ni, m->s_tab, m->s_slot2leaf, m->s_off, m->s_idx, m->s_pts, ncand, inst_off, P, Xl, Xf, gidx,
+                centre, st, 1);
+    // (query, node) pairs grouped by node
+    const int64_t np = n * n_nodes;
+    ARENA(pair_inst, int32_t, kPair0, np);
+    ARENA(nn, uint8_t, kPair1, n);
+    ARENA(cnt, int64_t, kTmp15, ni + 1);
+    ARENA(q_off, int64_t, kTmp16, ni + 1);
+    ARENA(cursor, int64_t, kTmp17, ni + 1);
+    ARENA(qidx, int64_t, kPair2, np);
+    ARENA(pd, double, kPair3, np);
+    ARENA(pg, double, kPair4, 3 * np);
+    ARENA(ps, uint8_t, kPair5, np);
+    double* pv = nullptr;
+    if (var) {
+        pv = (double*)m->ar.get(Arena::kPair6, sizeof(double) * np, st);
+        if (!pv) return fail(VGP_ERR_OOM, "device allocation failed");
+    }
+    CUDA_TRY(cudaMemsetAsync(cnt, 0, sizeof(int64_t) * (ni + 1), st));
+    CUDA_TRY(cudaMemsetAsync(cursor, 0, sizeof(int64_t) * (ni + 1), st));
+    smooth_pairs(q, n, G.q_slot, G.slot2group, G.gcen, m->s_tab, it, islot2inst, P, n_nodes, pair_inst, nn, cnt, st);
+    exclusive_scan_i64(cnt, q_off, ni, st, m->ar);
+    smooth_scatter(pair_inst, np, q_off, cursor, qidx, st);
+    CUDA_TRY(cudaMemsetAsync(ps, 0xFF, np, st));
+    SolveBatch b;
+    b.n_inst = ni;
+    b.inst_off = inst_off;
+    b.Xl = Xl;
+    b.Xf = Xf;
+    b.centre = centre;
+    b.q_off = q_off;
+    b.qidx = qidx;
+    b.qdiv = n_nodes;
+    b.qxyz = q;
+    b.d = pd;
+    b.grad = pg;
+    b.var = pv;
+    b.status = ps;
+    b.want_var = var != nullptr;
+    SolveStats ss;
+    solve_batch(b, P, m->dev_words, st, m->ar, &ss, nullptr, m->prm.profile != 0, m->prm.launch, &m->cfg);
+    smooth_blend(n, n_nodes, G.q_slot, nn, pd, pg, pv, ps, lambda, P, d, grad, var, status, st);
+    CUDA_TRY(cudaGetLastError());
+    vgp_stats S{};
+    S.n_points = m->s_n;
+    S.n_leaves = m->s_nl;
+    S.n_instances = ni;
+    S.n_train = T;
+    S.n_queries = n;
+    S.n_groups = G.ng;
+    for (int i = 0; i < 5; ++i) {
+        S.bucket_count[i] = ss.bucket_count[i];
+        S.t_bucket_ms[i] = ss.t_bucket_ms[i];
+        S.cfg_threads[i] = m->cfg.threads[i];
+        S.cfg_per_sm[i] = m->cfg.per_sm[i];
+    }
+    S.sum_n3 = ss.sum_n3;
+    S.sum_n2 = ss.sum_n2;
+    S.t_solve_ms = ss.t_solve_ms;
+    S.grid_leaves = m->g_leaves;
+    S.grid_capacity_leaves = m->pool_cap;
+    m->stats = S;
+    return VGP_OK;
+}
+
+int vgp_autotune(vgp_map* m, const float* q, int64_t n, vgp_stream stream) {
+    if (!m || n < 0 || (n > 0 && !q)) return fail(VGP_ERR_ARG, "vgp_autotune: bad argument");
+    if (!m->has_surface) return fail(VGP_ERR_STATE, "vgp_autotune before vgp_set_surface");
+    if (n == 0) return VGP_OK;
+    if (n >= (1ll << 31)) return fail(VGP_ERR_ARG, "at most 2^31 - 1 queries per call");
+    cudaStream_t st = (cudaStream_t)stream;
+    double* dtmp = (double*)m->ar.get(Arena::kBw0, sizeof(double) * n, st);
+    if (!dtmp) return fail(VGP_ERR_OOM, "allocation failed");
+    QueryPlan Q;
+    TRY(plan_queries(m, q, n, dtmp, nullptr, nullptr, nullptr, st, Q));
+    SolveBatch b;
+    b.n_inst = Q.ni;
+    b.inst_off = Q.inst_off;
+    b.Xl = Q.Xl;
+    b.Xf = Q.Xf;
+    b.centre = Q.centre;
+    b.q_off = Q.q_off;
+    b.qidx = Q.qidx;
+    b.qxyz = q;
+    b.d = dtmp;
+    // candidate launch shapes (threads per CTA, CTAs per SM cap) per size bucket
+    const int cand_t[4][5] = {{512, 512, 256, 128, 64}, {256, 256, 128, 64, 32},
+                              {256, 384, 512, 256, 128}, {128, 128, 64, 32, 256}};
+    const int cand_p[4][5] = {{1, 0, 0, 0, 0}, {2, 0, 0, 0, 0}, {1, 0, 0, 0, 0}, {4, 0, 0, 0, 0}};
+    double best[5] = {1e300, 1e300, 1e300, 1e300, 1e300};
+    SolveConfig chosen = m->cfg;
+    for (int c = 0; c < 4; ++c) {
+        SolveConfig cfg;
+        for (int i = 0; i < 5; ++i) {
+            cfg.threads[i] = cand_t[c][i];
+            cfg.per_sm[i] = cand_p[c][i];
+        }
+        SolveStats ss;
+        solve_batch(b, m->P, m->dev_words, st, m->ar, &ss, nullptr, true, 0, &cfg);
+        CUDA_TRY(cudaGetLastError());
+        for (int i = 0; i < 5; ++i)
+            if (ss.bucket_count[i] > 0 && ss.t_bucket_ms[i] < best[i]) {
+                best[i] = ss.t_bucket_ms[i];
+                chosen.threads[i] = cfg.threads[i];
+                chosen.per_sm[i] = cfg.per_sm[i];
+            }
+    }
+    m->cfg = chosen;
+    for (int i = 0; i < 5; ++i) {
+        m->stats.cfg_threads[i] = chosen.threads[i];
+        m->stats.cfg_per_sm[i] = chosen.per_sm[i];
+        m->stats.t_bucket_ms[i] = best[i] < 1e299 ? best[i] : 0.0;
+    }
     return VGP_OK;
 }
 
@@ -858,7 +1046,7 @@ int vgp_query_backward(vgp_map* m, const float* q, int64_t n, const double* dL_d
     bw.dL_dq = dL_dq;
     bw.dL_dX = dL_dX;
     bw.obar = obar;
-    solve_batch(b, m->P, m->dev_words, st, m->ar, nullptr, &bw);
+    solve_batch(b, m->P, m->dev_words, st, m->ar, nullptr, &bw, false, 0, &m->cfg);
     CUDA_TRY(cudaStreamSynchronize(st));
     CUDA_TRY(cudaGetLastError());
     return VGP_OK;
@@ -956,7 +1144,7 @@ extern "C" int vgp_gp_batch(vgp_map* m, int64_t n_inst, const int64_t* inst_off,
     b.status = status;
     b.want_var = var != nullptr;
     SolveStats ss;
-    solve_batch(b, m->P, m->dev_words, st, m->ar, &ss, nullptr, m->prm.profile != 0, m->prm.launch);
+    solve_batch(b, m->P, m->dev_words, st, m->ar, &ss, nullptr, m->prm.profile != 0, m->prm.launch, &m->cfg);
     CUDA_TRY(cudaGetLastError());
     vgp_stats S{};
     S.n_instances = n_inst;
@@ -966,6 +1154,11 @@ extern "C" int vgp_gp_batch(vgp_map* m, int64_t n_inst, const int64_t* inst_off,
     S.sum_n3 = ss.sum_n3;
     S.sum_n2 = ss.sum_n2;
     S.t_solve_ms = ss.t_solve_ms;
+    for (int i = 0; i < 5; ++i) {
+        S.t_bucket_ms[i] = ss.t_bucket_ms[i];
+        S.cfg_threads[i] = m->cfg.threads[i];
+        S.cfg_per_sm[i] = m->cfg.per_sm[i];
+    }
     m->stats = S;
     return VGP_OK;
 }

@@ -527,13 +527,14 @@ __global__ void k_insert_centres(const uint64_t* gcen, int ng, uint64_t* ikeys, 
 
 // Warp per instance: candidate count over the 27 leaves around the centre.
 __global__ void k_inst_count(const uint64_t* ikey, int ni, const uint64_t* skeys, uint32_t smask,
-                             const int32_t* sslot2leaf, const int64_t* soff, int cap, int64_t* ncand, int64_t* ninst) {
+                             const int32_t* sslot2leaf, const int64_t* soff, int cap, int64_t* ncand, int64_t* ninst,
+                             int single) {
     int I = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
     if (I >= ni) return;
     int cx, cy, cz;
     unpack_key(ikey[I], cx, cy, cz);
     int64_t c = 0;
-    if (lane < 27) {
+    if (lane < 27 && (!single || lane == 13)) {
         int64_t s = ht_find(skeys, smask, pack_key(cx + lane % 3 - 1, cy + (lane / 3) % 3 - 1, cz + lane / 9 - 1));
         if (s >= 0) {
             int l = sslot2leaf[s];
@@ -578,7 +579,8 @@ __device__ __forceinline__ int block_excl(int flag, int* warp_tot, int& total) {
 __global__ void __launch_bounds__(256) k_inst_gather(const uint64_t* ikey, const uint64_t* skeys, uint32_t smask,
                                                      const int32_t* sslot2leaf, const int64_t* soff, const int32_t* sidx,
                                                      const float* spts, const int64_t* ncand, const int64_t* inst_off,
-                                                     DevParams P, double* Xl, float* Xf, int64_t* gidx, double* centre) {
+                                                     DevParams P, double* Xl, float* Xf, int64_t* gidx, double* centre,
+                                                     int single) {
     __shared__ int64_t lo[27], cnt[28];
     __shared__ unsigned hist[256];
     __shared__ int warp_tot[8];
@@ -593,7 +595,8 @@ __global__ void __launch_bounds__(256) k_inst_gather(const uint64_t* ikey, const
                          __dmul_rn(__dadd_rn((double)(8 * cz), 3.5), P.vs)};
     if (t < 3) centre[3 * (int64_t)I + t] = c[t];
     if (t < 27) {
-        int64_t s = ht_find(skeys, smask, pack_key(cx + t % 3 - 1, cy + (t / 3) % 3 - 1, cz + t / 9 - 1));
+        int64_t s = (single && t != 13) ? -1
+                                        : ht_find(skeys, smask, pack_key(cx + t % 3 - 1, cy + (t / 3) % 3 - 1, cz + t / 9 - 1));
         if (s >= 0) {
             int l = sslot2leaf[s];
             lo[t] = soff[l];
@@ -775,19 +778,19 @@ void insert_centres(const uint64_t* gcen, int ng, const Table& it, int* err, cud
 }
 
 void inst_count(const uint64_t* ikey, int ni, const Table& s, const int32_t* sslot2leaf, const int64_t* soff, int cap,
-                int64_t* ncand, int64_t* ninst, cudaStream_t st) {
+                int64_t* ncand, int64_t* ninst, cudaStream_t st, int single) {
     if (ni > 0) {
-        k_inst_count<<<nblk((int64_t)ni * 32), TB, 0, st>>>(ikey, ni, s.keys, s.mask, sslot2leaf, soff, cap, ncand, ninst);
+        k_inst_count<<<nblk((int64_t)ni * 32), TB, 0, st>>>(ikey, ni, s.keys, s.mask, sslot2leaf, soff, cap, ncand, ninst, single);
         note_launch();
     }
 }
 
 void inst_gather(const uint64_t* ikey, int ni, const Table& s, const int32_t* sslot2leaf, const int64_t* soff,
                  const int32_t* sidx, const float* spts, const int64_t* ncand, const int64_t* inst_off,
-                 const DevParams& P, double* Xl, float* Xf, int64_t* gidx, double* centre, cudaStream_t st) {
+                 const DevParams& P, double* Xl, float* Xf, int64_t* gidx, double* centre, cudaStream_t st, int single) {
     if (ni > 0)
         k_inst_gather<<<ni, 256, 0, st>>>(ikey, s.keys, s.mask, sslot2leaf, soff, sidx, spts, ncand, inst_off, P, Xl, Xf,
-                                          gidx, centre);
+                                          gidx, centre, single);
         note_launch();
 }
 
@@ -802,6 +805,164 @@ void query_scatter(const int32_t* q_inst, int64_t n, const int64_t* q_off, int64
                    double* grad, double* var, uint8_t* status, cudaStream_t st) {
     if (n > 0) {
         k_query_scatter<<<nblk(n), TB, 0, st>>>(q_inst, n, q_off, cursor, qidx, d, grad, var, status);
+        note_launch();
+    }
+}
+
+// --------------------------------------------------------------------------------------
+// G-GPDF as per-leaf GPs blended by a smooth minimum (Sec. IV-D, Eq. 10)
+// --------------------------------------------------------------------------------------
+namespace {
+// Warp per query group: every occupied leaf of the centre leaf's 27-neighbourhood is a node.
+__global__ void k_smooth_nodes(const uint64_t* gcen, int ng, const uint64_t* skeys, uint32_t smask, uint64_t* ikeys,
+                               uint32_t imask, int* err) {
+    int g = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+    if (g >= ng || lane >= 27 || gcen[g] == kEmpty) return;
+    int cx, cy, cz;
+    unpack_key(gcen[g], cx, cy, cz);
+    const uint64_t k = pack_key(cx + lane % 3 - 1, cy + (lane / 3) % 3 - 1, cz + lane / 9 - 1);
+    if (ht_find(skeys, smask, k) >= 0) ht_insert(ikeys, imask, k, err);
+}
+
+// Thread per query: the Q nodes nearest to the query point (FP64 squared distance to the leaf
+// centre, ties to the smaller key) among the occupied leaves around its centre leaf; one
+// (query, node) pair per chosen node, pair id = query * Q + rank.
+__global__ void k_smooth_pairs(const float* q, int64_t n, const int32_t* q_slot, const int32_t* slot2group,
+                               const uint64_t* gcen, const uint64_t* skeys, uint32_t smask, const uint64_t* ikeys,
+                               uint32_t imask, const int32_t* islot2inst, DevParams P, int Q, int32_t* pair_inst,
+                               uint8_t* n_nodes, int64_t* inst_cnt) {
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    for (int t = 0; t < Q; ++t) pair_inst[i * Q + t] = -1;
+    n_nodes[i] = 0;
+    const int32_t s = q_slot[i];
+    if (s < 0) return;
+    const uint64_t ck = gcen[slot2group[s]];
+    if (ck == kEmpty) return;
+    int cx, cy, cz;
+    unpack_key(ck, cx, cy, cz);
+    const double xs[3] = {(double)q[3 * i], (double)q[3 * i + 1], (double)q[3 * i + 2]};
+    double bd[27];
+    uint64_t bk[27];
+    int nn = 0;
+    for (int t = 0; t < 27; ++t) {
+        const int F[3] = {cx + t % 3 - 1, cy + (t / 3) % 3 - 1, cz + t / 9 - 1};
+        const uint64_t k = pack_key(F[0], F[1], F[2]);
+        if (ht_find(skeys, smask, k) < 0) continue;
+        double e2 = 0.0;
+        for (int a = 0; a < 3; ++a) {
+            const double c = __dmul_rn(__dadd_rn((double)(8 * F[a]), 3.5), P.vs);
+            const double e = __dsub_rn(xs[a], c);
+            e2 = __dadd_rn(e2, __dmul_rn(e, e));
+        }
+        int pos = nn++;
+        while (pos > 0 && (bd[pos - 1] > e2 || (bd[pos - 1] == e2 && bk[pos - 1] > k))) {
+            bd[pos] = bd[pos - 1];
+            bk[pos] = bk[pos - 1];
+            --pos;
+        }
+        bd[pos] = e2;
+        bk[pos] = k;
+    }
+    const int use = nn < Q ? nn : Q;
+    for (int t = 0; t < use; ++t) {
+        const int64_t is = ht_find(ikeys, imask, bk[t]);
+        const int I = is >= 0 ? islot2inst[is] : -1;
+        pair_inst[i * Q + t] = I;
+        if (I >= 0) atomicAdd((unsigned long long*)&inst_cnt[I], 1ull);
+    }
+    n_nodes[i] = (uint8_t)use;
+}
+
+__global__ void k_smooth_scatter(const int32_t* pair_inst, int64_t npairs, const int64_t* q_off, int64_t* cursor,
+                                 int64_t* qidx) {
+    int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (p >= npairs) return;
+    const int32_t I = pair_inst[p];
+    if (I < 0) return;
+    const int64_t r = (int64_t)atomicAdd((unsigned long long*)&cursor[I], 1ull);
+    qidx[q_off[I] + r] = p;
+}
+
+// Thread per query: d = sum_q w_q d_q / sum_q w_q, w_q = exp(-lambda (d_q - min d)) over the
+// valid nodes; gradient = plain average of their gradients; variance = weighted average.
+__global__ void k_smooth_blend(int64_t n, int Q, const int32_t* q_slot, const uint8_t* n_nodes, const double* pd,
+                               const double* pg, const double* pv, const uint8_t* ps, double lambda, DevParams P,
+                               double* d, double* grad, double* var, uint8_t* status) {
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const int nn = n_nodes[i];
+    double dd, g[3] = {0.0, 0.0, 0.0}, vv = INFINITY;
+    int st;
+    if (q_slot[i] < 0 || nn == 0) {
+        st = q_slot[i] < 0 ? VGP_ST_BAD_INPUT : VGP_ST_NO_SUPPORT;
+        dd = INFINITY;
+    } else {
+        double dmin = INFINITY;
+        int n_ok = 0;
+        for (int t = 0; t < nn; ++t)
+            if (ps[i * Q + t] == VGP_ST_OK) {
+                ++n_ok;
+                dmin = fmin(dmin, pd[i * Q + t]);
+            }
+        if (n_ok == 0) {
+            st = ps[i * Q];
+            dd = st == VGP_ST_CLAMPED ? P.d_max : INFINITY;
+        } else {
+            double sw = 0.0, swd = 0.0, swv = 0.0;
+            for (int t = 0; t < nn; ++t) {
+                const int64_t p = i * Q + t;
+                if (ps[p] != VGP_ST_OK) continue;
+                const double w = exp(-lambda * (pd[p] - dmin));
+                sw += w;
+                swd += w * pd[p];
+                if (pv) swv += w * pv[p];
+                for (int a = 0; a < 3; ++a) g[a] += pg[3 * p + a];
+            }
+            dd = swd / sw;
+            vv = pv ? swv / sw : NAN;
+            for (int a = 0; a < 3; ++a) g[a] /= (double)n_ok;
+            st = VGP_ST_OK;
+        }
+    }
+    d[i] = dd;
+    if (grad)
+        for (int a = 0; a < 3; ++a) grad[3 * i + a] = g[a];
+    if (var) var[i] = vv;
+    if (status) status[i] = (uint8_t)st;
+}
+}  // namespace
+
+void smooth_nodes(const uint64_t* gcen, int ng, const Table& s, const Table& it, int* err, cudaStream_t st) {
+    if (ng > 0) {
+        k_smooth_nodes<<<nblk((int64_t)ng * 32), TB, 0, st>>>(gcen, ng, s.keys, s.mask, it.keys, it.mask, err);
+        note_launch();
+    }
+}
+
+void smooth_pairs(const float* q, int64_t n, const int32_t* q_slot, const int32_t* slot2group, const uint64_t* gcen,
+                  const Table& s, const Table& it, const int32_t* islot2inst, const DevParams& P, int Q,
+                  int32_t* pair_inst, uint8_t* n_nodes, int64_t* inst_cnt, cudaStream_t st) {
+    if (n > 0) {
+        k_smooth_pairs<<<nblk(n, 128), 128, 0, st>>>(q, n, q_slot, slot2group, gcen, s.keys, s.mask, it.keys, it.mask,
+                                                     islot2inst, P, Q, pair_inst, n_nodes, inst_cnt);
+        note_launch();
+    }
+}
+
+void smooth_scatter(const int32_t* pair_inst, int64_t npairs, const int64_t* q_off, int64_t* cursor, int64_t* qidx,
+                    cudaStream_t st) {
+    if (npairs > 0) {
+        k_smooth_scatter<<<nblk(npairs), TB, 0, st>>>(pair_inst, npairs, q_off, cursor, qidx);
+        note_launch();
+    }
+}
+
+void smooth_blend(int64_t n, int Q, const int32_t* q_slot, const uint8_t* n_nodes, const double* pd, const double* pg,
+                  const double* pv, const uint8_t* ps, double lambda, const DevParams& P, double* d, double* grad,
+                  double* var, uint8_t* status, cudaStream_t st) {
+    if (n > 0) {
+        k_smooth_blend<<<nblk(n), TB, 0, st>>>(n, Q, q_slot, n_nodes, pd, pg, pv, ps, lambda, P, d, grad, var, status);
         note_launch();
     }
 }

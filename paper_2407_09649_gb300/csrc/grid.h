@@ -41,10 +41,22 @@ void query_leaf(const float* q, int64_t n, const DevParams& P, const Table& t, i
 void group_centre(const uint64_t* gkeys, int ng, const Table& s, int R, uint64_t* gcen, cudaStream_t st);
 void insert_centres(const uint64_t* gcen, int ng, const Table& it, int* err, cudaStream_t st);
 void inst_count(const uint64_t* ikey, int ni, const Table& s, const int32_t* sslot2leaf, const int64_t* soff, int cap,
-                int64_t* ncand, int64_t* ninst, cudaStream_t st);
+                int64_t* ncand, int64_t* ninst, cudaStream_t st, int single = 0);
 void inst_gather(const uint64_t* ikey, int ni, const Table& s, const int32_t* sslot2leaf, const int64_t* soff,
                  const int32_t* sidx, const float* spts, const int64_t* ncand, const int64_t* inst_off,
-                 const DevParams& P, double* Xl, float* Xf, int64_t* gidx, double* centre, cudaStream_t st);
+                 const DevParams& P, double* Xl, float* Xf, int64_t* gidx, double* centre, cudaStream_t st,
+                 int single = 0);
+
+// G-GPDF blended per-leaf GPs (Eq. 10)
+void smooth_nodes(const uint64_t* gcen, int ng, const Table& s, const Table& it, int* err, cudaStream_t st);
+void smooth_pairs(const float* q, int64_t n, const int32_t* q_slot, const int32_t* slot2group, const uint64_t* gcen,
+                  const Table& s, const Table& it, const int32_t* islot2inst, const DevParams& P, int Q,
+                  int32_t* pair_inst, uint8_t* n_nodes, int64_t* inst_cnt, cudaStream_t st);
+void smooth_scatter(const int32_t* pair_inst, int64_t npairs, const int64_t* q_off, int64_t* cursor, int64_t* qidx,
+                    cudaStream_t st);
+void smooth_blend(int64_t n, int Q, const int32_t* q_slot, const uint8_t* n_nodes, const double* pd, const double* pg,
+                  const double* pv, const uint8_t* ps, double lambda, const DevParams& P, double* d, double* grad,
+                  double* var, uint8_t* status, cudaStream_t st);
 void query_route(const int32_t* q_slot, int64_t n, const int32_t* slot2group, const uint64_t* gcen, const Table& it,
                  const int32_t* islot2inst, int32_t* q_inst, int64_t* inst_qcnt, cudaStream_t st);
 void query_scatter(const int32_t* q_inst, int64_t n, const int64_t* q_off, int64_t* cursor, int64_t* qidx, double* d,

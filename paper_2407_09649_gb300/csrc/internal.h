@@ -18,7 +18,8 @@ public:
     enum Slot {
         kScan0, kScan1, kScan2, kHist, kOrder, kTmp0, kTmp1, kTmp2, kTmp3, kTmp4, kTmp5, kTmp6,
         kTmp7, kTmp8, kTmp9, kTmp10, kTmp11, kTmp12, kTmp13, kTmp14, kTmp15, kTmp16, kTmp17,
-        kWs0, kWs1, kWs2, kBw0, kBw1, kCounters, kNumSlots
+        kWs0, kWs1, kWs2, kBw0, kBw1, kPair0, kPair1, kPair2, kPair3, kPair4, kPair5, kPair6, kPair7,
+        kCounters, kNumSlots
     };
     void* get(Slot s, size_t bytes, cudaStream_t st);
     void release_all(cudaStream_t st);
@@ -40,6 +41,7 @@ struct SolveBatch {
     const uint64_t* inst_key = nullptr; // lattice instances: leaf key of each instance
     const int64_t* q_off = nullptr;     // [n_inst + 1] offsets into the position list
     const int64_t* qidx = nullptr;      // position -> query id (nullptr: identity)
+    int qdiv = 1;                       // query point of id q is qxyz[q / qdiv] (pairs)
     const float* qxyz = nullptr;        // world-frame query points (by query id)
     const uint64_t* qkey = nullptr;     // voxel-key queries (by position), if qxyz is null
     double* d = nullptr;                // outputs by query id
@@ -59,8 +61,17 @@ struct BackwardBatch {
     double* obar = nullptr;         // [n_positions] scratch
 };
 
+// Launch shape of the five size buckets of solve_batch (N > 224 with A in global memory,
+// then N <= 224, 128, 64, 32 with A in shared memory): threads per CTA and the cap on
+// resident CTAs per SM (0: as many as fit).  Chosen by vgp_autotune or the defaults.
+struct SolveConfig {
+    int threads[5] = {512, 512, 256, 128, 64};
+    int per_sm[5] = {1, 0, 0, 0, 0};
+};
+
 struct SolveStats {
     int64_t bucket_count[5] = {0, 0, 0, 0, 0};
+    double t_bucket_ms[5] = {0, 0, 0, 0, 0};  // per bucket, when profiling
     double sum_n3 = 0;
     double sum_n2 = 0;
     double t_solve_ms = 0;  // filled when profiling
@@ -79,7 +90,7 @@ void fill_i32(int32_t* p, int32_t v, int64_t n, cudaStream_t st);
 // error bits through *err_dev.  Synchronises once to read the size histogram.
 void solve_batch(const SolveBatch& b, const DevParams& P, int* err_dev, cudaStream_t st,
                  Arena& ar, SolveStats* stats, const BackwardBatch* bw = nullptr, bool profile = false,
-                 int launch = 0);
+                 int launch = 0, const SolveConfig* cfg = nullptr);
 
 // Set the thread-local message returned by vgp_last_error().
 void set_last_error(const char* msg);

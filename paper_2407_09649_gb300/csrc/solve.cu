@@ -23,6 +23,11 @@ namespace {
 __host__ __device__ __forceinline__ int64_t tix(int it, int jt) { return ((int64_t)it * (it + 1) / 2 + jt) * 64; }
 __host__ __device__ __forceinline__ int64_t n_tiles(int nt) { return (int64_t)nt * (nt + 1) / 2; }
 
+// Position of element (r, c) inside a 64-double tile: row major with the columns of rows
+// 2, 3, 6, 7 XOR-swizzled by 4, so the mma fragment loads (row g, column t) of the 32 lanes
+// of a warp hit distinct shared-memory banks in each half-warp.
+__host__ __device__ __forceinline__ int te(int r, int c) { return r * 8 + (c ^ ((r & 2) << 1)); }
+
 // row index of packed-triangle entry p (0 <= col <= row)
 __device__ __forceinline__ int tri_row(int p) {
     int r = (int)((sqrtf(8.0f * (float)p + 1.0f) - 1.0f) * 0.5f);
@@ -132,16 +137,17 @@ __device__ void chol_solve(const Shared& s, const double* A, int Nt, double* out
             const double* D = A + tix(kt, kt);
             for (int r = 0; r < 8; ++r) {
                 double v = z[8 * kt + r];
-                for (int c2 = 0; c2 < r; ++c2) v -= D[r * 8 + c2] * z[8 * kt + c2];
+                for (int c2 = 0; c2 < r; ++c2) v -= D[te(r, c2)] * z[8 * kt + c2];
                 z[8 * kt + r] = v * s.invd[8 * kt + r];
             }
         }
         __syncthreads();
         for (int i = 8 * (kt + 1) + tid; i < Np; i += nt) {
-            const double* T = A + tix(i >> 3, kt) + (i & 7) * 8;
+            const double* T = A + tix(i >> 3, kt);
+            const int r = i & 7;
             double v = z[i];
 #pragma unroll
-            for (int c2 = 0; c2 < 8; ++c2) v -= T[c2] * z[8 * kt + c2];
+            for (int c2 = 0; c2 < 8; ++c2) v -= T[te(r, c2)] * z[8 * kt + c2];
             z[i] = v;
         }
         __syncthreads();
@@ -151,16 +157,17 @@ __device__ void chol_solve(const Shared& s, const double* A, int Nt, double* out
             const double* D = A + tix(kt, kt);
             for (int r = 7; r >= 0; --r) {
                 double v = z[8 * kt + r];
-                for (int c2 = r + 1; c2 < 8; ++c2) v -= D[c2 * 8 + r] * out[8 * kt + c2];
+                for (int c2 = r + 1; c2 < 8; ++c2) v -= D[te(c2, r)] * out[8 * kt + c2];
                 out[8 * kt + r] = v * s.invd[8 * kt + r];
             }
         }
         __syncthreads();
         for (int j = tid; j < 8 * kt; j += nt) {
-            const double* T = A + tix(kt, j >> 3) + (j & 7);
+            const double* T = A + tix(kt, j >> 3);
+            const int cj = j & 7;
             double v = z[j];
 #pragma unroll
-            for (int c2 = 0; c2 < 8; ++c2) v -= T[c2 * 8] * out[8 * kt + c2];
+            for (int c2 = 0; c2 < 8; ++c2) v -= T[te(c2, cj)] * out[8 * kt + c2];
             z[j] = v;
         }
         __syncthreads();
@@ -200,7 +207,7 @@ __device__ bool fit_instance(const SolveCtx& c, const Shared& s, int N, int64_t 
             else if (j > i) v = 0.0;
             else if (j == i) v = 1.0 + c.P.s2;
             else v = kval_pair(c.P, s, lattice, i, j);
-            A[tl * 64 + e] = v;
+            A[tl * 64 + te(e >> 3, e & 7)] = v;
         }
     }
     __syncthreads();
@@ -211,31 +218,31 @@ __device__ bool fit_instance(const SolveCtx& c, const Shared& s, int N, int64_t 
             double* W = s.Tinv;
             bool bad = false;
             for (int j = 0; j < 8 && !bad; ++j) {
-                double v = D[j * 8 + j];
-                for (int k = 0; k < j; ++k) v -= D[j * 8 + k] * D[j * 8 + k];
+                double v = D[te(j, j)];
+                for (int k = 0; k < j; ++k) v -= D[te(j, k)] * D[te(j, k)];
                 if (!(v > 0.0)) {
                     bad = true;
                     break;
                 }
                 const double d = sqrt(v), inv = 1.0 / d;
-                D[j * 8 + j] = d;
+                D[te(j, j)] = d;
                 s.invd[8 * kt + j] = inv;
                 for (int i = j + 1; i < 8; ++i) {
-                    double u = D[i * 8 + j];
-                    for (int k = 0; k < j; ++k) u -= D[i * 8 + k] * D[j * 8 + k];
-                    D[i * 8 + j] = u * inv;
+                    double u = D[te(i, j)];
+                    for (int k = 0; k < j; ++k) u -= D[te(i, k)] * D[te(j, k)];
+                    D[te(i, j)] = u * inv;
                 }
             }
             if (bad) {
                 s_fail = 1;
             } else {
                 for (int j = 0; j < 8; ++j) {
-                    for (int i = 0; i < j; ++i) W[i * 8 + j] = 0.0;
-                    W[j * 8 + j] = s.invd[8 * kt + j];
+                    for (int i = 0; i < j; ++i) W[te(i, j)] = 0.0;
+                    W[te(j, j)] = s.invd[8 * kt + j];
                     for (int i = j + 1; i < 8; ++i) {
                         double u = 0.0;
-                        for (int k = j; k < i; ++k) u += D[i * 8 + k] * W[k * 8 + j];
-                        W[i * 8 + j] = -u * s.invd[8 * kt + i];
+                        for (int k = j; k < i; ++k) u += D[te(i, k)] * W[te(k, j)];
+                        W[te(i, j)] = -u * s.invd[8 * kt + i];
                     }
                 }
             }
@@ -245,18 +252,18 @@ __device__ bool fit_instance(const SolveCtx& c, const Shared& s, int N, int64_t 
         // panel: L_it,kt = A_it,kt * Tinv^T (kept in shared memory too when A is global)
         for (int it = kt + 1 + warp; it < Nt; it += nwarps) {
             double* T = A + tix(it, kt);
-            const double a0 = T[g * 8 + t], a1 = T[g * 8 + 4 + t];
-            const double b0 = s.Tinv[g * 8 + t], b1 = s.Tinv[g * 8 + 4 + t];
+            const double a0 = T[te(g, t)], a1 = T[te(g, 4 + t)];
+            const double b0 = s.Tinv[te(g, t)], b1 = s.Tinv[te(g, 4 + t)];
             double c0 = 0.0, c1 = 0.0;
             dmma(c0, c1, a0, b0);
             dmma(c0, c1, a1, b1);
             __syncwarp();
-            T[g * 8 + 2 * t] = c0;
-            T[g * 8 + 2 * t + 1] = c1;
+            T[te(g, 2 * t)] = c0;
+            T[te(g, 2 * t + 1)] = c1;
             if (s.panel) {
                 double* Pt = s.panel + (it - kt - 1) * 64;
-                Pt[g * 8 + 2 * t] = c0;
-                Pt[g * 8 + 2 * t + 1] = c1;
+                Pt[te(g, 2 * t)] = c0;
+                Pt[te(g, 2 * t + 1)] = c1;
             }
         }
         __syncthreads();
@@ -276,8 +283,8 @@ __device__ bool fit_instance(const SolveCtx& c, const Shared& s, int N, int64_t 
                 const double* Pj = s.panel ? s.panel + jj * 64 : A + tix(kt + 1 + jj, kt);
 #pragma unroll
                 for (int k = 0; k < 2; ++k) {
-                    na[r][k] = ii < M ? neg(Pi[g * 8 + 4 * k + t]) : 0.0;
-                    bb[r][k] = jj < M ? Pj[g * 8 + 4 * k + t] : 0.0;
+                    na[r][k] = ii < M ? neg(Pi[te(g, 4 * k + t)]) : 0.0;
+                    bb[r][k] = jj < M ? Pj[te(g, 4 * k + t)] : 0.0;
                 }
             }
             double cc[2][2][2];
@@ -291,8 +298,8 @@ __device__ bool fit_instance(const SolveCtx& c, const Shared& s, int N, int64_t 
                     cc[r][q][0] = cc[r][q][1] = 0.0;
                     if (valid[r][q]) {
                         const double* C = A + tix(kt + 1 + ii, kt + 1 + jj);
-                        cc[r][q][0] = C[g * 8 + 2 * t];
-                        cc[r][q][1] = C[g * 8 + 2 * t + 1];
+                        cc[r][q][0] = C[te(g, 2 * t)];
+                        cc[r][q][1] = C[te(g, 2 * t + 1)];
                     }
                 }
 #pragma unroll
@@ -307,8 +314,8 @@ __device__ bool fit_instance(const SolveCtx& c, const Shared& s, int N, int64_t 
                 for (int q = 0; q < 2; ++q)
                     if (valid[r][q]) {
                         double* C = A + tix(kt + 1 + i0 + r, kt + 1 + j0 + q);
-                        C[g * 8 + 2 * t] = cc[r][q][0];
-                        C[g * 8 + 2 * t + 1] = cc[r][q][1];
+                        C[te(g, 2 * t)] = cc[r][q][0];
+                        C[te(g, 2 * t + 1)] = cc[r][q][1];
                     }
         }
         __syncthreads();
@@ -390,9 +397,10 @@ __device__ __forceinline__ void query_local(const SolveCtx& c, int I, int64_t p,
         xg[1] = (double)j * c.P.vs;
         xg[2] = (double)k * c.P.vs;
     } else {
-        xg[0] = (double)c.b.qxyz[3 * qid];
-        xg[1] = (double)c.b.qxyz[3 * qid + 1];
-        xg[2] = (double)c.b.qxyz[3 * qid + 2];
+        const int64_t qp = qid / c.b.qdiv;
+        xg[0] = (double)c.b.qxyz[3 * qp];
+        xg[1] = (double)c.b.qxyz[3 * qp + 1];
+        xg[2] = (double)c.b.qxyz[3 * qp + 2];
     }
     for (int a = 0; a < 3; ++a) xl[a] = xg[a] - c.b.centre[3 * (int64_t)I + a];
 }
@@ -489,12 +497,12 @@ __device__ __forceinline__ double latent_var(const DevParams& P, const Shared& s
         }
         const int it = i >> 3, r = i & 7;
         for (int jt = 0; jt < it; ++jt) {
-            const double* T = A + tix(it, jt) + r * 8;
+            const double* T = A + tix(it, jt);
 #pragma unroll
-            for (int c2 = 0; c2 < 8; ++c2) sum -= T[c2] * V[(int64_t)(8 * jt + c2) * stride];
+            for (int c2 = 0; c2 < 8; ++c2) sum -= T[te(r, c2)] * V[(int64_t)(8 * jt + c2) * stride];
         }
-        const double* T = A + tix(it, it) + r * 8;
-        for (int c2 = 0; c2 < r; ++c2) sum -= T[c2] * V[(int64_t)(8 * it + c2) * stride];
+        const double* T = A + tix(it, it);
+        for (int c2 = 0; c2 < r; ++c2) sum -= T[te(r, c2)] * V[(int64_t)(8 * it + c2) * stride];
         const double vi = sum * s.invd[i];
         V[(int64_t)i * stride] = vi;
         acc += vi * vi;
@@ -704,7 +712,9 @@ int solve_launch_static(const SolveBatch& b, const DevParams& P, int* err_dev, i
 }
 
 void solve_batch(const SolveBatch& b, const DevParams& P, int* err_dev, cudaStream_t st, Arena& ar, SolveStats* stats,
-                 const BackwardBatch* bw, bool profile, int launch) {
+                 const BackwardBatch* bw, bool profile, int launch, const SolveConfig* cfg) {
+    const SolveConfig dflt;
+    if (!cfg) cfg = &dflt;
     const int64_t n = b.n_inst;
     if (n <= 0) return;
     // size histogram and decreasing-size order
@@ -744,8 +754,9 @@ void solve_batch(const SolveBatch& b, const DevParams& P, int* err_dev, cudaStre
     struct Bucket {
         int lo, hi, smem_a, threads;
     };
-    const Bucket buckets[] = {{225, 1024, 0, 512}, {129, 224, 1, 512}, {65, 128, 1, 256},
-                              {33, 64, 1, 128},    {0, 32, 1, 64}};
+    const Bucket buckets[] = {{225, 1024, 0, cfg->threads[0]}, {129, 224, 1, cfg->threads[1]},
+                              {65, 128, 1, cfg->threads[2]},   {33, 64, 1, cfg->threads[3]},
+                              {0, 32, 1, cfg->threads[4]}};
     int dev = 0, n_sm = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev);
@@ -820,14 +831,29 @@ void solve_batch(const SolveBatch& b, const DevParams& P, int* err_dev, cudaStre
         int per_sm = 0;
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, bk.threads, shm);
         per_sm = std::max(per_sm, 1);
-        if (!c.a_in_smem) per_sm = 1;  // keep the global working set near L2 size
+        if (cfg->per_sm[bi] > 0) per_sm = std::min(per_sm, cfg->per_sm[bi]);
         const int grid = (int)std::min<int64_t>(cnt, (int64_t)n_sm * per_sm);
         c.ws_a_stride = c.a_in_smem ? 0 : n_tiles(c.npad / 8) * 64;
         c.ws_a = c.a_in_smem ? nullptr : (double*)ar.get(Arena::kWs0, sizeof(double) * c.ws_a_stride * grid, st);
         c.ws_v_stride = (int64_t)c.npad * bk.threads;
         c.ws_v = (b.want_var && !bw) ? (double*)ar.get(Arena::kWs1, sizeof(double) * c.ws_v_stride * grid, st) : nullptr;
+        cudaEvent_t b0 = nullptr, b1 = nullptr;
+        if (profile) {
+            cudaEventCreate(&b0);
+            cudaEventCreate(&b1);
+            cudaEventRecord(b0, st);
+        }
         kern<<<grid, bk.threads, shm, st>>>(c);
         note_launch();
+        if (profile) {
+            cudaEventRecord(b1, st);
+            cudaEventSynchronize(b1);
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, b0, b1);
+            if (stats) stats->t_bucket_ms[bi] += ms;
+            cudaEventDestroy(b0);
+            cudaEventDestroy(b1);
+        }
         done += cnt;
         ++bi;
     }

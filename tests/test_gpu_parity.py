@@ -317,3 +317,45 @@ def test_table_exp_matches_libm(vg):
     _lib.check(_lib.load().vgp_debug_exp_neg(m._h, C.c_void_p(big.data_ptr()), C.c_void_p(r.data_ptr()), 2,
                                              C.c_void_p(torch.cuda.current_stream().cuda_stream)))
     assert r.cpu().tolist() == [0.0, 0.0]
+
+
+# ----------------------------------------------------------------------------------
+# G-GPDF as blended per-leaf GPs (Eq. 10)
+# ----------------------------------------------------------------------------------
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_query_smooth_parity(vg, orc, precision):
+    surf, q = _query_scene(9)
+    P = orc.params(max_pts_leaf=128)
+    S = orc.Surface(surf, P)
+    for n_nodes, lam in ((8, 100.0), (3, 20.0)):
+        ref = S.query_smooth(q, n_nodes=n_nodes, lam=lam, want_var=True)
+        m = vg.Map(precision=precision, max_pts_leaf=128)
+        m.set_surface(torch.from_numpy(surf).cuda())
+        out = m.query_smooth(torch.from_numpy(q).cuda(), n_nodes=n_nodes, lam=lam, grad=True, var=True)
+        d, g, v, s = (out[k].cpu().numpy() for k in ("d", "grad", "var", "status"))
+        ok = ref["status"] == 0
+        assert s[-2] == 3 and s[-1] == 1
+        if precision == "fp64":
+            assert np.array_equal(s, ref["status"])
+            assert np.abs(d[ok] - ref["d"][ok]).max() <= D_TOL
+            big = ok & (np.linalg.norm(ref["grad"], axis=1) > 0.1)
+            assert _angle_deg(g[big], ref["grad"][big]).max() <= ANG_TOL_DEG
+            fin = ok & np.isfinite(ref["var"])
+            np.testing.assert_allclose(v[fin], ref["var"][fin], rtol=1e-5, atol=1e-12)
+        else:
+            mid = ok & (ref["d"] > 2e-3) & (ref["d"] < 9.0)
+            assert np.array_equal(s[mid], ref["status"][mid])
+            assert np.abs(d[mid] - ref["d"][mid]).max() <= D_TOL_MIXED
+
+
+def test_autotune_keeps_results(vg):
+    surf, q = _query_scene(10)
+    m = vg.Map(precision="fp64")
+    m.set_surface(torch.from_numpy(surf).cuda())
+    qt = torch.from_numpy(q).cuda()
+    a = m.query(qt, grad=True)["d"].cpu().numpy()
+    cfg = m.autotune(qt)
+    assert len(cfg["threads"]) == 5 and all(t % 32 == 0 for t in cfg["threads"])
+    b = m.query(qt, grad=True)["d"].cpu().numpy()
+    fin = np.isfinite(a)
+    np.testing.assert_allclose(b[fin], a[fin], rtol=1e-12, atol=1e-14)
