@@ -63,6 +63,9 @@ def lib():
         L.or_gp_batch.restype = C.c_int
         L.or_frame_build.argtypes = [C.POINTER(Params), vp, i64]
         L.or_frame_build.restype = vp
+        L.or_frame_build2.argtypes = [C.POINTER(Params), vp, i64, vp, C.c_int, vp, i64]
+        L.or_frame_build2.restype = vp
+        L.or_frame_signs.argtypes = [vp, vp]
         L.or_frame_free.argtypes = [vp]
         L.or_frame_count.argtypes = [vp, C.c_int]
         L.or_frame_count.restype = i64
@@ -187,14 +190,24 @@ class Frame:
     v: np.ndarray
     grad: np.ndarray
     status: np.ndarray
+    sign: np.ndarray = None
 
 
-def frame(pts, P: Params | None = None) -> Frame:
-    """One L-GPDF frame: voxelise, fit one GP per leaf, infer at all testing voxels."""
+def frame(pts, P: Params | None = None, origin=None, normal_steps: int = 3, known=None) -> Frame:
+    """One L-GPDF frame: voxelise, fit one GP per leaf, infer at all testing voxels.  Without
+    ``origin`` the testing voxels are the dilated GP leaves; with the sensor ``origin`` they are
+    the ray-cast set of Sec. IV-B (``known``: sorted voxel keys with earlier measurements) and
+    the distances are signed."""
     P = P or params()
     pts = _f32(pts)
     L = lib()
-    h = L.or_frame_build(C.byref(P), _p(pts), len(pts))
+    if origin is None:
+        h = L.or_frame_build(C.byref(P), _p(pts), len(pts))
+    else:
+        o = np.ascontiguousarray(origin, np.float64)
+        kn = np.ascontiguousarray(np.sort(np.asarray(known if known is not None else [], np.uint64)), np.uint64)
+        h = L.or_frame_build2(C.byref(P), _p(pts), len(pts), _p(o), int(normal_steps), _p(kn) if len(kn) else None,
+                              len(kn))
     if not h:
         raise MemoryError("oracle frame build failed")
     try:
@@ -205,6 +218,8 @@ def frame(pts, P: Params | None = None) -> Frame:
         L.or_frame_leaves(h, _p(f.leaf_key), _p(f.leaf_nocc), _p(f.inst_off), _p(f.X), _p(f.alpha))
         L.or_frame_tests(h, _p(f.test_key), _p(f.test_inst_key), _p(f.d), _p(f.v), _p(f.grad),
                          _p(f.status))
+        f.sign = np.zeros(nt, np.int8)
+        L.or_frame_signs(h, _p(f.sign))
     finally:
         L.or_frame_free(h)
     return f

@@ -341,6 +341,7 @@ typedef struct {
     double* test_v;
     double* test_grad;
     uint8_t* test_status;
+    int8_t* test_sign;
 } or_frame;
 
 static void voxel_of_bit(const int64_t leaf[3], int bit, int64_t ijk[3]) {
@@ -353,11 +354,143 @@ void or_frame_free(or_frame* F) {
     if (!F) return;
     free(F->leaf_key); free(F->leaf_nocc); free(F->inst_off); free(F->X); free(F->L_off);
     free(F->L); free(F->alpha); free(F->fit_ok); free(F->test_key); free(F->test_inst_key);
-    free(F->test_d); free(F->test_v); free(F->test_grad); free(F->test_status);
+    free(F->test_d); free(F->test_v); free(F->test_grad); free(F->test_status); free(F->test_sign);
     free(F);
 }
 
+/*
+ * Testing points by ray casting from the sensor origin (Sec. IV-B).  The paper casts a ray from
+ * the sensor origin to each surface voxel and queries the voxels on it that hold earlier
+ * measurements, adds voxels along each surface voxel's normal, and signs the distance from
+ * the sensor origin.  Readings taken here:
+ *   - rays: the integer 3D Bresenham line from the origin's voxel to the surface voxel (the
+ *     surface voxel itself excluded); a voxel on it is kept if it is in `known` (voxels of
+ *     the global grid before this frame);
+ *   - normal: smallest-eigenvalue eigenvector of the scatter of the occupied voxels in the
+ *     3x3x3 block around the surface voxel (at least 3 of them), from the exact integer
+ *     matrix n * sum(o o^T) - (sum o)(sum o)^T by cyclic Jacobi rotations in FP64, oriented
+ *     towards the origin; voxels round(s + k n), k = +-1..+-K;
+ *   - sign: + for surface voxels, ray voxels and k > 0, - for k < 0; a voxel reached with
+ *     both signs is +.
+ */
+static void jacobi3(double a[3][3], double v[3][3]) {
+    for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j) v[i][j] = i == j ? 1.0 : 0.0;
+    static const int PQ[3][2] = {{0, 1}, {0, 2}, {1, 2}};
+    for (int sweep = 0; sweep < 12; ++sweep) {
+        for (int r = 0; r < 3; ++r) {
+            int p = PQ[r][0], q = PQ[r][1];
+            if (a[p][q] == 0.0) continue;
+            double theta = (a[q][q] - a[p][p]) / (2.0 * a[p][q]);
+            double t = 1.0 / (fabs(theta) + sqrt(theta * theta + 1.0));
+            if (theta < 0.0) t = -t;
+            double c = 1.0 / sqrt(t * t + 1.0), sn = t * c;
+            for (int k = 0; k < 3; ++k) {
+                double akp = a[k][p], akq = a[k][q];
+                a[k][p] = c * akp - sn * akq;
+                a[k][q] = sn * akp + c * akq;
+            }
+            for (int k = 0; k < 3; ++k) {
+                double apk = a[p][k], aqk = a[q][k];
+                a[p][k] = c * apk - sn * aqk;
+                a[q][k] = sn * apk + c * aqk;
+            }
+            for (int k = 0; k < 3; ++k) {
+                double vkp = v[k][p], vkq = v[k][q];
+                v[k][p] = c * vkp - sn * vkq;
+                v[k][q] = sn * vkp + c * vkq;
+            }
+        }
+    }
+}
+
+/* unit normal of surface voxel s (or 0 if fewer than 3 occupied voxels around it) */
+static int voxel_normal(const uint64_t* occ, int64_t nocc, const int64_t s[3], double n[3]) {
+    int64_t cnt = 0, S1[3] = {0, 0, 0}, S2[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};
+    for (int dz = -1; dz <= 1; ++dz)
+        for (int dy = -1; dy <= 1; ++dy)
+            for (int dx = -1; dx <= 1; ++dx) {
+                if (find_key(occ, nocc, pack_key(s[0] + dx, s[1] + dy, s[2] + dz)) < 0) continue;
+                int64_t o[3] = {dx, dy, dz};
+                ++cnt;
+                for (int a = 0; a < 3; ++a) {
+                    S1[a] += o[a];
+                    for (int b = 0; b < 3; ++b) S2[a][b] += o[a] * o[b];
+                }
+            }
+    if (cnt < 3) return 0;
+    double A[3][3], V[3][3];
+    for (int a = 0; a < 3; ++a)
+        for (int b = 0; b < 3; ++b) A[a][b] = (double)(cnt * S2[a][b] - S1[a] * S1[b]);
+    jacobi3(A, V);
+    int k = 0;
+    for (int j = 1; j < 3; ++j) if (A[j][j] < A[k][k]) k = j;
+    double nn = sqrt(V[0][k] * V[0][k] + V[1][k] * V[1][k] + V[2][k] * V[2][k]);
+    for (int a = 0; a < 3; ++a) n[a] = V[a][k] / nn;
+    return 1;
+}
+
+typedef struct {
+    uint64_t key;
+    int32_t sign;
+    int32_t pad;
+} ksign;
+
+static int cmp_ksign(const void* a, const void* b) {
+    const ksign* x = (const ksign*)a;
+    const ksign* y = (const ksign*)b;
+    if (x->key != y->key) return x->key < y->key ? -1 : 1;
+    return (x->sign < y->sign) - (x->sign > y->sign); /* + first */
+}
+
+typedef struct {
+    ksign* v;
+    int64_t n, cap;
+} kslist;
+
+static void ks_push(kslist* L, int64_t x, int64_t y, int64_t z, int sign) {
+    if (!(x > -IJK_LIMIT && x < IJK_LIMIT && y > -IJK_LIMIT && y < IJK_LIMIT && z > -IJK_LIMIT && z < IJK_LIMIT)) return;
+    if (L->n == L->cap) {
+        L->cap = L->cap ? 2 * L->cap : 1024;
+        L->v = (ksign*)realloc(L->v, sizeof(ksign) * L->cap);
+    }
+    L->v[L->n].key = pack_key(x, y, z);
+    L->v[L->n].sign = sign;
+    L->v[L->n].pad = 0;
+    L->n++;
+}
+
+/* integer 3D Bresenham from a to b, b excluded */
+static void bresenham(const int64_t a[3], const int64_t b[3], const uint64_t* known, int64_t nknown, kslist* L) {
+    int64_t d[3], st[3], p[3] = {a[0], a[1], a[2]};
+    for (int k = 0; k < 3; ++k) {
+        d[k] = b[k] > a[k] ? b[k] - a[k] : a[k] - b[k];
+        st[k] = b[k] > a[k] ? 1 : -1;
+    }
+    int m = 0;
+    if (d[1] > d[m]) m = 1;
+    if (d[2] > d[m]) m = 2;
+    int u = (m + 1) % 3, w = (m + 2) % 3;
+    int64_t eu = 2 * d[u] - d[m], ew = 2 * d[w] - d[m];
+    for (int64_t i = 0; i < d[m]; ++i) {
+        if (find_key(known, nknown, pack_key(p[0], p[1], p[2])) >= 0) ks_push(L, p[0], p[1], p[2], 1);
+        if (eu > 0) { p[u] += st[u]; eu -= 2 * d[m]; }
+        if (ew > 0) { p[w] += st[w]; ew -= 2 * d[m]; }
+        eu += 2 * d[u];
+        ew += 2 * d[w];
+        p[m] += st[m];
+    }
+}
+
+or_frame* or_frame_build2(const or_params* P, const float* pts, int64_t n, const double* origin, int normal_steps,
+                          const uint64_t* known, int64_t n_known);
+
 or_frame* or_frame_build(const or_params* P, const float* pts, int64_t n) {
+    return or_frame_build2(P, pts, n, NULL, 0, NULL, 0);
+}
+
+or_frame* or_frame_build2(const or_params* P, const float* pts, int64_t n, const double* origin, int normal_steps,
+                          const uint64_t* known, int64_t n_known) {
     or_frame* F = (or_frame*)calloc(1, sizeof(or_frame));
     if (!F) return NULL;
     F->P = *P;
@@ -433,88 +566,156 @@ or_frame* or_frame_build(const or_params* P, const float* pts, int64_t n) {
                                           F->alpha + F->inst_off[l]);
     }
     free(run_start);
-    free(R);
-    /* 3. testing voxels: every voxel of every GP leaf and of its 26 neighbours */
-    uint64_t* tl = (uint64_t*)malloc(sizeof(uint64_t) * (27 * nl + 1));
-    int64_t ntl = 0;
-    for (int64_t l = 0; l < nl; ++l) {
-        int64_t leaf[3];
-        unpack_key(F->leaf_key[l], leaf);
-        for (int dz = -1; dz <= 1; ++dz)
-            for (int dy = -1; dy <= 1; ++dy)
-                for (int dx = -1; dx <= 1; ++dx) tl[ntl++] = pack_key(leaf[0] + dx, leaf[1] + dy, leaf[2] + dz);
+    /* 3. testing voxels: the dilated GP leaves (no origin), or the ray-cast set (Sec. IV-B) */
+    kslist TL = {NULL, 0, 0};
+    if (!origin) {
+        uint64_t* tl = (uint64_t*)malloc(sizeof(uint64_t) * (27 * nl + 1));
+        int64_t ntl = 0;
+        for (int64_t l = 0; l < nl; ++l) {
+            int64_t leaf[3];
+            unpack_key(F->leaf_key[l], leaf);
+            for (int dz = -1; dz <= 1; ++dz)
+                for (int dy = -1; dy <= 1; ++dy)
+                    for (int dx = -1; dx <= 1; ++dx) tl[ntl++] = pack_key(leaf[0] + dx, leaf[1] + dy, leaf[2] + dz);
+        }
+        qsort(tl, (size_t)ntl, sizeof(uint64_t), cmp_u64);
+        int64_t ut = 0;
+        for (int64_t i = 0; i < ntl; ++i) if (ut == 0 || tl[i] != tl[ut - 1]) tl[ut++] = tl[i];
+        for (int64_t t = 0; t < ut; ++t) {
+            int64_t M[3];
+            unpack_key(tl[t], M);
+            for (int b = 0; b < 512; ++b) {
+                int64_t ijk[3];
+                voxel_of_bit(M, b, ijk);
+                ks_push(&TL, ijk[0], ijk[1], ijk[2], 1);
+            }
+        }
+        free(tl);
+    } else {
+        /* occupied voxels of this frame, sorted */
+        uint64_t* occ = (uint64_t*)malloc(sizeof(uint64_t) * (u + 1));
+        for (int64_t i = 0; i < u; ++i) {
+            int64_t leaf[3], ijk[3];
+            unpack_key(R[i].lkey, leaf);
+            voxel_of_bit(leaf, R[i].bit, ijk);
+            occ[i] = pack_key(ijk[0], ijk[1], ijk[2]);
+        }
+        qsort(occ, (size_t)u, sizeof(uint64_t), cmp_u64);
+        int64_t ov[3];
+        int have_o = voxel_ijk(origin, vs, ov);
+        for (int64_t i = 0; i < u; ++i) {
+            int64_t sv[3];
+            unpack_key(occ[i], sv);
+            ks_push(&TL, sv[0], sv[1], sv[2], 1);
+            double nrm[3];
+            if (have_o && voxel_normal(occ, u, sv, nrm)) {
+                double e = 0.0;
+                for (int a = 0; a < 3; ++a) e += nrm[a] * (origin[a] - (double)sv[a] * vs);
+                if (e < 0.0) for (int a = 0; a < 3; ++a) nrm[a] = -nrm[a];
+                for (int k = -normal_steps; k <= normal_steps; ++k) {
+                    if (k == 0) continue;
+                    int64_t v[3];
+                    for (int a = 0; a < 3; ++a) v[a] = sv[a] + (int64_t)floor((double)k * nrm[a] + 0.5);
+                    ks_push(&TL, v[0], v[1], v[2], k > 0 ? 1 : -1);
+                }
+            }
+            if (have_o) bresenham(ov, sv, known, n_known, &TL);
+        }
+        free(occ);
     }
-    qsort(tl, (size_t)ntl, sizeof(uint64_t), cmp_u64);
+    qsort(TL.v, (size_t)TL.n, sizeof(ksign), cmp_ksign);
     int64_t nt = 0;
-    for (int64_t i = 0; i < ntl; ++i) if (nt == 0 || tl[i] != tl[nt - 1]) tl[nt++] = tl[i];
-    F->n_test = nt * 512;
+    for (int64_t i = 0; i < TL.n; ++i)
+        if (nt == 0 || TL.v[i].key != TL.v[nt - 1].key) TL.v[nt++] = TL.v[i];  /* + sorts first */
+    free(R);
+    F->n_test = nt;
     F->test_key = (uint64_t*)malloc(sizeof(uint64_t) * (F->n_test + 1));
     F->test_inst_key = (uint64_t*)malloc(sizeof(uint64_t) * (F->n_test + 1));
     F->test_d = (double*)malloc(sizeof(double) * (F->n_test + 1));
     F->test_v = (double*)malloc(sizeof(double) * (F->n_test + 1));
     F->test_grad = (double*)malloc(sizeof(double) * 3 * (F->n_test + 1));
     F->test_status = (uint8_t*)malloc(F->n_test + 1);
+    F->test_sign = (int8_t*)malloc(F->n_test + 1);
     int Nmax = 1;
     for (int64_t l = 0; l < nl; ++l) {
         int64_t N = F->inst_off[l + 1] - F->inst_off[l];
         if (N > Nmax) Nmax = (int)N;
     }
+    /* 4. closest GP node per testing voxel, inference, sign */
 #pragma omp parallel
     {
         double* kb = (double*)malloc(sizeof(double) * Nmax);
         double* vb = (double*)malloc(sizeof(double) * Nmax);
-#pragma omp for schedule(dynamic, 4)
-        for (int64_t t = 0; t < nt; ++t) {
-            int64_t M[3];
-            unpack_key(tl[t], M);
-            int64_t own = find_key(F->leaf_key, nl, tl[t]);
-            for (int b = 0; b < 512; ++b) {
-                int64_t ijk[3];
-                voxel_of_bit(M, b, ijk);
-                int64_t inst = own;
-                if (inst < 0) {
-                    int64_t best_d2 = INT64_MAX;
-                    for (int dz = -1; dz <= 1; ++dz)
-                        for (int dy = -1; dy <= 1; ++dy)
-                            for (int dx = -1; dx <= 1; ++dx) {
-                                if (!dx && !dy && !dz) continue;
-                                int64_t Fl[3] = {M[0] + dx, M[1] + dy, M[2] + dz};
-                                int64_t f = find_key(F->leaf_key, nl, pack_key(Fl[0], Fl[1], Fl[2]));
-                                if (f < 0) continue;
-                                int64_t d2 = 0;
-                                for (int a = 0; a < 3; ++a) {
-                                    int64_t e = 2 * ijk[a] - (16 * Fl[a] + 7);
-                                    d2 += e * e;
-                                }
-                                if (d2 < best_d2) { best_d2 = d2; inst = f; }
+#pragma omp for schedule(dynamic, 256)
+        for (int64_t o = 0; o < nt; ++o) {
+            int64_t ijk[3], M[3];
+            int32_t bit;
+            unpack_key(TL.v[o].key, ijk);
+            leaf_of(ijk, M, &bit);
+            int64_t inst = find_key(F->leaf_key, nl, pack_key(M[0], M[1], M[2]));
+            if (inst < 0) {
+                int64_t best_d2 = INT64_MAX;
+                for (int dz = -1; dz <= 1; ++dz)
+                    for (int dy = -1; dy <= 1; ++dy)
+                        for (int dx = -1; dx <= 1; ++dx) {
+                            if (!dx && !dy && !dz) continue;
+                            int64_t Fl[3] = {M[0] + dx, M[1] + dy, M[2] + dz};
+                            int64_t f = find_key(F->leaf_key, nl, pack_key(Fl[0], Fl[1], Fl[2]));
+                            if (f < 0) continue;
+                            int64_t d2 = 0;
+                            for (int a = 0; a < 3; ++a) {
+                                int64_t e = 2 * ijk[a] - (16 * Fl[a] + 7);
+                                d2 += e * e;
                             }
-                }
-                int64_t o = t * 512 + b;
-                F->test_key[o] = pack_key(ijk[0], ijk[1], ijk[2]);
-                or_eval r;
-                double xs[3] = {(double)ijk[0] * vs, (double)ijk[1] * vs, (double)ijk[2] * vs};
-                if (inst < 0) {
-                    eval_invalid(&r, ST_NO_SUPPORT);
-                    F->test_inst_key[o] = 0;
-                } else {
-                    F->test_inst_key[o] = F->leaf_key[inst];
-                    int N = (int)(F->inst_off[inst + 1] - F->inst_off[inst]);
-                    if (!F->fit_ok[inst]) eval_invalid(&r, ST_FACTOR_FAIL);
-                    else gp_eval(F->X + 3 * F->inst_off[inst], N, F->L + F->L_off[inst],
-                                 F->alpha + F->inst_off[inst], xs, P, 1, kb, vb, &r);
-                }
-                F->test_d[o] = r.d;
-                F->test_v[o] = r.v;
-                for (int a = 0; a < 3; ++a) F->test_grad[3 * o + a] = r.gd[a];
-                F->test_status[o] = (uint8_t)r.status;
+                            if (d2 < best_d2) { best_d2 = d2; inst = f; }
+                        }
             }
+            if (inst < 0) { /* beyond the 26 neighbours: nearest GP leaf within the search radius */
+                int Rr = P->max_leaf_search;
+                int64_t best_d2 = INT64_MAX;
+                uint64_t best_key = 0;
+                for (int dz = -Rr; dz <= Rr; ++dz)
+                    for (int dy = -Rr; dy <= Rr; ++dy)
+                        for (int dx = -Rr; dx <= Rr; ++dx) {
+                            int64_t Fl[3] = {M[0] + dx, M[1] + dy, M[2] + dz};
+                            uint64_t k = pack_key(Fl[0], Fl[1], Fl[2]);
+                            int64_t f = find_key(F->leaf_key, nl, k);
+                            if (f < 0) continue;
+                            int64_t d2 = 0;
+                            for (int a = 0; a < 3; ++a) {
+                                int64_t e = 2 * ijk[a] - (16 * Fl[a] + 7);
+                                d2 += e * e;
+                            }
+                            if (d2 < best_d2 || (d2 == best_d2 && k < best_key)) { best_d2 = d2; best_key = k; inst = f; }
+                        }
+            }
+            F->test_key[o] = TL.v[o].key;
+            F->test_sign[o] = (int8_t)TL.v[o].sign;
+            or_eval r;
+            double xs[3] = {(double)ijk[0] * vs, (double)ijk[1] * vs, (double)ijk[2] * vs};
+            if (inst < 0) {
+                eval_invalid(&r, ST_NO_SUPPORT);
+                F->test_inst_key[o] = 0;
+            } else {
+                F->test_inst_key[o] = F->leaf_key[inst];
+                int N = (int)(F->inst_off[inst + 1] - F->inst_off[inst]);
+                if (!F->fit_ok[inst]) eval_invalid(&r, ST_FACTOR_FAIL);
+                else gp_eval(F->X + 3 * F->inst_off[inst], N, F->L + F->L_off[inst], F->alpha + F->inst_off[inst], xs,
+                             P, 1, kb, vb, &r);
+            }
+            double sg = (double)TL.v[o].sign;
+            F->test_d[o] = r.status == ST_OK || r.status == ST_CLAMPED ? sg * r.d : r.d;
+            F->test_v[o] = r.v;
+            for (int a = 0; a < 3; ++a) F->test_grad[3 * o + a] = sg * r.gd[a];
+            F->test_status[o] = (uint8_t)r.status;
         }
         free(kb);
         free(vb);
     }
-    free(tl);
+    free(TL.v);
     return F;
 }
+
 
 int64_t or_frame_count(const or_frame* F, int what) {
     if (what == 0) return F->n_leaves;
@@ -531,6 +732,10 @@ void or_frame_leaves(const or_frame* F, uint64_t* key, int32_t* nocc, int64_t* i
     if (inst_off) memcpy(inst_off, F->inst_off, sizeof(int64_t) * (nl + 1));
     if (X) memcpy(X, F->X, sizeof(double) * 3 * T);
     if (alpha) memcpy(alpha, F->alpha, sizeof(double) * T);
+}
+
+void or_frame_signs(const or_frame* F, int8_t* sign) {
+    if (sign) memcpy(sign, F->test_sign, F->n_test);
 }
 
 void or_frame_tests(const or_frame* F, uint64_t* key, uint64_t* inst_key, double* d, double* v,
