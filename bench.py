@@ -314,6 +314,24 @@ def comparisons(S, Q, S_h, args):
         out.setdefault("lgpdf_room", {})[prec] = {"voxels_per_s": nvox / sec, "frames": len(frames),
                                                  "ms_per_frame": 1e3 * sec / len(frames),
                                                  "testing_voxels_per_frame": nvox / len(frames)}
+    # L-GPDF with the paper's testing points: ray-cast from the sensor origin, signed distances
+    poses = [room.camera_pose(k)[0] for k in range(args.room_frames)]
+    mr = Map(precision="mixed", max_pts_leaf=512)
+    mr.fuse(mr.build_frame(frames[0], origin=poses[0]))
+    torch.cuda.synchronize()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    nvox = 0
+    a.record()
+    for fr, o in zip(frames, poses):
+        f = mr.build_frame(fr, origin=o)
+        nvox += f.n_test
+        mr.fuse(f)
+    b.record()
+    torch.cuda.synchronize()
+    sec = a.elapsed_time(b) / 1e3
+    out["lgpdf_room_raycast"] = {"voxels_per_s": nvox / sec, "frames": len(frames),
+                                 "ms_per_frame": 1e3 * sec / len(frames),
+                                 "testing_voxels_per_frame": nvox / len(frames), "precision": "mixed"}
     # independent-instance sweep (N log-uniform in [4, 1024], 512 queries each)
     io, X, qo, Qw = scenes.patch_sweep(n_inst=args.sweep_inst, seed=4)
     io_d = torch.from_numpy(io).cuda()

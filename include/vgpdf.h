@@ -106,6 +106,8 @@ enum {
  *                    reverting log in FP64.
  *   profile          0 (default) or 1: record CUDA events around the GP solve kernels and
  *                    report their time in vgp_stats.t_solve_ms (adds one stream sync per call).
+ *   normal_steps     K in [0, 16] (default 3): with a sensor origin, vgp_build_frame also tests
+ *                    the voxels round(s + k n), k = +-1..+-K, along each surface voxel's normal.
  *   launch           VGP_LAUNCH_BATCHED (default): all GP instances of a call run in a few
  *                    persistent launches, one per size bucket, largest first.
  *                    VGP_LAUNCH_PER_INSTANCE: one kernel launch per instance, in instance
@@ -124,7 +126,7 @@ typedef struct {
     int32_t precision;
     int32_t profile;     /* nonzero: time the solve kernels with CUDA events (vgp_stats) */
     int32_t launch;      /* VGP_LAUNCH_BATCHED (0) or VGP_LAUNCH_PER_INSTANCE (1) */
-    int32_t reserved;    /* must be zero */
+    int32_t normal_steps;/* ray-cast testing points: voxels along each surface normal, each side */
 } vgp_params;
 
 /* Counters of the most recent call on a map (host copy; informational). */
@@ -159,15 +161,25 @@ int vgp_destroy(vgp_map* m);
  * L-GPDF of one frame (Sec. IV-A, IV-B; Eqs. 1-4).
  *   pts_dev  [n][3] float32 world-frame points (device).  Non-finite points and points with
  *            |p / voxel_size| >= 2^20 - 64 are ignored.  n >= 0 (n == 0 gives an empty frame).
- * Voxelises with ijk = floor(p / voxel_size + 1/2) (IEEE FP64), builds one GP per occupied
- * leaf on its (capped) voxel centres, and infers distance d and variance v at every voxel of
- * every occupied leaf and of its 26 neighbour leaves (the testing voxels), each voxel using
- * the GP of its own leaf if that leaf holds one, else of the neighbour leaf whose centre is
- * nearest (ties to the first in (dz, dy, dx) order from -1 to 1).
+ *   origin   host pointer to the sensor origin (3 doubles, world frame), or NULL.
+ * Voxelises with ijk = floor(p / voxel_size + 1/2) (IEEE FP64) and builds one GP per occupied
+ * leaf on its (capped) voxel centres.  Testing voxels:
+ *   - origin == NULL: every voxel of every occupied leaf and of its 26 neighbour leaves;
+ *     distances unsigned;
+ *   - origin given (Sec. IV-B): the occupied voxels; the voxels round(s + k n),
+ *     k = +-1..+-normal_steps, along the normal n of each occupied voxel s (smallest-eigenvalue
+ *     eigenvector of the scatter of the occupied voxels in its 3x3x3 block, at least 3, oriented
+ *     towards the origin); and the voxels on the integer 3D Bresenham line from the origin's
+ *     voxel to each occupied voxel that already hold a value in the map's global grid.
+ *     Distances and gradients are signed: + on the sensor side (occupied, ray, k > 0),
+ *     - for k < 0 (a voxel reached with both signs is +).
+ * Each testing voxel uses the GP of its own leaf if that leaf holds one, else of the neighbour
+ * leaf whose centre is nearest (ties to the first in (dz, dy, dx) order from -1 to 1), else the
+ * nearest GP leaf within max_leaf_search (ties to the smaller key), else status NO_SUPPORT.
  * On success *out receives a new frame (free with vgp_frame_destroy).  Synchronises the
  * stream several times to size its buffers.
  */
-int vgp_build_frame(vgp_map* m, const float* pts_dev, int64_t n, vgp_stream stream,
+int vgp_build_frame(vgp_map* m, const float* pts_dev, int64_t n, const double* origin, vgp_stream stream,
                     vgp_frame** out);
 
 /*

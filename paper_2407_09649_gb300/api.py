@@ -128,10 +128,15 @@ class Map:
         self._surface_key = None
 
     # -- L-GPDF ----------------------------------------------------------------------
-    def build_frame(self, pts) -> Frame:
+    def build_frame(self, pts, origin=None) -> Frame:
+        """L-GPDF of one frame; with the sensor ``origin`` (3 floats) the testing voxels are
+        the ray-cast set and distances are signed."""
         pts = _dev_f32(pts, "pts")
         h = C.c_void_p()
-        L.check(L.load().vgp_build_frame(self._h, _ptr(pts), pts.shape[0], _stream(), C.byref(h)))
+        o = None
+        if origin is not None:
+            o = (C.c_double * 3)(*[float(x) for x in origin])
+        L.check(L.load().vgp_build_frame(self._h, _ptr(pts), pts.shape[0], o, _stream(), C.byref(h)))
         return Frame(self, h)
 
     def fuse(self, frame: Frame) -> None:

@@ -212,6 +212,7 @@ void vgp_default_params(vgp_params* p) {
     p->max_leaf_search = 8;
     p->fusion = VGP_FUSE_INVVAR;
     p->precision = VGP_MIXED;
+    p->normal_steps = 3;
 }
 
 int vgp_create(const vgp_params* p, vgp_map** out) {
@@ -226,7 +227,7 @@ int vgp_create(const vgp_params* p, vgp_map** out) {
     if (p->max_leaf_search < 0 || p->max_leaf_search > 16) return fail(VGP_ERR_ARG, "max_leaf_search must be in [0, 16]");
     if (p->fusion != VGP_FUSE_INVVAR && p->fusion != VGP_FUSE_TSDF) return fail(VGP_ERR_ARG, "unknown fusion rule");
     if (p->precision != VGP_FP64 && p->precision != VGP_MIXED) return fail(VGP_ERR_ARG, "unknown precision");
-    if (p->reserved) return fail(VGP_ERR_ARG, "reserved fields must be zero");
+    if (p->normal_steps < 0 || p->normal_steps > 16) return fail(VGP_ERR_ARG, "normal_steps must be in [0, 16]");
     if (p->launch != VGP_LAUNCH_BATCHED && p->launch != VGP_LAUNCH_PER_INSTANCE) return fail(VGP_ERR_ARG, "unknown launch mode");
     if (p->profile != 0 && p->profile != 1) return fail(VGP_ERR_ARG, "profile must be 0 or 1");
     vgp_map* m = new (std::nothrow) vgp_map();
@@ -305,7 +306,8 @@ int vgp_get_stats(const vgp_map* m, vgp_stats* out) {
 }
 
 // ---------------------------------- frame ----------------------------------------------
-int vgp_build_frame(vgp_map* m, const float* pts, int64_t n, vgp_stream stream, vgp_frame** out) {
+int vgp_build_frame(vgp_map* m, const float* pts, int64_t n, const double* origin, vgp_stream stream,
+                    vgp_frame** out) {
     if (!m || !out || n < 0 || (n > 0 && !pts)) return fail(VGP_ERR_ARG, "vgp_build_frame: bad argument");
     if (n > (1ll << 30)) return fail(VGP_ERR_ARG, "vgp_build_frame: n too large");
     *out = nullptr;
@@ -361,42 +363,117 @@ int vgp_build_frame(vgp_map* m, const float* pts, int64_t n, vgp_stream stream, 
     f->centre = f->alloc<double>(3 * (int64_t)nl, st);
     if (!f->X || !f->Xl || !f->Xf || !f->Xi || !f->alpha || !f->centre) return bail(VGP_ERR_OOM, "allocation failed");
     frame_leaf_points(flist, flkeys, nl, fmasks, f->nocc, f->inst_off, P, f->X, f->Xl, f->Xf, f->Xi, f->centre, st);
-    // 3. testing leaves: occupied leaves and their 26 neighbours
-    Table tt;
-    uint32_t Ct = pow2_at_least(2 * 27 * (int64_t)std::max(nl, 1));
-    tt.mask = Ct - 1;
-    tt.keys = (uint64_t*)m->ar.get(Arena::kTmp6, sizeof(uint64_t) * Ct, st);
-    uint64_t* tl_keys = (uint64_t*)m->ar.get(Arena::kTmp7, sizeof(uint64_t) * Ct, st);
-    if (!tt.keys || !tl_keys) return bail(VGP_ERR_OOM, "allocation failed");
-    cudaMemsetAsync(tt.keys, 0xFF, sizeof(uint64_t) * Ct, st);
-    frame_dilate(f->leaf_key, nl, tt, m->dev_words, st);
-    collect_table(tt, nullptr, nullptr, tl_keys, m->dev_words + 2, Ct, m->dev_words, st);
-    if (read_words(m, st) != VGP_OK) return bail(VGP_ERR_CUDA, "sync failed");
-    if (check_err(m, "vgp_build_frame") != VGP_OK) {
-        std::string msg = g_last_error;
-        vgp_frame_destroy(f);
-        g_last_error = msg;
-        return VGP_ERR_TABLE_FULL;
+    int64_t n_assigned = -1;      // ray-cast path: testing voxels with a GP node (the rest follow)
+    int8_t* gsign = nullptr;
+    int64_t* q_off = nullptr;
+    if (!origin) {
+        // 3. testing leaves: occupied leaves and their 26 neighbours
+        Table tt;
+        uint32_t Ct = pow2_at_least(2 * 27 * (int64_t)std::max(nl, 1));
+        tt.mask = Ct - 1;
+        tt.keys = (uint64_t*)m->ar.get(Arena::kTmp6, sizeof(uint64_t) * Ct, st);
+        uint64_t* tl_keys = (uint64_t*)m->ar.get(Arena::kTmp7, sizeof(uint64_t) * Ct, st);
+        if (!tt.keys || !tl_keys) return bail(VGP_ERR_OOM, "allocation failed");
+        cudaMemsetAsync(tt.keys, 0xFF, sizeof(uint64_t) * Ct, st);
+        frame_dilate(f->leaf_key, nl, tt, m->dev_words, st);
+        collect_table(tt, nullptr, nullptr, tl_keys, m->dev_words + 2, Ct, m->dev_words, st);
+        if (read_words(m, st) != VGP_OK) return bail(VGP_ERR_CUDA, "sync failed");
+        if (check_err(m, "vgp_build_frame") != VGP_OK) {
+            std::string msg = g_last_error;
+            vgp_frame_destroy(f);
+            g_last_error = msg;
+            return VGP_ERR_TABLE_FULL;
+        }
+        const int ntl = m->host_words[2];
+        // 4. closest-node choice per testing voxel; group voxels by instance
+        int64_t* inst_cnt = (int64_t*)m->ar.get(Arena::kTmp8, sizeof(int64_t) * (nl + 1), st);
+        q_off = (int64_t*)m->ar.get(Arena::kTmp9, sizeof(int64_t) * (nl + 1), st);
+        int64_t* cursor = (int64_t*)m->ar.get(Arena::kTmp10, sizeof(int64_t) * (nl + 1), st);
+        if (!inst_cnt || !q_off || !cursor) return bail(VGP_ERR_OOM, "allocation failed");
+        cudaMemsetAsync(inst_cnt, 0, sizeof(int64_t) * (nl + 1), st);
+        cudaMemsetAsync(cursor, 0, sizeof(int64_t) * (nl + 1), st);
+        frame_assign_tests(tl_keys, ntl, ft, fslot2leaf, inst_cnt, m->dev_words + 4, st);
+        exclusive_scan_i64(inst_cnt, q_off, nl, st, m->ar);
+        const int64_t ntest = (int64_t)ntl * 512;
+        f->ntest = ntest;
+        f->tkey = f->alloc<uint64_t>(ntest, st);
+        f->d = f->alloc<double>(ntest, st);
+        f->v = f->alloc<double>(ntest, st);
+        f->grad = f->alloc<double>(3 * ntest, st);
+        f->status = f->alloc<uint8_t>(ntest, st);
+        if (!f->tkey || !f->d || !f->v || !f->grad || !f->status) return bail(VGP_ERR_OOM, "allocation failed");
+        frame_scatter_tests(tl_keys, ntl, ft, fslot2leaf, q_off, cursor, f->tkey, st);
+    } else {
+        // 3'. ray-cast testing points (Sec. IV-B): surface voxels, normal voxels, known voxels on rays
+        const int K = m->prm.normal_steps;
+        int64_t* nocc64 = (int64_t*)m->ar.get(Arena::kTmp8, sizeof(int64_t) * (nl + 1), st);
+        int64_t* soff = (int64_t*)m->ar.get(Arena::kTmp9, sizeof(int64_t) * (nl + 1), st);
+        if (!nocc64 || !soff) return bail(VGP_ERR_OOM, "allocation failed");
+        widen_i32(f->nocc, nocc64, nl, st);
+        exclusive_scan_i64(nocc64, soff, nl, st, m->ar);
+        int64_t U = 0;
+        cudaMemcpyAsync(&U, soff + nl, sizeof(int64_t), cudaMemcpyDeviceToHost, st);
+        if (cudaStreamSynchronize(st) != cudaSuccess) return bail(VGP_ERR_CUDA, "sync failed");
+        uint64_t* svox = (uint64_t*)m->ar.get(Arena::kPair0, sizeof(uint64_t) * std::max<int64_t>(U, 1), st);
+        if (!svox) return bail(VGP_ERR_OOM, "allocation failed");
+        frame_surface_voxels(flist, flkeys, nl, fmasks, soff, svox, st);
+        double o[3] = {origin[0], origin[1], origin[2]};
+        int ov[3] = {0, 0, 0}, have_o = 1;
+        for (int a = 0; a < 3; ++a) {
+            if (!std::isfinite(o[a])) { have_o = 0; break; }
+            const double t = o[a] / P.vs;
+            const double u = t + 0.5;
+            const double fl = std::floor(u);
+            if (!(fl > -kIjkLimit && fl < kIjkLimit)) { have_o = 0; break; }
+            ov[a] = (int)fl;
+        }
+        uint32_t Ct = pow2_at_least(2 * (U * (2 * K + 1) + (int64_t)m->g_leaves * 512 + 1024));
+        Table tt;
+        unsigned* tflags = nullptr;
+        for (int attempt = 0;; ++attempt) {
+            tt.mask = Ct - 1;
+            tt.keys = (uint64_t*)m->ar.get(Arena::kTmp6, sizeof(uint64_t) * Ct, st);
+            tflags = (unsigned*)m->ar.get(Arena::kTmp7, sizeof(unsigned) * Ct, st);
+            if (!tt.keys || !tflags) return bail(VGP_ERR_OOM, "allocation failed");
+            cudaMemsetAsync(tt.keys, 0xFF, sizeof(uint64_t) * Ct, st);
+            cudaMemsetAsync(tflags, 0, sizeof(unsigned) * Ct, st);
+            cudaMemsetAsync(m->dev_words, 0, sizeof(int), st);
+            frame_raycast_tests(svox, U, ft, fmasks, m->g, m->g_slot2pool, m->g_known, o, have_o, ov, P.vs, K, tt, tflags,
+                                m->dev_words, st);
+            if (read_words(m, st) != VGP_OK) return bail(VGP_ERR_CUDA, "sync failed");
+            if (!(m->host_words[0] & kErrTableFull)) break;
+            if (attempt >= 4 || Ct >= (1u << 31)) return bail(VGP_ERR_TABLE_FULL, "testing-voxel table full");
+            Ct <<= 2;
+        }
+        uint64_t* tkey_u = (uint64_t*)m->ar.get(Arena::kPair1, sizeof(uint64_t) * Ct, st);
+        int8_t* tsign_u = (int8_t*)m->ar.get(Arena::kPair2, Ct, st);
+        if (!tkey_u || !tsign_u) return bail(VGP_ERR_OOM, "allocation failed");
+        frame_collect_tests(tt, tflags, tkey_u, tsign_u, m->dev_words + 2, st);
+        if (read_words(m, st) != VGP_OK) return bail(VGP_ERR_CUDA, "sync failed");
+        const int64_t nt = m->host_words[2];
+        int32_t* tinst = (int32_t*)m->ar.get(Arena::kPair3, sizeof(int32_t) * std::max<int64_t>(nt, 1), st);
+        int64_t* inst_cnt = (int64_t*)m->ar.get(Arena::kTmp10, sizeof(int64_t) * (nl + 1), st);
+        q_off = (int64_t*)m->ar.get(Arena::kTmp15, sizeof(int64_t) * (nl + 1), st);
+        int64_t* cursor = (int64_t*)m->ar.get(Arena::kTmp16, sizeof(int64_t) * (nl + 1), st);
+        gsign = (int8_t*)m->ar.get(Arena::kPair4, std::max<int64_t>(nt, 1), st);
+        if (!tinst || !inst_cnt || !q_off || !cursor || !gsign) return bail(VGP_ERR_OOM, "allocation failed");
+        cudaMemsetAsync(inst_cnt, 0, sizeof(int64_t) * (nl + 1), st);
+        cudaMemsetAsync(cursor, 0, sizeof(int64_t) * (nl + 1), st);
+        cudaMemsetAsync(m->dev_words + 4, 0, 2 * sizeof(int), st);
+        frame_assign_list(tkey_u, nt, ft, fslot2leaf, P.search_r, tinst, inst_cnt, m->dev_words + 4, st);
+        exclusive_scan_i64(inst_cnt, q_off, nl, st, m->ar);
+        if (read_words(m, st) != VGP_OK) return bail(VGP_ERR_CUDA, "sync failed");
+        n_assigned = nt - m->host_words[4];
+        f->ntest = nt;
+        f->tkey = f->alloc<uint64_t>(nt, st);
+        f->d = f->alloc<double>(nt, st);
+        f->v = f->alloc<double>(nt, st);
+        f->grad = f->alloc<double>(3 * nt, st);
+        f->status = f->alloc<uint8_t>(nt, st);
+        if (!f->tkey || !f->d || !f->v || !f->grad || !f->status) return bail(VGP_ERR_OOM, "allocation failed");
+        frame_scatter_list(tkey_u, tsign_u, nt, tinst, q_off, cursor, n_assigned, m->dev_words + 5, f->tkey, gsign, st);
+        cudaMemsetAsync(m->dev_words + 4, 0, 2 * sizeof(int), st);
     }
-    const int ntl = m->host_words[2];
-    // 4. closest-node choice per testing voxel; group voxels by instance
-    int64_t* inst_cnt = (int64_t*)m->ar.get(Arena::kTmp8, sizeof(int64_t) * (nl + 1), st);
-    int64_t* q_off = (int64_t*)m->ar.get(Arena::kTmp9, sizeof(int64_t) * (nl + 1), st);
-    int64_t* cursor = (int64_t*)m->ar.get(Arena::kTmp10, sizeof(int64_t) * (nl + 1), st);
-    if (!inst_cnt || !q_off || !cursor) return bail(VGP_ERR_OOM, "allocation failed");
-    cudaMemsetAsync(inst_cnt, 0, sizeof(int64_t) * (nl + 1), st);
-    cudaMemsetAsync(cursor, 0, sizeof(int64_t) * (nl + 1), st);
-    frame_assign_tests(tl_keys, ntl, ft, fslot2leaf, inst_cnt, m->dev_words + 4, st);
-    exclusive_scan_i64(inst_cnt, q_off, nl, st, m->ar);
-    const int64_t ntest = (int64_t)ntl * 512;
-    f->ntest = ntest;
-    f->tkey = f->alloc<uint64_t>(ntest, st);
-    f->d = f->alloc<double>(ntest, st);
-    f->v = f->alloc<double>(ntest, st);
-    f->grad = f->alloc<double>(3 * ntest, st);
-    f->status = f->alloc<uint8_t>(ntest, st);
-    if (!f->tkey || !f->d || !f->v || !f->grad || !f->status) return bail(VGP_ERR_OOM, "allocation failed");
-    frame_scatter_tests(tl_keys, ntl, ft, fslot2leaf, q_off, cursor, f->tkey, st);
     // 5. factorise every leaf GP and infer at its testing voxels
     SolveBatch b;
     b.n_inst = nl;
@@ -416,14 +493,15 @@ int vgp_build_frame(vgp_map* m, const float* pts, int64_t n, vgp_stream stream, 
     b.want_var = 1;
     SolveStats ss;
     solve_batch(b, P, m->dev_words, st, m->ar, &ss, nullptr, m->prm.profile != 0, m->prm.launch, &m->cfg);
+    if (origin) frame_orphans_and_sign(f->ntest, n_assigned, gsign, f->d, f->grad, f->v, f->status, st);
     if (read_words(m, st) != VGP_OK) return bail(VGP_ERR_CUDA, "sync failed");
-    if (m->host_words[4] != 0) return bail(VGP_ERR_STATE, "testing voxel without a neighbouring GP leaf");
+    if (!origin && m->host_words[4] != 0) return bail(VGP_ERR_STATE, "testing voxel without a neighbouring GP leaf");
     cudaError_t ce = cudaGetLastError();
     if (ce != cudaSuccess) return bail(VGP_ERR_CUDA, cudaGetErrorString(ce));
     S.n_leaves = nl;
     S.n_instances = nl;
     S.n_train = T;
-    S.n_queries = ntest;
+    S.n_queries = f->ntest;
     for (int i = 0; i < 5; ++i) S.bucket_count[i] = ss.bucket_count[i];
     S.sum_n3 = ss.sum_n3;
     S.sum_n2 = ss.sum_n2;

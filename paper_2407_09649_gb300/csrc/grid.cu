@@ -73,6 +73,10 @@ __global__ void k_fill_u64(uint64_t* p, uint64_t v, int64_t n) {
     int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (i < n) p[i] = v;
 }
+__global__ void k_widen_i32(const int32_t* in, int64_t* out, int64_t n) {
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i < n) out[i] = in[i];
+}
 __global__ void k_fill_i32(int32_t* p, int32_t v, int64_t n) {
     int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (i < n) p[i] = v;
@@ -113,6 +117,12 @@ void fill_i64(int64_t* p, int64_t v, int64_t n, cudaStream_t st) {
 void fill_u64(uint64_t* p, uint64_t v, int64_t n, cudaStream_t st) {
     if (n > 0) {
         k_fill_u64<<<nblk(n), TB, 0, st>>>(p, v, n);
+        note_launch();
+    }
+}
+void widen_i32(const int32_t* in, int64_t* out, int64_t n, cudaStream_t st) {
+    if (n > 0) {
+        k_widen_i32<<<nblk(n), TB, 0, st>>>(in, out, n);
         note_launch();
     }
 }
@@ -358,6 +368,326 @@ void frame_scatter_tests(const uint64_t* tl_keys, int ntl, const Table& ft, cons
                          const int64_t* q_off, int64_t* cursor, uint64_t* tkey, cudaStream_t st) {
     if (ntl > 0) {
         k_scatter_tests<<<ntl, 512, 0, st>>>(tl_keys, ft.keys, ft.mask, slot2leaf, q_off, cursor, tkey);
+        note_launch();
+    }
+}
+
+// --------------------------------------------------------------------------------------
+// ray-cast testing points (Sec. IV-B): surface voxels, voxels along their normals, voxels
+// with earlier measurements on the sensor rays; sign by sensor side
+// --------------------------------------------------------------------------------------
+namespace {
+// Warp per frame leaf: every occupied voxel (uncapped), in bit order, at soff[l].
+__global__ void k_surface_voxels(const int32_t* list, const uint64_t* lkeys, int nl, const unsigned long long* masks,
+                                 const int64_t* soff, uint64_t* svox) {
+    int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+    if (warp >= nl) return;
+    const int s = list[warp];
+    int lx, ly, lz;
+    unpack_key(lkeys[warp], lx, ly, lz);
+    int64_t base = soff[warp];
+    for (int w = 0; w < 8; ++w) {
+        const unsigned long long m = masks[(int64_t)s * 8 + w];
+        for (int half = 0; half < 2; ++half) {
+            const unsigned mm = (unsigned)(m >> (32 * half));
+            const bool on = (mm >> lane) & 1u;
+            const unsigned b = __ballot_sync(0xffffffffu, on);
+            if (on) {
+                const int bit = w * 64 + half * 32 + lane;
+                const int r = __popc(b & ((1u << lane) - 1u));
+                svox[base + r] = pack_key(8 * lx + (bit & 7), 8 * ly + ((bit >> 3) & 7), 8 * lz + (bit >> 6));
+            }
+            base += __popc(b);
+        }
+    }
+}
+
+__device__ __forceinline__ bool frame_occupied(const uint64_t* fkeys, uint32_t fmask, const unsigned long long* masks,
+                                               int x, int y, int z) {
+    const int64_t s = ht_find(fkeys, fmask, pack_key(leaf_coord(x), leaf_coord(y), leaf_coord(z)));
+    if (s < 0) return false;
+    const int bit = (x & 7) + 8 * (y & 7) + 64 * (z & 7);
+    return (masks[s * 8 + (bit >> 6)] >> (bit & 63)) & 1ull;
+}
+
+__device__ __forceinline__ bool grid_known(const uint64_t* gkeys, uint32_t gmask, const int32_t* slot2pool,
+                                           const unsigned long long* known, int x, int y, int z) {
+    if (!gkeys) return false;
+    const int64_t s = ht_find(gkeys, gmask, pack_key(leaf_coord(x), leaf_coord(y), leaf_coord(z)));
+    if (s < 0) return false;
+    const int p = slot2pool[s];
+    if (p < 0) return false;
+    const int bit = (x & 7) + 8 * (y & 7) + 64 * (z & 7);
+    return (known[(int64_t)p * 8 + (bit >> 6)] >> (bit & 63)) & 1ull;
+}
+
+__device__ __forceinline__ void add_test(uint64_t* tkeys, uint32_t tmask, unsigned* tflags, int x, int y, int z,
+                                         int sign, int* err) {
+    if (!(x > -kIjkLimit && x < kIjkLimit && y > -kIjkLimit && y < kIjkLimit && z > -kIjkLimit && z < kIjkLimit)) return;
+    const int64_t s = ht_insert(tkeys, tmask, pack_key(x, y, z), err);
+    if (s >= 0) atomicOr(&tflags[s], sign > 0 ? 1u : 2u);
+}
+
+// Cyclic Jacobi rotations on a symmetric 3x3 (fixed 12 sweeps), every operation explicitly
+// rounded so that the result is the same sequence of IEEE operations on every target.
+__device__ void jacobi3_rn(double a[3][3], double v[3][3]) {
+    for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j) v[i][j] = i == j ? 1.0 : 0.0;
+    const int PQ[3][2] = {{0, 1}, {0, 2}, {1, 2}};
+    for (int sweep = 0; sweep < 12; ++sweep) {
+        for (int r = 0; r < 3; ++r) {
+            const int p = PQ[r][0], q = PQ[r][1];
+            if (a[p][q] == 0.0) continue;
+            const double theta = __ddiv_rn(__dsub_rn(a[q][q], a[p][p]), __dmul_rn(2.0, a[p][q]));
+            double t = __ddiv_rn(1.0, __dadd_rn(fabs(theta), __dsqrt_rn(__dadd_rn(__dmul_rn(theta, theta), 1.0))));
+            if (theta < 0.0) t = -t;
+            const double c = __ddiv_rn(1.0, __dsqrt_rn(__dadd_rn(__dmul_rn(t, t), 1.0)));
+            const double sn = __dmul_rn(t, c);
+            for (int k = 0; k < 3; ++k) {
+                const double akp = a[k][p], akq = a[k][q];
+                a[k][p] = __dsub_rn(__dmul_rn(c, akp), __dmul_rn(sn, akq));
+                a[k][q] = __dadd_rn(__dmul_rn(sn, akp), __dmul_rn(c, akq));
+            }
+            for (int k = 0; k < 3; ++k) {
+                const double apk = a[p][k], aqk = a[q][k];
+                a[p][k] = __dsub_rn(__dmul_rn(c, apk), __dmul_rn(sn, aqk));
+                a[q][k] = __dadd_rn(__dmul_rn(sn, apk), __dmul_rn(c, aqk));
+            }
+            for (int k = 0; k < 3; ++k) {
+                const double vkp = v[k][p], vkq = v[k][q];
+                v[k][p] = __dsub_rn(__dmul_rn(c, vkp), __dmul_rn(sn, vkq));
+                v[k][q] = __dadd_rn(__dmul_rn(sn, vkp), __dmul_rn(c, vkq));
+            }
+        }
+    }
+}
+
+// Thread per surface voxel.
+__global__ void k_raycast_tests(const uint64_t* svox, int64_t ns, const uint64_t* fkeys, uint32_t fmask,
+                                const unsigned long long* fmasks, const uint64_t* gkeys, uint32_t gmask,
+                                const int32_t* g_slot2pool, const unsigned long long* g_known, double ox, double oy,
+                                double oz, int have_o, int ovx, int ovy, int ovz, double vs, int K, uint64_t* tkeys,
+                                uint32_t tmask, unsigned* tflags, int* err) {
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= ns) return;
+    int sv[3];
+    unpack_key(svox[i], sv[0], sv[1], sv[2]);
+    add_test(tkeys, tmask, tflags, sv[0], sv[1], sv[2], 1, err);
+    if (!have_o) return;
+    // normal from the exact integer scatter of the occupied 3x3x3 block
+    long long cnt = 0, S1[3] = {0, 0, 0}, S2[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};
+    for (int dz = -1; dz <= 1; ++dz)
+        for (int dy = -1; dy <= 1; ++dy)
+            for (int dx = -1; dx <= 1; ++dx) {
+                if (!frame_occupied(fkeys, fmask, fmasks, sv[0] + dx, sv[1] + dy, sv[2] + dz)) continue;
+                const long long o[3] = {dx, dy, dz};
+                ++cnt;
+                for (int a = 0; a < 3; ++a) {
+                    S1[a] += o[a];
+                    for (int b = 0; b < 3; ++b) S2[a][b] += o[a] * o[b];
+                }
+            }
+    if (cnt >= 3 && K > 0) {
+        double A[3][3], V[3][3];
+        for (int a = 0; a < 3; ++a)
+            for (int b = 0; b < 3; ++b) A[a][b] = (double)(cnt * S2[a][b] - S1[a] * S1[b]);
+        jacobi3_rn(A, V);
+        int k = 0;
+        for (int j = 1; j < 3; ++j)
+            if (A[j][j] < A[k][k]) k = j;
+        const double nn =
+            __dsqrt_rn(__dadd_rn(__dadd_rn(__dmul_rn(V[0][k], V[0][k]), __dmul_rn(V[1][k], V[1][k])), __dmul_rn(V[2][k], V[2][k])));
+        double nrm[3];
+        for (int a = 0; a < 3; ++a) nrm[a] = __ddiv_rn(V[a][k], nn);
+        const double org[3] = {ox, oy, oz};
+        double e = 0.0;
+        for (int a = 0; a < 3; ++a) e = __dadd_rn(e, __dmul_rn(nrm[a], __dsub_rn(org[a], __dmul_rn((double)sv[a], vs))));
+        if (e < 0.0)
+            for (int a = 0; a < 3; ++a) nrm[a] = -nrm[a];
+        for (int kk = -K; kk <= K; ++kk) {
+            if (kk == 0) continue;
+            int v[3];
+            for (int a = 0; a < 3; ++a) v[a] = sv[a] + (int)floor(__dadd_rn(__dmul_rn((double)kk, nrm[a]), 0.5));
+            add_test(tkeys, tmask, tflags, v[0], v[1], v[2], kk > 0 ? 1 : -1, err);
+        }
+    }
+    // integer 3D Bresenham from the origin's voxel to the surface voxel (excluded)
+    const int a0[3] = {ovx, ovy, ovz};
+    long long d[3], st[3], pcur[3] = {a0[0], a0[1], a0[2]};
+    for (int k = 0; k < 3; ++k) {
+        d[k] = sv[k] > a0[k] ? (long long)sv[k] - a0[k] : (long long)a0[k] - sv[k];
+        st[k] = sv[k] > a0[k] ? 1 : -1;
+    }
+    int m = 0;
+    if (d[1] > d[m]) m = 1;
+    if (d[2] > d[m]) m = 2;
+    const int u = (m + 1) % 3, w = (m + 2) % 3;
+    long long eu = 2 * d[u] - d[m], ew = 2 * d[w] - d[m];
+    for (long long step = 0; step < d[m]; ++step) {
+        if (grid_known(gkeys, gmask, g_slot2pool, g_known, (int)pcur[0], (int)pcur[1], (int)pcur[2]))
+            add_test(tkeys, tmask, tflags, (int)pcur[0], (int)pcur[1], (int)pcur[2], 1, err);
+        if (eu > 0) {
+            pcur[u] += st[u];
+            eu -= 2 * d[m];
+        }
+        if (ew > 0) {
+            pcur[w] += st[w];
+            ew -= 2 * d[m];
+        }
+        eu += 2 * d[u];
+        ew += 2 * d[w];
+        pcur[m] += st[m];
+    }
+}
+
+// Thread per testing voxel: closest GP leaf (own leaf; else the nearest of the 26 neighbours,
+// ties in (dz, dy, dx) order; else the nearest within the search radius, ties to the smaller
+// key), or -1.
+__global__ void k_assign_list(const uint64_t* tkey, int64_t nt, const uint64_t* fkeys, uint32_t fmask,
+                              const int32_t* slot2leaf, int R, int32_t* tinst, int64_t* inst_cnt, int* n_orphan) {
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= nt) return;
+    int x, y, z;
+    unpack_key(tkey[i], x, y, z);
+    const int M[3] = {leaf_coord(x), leaf_coord(y), leaf_coord(z)};
+    const int ijk[3] = {x, y, z};
+    int inst = -1;
+    int64_t s = ht_find(fkeys, fmask, pack_key(M[0], M[1], M[2]));
+    if (s >= 0) inst = slot2leaf[s];
+    if (inst < 0) {
+        long long best = 0;
+        for (int d = 0; d < 27; ++d) {
+            if (d == 13) continue;
+            const int F[3] = {M[0] + d % 3 - 1, M[1] + (d / 3) % 3 - 1, M[2] + d / 9 - 1};
+            const int64_t fs = ht_find(fkeys, fmask, pack_key(F[0], F[1], F[2]));
+            if (fs < 0) continue;
+            long long d2 = 0;
+            for (int a = 0; a < 3; ++a) {
+                const long long e = 2ll * ijk[a] - (16ll * F[a] + 7);
+                d2 += e * e;
+            }
+            if (inst < 0 || d2 < best) {
+                best = d2;
+                inst = slot2leaf[fs];
+            }
+        }
+    }
+    if (inst < 0) {
+        long long best = 0;
+        uint64_t bkey = 0;
+        for (int dz = -R; dz <= R; ++dz)
+            for (int dy = -R; dy <= R; ++dy)
+                for (int dx = -R; dx <= R; ++dx) {
+                    const int F[3] = {M[0] + dx, M[1] + dy, M[2] + dz};
+                    const uint64_t k = pack_key(F[0], F[1], F[2]);
+                    const int64_t fs = ht_find(fkeys, fmask, k);
+                    if (fs < 0) continue;
+                    long long d2 = 0;
+                    for (int a = 0; a < 3; ++a) {
+                        const long long e = 2ll * ijk[a] - (16ll * F[a] + 7);
+                        d2 += e * e;
+                    }
+                    if (inst < 0 || d2 < best || (d2 == best && k < bkey)) {
+                        best = d2;
+                        bkey = k;
+                        inst = slot2leaf[fs];
+                    }
+                }
+    }
+    tinst[i] = inst;
+    if (inst >= 0) atomicAdd((unsigned long long*)&inst_cnt[inst], 1ull);
+    else atomicAdd(n_orphan, 1);
+}
+
+__global__ void k_scatter_list(const uint64_t* tkey, const int8_t* tsign_in, int64_t nt, const int32_t* tinst,
+                               const int64_t* q_off, int64_t* cursor, int64_t orphan_base, int* orphan_cursor,
+                               uint64_t* gkey, int8_t* gsign) {
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= nt) return;
+    const int I = tinst[i];
+    int64_t pos;
+    if (I >= 0) pos = q_off[I] + (int64_t)atomicAdd((unsigned long long*)&cursor[I], 1ull);
+    else pos = orphan_base + atomicAdd(orphan_cursor, 1);
+    gkey[pos] = tkey[i];
+    gsign[pos] = tsign_in[i];
+}
+
+__global__ void k_collect_tests(const uint64_t* keys, const unsigned* flags, int64_t cap, uint64_t* out_key,
+                                int8_t* out_sign, int* count) {
+    const int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (s >= cap || keys[s] == kEmpty) return;
+    const int i = atomicAdd(count, 1);
+    out_key[i] = keys[s];
+    out_sign[i] = (flags[s] & 1u) ? 1 : -1;
+}
+
+__global__ void k_orphans_and_sign(int64_t nt, int64_t n_assigned, const int8_t* sign, double* d, double* grad,
+                                   double* v, uint8_t* status) {
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= nt) return;
+    if (i >= n_assigned) {
+        d[i] = INFINITY;
+        v[i] = INFINITY;
+        grad[3 * i] = grad[3 * i + 1] = grad[3 * i + 2] = 0.0;
+        status[i] = VGP_ST_NO_SUPPORT;
+        return;
+    }
+    if (sign[i] < 0) {
+        if (status[i] == VGP_ST_OK || status[i] == VGP_ST_CLAMPED) d[i] = -d[i];
+        for (int a = 0; a < 3; ++a) grad[3 * i + a] = -grad[3 * i + a];
+    }
+}
+}  // namespace
+
+void frame_surface_voxels(const int32_t* list, const uint64_t* lkeys, int nl, const unsigned long long* masks,
+                          const int64_t* soff, uint64_t* svox, cudaStream_t st) {
+    if (nl > 0) {
+        k_surface_voxels<<<nblk((int64_t)nl * 32), TB, 0, st>>>(list, lkeys, nl, masks, soff, svox);
+        note_launch();
+    }
+}
+
+void frame_raycast_tests(const uint64_t* svox, int64_t ns, const Table& ft, const unsigned long long* fmasks,
+                         const Table& g, const int32_t* g_slot2pool, const unsigned long long* g_known,
+                         const double origin[3], int have_o, const int ov[3], double vs, int K, const Table& tt,
+                         unsigned* tflags, int* err, cudaStream_t st) {
+    if (ns > 0) {
+        k_raycast_tests<<<nblk(ns, 128), 128, 0, st>>>(svox, ns, ft.keys, ft.mask, fmasks, g.keys, g.mask, g_slot2pool,
+                                                       g_known, origin[0], origin[1], origin[2], have_o, ov[0], ov[1],
+                                                       ov[2], vs, K, tt.keys, tt.mask, tflags, err);
+        note_launch();
+    }
+}
+
+void frame_collect_tests(const Table& tt, const unsigned* tflags, uint64_t* out_key, int8_t* out_sign, int* count,
+                         cudaStream_t st) {
+    cudaMemsetAsync(count, 0, sizeof(int), st);
+    k_collect_tests<<<nblk(tt.cap()), TB, 0, st>>>(tt.keys, tflags, (int64_t)tt.cap(), out_key, out_sign, count);
+    note_launch();
+}
+
+void frame_assign_list(const uint64_t* tkey, int64_t nt, const Table& ft, const int32_t* slot2leaf, int R,
+                       int32_t* tinst, int64_t* inst_cnt, int* n_orphan, cudaStream_t st) {
+    if (nt > 0) {
+        k_assign_list<<<nblk(nt, 128), 128, 0, st>>>(tkey, nt, ft.keys, ft.mask, slot2leaf, R, tinst, inst_cnt, n_orphan);
+        note_launch();
+    }
+}
+
+void frame_scatter_list(const uint64_t* tkey, const int8_t* tsign, int64_t nt, const int32_t* tinst, const int64_t* q_off,
+                        int64_t* cursor, int64_t orphan_base, int* orphan_cursor, uint64_t* gkey, int8_t* gsign,
+                        cudaStream_t st) {
+    if (nt > 0) {
+        k_scatter_list<<<nblk(nt), TB, 0, st>>>(tkey, tsign, nt, tinst, q_off, cursor, orphan_base, orphan_cursor, gkey,
+                                               gsign);
+        note_launch();
+    }
+}
+
+void frame_orphans_and_sign(int64_t nt, int64_t n_assigned, const int8_t* sign, double* d, double* grad, double* v,
+                            uint8_t* status, cudaStream_t st) {
+    if (nt > 0) {
+        k_orphans_and_sign<<<nblk(nt), TB, 0, st>>>(nt, n_assigned, sign, d, grad, v, status);
         note_launch();
     }
 }

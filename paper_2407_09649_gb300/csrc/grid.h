@@ -28,6 +28,23 @@ void frame_assign_tests(const uint64_t* tl_keys, int ntl, const Table& ft, const
 void frame_scatter_tests(const uint64_t* tl_keys, int ntl, const Table& ft, const int32_t* slot2leaf,
                          const int64_t* q_off, int64_t* cursor, uint64_t* tkey, cudaStream_t st);
 
+// ray-cast testing points (Sec. IV-B)
+void frame_surface_voxels(const int32_t* list, const uint64_t* lkeys, int nl, const unsigned long long* masks,
+                          const int64_t* soff, uint64_t* svox, cudaStream_t st);
+void frame_raycast_tests(const uint64_t* svox, int64_t ns, const Table& ft, const unsigned long long* fmasks,
+                         const Table& g, const int32_t* g_slot2pool, const unsigned long long* g_known,
+                         const double origin[3], int have_o, const int ov[3], double vs, int K, const Table& tt,
+                         unsigned* tflags, int* err, cudaStream_t st);
+void frame_collect_tests(const Table& tt, const unsigned* tflags, uint64_t* out_key, int8_t* out_sign, int* count,
+                         cudaStream_t st);
+void frame_assign_list(const uint64_t* tkey, int64_t nt, const Table& ft, const int32_t* slot2leaf, int R,
+                       int32_t* tinst, int64_t* inst_cnt, int* n_orphan, cudaStream_t st);
+void frame_scatter_list(const uint64_t* tkey, const int8_t* tsign, int64_t nt, const int32_t* tinst, const int64_t* q_off,
+                        int64_t* cursor, int64_t orphan_base, int* orphan_cursor, uint64_t* gkey, int8_t* gsign,
+                        cudaStream_t st);
+void frame_orphans_and_sign(int64_t nt, int64_t n_assigned, const int8_t* sign, double* d, double* grad, double* v,
+                            uint8_t* status, cudaStream_t st);
+
 // surface (G-GPDF)
 void surface_bin(const float* pts, int64_t n, const DevParams& P, const Table& t, int32_t* pt_slot, int32_t* slot_cnt,
                  int* n_valid, int* err, cudaStream_t st);

@@ -85,6 +85,7 @@ void exclusive_scan_i64(const int64_t* in, int64_t* out, int64_t n, cudaStream_t
 void fill_i64(int64_t* p, int64_t v, int64_t n, cudaStream_t st);
 void fill_u64(uint64_t* p, uint64_t v, int64_t n, cudaStream_t st);
 void fill_i32(int32_t* p, int32_t v, int64_t n, cudaStream_t st);
+void widen_i32(const int32_t* in, int64_t* out, int64_t n, cudaStream_t st);
 
 // Solve every instance of the batch (factorise, alpha, evaluate its queries).  Returns
 // error bits through *err_dev.  Synchronises once to read the size histogram.

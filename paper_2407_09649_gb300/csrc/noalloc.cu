@@ -112,7 +112,7 @@ __global__ void k_static_prep(const int64_t* inst_off, int64_t n_inst, const flo
 bool params_ok(const vgp_params* p) {
     return p && p->voxel_size > 0 && std::isfinite(p->voxel_size) && p->lengthscale > 0 && std::isfinite(p->lengthscale) &&
            p->sigma_occ > 0 && std::isfinite(p->sigma_occ) && p->d_max > 0 && p->d_var_floor > 0 &&
-           (p->precision == VGP_FP64 || p->precision == VGP_MIXED) && !p->reserved;
+           (p->precision == VGP_FP64 || p->precision == VGP_MIXED);
 }
 
 }  // namespace
