@@ -77,6 +77,10 @@ def lib():
         L.or_grid_size.argtypes = [vp]
         L.or_grid_size.restype = i64
         L.or_grid_export.argtypes = [vp] * 5
+        L.or_grid_crossings.argtypes = [vp, C.c_double, C.c_int, vp, vp, vp]
+        L.or_grid_crossings.restype = i64
+        L.or_grid_mesh.argtypes = [vp, C.c_double, C.c_int, vp, vp, vp]
+        L.or_grid_mesh.restype = i64
         L.or_surface_new.argtypes = [C.POINTER(Params), vp, i64]
         L.or_surface_new.restype = vp
         L.or_surface_free.argtypes = [vp]
@@ -255,6 +259,61 @@ class Grid:
         fl = np.zeros(n, np.uint8)
         lib().or_grid_export(self.h, _p(k), _p(D), _p(V), _p(fl))
         return k, D, V, fl
+
+    def crossings(self, voxel_size: float, active_only: bool = False):
+        """Zero crossings owned by the voxels of all leaves (or of the leaves touched by the
+        latest fusion): float32 points (n, 3), owner voxel keys, slots 2 axis + (+ side)."""
+        L = lib()
+        n = L.or_grid_crossings(self.h, float(voxel_size), int(active_only), None, None, None)
+        xyz = np.zeros((n, 3), np.float32)
+        owner = np.zeros(n, np.uint64)
+        slot = np.zeros(n, np.uint8)
+        L.or_grid_crossings(self.h, float(voxel_size), int(active_only), _p(xyz), _p(owner), _p(slot))
+        return xyz, owner, slot
+
+    def mesh(self, voxel_size: float, active_only: bool = False):
+        """Marching-cubes triangle soup: xyz (T, 3, 3) FP64, edge keys (T, 3), edge axes (T, 3)."""
+        L = lib()
+        n = L.or_grid_mesh(self.h, float(voxel_size), int(active_only), None, None, None)
+        xyz = np.zeros((n, 3, 3))
+        ek = np.zeros((n, 3), np.uint64)
+        ea = np.zeros((n, 3), np.uint8)
+        L.or_grid_mesh(self.h, float(voxel_size), int(active_only), _p(xyz), _p(ek), _p(ea))
+        return xyz, ek, ea
+
+
+def leaf_key_of_points(xyz, voxel_size: float) -> np.ndarray:
+    """Leaf key of each float32 point (voxel floor(p / vs + 1/2), leaf floor(voxel / 8))."""
+    p = np.asarray(xyz, np.float32).astype(np.float64)
+    ijk = np.floor(p / voxel_size + 0.5).astype(np.int64)
+    lf = np.floor_divide(ijk, 8)
+    return pack_key(lf) if len(p) else np.zeros(0, np.uint64)
+
+
+class SurfaceStore:
+    """Zero-crossing training set of the G-GPDF, kept per leaf (Sec. IV-D): after each
+    fusion the leaves it touched get their crossings recomputed and replace their old ones;
+    the other leaves keep theirs."""
+
+    def __init__(self, voxel_size: float):
+        self.vs = float(voxel_size)
+        self.leaf = {}
+
+    def update(self, grid: Grid):
+        k, _, _, fl = grid.export()
+        keys = k[(fl & 1) == 1]
+        for a in np.unique(pack_key(np.floor_divide(unpack_key(keys), 8))).tolist() if len(keys) else []:
+            self.leaf.pop(int(a), None)
+        xyz, _, _ = grid.crossings(self.vs, active_only=True)
+        lk = leaf_key_of_points(xyz, self.vs)
+        for a in np.unique(lk).tolist():
+            self.leaf[int(a)] = xyz[lk == a]
+
+    def points(self) -> np.ndarray:
+        """All stored crossings, leaves in ascending key order (in-leaf order kept)."""
+        if not self.leaf:
+            return np.zeros((0, 3), np.float32)
+        return np.concatenate([self.leaf[k] for k in sorted(self.leaf)], 0)
 
 
 class Surface:

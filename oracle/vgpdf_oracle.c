@@ -21,7 +21,9 @@
  *   - G-GPDF queries against the GP of the query's 27-leaf neighbourhood (Sec. IV-D,
  *     with the neighbourhood search done on the leaf lattice instead of a kd-tree);
  *   - the backward pass of the distance w.r.t. query and surface points, derived from
- *     Eq. 1 by differentiating alpha = A^-1 1.
+ *     Eq. 1 by differentiating alpha = A^-1 1;
+ *   - zero crossings and marching cubes over the fused grid, restricted to the leaves the
+ *     latest fusion touched (Sec. IV-D): the G-GPDF training points and the mesh.
  *
  * The paper leaves the following open; this file takes these readings:
  *   - voxel index ijk = floor(p / vs + 1/2) in IEEE FP64 (p widened from float32);
@@ -874,6 +876,203 @@ void or_grid_export(const or_grid* g, uint64_t* key, double* D, double* V, uint8
             flags[i] = l >= 0 ? g->lflag[l] : 0;
         }
     }
+}
+
+/* ------------------------------------------------------------------------------------ */
+/* zero crossings and marching cubes over the fused grid (Sec. IV-D)                     */
+/*                                                                                      */
+/* The fused values D live at voxel centres c(ijk) = ijk * vs.  A voxel is inside when   */
+/* D < 0.  Each axis edge between two known neighbouring voxels a and b = a + e_axis     */
+/* whose insides differ carries one zero crossing, placed by linear interpolation from   */
+/* the lower end a: t = D_a / (D_a - D_b), p_axis = (a_axis + t) vs, the other two        */
+/* coordinates a_k vs.  As a G-GPDF training point the crossing is rounded to float32;   */
+/* it belongs to the voxel that float32 point falls in (always a or b), and so to that   */
+/* voxel's leaf.  Marching cubes runs on the cells whose lower corner lies in a selected */
+/* leaf and whose 8 corners are all known; each cell's polygon loops come from walking   */
+/* its six faces, where every in->out edge (counter-clockwise seen from outside) is      */
+/* joined to the out->in edge that closes the run of inside corners behind it, so inside */
+/* corners that only touch diagonally stay apart.  The loops are fanned from their       */
+/* lowest local edge and oriented so that triangle normals point to increasing D.        */
+/* ------------------------------------------------------------------------------------ */
+static const gvox* grid_find(const or_grid* g, const int64_t ijk[3]) {
+    for (int a = 0; a < 3; ++a)
+        if (ijk[a] <= -KEY_BIAS || ijk[a] >= KEY_BIAS) return NULL;
+    uint64_t k = pack_key(ijk[0], ijk[1], ijk[2]);
+    int64_t lo = 0, hi = g->n;
+    while (lo < hi) {
+        int64_t mid = lo + (hi - lo) / 2;
+        if (g->v[mid].key < k) lo = mid + 1; else hi = mid;
+    }
+    return (lo < g->n && g->v[lo].key == k) ? &g->v[lo] : NULL;
+}
+
+static int leaf_selected(const or_grid* g, uint64_t leaf_key, int active_only) {
+    int64_t l = find_key(g->lkey, g->nl, leaf_key);
+    if (l < 0) return 0;
+    return active_only ? (g->lflag[l] & 1) : 1;
+}
+
+/* the crossing on the edge from voxel a along `axis`, in FP64 */
+static void crossing_point(const int64_t a[3], int axis, double Da, double Db, double vs, double p[3]) {
+    double t = Da / (Da - Db);
+    for (int k = 0; k < 3; ++k) p[k] = (double)a[k] * vs;
+    p[axis] = ((double)a[axis] + t) * vs;
+}
+
+typedef struct {
+    uint64_t leaf;
+    int32_t bit, slot;
+    float p[3];
+    uint64_t owner;
+} xrec;
+
+static int cmp_xrec(const void* a, const void* b) {
+    const xrec* x = (const xrec*)a;
+    const xrec* y = (const xrec*)b;
+    if (x->leaf != y->leaf) return x->leaf < y->leaf ? -1 : 1;
+    if (x->bit != y->bit) return x->bit < y->bit ? -1 : 1;
+    return (x->slot > y->slot) - (x->slot < y->slot);
+}
+
+/* Zero crossings owned by the voxels of the selected leaves (all leaves, or those
+ * touched by the latest fusion), ordered by leaf key, then in-leaf voxel bit, then
+ * slot = 2 axis + (neighbour on the + side).  Returns the count; fills the outputs when
+ * they are given (xyz: 3 floats per crossing). */
+int64_t or_grid_crossings(const or_grid* g, double vs, int active_only, float* xyz, uint64_t* owner,
+                          uint8_t* slot) {
+    int64_t cap = 16, m = 0;
+    xrec* R = (xrec*)malloc(sizeof(xrec) * cap);
+    for (int64_t i = 0; i < g->n; ++i) {
+        int64_t v[3], leaf[3];
+        int32_t bit;
+        unpack_key(g->v[i].key, v);
+        leaf_of(v, leaf, &bit);
+        uint64_t lk = pack_key(leaf[0], leaf[1], leaf[2]);
+        if (!leaf_selected(g, lk, active_only)) continue;
+        for (int s = 0; s < 6; ++s) {
+            int axis = s / 2, dir = (s & 1) ? 1 : -1;
+            int64_t nb[3] = {v[0], v[1], v[2]};
+            nb[axis] += dir;
+            const gvox* o = grid_find(g, nb);
+            if (!o) continue;
+            const gvox *lo = dir > 0 ? &g->v[i] : o, *hi = dir > 0 ? o : &g->v[i];
+            if ((lo->D < 0.0) == (hi->D < 0.0)) continue;
+            int64_t a[3] = {v[0], v[1], v[2]};
+            if (dir < 0) a[axis] -= 1;
+            double p[3];
+            crossing_point(a, axis, lo->D, hi->D, vs, p);
+            float pf[3] = {(float)p[0], (float)p[1], (float)p[2]};
+            double pd[3] = {(double)pf[0], (double)pf[1], (double)pf[2]};
+            int64_t w[3];
+            if (!voxel_ijk(pd, vs, w) || w[0] != v[0] || w[1] != v[1] || w[2] != v[2]) continue;
+            if (m == cap) { cap *= 2; R = (xrec*)realloc(R, sizeof(xrec) * cap); }
+            R[m].leaf = lk; R[m].bit = bit; R[m].slot = s;
+            R[m].p[0] = pf[0]; R[m].p[1] = pf[1]; R[m].p[2] = pf[2];
+            R[m].owner = g->v[i].key;
+            ++m;
+        }
+    }
+    qsort(R, (size_t)m, sizeof(xrec), cmp_xrec);
+    for (int64_t i = 0; i < m; ++i) {
+        if (xyz) { xyz[3 * i] = R[i].p[0]; xyz[3 * i + 1] = R[i].p[1]; xyz[3 * i + 2] = R[i].p[2]; }
+        if (owner) owner[i] = R[i].owner;
+        if (slot) slot[i] = (uint8_t)R[i].slot;
+    }
+    free(R);
+    return m;
+}
+
+/* corners of the face with outward normal (2 side - 1) e_axis, counter-clockwise seen
+ * from outside; corner index = x + 2 y + 4 z of the cell-local offset */
+static void face_corners(int axis, int side, int q[4]) {
+    static const int cyc[4][2] = {{0, 0}, {1, 0}, {1, 1}, {0, 1}}; /* CCW in (u, w) seen from +axis */
+    int u = (axis + 1) % 3, w = (axis + 2) % 3;                   /* e_u x e_w = e_axis */
+    for (int i = 0; i < 4; ++i) {
+        int j = side ? i : (4 - i) % 4;
+        int c[3];
+        c[axis] = side; c[u] = cyc[j][0]; c[w] = cyc[j][1];
+        q[i] = c[0] + 2 * c[1] + 4 * c[2];
+    }
+}
+
+/* cell-local edge between corners c0, c1 (differing in one bit): 3 * lower corner + axis */
+static int cell_edge(int c0, int c1) {
+    int x = c0 ^ c1, axis = x == 1 ? 0 : (x == 2 ? 1 : 2);
+    int lo = c0 < c1 ? c0 : c1;
+    return 3 * lo + axis;
+}
+
+/* Triangles of one cell from its inside mask; out[3 t + j] are cell-local edges
+ * (3 * lower corner + axis).  Returns the triangle count. */
+static int cell_triangles(int inside_mask, int* out) {
+    int next[24];
+    for (int e = 0; e < 24; ++e) next[e] = -1;
+    for (int axis = 0; axis < 3; ++axis)
+        for (int side = 0; side < 2; ++side) {
+            int q[4];
+            face_corners(axis, side, q);
+            for (int k = 0; k < 4; ++k) {
+                int ck = q[k], cn = q[(k + 1) % 4];
+                if (!((inside_mask >> ck) & 1) || ((inside_mask >> cn) & 1)) continue;
+                int j = k;
+                while ((inside_mask >> q[(j + 3) % 4]) & 1) j = (j + 3) % 4;
+                next[cell_edge(ck, cn)] = cell_edge(q[(j + 3) % 4], q[j]);
+            }
+        }
+    int seen[24] = {0}, nt = 0;
+    for (int e = 0; e < 24; ++e) {
+        if (next[e] < 0 || seen[e]) continue;
+        int loop[24], m = 0;
+        for (int f = e; !seen[f]; f = next[f]) { seen[f] = 1; loop[m++] = f; }
+        /* the face walk runs the loop with normals toward the inside: fan it reversed */
+        for (int i = 1; i + 1 < m; ++i) {
+            out[3 * nt] = loop[0];
+            out[3 * nt + 1] = loop[i + 1];
+            out[3 * nt + 2] = loop[i];
+            ++nt;
+        }
+    }
+    return nt;
+}
+
+/* Marching-cubes triangles of the cells whose lower corner lies in a selected leaf and
+ * whose 8 corners are known.  Per triangle: xyz 9 doubles (FP64 crossing points), and
+ * for each vertex its edge as (key of the edge's lower voxel, axis).  Cells in ascending
+ * key order of the lower corner, triangles in fan order.  Returns the triangle count. */
+int64_t or_grid_mesh(const or_grid* g, double vs, int active_only, double* xyz, uint64_t* ekey, uint8_t* eaxis) {
+    int64_t nt = 0;
+    for (int64_t i = 0; i < g->n; ++i) {
+        int64_t v[3], leaf[3];
+        int32_t bit;
+        unpack_key(g->v[i].key, v);
+        leaf_of(v, leaf, &bit);
+        if (!leaf_selected(g, pack_key(leaf[0], leaf[1], leaf[2]), active_only)) continue;
+        double D[8];
+        int mask = 0, ok = 1;
+        for (int c = 0; c < 8 && ok; ++c) {
+            int64_t w[3] = {v[0] + (c & 1), v[1] + ((c >> 1) & 1), v[2] + ((c >> 2) & 1)};
+            const gvox* o = grid_find(g, w);
+            if (!o) { ok = 0; break; }
+            D[c] = o->D;
+            if (D[c] < 0.0) mask |= 1 << c;
+        }
+        if (!ok || mask == 0 || mask == 255) continue;
+        int tri[3 * 24];
+        int n = cell_triangles(mask, tri);
+        for (int t = 0; t < n; ++t, ++nt) {
+            for (int j = 0; j < 3; ++j) {
+                int e = tri[3 * t + j], lc = e / 3, axis = e % 3;
+                int64_t a[3] = {v[0] + (lc & 1), v[1] + ((lc >> 1) & 1), v[2] + ((lc >> 2) & 1)};
+                int uc = lc | (1 << axis);
+                double p[3];
+                crossing_point(a, axis, D[lc], D[uc], vs, p);
+                if (xyz) for (int k = 0; k < 3; ++k) xyz[9 * nt + 3 * j + k] = p[k];
+                if (ekey) ekey[3 * nt + j] = pack_key(a[0], a[1], a[2]);
+                if (eaxis) eaxis[3 * nt + j] = (uint8_t)axis;
+            }
+        }
+    }
+    return nt;
 }
 
 /* ------------------------------------------------------------------------------------ */
