@@ -55,6 +55,7 @@ extern "C" {
 
 typedef struct vgp_map vgp_map;
 typedef struct vgp_frame vgp_frame;
+typedef struct vgp_mesh vgp_mesh;
 typedef void* vgp_stream; /* cudaStream_t */
 
 enum {
@@ -241,6 +242,62 @@ int vgp_import_grid(vgp_map* m, int64_t n, const uint64_t* keys, const double* D
  * Synchronises the stream.
  */
 int vgp_set_surface(vgp_map* m, const float* pts_dev, int64_t n, vgp_stream stream);
+
+/*
+ * Zero crossings and marching cubes over the fused grid (Sec. IV-D: after fusion the touched
+ * leaves are active; marching cubes recovers the surface there and its zero crossings train
+ * the G-GPDF).  The fused value D of a voxel sits at its centre ijk * voxel_size; a voxel is
+ * inside when D < 0.
+ *   - zero crossing: on every axis edge between two known neighbouring voxels a, b = a + e_axis
+ *     whose insides differ, at p_axis = (a_axis + t) vs with t = D_a / (D_a - D_b), the other two
+ *     coordinates a_k vs (round-to-nearest FP64, no contraction); rounded to float32 it belongs
+ *     to the voxel it falls in (one of a, b).  Slot = 2 axis + (the other end is on the + side).
+ *   - marching cubes: every cell whose lower corner lies in a selected leaf and whose 8 corners
+ *     are known; per inside mask the triangles come from walking the cell's faces, ambiguous
+ *     faces keeping diagonal inside corners apart (so a face is split alike from both cells and
+ *     the mesh is closed where the grid is), loops fanned from their first edge in
+ *     (lower corner, axis) order, normals towards increasing D.
+ * active_only = 1 selects the leaves the latest vgp_fuse touched, 0 all leaves.  The handle
+ * owns device arrays, read with the two accessors below (pointers valid until
+ * vgp_mesh_destroy):
+ *   crossings: xyz [n][3] float32, owner [n] voxel key, slot [n] uint8; grouped by leaf, in a
+ *              leaf in voxel-bit then slot order; the order of the leaf groups is unspecified.
+ *   triangles: xyz [n][3][3] FP64 vertices; edge_key [n][3] key of each vertex's edge lower
+ *              voxel, edge_axis [n][3]; a leaf's triangles by lower-corner bit; leaf order
+ *              unspecified.  Shared vertices repeat; (edge_key, edge_axis) identifies them.
+ * want_triangles = 0 skips the triangles (n = 0).  An empty grid gives empty arrays.
+ * Synchronises the stream.
+ */
+int vgp_extract_mesh(vgp_map* m, int active_only, int want_triangles, vgp_stream stream, vgp_mesh** out);
+int vgp_mesh_crossings(const vgp_mesh* mesh, int64_t* n, const float** xyz_dev, const uint64_t** owner_dev,
+                       const uint8_t** slot_dev);
+int vgp_mesh_triangles(const vgp_mesh* mesh, int64_t* n, const double** xyz_dev, const uint64_t** edge_key_dev,
+                       const uint8_t** edge_axis_dev);
+void vgp_mesh_destroy(vgp_mesh* mesh);
+
+/*
+ * Host copy of the marching-cubes table the kernels use (no device work): tab [256][16] cell
+ * edges, three per triangle, edge = 4 axis + bit_u + 2 bit_w with (u, w) = (axis + 1,
+ * axis + 2) mod 3 the lower corner's other coordinates; ntri [256] triangles per inside mask
+ * (corner c = x + 2 y + 4 z).
+ */
+void vgp_debug_mc_table(uint8_t* tab, uint8_t* ntri);
+
+/*
+ * G-GPDF training set from the map (Sec. IV-D): the map keeps the zero crossings per leaf.
+ * This call drops the kept points that lie in leaves the latest vgp_fuse touched, appends the
+ * zero crossings of those leaves (as vgp_extract_mesh with active_only = 1 lists them), and
+ * trains the G-GPDF on the result as vgp_set_surface would (replacing any surface set
+ * before).  Kept points keep their order; each touched leaf's crossings follow in voxel-bit,
+ * slot order.  Synchronises the stream.
+ */
+int vgp_update_surface(vgp_map* m, vgp_stream stream);
+
+/*
+ * The map's kept G-GPDF training set: n points, device float32 [n][3] owned by the map and
+ * valid until the next vgp_update_surface or vgp_destroy.
+ */
+int vgp_surface_points(vgp_map* m, int64_t* n, const float** xyz_dev);
 
 /*
  * G-GPDF query (Sec. IV-D; Eqs. 1-5).  For each query point q_dev[i] (float32 [n][3]):

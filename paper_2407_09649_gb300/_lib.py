@@ -53,6 +53,13 @@ SIGNATURES = [
     ("vgp_query_backward", _i32, [_vp, _vp, _i64, _vp, _vp, _vp, _vp]),
     ("vgp_autotune", _i32, [_vp, _vp, _i64, _vp]),
     ("vgp_query_smooth", _i32, [_vp, _vp, _i64, C.c_int32, C.c_double, _vp, _vp, _vp, _vp, _vp]),
+    ("vgp_extract_mesh", _i32, [_vp, _i32, _i32, _vp, _PP]),
+    ("vgp_mesh_crossings", _i32, [_vp, C.POINTER(C.c_int64), _PP, _PP, _PP]),
+    ("vgp_mesh_triangles", _i32, [_vp, C.POINTER(C.c_int64), _PP, _PP, _PP]),
+    ("vgp_mesh_destroy", None, [_vp]),
+    ("vgp_debug_mc_table", None, [_vp, _vp]),
+    ("vgp_update_surface", _i32, [_vp, _vp]),
+    ("vgp_surface_points", _i32, [_vp, C.POINTER(C.c_int64), _PP]),
     ("vgp_gp_batch", _i32, [_vp, _i64, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp]),
     ("vgp_gp_batch_static", _i32, [C.POINTER(VgpParams), _i64, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp]),
     ("vgp_get_stats", _i32, [_vp, C.POINTER(VgpStats)]),

@@ -172,6 +172,44 @@ class Map:
         self._surface = pts
         self._surface_key = (pts.data_ptr(), tuple(pts.shape), pts._version)
 
+    def extract_mesh(self, active_only: bool = False, triangles: bool = True) -> dict:
+        """Zero crossings and marching-cubes triangles of the fused grid (vgp_extract_mesh):
+        ``crossings`` = (xyz float32 (n, 3), owner voxel keys, slots), ``triangles`` =
+        (xyz float64 (T, 3, 3), edge keys (T, 3), edge axes (T, 3))."""
+        lib = L.load()
+        h = C.c_void_p()
+        L.check(lib.vgp_extract_mesh(self._h, int(active_only), int(triangles), _stream(), C.byref(h)))
+        try:
+            n = C.c_int64()
+            x, o, sl = C.c_void_p(), C.c_void_p(), C.c_void_p()
+            L.check(lib.vgp_mesh_crossings(h, C.byref(n), C.byref(x), C.byref(o), C.byref(sl)))
+            n = n.value
+            cross = (_view(x.value, (n, 3), "<f4", torch.float32), _view(o.value, (n,), "<u8", torch.uint64),
+                     _view(sl.value, (n,), "|u1", torch.uint8))
+            nt = C.c_int64()
+            L.check(lib.vgp_mesh_triangles(h, C.byref(nt), C.byref(x), C.byref(o), C.byref(sl)))
+            nt = nt.value
+            tri = (_view(x.value, (nt, 3, 3), "<f8", torch.float64), _view(o.value, (nt, 3), "<u8", torch.uint64),
+                   _view(sl.value, (nt, 3), "|u1", torch.uint8))
+        finally:
+            lib.vgp_mesh_destroy(h)
+        return dict(crossings=cross, triangles=tri)
+
+    def update_surface(self) -> int:
+        """Refresh the G-GPDF training set from the zero crossings of the leaves the latest
+        fusion touched and train the G-GPDF on it (vgp_update_surface).  Returns its size."""
+        L.check(L.load().vgp_update_surface(self._h, _stream()))
+        pts = self.surface_points()
+        self._surface = pts
+        self._surface_key = (pts.data_ptr(), tuple(pts.shape), pts._version)
+        return pts.shape[0]
+
+    def surface_points(self) -> torch.Tensor:
+        """Copy of the map's kept G-GPDF training set (float32 (n, 3))."""
+        n, x = C.c_int64(), C.c_void_p()
+        L.check(L.load().vgp_surface_points(self._h, C.byref(n), C.byref(x)))
+        return _view(x.value, (n.value, 3), "<f4", torch.float32)
+
     def surface_is(self, pts: torch.Tensor) -> bool:
         return self._surface_key == (pts.data_ptr(), tuple(pts.shape), pts._version)
 

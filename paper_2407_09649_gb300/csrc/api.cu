@@ -11,6 +11,7 @@
 #include <vector>
 
 #include "grid.h"
+#include "mesh.h"
 
 using namespace vgp;
 
@@ -115,6 +116,11 @@ struct vgp_map {
     int32_t* s_idx = nullptr;
     int64_t s_idx_cap = 0, s_off_cap = 0;
     bool has_surface = false;
+    // G-GPDF training set kept per leaf from the grid's zero crossings (vgp_update_surface)
+    float* ps_pts = nullptr;
+    float* ps_tmp = nullptr;
+    int64_t ps_n = 0, ps_cap = 0, ps_tmp_cap = 0;
+    uint8_t* mc_tab = nullptr;  // marching-cubes table: 256 x 16 cell edges, then 256 counts
     vgp_stats stats{};
     SolveConfig cfg;  // launch shape per size bucket (vgp_autotune)
 };
@@ -267,6 +273,14 @@ int vgp_create(const vgp_params* p, vgp_map** out) {
     m->P.exp_tab = m->tables;
     m->P.lat_tab = m->tables + 256;
     m->P.lat_tab_f = m->tables_f;
+    std::vector<uint8_t> mc(256 * 17, 0);
+    build_mc_table(mc.data(), mc.data() + 256 * 16);
+    if (cudaMalloc(&m->mc_tab, mc.size()) != cudaSuccess) {
+        cudaGetLastError();
+        vgp_destroy(m);
+        return fail(VGP_ERR_OOM, "vgp_create: table allocation failed");
+    }
+    cudaMemcpy(m->mc_tab, mc.data(), mc.size(), cudaMemcpyHostToDevice);
     *out = m;
     return VGP_OK;
 }
@@ -289,6 +303,9 @@ int vgp_destroy(vgp_map* m) {
     cudaFree(m->s_slot2leaf);
     cudaFree(m->s_off);
     cudaFree(m->s_idx);
+    cudaFree(m->ps_pts);
+    cudaFree(m->ps_tmp);
+    cudaFree(m->mc_tab);
     delete m;
     return VGP_OK;
 }
@@ -770,6 +787,209 @@ int vgp_set_surface(vgp_map* m, const float* pts, int64_t n, vgp_stream stream) 
     CUDA_TRY(cudaGetLastError());
     m->s_nl = nl;
     m->has_surface = true;
+    return VGP_OK;
+}
+
+// ------------------------- zero crossings and marching cubes (Sec. IV-D) ----------------
+static GridView grid_view(const vgp_map* m) {
+    return GridView{m->g.keys, m->g.mask, m->g_slot2pool, m->g_known, m->g_D};
+}
+
+// leaves of the grid (all, or those the latest fusion touched), in arena slots kTmp5/kTmp6
+static int select_leaves(vgp_map* m, int active_only, cudaStream_t st, int32_t** lpool, uint64_t** lkey, int* nl) {
+    *nl = 0;
+    if (!m->g.keys || m->g_leaves <= 0) return VGP_OK;
+    ARENA(lp, int32_t, kTmp5, m->g_leaves);
+    ARENA(lk, uint64_t, kTmp6, m->g_leaves);
+    CUDA_TRY(cudaMemsetAsync(m->dev_words, 0, sizeof(int) * 8, st));
+    mesh_leaf_list(grid_view(m), m->g_flags, active_only, lp, lk, m->dev_words + 2, st);
+    TRY(read_words(m, st));
+    *nl = m->host_words[2];
+    *lpool = lp;
+    *lkey = lk;
+    return VGP_OK;
+}
+
+// the last entry of a device offset array
+static int read_total(const int64_t* off_end, cudaStream_t st, int64_t* total) {
+    CUDA_TRY(cudaMemcpyAsync(total, off_end, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+    CUDA_TRY(cudaStreamSynchronize(st));
+    return VGP_OK;
+}
+
+struct vgp_mesh {
+    int64_t nx = 0, nt = 0;
+    float* xyz = nullptr;
+    uint64_t* owner = nullptr;
+    uint8_t* slot = nullptr;
+    double* txyz = nullptr;
+    uint64_t* tkey = nullptr;
+    uint8_t* taxis = nullptr;
+};
+
+void vgp_mesh_destroy(vgp_mesh* h) {
+    if (!h) return;
+    cudaFree(h->xyz);
+    cudaFree(h->owner);
+    cudaFree(h->slot);
+    cudaFree(h->txyz);
+    cudaFree(h->tkey);
+    cudaFree(h->taxis);
+    delete h;
+}
+
+static int extract_into(vgp_map* m, int active_only, int want_triangles, cudaStream_t st, vgp_mesh* h) {
+    int32_t* lp = nullptr;
+    uint64_t* lk = nullptr;
+    int nl = 0;
+    TRY(select_leaves(m, active_only, st, &lp, &lk, &nl));
+    if (nl == 0) return VGP_OK;
+    const double vs = m->prm.voxel_size;
+    const GridView g = grid_view(m);
+    ARENA(cnt, int64_t, kTmp7, nl + 1);
+    ARENA(off, int64_t, kTmp8, nl + 1);
+    mesh_crossings(g, lp, lk, nl, vs, cnt, nullptr, 0, nullptr, nullptr, nullptr, false, st);
+    exclusive_scan_i64(cnt, off, nl, st, m->ar);
+    TRY(read_total(off + nl, st, &h->nx));
+    if (cudaMalloc(&h->xyz, sizeof(float) * 3 * std::max<int64_t>(h->nx, 1)) != cudaSuccess ||
+        cudaMalloc(&h->owner, sizeof(uint64_t) * std::max<int64_t>(h->nx, 1)) != cudaSuccess ||
+        cudaMalloc(&h->slot, std::max<int64_t>(h->nx, 1)) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(VGP_ERR_OOM, "vgp_extract_mesh: crossing allocation failed");
+    }
+    mesh_crossings(g, lp, lk, nl, vs, cnt, off, 0, h->xyz, h->owner, h->slot, true, st);
+    if (want_triangles) {
+        const uint8_t* tab = m->mc_tab;
+        mesh_triangles(g, lp, lk, nl, tab, tab + 256 * 16, vs, cnt, nullptr, nullptr, nullptr, nullptr, false, st);
+        exclusive_scan_i64(cnt, off, nl, st, m->ar);
+        TRY(read_total(off + nl, st, &h->nt));
+        if (cudaMalloc(&h->txyz, sizeof(double) * 9 * std::max<int64_t>(h->nt, 1)) != cudaSuccess ||
+            cudaMalloc(&h->tkey, sizeof(uint64_t) * 3 * std::max<int64_t>(h->nt, 1)) != cudaSuccess ||
+            cudaMalloc(&h->taxis, 3 * std::max<int64_t>(h->nt, 1)) != cudaSuccess) {
+            cudaGetLastError();
+            return fail(VGP_ERR_OOM, "vgp_extract_mesh: triangle allocation failed");
+        }
+        mesh_triangles(g, lp, lk, nl, tab, tab + 256 * 16, vs, cnt, off, h->txyz, h->tkey, h->taxis, true, st);
+    }
+    CUDA_TRY(cudaStreamSynchronize(st));
+    CUDA_TRY(cudaGetLastError());
+    return VGP_OK;
+}
+
+int vgp_extract_mesh(vgp_map* m, int active_only, int want_triangles, vgp_stream stream, vgp_mesh** out) {
+    if (!m || !out || (active_only != 0 && active_only != 1) || (want_triangles != 0 && want_triangles != 1))
+        return fail(VGP_ERR_ARG, "vgp_extract_mesh: bad argument");
+    *out = nullptr;
+    vgp_mesh* h = new (std::nothrow) vgp_mesh();
+    if (!h) return fail(VGP_ERR_OOM, "host allocation failed");
+    const int rc = extract_into(m, active_only, want_triangles, (cudaStream_t)stream, h);
+    if (rc != VGP_OK) {
+        vgp_mesh_destroy(h);
+        return rc;
+    }
+    *out = h;
+    return VGP_OK;
+}
+
+int vgp_mesh_crossings(const vgp_mesh* h, int64_t* n, const float** xyz, const uint64_t** owner,
+                       const uint8_t** slot) {
+    if (!h || !n) return fail(VGP_ERR_ARG, "vgp_mesh_crossings: null argument");
+    *n = h->nx;
+    if (xyz) *xyz = h->xyz;
+    if (owner) *owner = h->owner;
+    if (slot) *slot = h->slot;
+    return VGP_OK;
+}
+
+int vgp_mesh_triangles(const vgp_mesh* h, int64_t* n, const double** xyz, const uint64_t** edge_key,
+                       const uint8_t** edge_axis) {
+    if (!h || !n) return fail(VGP_ERR_ARG, "vgp_mesh_triangles: null argument");
+    *n = h->nt;
+    if (xyz) *xyz = h->txyz;
+    if (edge_key) *edge_key = h->tkey;
+    if (edge_axis) *edge_axis = h->taxis;
+    return VGP_OK;
+}
+
+void vgp_debug_mc_table(uint8_t* tab, uint8_t* ntri) {
+    if (!tab || !ntri) return;
+    std::fill(tab, tab + 256 * 16, (uint8_t)0);
+    build_mc_table(tab, ntri);
+}
+
+static int grow_f32(float** p, int64_t* cap, int64_t need) {
+    if (need <= *cap) return VGP_OK;
+    const int64_t c = std::max<int64_t>(need + need / 4, 1024);
+    cudaFree(*p);
+    *p = nullptr;
+    *cap = 0;
+    if (cudaMalloc(p, sizeof(float) * 3 * c) != cudaSuccess) {
+        cudaGetLastError();
+        *p = nullptr;
+        return fail(VGP_ERR_OOM, "training-set allocation failed");
+    }
+    *cap = c;
+    return VGP_OK;
+}
+
+int vgp_update_surface(vgp_map* m, vgp_stream stream) {
+    if (!m) return fail(VGP_ERR_ARG, "vgp_update_surface: null map");
+    cudaStream_t st = (cudaStream_t)stream;
+    const double vs = m->prm.voxel_size;
+    const GridView g = grid_view(m);
+    const bool have_grid = m->g.keys && m->g_leaves > 0;
+    // 1. the stored points of leaves the latest fusion did not touch stay, in order
+    const int64_t n0 = m->ps_n;
+    int64_t kept = n0;
+    int64_t* keep = nullptr;
+    int64_t* pos = nullptr;
+    if (n0 > 0 && have_grid) {
+        ARENA(keep_, int64_t, kTmp9, n0 + 1);
+        ARENA(pos_, int64_t, kTmp10, n0 + 1);
+        keep = keep_;
+        pos = pos_;
+        store_keep(m->ps_pts, n0, vs, g, m->g_flags, keep, st);
+        exclusive_scan_i64(keep, pos, n0, st, m->ar);
+        TRY(read_total(pos + n0, st, &kept));
+    }
+    // 2. crossings of the touched leaves
+    int32_t* lp = nullptr;
+    uint64_t* lk = nullptr;
+    int nl = 0;
+    int64_t added = 0;
+    int64_t *cnt = nullptr, *off = nullptr;
+    if (have_grid) {
+        TRY(select_leaves(m, 1, st, &lp, &lk, &nl));
+        if (nl > 0) {
+            ARENA(cnt_, int64_t, kTmp7, nl + 1);
+            ARENA(off_, int64_t, kTmp8, nl + 1);
+            cnt = cnt_;
+            off = off_;
+            mesh_crossings(g, lp, lk, nl, vs, cnt, nullptr, 0, nullptr, nullptr, nullptr, false, st);
+            exclusive_scan_i64(cnt, off, nl, st, m->ar);
+            TRY(read_total(off + nl, st, &added));
+        }
+    }
+    // 3. new training set = kept points, then the new crossings leaf by leaf
+    const int64_t n1 = kept + added;
+    if (n1 >= (1ll << 31)) return fail(VGP_ERR_ARG, "vgp_update_surface: training set above 2^31 - 1 points");
+    TRY(grow_f32(&m->ps_tmp, &m->ps_tmp_cap, n1));
+    if (keep)
+        store_compact(m->ps_pts, n0, keep, pos, m->ps_tmp, st);
+    else if (n0 > 0)
+        CUDA_TRY(cudaMemcpyAsync(m->ps_tmp, m->ps_pts, sizeof(float) * 3 * n0, cudaMemcpyDeviceToDevice, st));
+    if (added > 0) mesh_crossings(g, lp, lk, nl, vs, cnt, off, kept, m->ps_tmp, nullptr, nullptr, true, st);
+    std::swap(m->ps_pts, m->ps_tmp);
+    std::swap(m->ps_cap, m->ps_tmp_cap);
+    m->ps_n = n1;
+    // 4. the G-GPDF is trained on the new set
+    return vgp_set_surface(m, m->ps_pts, n1, stream);
+}
+
+int vgp_surface_points(vgp_map* m, int64_t* n, const float** xyz) {
+    if (!m || !n) return fail(VGP_ERR_ARG, "vgp_surface_points: null argument");
+    *n = m->ps_n;
+    if (xyz) *xyz = m->ps_pts;
     return VGP_OK;
 }
 
