@@ -332,6 +332,27 @@ def comparisons(S, Q, S_h, args):
     out["lgpdf_room_raycast"] = {"voxels_per_s": nvox / sec, "frames": len(frames),
                                  "ms_per_frame": 1e3 * sec / len(frames),
                                  "testing_voxels_per_frame": nvox / len(frames), "precision": "mixed"}
+    # whole mapping step per frame: ray-cast L-GPDF, fusion, zero crossings of the touched leaves,
+    # G-GPDF retrained on the kept training set; then the marching-cubes mesh of the whole map
+    mp = Map(precision="mixed", max_pts_leaf=512)
+    mp.fuse(mp.build_frame(frames[0], origin=poses[0]))
+    mp.update_surface()
+    torch.cuda.synchronize()
+    a.record()
+    for fr, o in zip(frames, poses):
+        mp.fuse(mp.build_frame(fr, origin=o))
+        mp.update_surface()
+    b.record()
+    torch.cuda.synchronize()
+    sec = a.elapsed_time(b) / 1e3
+    a.record()
+    mesh = mp.extract_mesh(active_only=False, triangles=True)
+    b.record()
+    torch.cuda.synchronize()
+    out["room_mapping_step"] = {"ms_per_frame": 1e3 * sec / len(frames), "frames": len(frames),
+                                "training_points": int(mp.surface_points().shape[0]),
+                                "mesh_ms": a.elapsed_time(b), "mesh_triangles": int(mesh["triangles"][0].shape[0]),
+                                "zero_crossings": int(mesh["crossings"][0].shape[0]), "precision": "mixed"}
     # independent-instance sweep (N log-uniform in [4, 1024], 512 queries each)
     io, X, qo, Qw = scenes.patch_sweep(n_inst=args.sweep_inst, seed=4)
     io_d = torch.from_numpy(io).cuda()
