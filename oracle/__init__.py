@@ -38,13 +38,15 @@ class Params(C.Structure):
     _fields_ = [("voxel_size", C.c_double), ("lengthscale", C.c_double),
                 ("sigma_occ", C.c_double), ("d_max", C.c_double), ("d_var_floor", C.c_double),
                 ("max_pts_leaf", C.c_int32), ("max_pts_group", C.c_int32),
-                ("max_leaf_search", C.c_int32), ("fusion", C.c_int32)]
+                ("max_leaf_search", C.c_int32), ("fusion", C.c_int32),
+                ("sigma_prop", C.c_double), ("n_props", C.c_int32), ("pad_", C.c_int32)]
 
 
 def params(voxel_size=0.1, lengthscale=0.3, sigma_occ=0.01, d_max=10.0, d_var_floor=1e-3,
-           max_pts_leaf=64, max_pts_group=1024, max_leaf_search=8, fusion=0) -> Params:
+           max_pts_leaf=64, max_pts_group=1024, max_leaf_search=8, fusion=0, sigma_prop=0.1,
+           n_props=0) -> Params:
     return Params(voxel_size, lengthscale, sigma_occ, d_max, d_var_floor, max_pts_leaf,
-                  max_pts_group, max_leaf_search, fusion)
+                  max_pts_group, max_leaf_search, fusion, sigma_prop, n_props, 0)
 
 
 _lib = None
@@ -65,6 +67,10 @@ def lib():
         L.or_frame_build.restype = vp
         L.or_frame_build2.argtypes = [C.POINTER(Params), vp, i64, vp, C.c_int, vp, i64]
         L.or_frame_build2.restype = vp
+        L.or_frame_build3.argtypes = [C.POINTER(Params), vp, vp, i64, vp, C.c_int, vp, i64]
+        L.or_frame_build3.restype = vp
+        L.or_frame_props.argtypes = [vp, vp, vp]
+        L.or_frame_props.restype = C.c_int
         L.or_frame_signs.argtypes = [vp, vp]
         L.or_frame_free.argtypes = [vp]
         L.or_frame_count.argtypes = [vp, C.c_int]
@@ -74,12 +80,16 @@ def lib():
         L.or_grid_new.restype = vp
         L.or_grid_free.argtypes = [vp]
         L.or_grid_fuse.argtypes = [vp, C.c_int, vp, vp, vp, vp, i64]
+        L.or_grid_fuse2.argtypes = [vp, C.c_int, vp, vp, vp, vp, vp, vp, C.c_int, i64]
+        L.or_grid_fuse2.restype = C.c_int
+        L.or_grid_export_props.argtypes = [vp, vp, vp]
+        L.or_grid_export_props.restype = C.c_int
         L.or_grid_size.argtypes = [vp]
         L.or_grid_size.restype = i64
         L.or_grid_export.argtypes = [vp] * 5
-        L.or_grid_crossings.argtypes = [vp, C.c_double, C.c_int, vp, vp, vp]
+        L.or_grid_crossings.argtypes = [vp, C.c_double, C.c_int, vp, vp, vp, vp]
         L.or_grid_crossings.restype = i64
-        L.or_grid_mesh.argtypes = [vp, C.c_double, C.c_int, vp, vp, vp]
+        L.or_grid_mesh.argtypes = [vp, C.c_double, C.c_int, vp, vp, vp, vp]
         L.or_grid_mesh.restype = i64
         L.or_surface_new.argtypes = [C.POINTER(Params), vp, i64]
         L.or_surface_new.restype = vp
@@ -195,23 +205,29 @@ class Frame:
     grad: np.ndarray
     status: np.ndarray
     sign: np.ndarray = None
+    c: np.ndarray = None  # surface-property means (n_test, n_props), Eq. 6
+    w: np.ndarray = None  # surface-property variances (n_test,)
 
 
-def frame(pts, P: Params | None = None, origin=None, normal_steps: int = 3, known=None) -> Frame:
+def frame(pts, P: Params | None = None, origin=None, normal_steps: int = 3, known=None, props=None) -> Frame:
     """One L-GPDF frame: voxelise, fit one GP per leaf, infer at all testing voxels.  Without
     ``origin`` the testing voxels are the dilated GP leaves; with the sensor ``origin`` they are
     the ray-cast set of Sec. IV-B (``known``: sorted voxel keys with earlier measurements) and
-    the distances are signed."""
+    the distances are signed.  ``props`` (n, P.n_props) float32 gives each point's surface
+    properties; the frame then also infers their means and variances (Eq. 6)."""
     P = P or params()
     pts = _f32(pts)
     L = lib()
+    pr = None
+    if props is not None and P.n_props > 0:
+        pr = np.ascontiguousarray(np.asarray(props, np.float32).reshape(len(pts), P.n_props))
     if origin is None:
-        h = L.or_frame_build(C.byref(P), _p(pts), len(pts))
+        h = L.or_frame_build3(C.byref(P), _p(pts), _p(pr) if pr is not None else None, len(pts), None, 0, None, 0)
     else:
         o = np.ascontiguousarray(origin, np.float64)
         kn = np.ascontiguousarray(np.sort(np.asarray(known if known is not None else [], np.uint64)), np.uint64)
-        h = L.or_frame_build2(C.byref(P), _p(pts), len(pts), _p(o), int(normal_steps), _p(kn) if len(kn) else None,
-                              len(kn))
+        h = L.or_frame_build3(C.byref(P), _p(pts), _p(pr) if pr is not None else None, len(pts), _p(o),
+                              int(normal_steps), _p(kn) if len(kn) else None, len(kn))
     if not h:
         raise MemoryError("oracle frame build failed")
     try:
@@ -224,6 +240,10 @@ def frame(pts, P: Params | None = None, origin=None, normal_steps: int = 3, know
                          _p(f.status))
         f.sign = np.zeros(nt, np.int8)
         L.or_frame_signs(h, _p(f.sign))
+        if pr is not None:
+            f.c = np.zeros((nt, P.n_props))
+            f.w = np.zeros(nt)
+            L.or_frame_props(h, _p(f.c), _p(f.w))
     finally:
         L.or_frame_free(h)
     return f
@@ -241,15 +261,34 @@ class Grid:
             lib().or_grid_free(self.h)
             self.h = None
 
-    def fuse(self, key, d, v, status):
+    def fuse(self, key, d, v, status, c=None, w=None):
         key = np.ascontiguousarray(key, np.uint64)
         d = _f64(d)
         v = _f64(v)
         status = np.ascontiguousarray(status, np.uint8)
-        lib().or_grid_fuse(self.h, self.fusion, _p(key), _p(d), _p(v), _p(status), len(key))
+        if c is None:
+            lib().or_grid_fuse(self.h, self.fusion, _p(key), _p(d), _p(v), _p(status), len(key))
+            return
+        c = np.ascontiguousarray(np.asarray(c, np.float64).reshape(len(key), -1))
+        w = _f64(w)
+        rc = lib().or_grid_fuse2(self.h, self.fusion, _p(key), _p(d), _p(v), _p(status), _p(c), _p(w), c.shape[1],
+                                 len(key))
+        if rc != 0:
+            raise ValueError("at most 4 property channels")
 
     def fuse_frame(self, f: Frame):
-        self.fuse(f.test_key, f.d, f.v, f.status)
+        self.fuse(f.test_key, f.d, f.v, f.status, f.c, f.w)
+
+    def export_props(self):
+        """Fused surface properties (n, n_props) and their variances (weights for Eq. 9) in key
+        order; NaN where no property was fused."""
+        L = lib()
+        n = L.or_grid_size(self.h)
+        npr = L.or_grid_export_props(self.h, None, None)
+        Cp = np.zeros((n, npr))
+        W = np.zeros(n)
+        L.or_grid_export_props(self.h, _p(Cp), _p(W))
+        return Cp, W
 
     def export(self):
         n = lib().or_grid_size(self.h)
@@ -260,26 +299,32 @@ class Grid:
         lib().or_grid_export(self.h, _p(k), _p(D), _p(V), _p(fl))
         return k, D, V, fl
 
-    def crossings(self, voxel_size: float, active_only: bool = False):
+    def crossings(self, voxel_size: float, active_only: bool = False, props: bool = False):
         """Zero crossings owned by the voxels of all leaves (or of the leaves touched by the
-        latest fusion): float32 points (n, 3), owner voxel keys, slots 2 axis + (+ side)."""
+        latest fusion): float32 points (n, 3), owner voxel keys, slots 2 axis + (+ side); with
+        ``props`` also the interpolated fused properties (n, n_props)."""
         L = lib()
-        n = L.or_grid_crossings(self.h, float(voxel_size), int(active_only), None, None, None)
+        n = L.or_grid_crossings(self.h, float(voxel_size), int(active_only), None, None, None, None)
+        npr = L.or_grid_export_props(self.h, None, None)
         xyz = np.zeros((n, 3), np.float32)
         owner = np.zeros(n, np.uint64)
         slot = np.zeros(n, np.uint8)
-        L.or_grid_crossings(self.h, float(voxel_size), int(active_only), _p(xyz), _p(owner), _p(slot))
-        return xyz, owner, slot
+        cp = np.zeros((n, npr))
+        L.or_grid_crossings(self.h, float(voxel_size), int(active_only), _p(xyz), _p(owner), _p(slot), _p(cp))
+        return (xyz, owner, slot, cp) if props else (xyz, owner, slot)
 
-    def mesh(self, voxel_size: float, active_only: bool = False):
-        """Marching-cubes triangle soup: xyz (T, 3, 3) FP64, edge keys (T, 3), edge axes (T, 3)."""
+    def mesh(self, voxel_size: float, active_only: bool = False, props: bool = False):
+        """Marching-cubes triangle soup: xyz (T, 3, 3) FP64, edge keys (T, 3), edge axes (T, 3);
+        with ``props`` also the interpolated fused properties per vertex (T, 3, n_props)."""
         L = lib()
-        n = L.or_grid_mesh(self.h, float(voxel_size), int(active_only), None, None, None)
+        n = L.or_grid_mesh(self.h, float(voxel_size), int(active_only), None, None, None, None)
+        npr = L.or_grid_export_props(self.h, None, None)
         xyz = np.zeros((n, 3, 3))
         ek = np.zeros((n, 3), np.uint64)
         ea = np.zeros((n, 3), np.uint8)
-        L.or_grid_mesh(self.h, float(voxel_size), int(active_only), _p(xyz), _p(ek), _p(ea))
-        return xyz, ek, ea
+        vp_ = np.zeros((n, 3, npr))
+        L.or_grid_mesh(self.h, float(voxel_size), int(active_only), _p(xyz), _p(ek), _p(ea), _p(vp_))
+        return (xyz, ek, ea, vp_) if props else (xyz, ek, ea)
 
 
 def leaf_key_of_points(xyz, voxel_size: float) -> np.ndarray:

@@ -23,7 +23,12 @@
  *   - the backward pass of the distance w.r.t. query and surface points, derived from
  *     Eq. 1 by differentiating alpha = A^-1 1;
  *   - zero crossings and marching cubes over the fused grid, restricted to the leaves the
- *     latest fusion touched (Sec. IV-D): the G-GPDF training points and the mesh.
+ *     latest fusion touched (Sec. IV-D): the G-GPDF training points and the mesh;
+ *   - surface properties (Eq. 6): each voxel's property is the mean of its points'; per leaf
+ *     a GP with the same kernel and noise sigma_prop gives c = k^T (K + sigma_prop^2 I)^-1 y
+ *     and w = 1 - k^T (K + sigma_prop^2 I)^-1 k at the testing voxels; they are fused with the
+ *     rules of Eqs. 8-9 using w, where the distance is fused; crossings and mesh vertices
+ *     carry the fused properties interpolated with the crossing's t.
  *
  * The paper leaves the following open; this file takes these readings:
  *   - voxel index ijk = floor(p / vs + 1/2) in IEEE FP64 (p widened from float32);
@@ -68,7 +73,12 @@ typedef struct {
     int32_t max_pts_group;  /* per-neighbourhood cap (G-GPDF) */
     int32_t max_leaf_search;/* Chebyshev leaf radius of the fallback search */
     int32_t fusion;         /* 0: inverse variance (Eqs. 7-8); 1: TSDF weights (Eq. 9) */
+    double sigma_prop;      /* noise std of the surface-property GP (Eq. 6) */
+    int32_t n_props;        /* property channels per point, 0..4 */
+    int32_t pad_;
 } or_params;
+
+#define MAX_PROPS 4
 
 enum { ST_OK = 0, ST_NO_SUPPORT = 1, ST_CLAMPED = 2, ST_BAD_INPUT = 3, ST_FACTOR_FAIL = 4 };
 
@@ -316,13 +326,15 @@ typedef struct {
     uint64_t lkey;
     int32_t bit;
     int32_t pad;
+    int64_t idx; /* input point index */
 } vox_rec;
 
 static int cmp_vox(const void* a, const void* b) {
     const vox_rec* x = (const vox_rec*)a;
     const vox_rec* y = (const vox_rec*)b;
     if (x->lkey != y->lkey) return x->lkey < y->lkey ? -1 : 1;
-    return (x->bit > y->bit) - (x->bit < y->bit);
+    if (x->bit != y->bit) return (x->bit > y->bit) - (x->bit < y->bit);
+    return (x->idx > y->idx) - (x->idx < y->idx);
 }
 
 typedef struct {
@@ -344,6 +356,14 @@ typedef struct {
     double* test_grad;
     uint8_t* test_status;
     int8_t* test_sign;
+    /* surface properties (Eq. 6), when given */
+    int n_props;
+    double* Y;            /* [T][n_props] voxel-mean property at each training point */
+    double* Lc;           /* packed factors of K + sigma_prop^2 I */
+    double* alpha_c;      /* [T][n_props] */
+    uint8_t* fitc_ok;
+    double* test_c;       /* [n_test][n_props] */
+    double* test_w;       /* [n_test] */
 } or_frame;
 
 static void voxel_of_bit(const int64_t leaf[3], int bit, int64_t ijk[3]) {
@@ -357,6 +377,7 @@ void or_frame_free(or_frame* F) {
     free(F->leaf_key); free(F->leaf_nocc); free(F->inst_off); free(F->X); free(F->L_off);
     free(F->L); free(F->alpha); free(F->fit_ok); free(F->test_key); free(F->test_inst_key);
     free(F->test_d); free(F->test_v); free(F->test_grad); free(F->test_status); free(F->test_sign);
+    free(F->Y); free(F->Lc); free(F->alpha_c); free(F->fitc_ok); free(F->test_c); free(F->test_w);
     free(F);
 }
 
@@ -484,15 +505,58 @@ static void bresenham(const int64_t a[3], const int64_t b[3], const uint64_t* kn
     }
 }
 
-or_frame* or_frame_build2(const or_params* P, const float* pts, int64_t n, const double* origin, int normal_steps,
-                          const uint64_t* known, int64_t n_known);
-
+or_frame* or_frame_build3(const or_params* P, const float* pts, const float* props, int64_t n, const double* origin,
+                          int normal_steps, const uint64_t* known, int64_t n_known);
 or_frame* or_frame_build(const or_params* P, const float* pts, int64_t n) {
-    return or_frame_build2(P, pts, n, NULL, 0, NULL, 0);
+    return or_frame_build3(P, pts, NULL, n, NULL, 0, NULL, 0);
 }
-
 or_frame* or_frame_build2(const or_params* P, const float* pts, int64_t n, const double* origin, int normal_steps,
                           const uint64_t* known, int64_t n_known) {
+    return or_frame_build3(P, pts, NULL, n, origin, normal_steps, known, n_known);
+}
+
+/* Surface-property GP of one leaf (Eq. 6): Lc = chol(K + sigma_prop^2 I), and for each
+ * channel alpha_c = (K + sigma_prop^2 I)^-1 y_c.  Y and alpha_c are [N][nc]. */
+static int gp_fit_props(const double* X, int N, const or_params* P, int nc, const double* Y, double* Lc,
+                        double* alpha_c) {
+    double s2 = P->sigma_prop * P->sigma_prop;
+    for (int i = 0; i < N; ++i) {
+        for (int j = 0; j < i; ++j) Lc[PK(i, j)] = se_kernel(X + 3 * i, X + 3 * j, P->lengthscale);
+        Lc[PK(i, i)] = 1.0 + s2;
+    }
+    if (!cholesky_packed(Lc, N)) return 0;
+    double* y = (double*)malloc(sizeof(double) * (N > 0 ? N : 1));
+    double* z = (double*)malloc(sizeof(double) * (N > 0 ? N : 1));
+    double* a = (double*)malloc(sizeof(double) * (N > 0 ? N : 1));
+    for (int c = 0; c < nc; ++c) {
+        for (int i = 0; i < N; ++i) y[i] = Y[(int64_t)i * nc + c];
+        forward_subst(Lc, N, y, z);
+        back_subst(Lc, N, z, a);
+        for (int i = 0; i < N; ++i) alpha_c[(int64_t)i * nc + c] = a[i];
+    }
+    free(y); free(z); free(a);
+    return 1;
+}
+
+/* Property mean c_c = k^T alpha_c (Eq. 6) and variance w = 1 - |Lc^-1 k|^2 (the posterior
+ * variance read as for Eq. 2) at xs. */
+static void gp_eval_props(const double* X, int N, const double* Lc, const double* alpha_c, int nc,
+                          const double xs[3], double l, double* kbuf, double* vbuf, double* c_out, double* w_out) {
+    for (int c = 0; c < nc; ++c) c_out[c] = 0.0;
+    for (int j = 0; j < N; ++j) {
+        double k = se_kernel(xs, X + 3 * j, l);
+        kbuf[j] = k;
+        for (int c = 0; c < nc; ++c) c_out[c] += alpha_c[(int64_t)j * nc + c] * k;
+    }
+    forward_subst(Lc, N, kbuf, vbuf);
+    double s = 0.0;
+    for (int j = 0; j < N; ++j) s += vbuf[j] * vbuf[j];
+    double w = 1.0 - s;
+    *w_out = w > 0.0 ? w : 0.0;
+}
+
+or_frame* or_frame_build3(const or_params* P, const float* pts, const float* props, int64_t n, const double* origin,
+                          int normal_steps, const uint64_t* known, int64_t n_known) {
     or_frame* F = (or_frame*)calloc(1, sizeof(or_frame));
     if (!F) return NULL;
     F->P = *P;
@@ -509,12 +573,26 @@ or_frame* or_frame_build2(const or_params* P, const float* pts, int64_t n, const
         R[m].lkey = pack_key(leaf[0], leaf[1], leaf[2]);
         R[m].bit = bit;
         R[m].pad = 0;
+        R[m].idx = i;
         ++m;
     }
     qsort(R, (size_t)m, sizeof(vox_rec), cmp_vox);
+    /* unique voxels; with properties, each voxel's property is the mean over its points
+     * (summed in FP64 in ascending point index) */
+    const int nc = (props && P->n_props > 0) ? P->n_props : 0;
+    double* vmean = nc ? (double*)calloc((size_t)(m + 1) * nc, sizeof(double)) : NULL;
+    int64_t* vcnt = nc ? (int64_t*)calloc((size_t)(m + 1), sizeof(int64_t)) : NULL;
     int64_t u = 0;
-    for (int64_t i = 0; i < m; ++i)
+    for (int64_t i = 0; i < m; ++i) {
         if (u == 0 || R[i].lkey != R[u - 1].lkey || R[i].bit != R[u - 1].bit) R[u++] = R[i];
+        if (nc) {
+            for (int c = 0; c < nc; ++c) vmean[(u - 1) * nc + c] += (double)props[R[i].idx * nc + c];
+            vcnt[u - 1]++;
+        }
+    }
+    if (nc)
+        for (int64_t i = 0; i < u; ++i)
+            for (int c = 0; c < nc; ++c) vmean[i * nc + c] /= (double)vcnt[i];
     /* 2. leaves, occupied counts, capped training sets */
     int64_t nl = 0;
     for (int64_t i = 0; i < u; ++i) if (i == 0 || R[i].lkey != R[i - 1].lkey) ++nl;
@@ -552,6 +630,13 @@ or_frame* or_frame_build2(const or_params* P, const float* pts, int64_t n, const
     F->L = (double*)malloc(sizeof(double) * (F->L_off[nl] + 1));
     F->alpha = (double*)malloc(sizeof(double) * (T + 1));
     F->fit_ok = (uint8_t*)malloc(nl + 1);
+    F->n_props = nc;
+    if (nc) {
+        F->Y = (double*)malloc(sizeof(double) * (T + 1) * nc);
+        F->Lc = (double*)malloc(sizeof(double) * (F->L_off[nl] + 1));
+        F->alpha_c = (double*)malloc(sizeof(double) * (T + 1) * nc);
+        F->fitc_ok = (uint8_t*)malloc(nl + 1);
+    }
 #pragma omp parallel for schedule(dynamic, 4)
     for (int64_t l = 0; l < nl; ++l) {
         int64_t nocc = F->leaf_nocc[l];
@@ -563,11 +648,17 @@ or_frame* or_frame_build2(const or_params* P, const float* pts, int64_t n, const
             int64_t ijk[3];
             voxel_of_bit(leaf, R[run_start[l] + pick].bit, ijk);
             for (int a = 0; a < 3; ++a) F->X[3 * (F->inst_off[l] + k) + a] = (double)ijk[a] * vs;
+            for (int c = 0; c < nc; ++c) F->Y[(F->inst_off[l] + k) * nc + c] = vmean[(run_start[l] + pick) * nc + c];
         }
         F->fit_ok[l] = (uint8_t)or_gp_fit(F->X + 3 * F->inst_off[l], (int)N, P, F->L + F->L_off[l],
                                           F->alpha + F->inst_off[l]);
+        if (nc)
+            F->fitc_ok[l] = (uint8_t)gp_fit_props(F->X + 3 * F->inst_off[l], (int)N, P, nc, F->Y + F->inst_off[l] * nc,
+                                                  F->Lc + F->L_off[l], F->alpha_c + F->inst_off[l] * nc);
     }
     free(run_start);
+    free(vmean);
+    free(vcnt);
     /* 3. testing voxels: the dilated GP leaves (no origin), or the ray-cast set (Sec. IV-B) */
     kslist TL = {NULL, 0, 0};
     if (!origin) {
@@ -638,6 +729,10 @@ or_frame* or_frame_build2(const or_params* P, const float* pts, int64_t n, const
     F->test_grad = (double*)malloc(sizeof(double) * 3 * (F->n_test + 1));
     F->test_status = (uint8_t*)malloc(F->n_test + 1);
     F->test_sign = (int8_t*)malloc(F->n_test + 1);
+    if (nc) {
+        F->test_c = (double*)malloc(sizeof(double) * (F->n_test + 1) * nc);
+        F->test_w = (double*)malloc(sizeof(double) * (F->n_test + 1));
+    }
     int Nmax = 1;
     for (int64_t l = 0; l < nl; ++l) {
         int64_t N = F->inst_off[l + 1] - F->inst_off[l];
@@ -710,6 +805,17 @@ or_frame* or_frame_build2(const or_params* P, const float* pts, int64_t n, const
             F->test_v[o] = r.v;
             for (int a = 0; a < 3; ++a) F->test_grad[3 * o + a] = sg * r.gd[a];
             F->test_status[o] = (uint8_t)r.status;
+            if (nc) {
+                if (inst < 0 || !F->fitc_ok[inst]) {
+                    for (int c = 0; c < nc; ++c) F->test_c[o * nc + c] = NAN;
+                    F->test_w[o] = INFINITY;
+                } else {
+                    int N = (int)(F->inst_off[inst + 1] - F->inst_off[inst]);
+                    gp_eval_props(F->X + 3 * F->inst_off[inst], N, F->Lc + F->L_off[inst],
+                                  F->alpha_c + F->inst_off[inst] * nc, nc, xs, P->lengthscale, kb, vb,
+                                  F->test_c + o * nc, F->test_w + o);
+                }
+            }
         }
         free(kb);
         free(vb);
@@ -736,6 +842,14 @@ void or_frame_leaves(const or_frame* F, uint64_t* key, int32_t* nocc, int64_t* i
     if (alpha) memcpy(alpha, F->alpha, sizeof(double) * T);
 }
 
+/* property means [n_test][n_props] and variances [n_test]; returns n_props (0: none) */
+int or_frame_props(const or_frame* F, double* c, double* w) {
+    if (!F->n_props) return 0;
+    if (c) memcpy(c, F->test_c, sizeof(double) * F->n_test * F->n_props);
+    if (w) memcpy(w, F->test_w, sizeof(double) * F->n_test);
+    return F->n_props;
+}
+
 void or_frame_signs(const or_frame* F, int8_t* sign) {
     if (sign) memcpy(sign, F->test_sign, F->n_test);
 }
@@ -757,6 +871,8 @@ void or_frame_tests(const or_frame* F, uint64_t* key, uint64_t* inst_key, double
 typedef struct {
     uint64_t key;
     double D, V;
+    double C[MAX_PROPS]; /* fused surface properties; W = NaN: none fused yet */
+    double W;
 } gvox;
 
 typedef struct {
@@ -765,6 +881,7 @@ typedef struct {
     int64_t nl;
     uint64_t* lkey; /* sorted */
     uint8_t* lflag; /* bit0: touched by the latest fuse; bit1: ever touched */
+    int n_props;
 } or_grid;
 
 or_grid* or_grid_new(void) { return (or_grid*)calloc(1, sizeof(or_grid)); }
@@ -778,6 +895,8 @@ typedef struct {
     uint64_t key;
     double d, v;
     int64_t order;
+    double c[MAX_PROPS], w;
+    int hasp;
 } fin;
 
 static int cmp_fin(const void* a, const void* b) {
@@ -810,14 +929,61 @@ static void fuse_one(int mode, double* D, double* V, double d, double v) {
     }
 }
 
+/* Surface-property fusion (the last sentence of Sec. IV-C): the rules of fuse_one applied to
+ * every channel of C with the shared variance (or weight) W and the new variance w. */
+static void fuse_props(int mode, double* C, double* W, const double* c, double w, int nc) {
+    if (isnan(*W)) {
+        for (int k = 0; k < nc; ++k) C[k] = c[k];
+        *W = mode == 0 ? w : 1.0 - w;
+        return;
+    }
+    if (mode == 0) {
+        double Wp = *W;
+        double a = Wp / (Wp + w);
+        double b = w / (Wp + w);
+        for (int k = 0; k < nc; ++k) C[k] = a * c[k] + b * C[k];
+        *W = 1.0 / (1.0 / Wp + 1.0 / w);
+    } else {
+        double Wp = *W, ww = 1.0 - w;
+        double a = ww / (Wp + ww);
+        double b = Wp / (Wp + ww);
+        for (int k = 0; k < nc; ++k) C[k] = a * c[k] + b * C[k];
+        *W = Wp + ww;
+    }
+}
+
+int or_grid_fuse2(or_grid* g, int mode, const uint64_t* key, const double* d, const double* v,
+                  const uint8_t* status, const double* c, const double* w, int nc, int64_t n);
+
 int or_grid_fuse(or_grid* g, int mode, const uint64_t* key, const double* d, const double* v,
                  const uint8_t* status, int64_t n) {
+    return or_grid_fuse2(g, mode, key, d, v, status, NULL, NULL, 0, n);
+}
+
+/* Fusion of one frame's testing voxels; with c / w (nc channels) the surface properties of
+ * the voxels whose distance is fused are fused too, when every channel is finite and w is a
+ * valid variance (finite, > 0, and < 1 for Eq. 9). */
+int or_grid_fuse2(or_grid* g, int mode, const uint64_t* key, const double* d, const double* v,
+                  const uint8_t* status, const double* c, const double* w, int nc, int64_t n) {
+    if (nc < 0 || nc > MAX_PROPS) return -1;
+    if (!c || !w) nc = 0;
+    if (nc > g->n_props) g->n_props = nc;
     fin* in = (fin*)malloc(sizeof(fin) * (n > 0 ? n : 1));
     int64_t m = 0;
     for (int64_t i = 0; i < n; ++i) {
         if (status[i] != ST_OK || !isfinite(d[i]) || !isfinite(v[i]) || !(v[i] > 0.0)) continue;
         if (mode == 1 && !(v[i] < 1.0)) continue;
         in[m].key = key[i]; in[m].d = d[i]; in[m].v = v[i]; in[m].order = i;
+        in[m].hasp = 0;
+        if (nc) {
+            int ok = isfinite(w[i]) && w[i] > 0.0 && (mode == 0 || w[i] < 1.0);
+            for (int k = 0; k < nc; ++k) {
+                in[m].c[k] = c[i * nc + k];
+                if (!isfinite(in[m].c[k])) ok = 0;
+            }
+            in[m].w = w[i];
+            in[m].hasp = ok;
+        }
         ++m;
     }
     qsort(in, (size_t)m, sizeof(fin), cmp_fin);
@@ -831,9 +997,16 @@ int or_grid_fuse(or_grid* g, int mode, const uint64_t* key, const double* d, con
             cur.key = in[b].key;
             cur.D = in[b].d;
             cur.V = mode == 0 ? in[b].v : 1.0 - in[b].v;
+            for (int k = 0; k < MAX_PROPS; ++k) cur.C[k] = NAN;
+            cur.W = NAN;
+            if (in[b].hasp) fuse_props(mode, cur.C, &cur.W, in[b].c, in[b].w, nc);
             ++b;
         }
-        while (b < m && in[b].key == cur.key) { fuse_one(mode, &cur.D, &cur.V, in[b].d, in[b].v); ++b; }
+        while (b < m && in[b].key == cur.key) {
+            fuse_one(mode, &cur.D, &cur.V, in[b].d, in[b].v);
+            if (in[b].hasp) fuse_props(mode, cur.C, &cur.W, in[b].c, in[b].w, nc);
+            ++b;
+        }
         out[o++] = cur;
     }
     free(g->v);
@@ -865,6 +1038,16 @@ int or_grid_fuse(or_grid* g, int mode, const uint64_t* key, const double* d, con
 }
 
 int64_t or_grid_size(const or_grid* g) { return g->n; }
+
+/* fused properties [n][n_props] and their variances (weights for Eq. 9) in key order;
+ * returns n_props */
+int or_grid_export_props(const or_grid* g, double* C, double* W) {
+    for (int64_t i = 0; i < g->n; ++i) {
+        if (C) for (int k = 0; k < g->n_props; ++k) C[i * g->n_props + k] = g->v[i].C[k];
+        if (W) W[i] = g->v[i].W;
+    }
+    return g->n_props;
+}
 
 void or_grid_export(const or_grid* g, uint64_t* key, double* D, double* V, uint8_t* flags) {
     for (int64_t i = 0; i < g->n; ++i) {
@@ -924,7 +1107,16 @@ typedef struct {
     int32_t bit, slot;
     float p[3];
     uint64_t owner;
+    double c[MAX_PROPS];
 } xrec;
+
+/* property at a crossing: the fused properties of the two ends interpolated with the same t
+ * (NaN unless both ends carry properties) */
+static void crossing_props(const gvox* lo, const gvox* hi, int nc, double* out) {
+    double t = lo->D / (lo->D - hi->D);
+    for (int k = 0; k < nc; ++k)
+        out[k] = (isnan(lo->W) || isnan(hi->W)) ? NAN : lo->C[k] + t * (hi->C[k] - lo->C[k]);
+}
 
 static int cmp_xrec(const void* a, const void* b) {
     const xrec* x = (const xrec*)a;
@@ -939,7 +1131,8 @@ static int cmp_xrec(const void* a, const void* b) {
  * slot = 2 axis + (neighbour on the + side).  Returns the count; fills the outputs when
  * they are given (xyz: 3 floats per crossing). */
 int64_t or_grid_crossings(const or_grid* g, double vs, int active_only, float* xyz, uint64_t* owner,
-                          uint8_t* slot) {
+                          uint8_t* slot, double* cprop) {
+    const int nc = g->n_props;
     int64_t cap = 16, m = 0;
     xrec* R = (xrec*)malloc(sizeof(xrec) * cap);
     for (int64_t i = 0; i < g->n; ++i) {
@@ -969,6 +1162,7 @@ int64_t or_grid_crossings(const or_grid* g, double vs, int active_only, float* x
             R[m].leaf = lk; R[m].bit = bit; R[m].slot = s;
             R[m].p[0] = pf[0]; R[m].p[1] = pf[1]; R[m].p[2] = pf[2];
             R[m].owner = g->v[i].key;
+            crossing_props(lo, hi, nc, R[m].c);
             ++m;
         }
     }
@@ -977,6 +1171,7 @@ int64_t or_grid_crossings(const or_grid* g, double vs, int active_only, float* x
         if (xyz) { xyz[3 * i] = R[i].p[0]; xyz[3 * i + 1] = R[i].p[1]; xyz[3 * i + 2] = R[i].p[2]; }
         if (owner) owner[i] = R[i].owner;
         if (slot) slot[i] = (uint8_t)R[i].slot;
+        if (cprop) for (int k = 0; k < nc; ++k) cprop[i * nc + k] = R[i].c[k];
     }
     free(R);
     return m;
@@ -1039,7 +1234,9 @@ static int cell_triangles(int inside_mask, int* out) {
  * whose 8 corners are known.  Per triangle: xyz 9 doubles (FP64 crossing points), and
  * for each vertex its edge as (key of the edge's lower voxel, axis).  Cells in ascending
  * key order of the lower corner, triangles in fan order.  Returns the triangle count. */
-int64_t or_grid_mesh(const or_grid* g, double vs, int active_only, double* xyz, uint64_t* ekey, uint8_t* eaxis) {
+int64_t or_grid_mesh(const or_grid* g, double vs, int active_only, double* xyz, uint64_t* ekey, uint8_t* eaxis,
+                     double* vprop) {
+    const int nc = g->n_props;
     int64_t nt = 0;
     for (int64_t i = 0; i < g->n; ++i) {
         int64_t v[3], leaf[3];
@@ -1048,11 +1245,13 @@ int64_t or_grid_mesh(const or_grid* g, double vs, int active_only, double* xyz, 
         leaf_of(v, leaf, &bit);
         if (!leaf_selected(g, pack_key(leaf[0], leaf[1], leaf[2]), active_only)) continue;
         double D[8];
+        const gvox* corner[8];
         int mask = 0, ok = 1;
         for (int c = 0; c < 8 && ok; ++c) {
             int64_t w[3] = {v[0] + (c & 1), v[1] + ((c >> 1) & 1), v[2] + ((c >> 2) & 1)};
             const gvox* o = grid_find(g, w);
             if (!o) { ok = 0; break; }
+            corner[c] = o;
             D[c] = o->D;
             if (D[c] < 0.0) mask |= 1 << c;
         }
@@ -1069,6 +1268,7 @@ int64_t or_grid_mesh(const or_grid* g, double vs, int active_only, double* xyz, 
                 if (xyz) for (int k = 0; k < 3; ++k) xyz[9 * nt + 3 * j + k] = p[k];
                 if (ekey) ekey[3 * nt + j] = pack_key(a[0], a[1], a[2]);
                 if (eaxis) eaxis[3 * nt + j] = (uint8_t)axis;
+                if (vprop && nc) crossing_props(corner[lc], corner[uc], nc, vprop + (3 * nt + j) * nc);
             }
         }
     }
