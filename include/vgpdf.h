@@ -128,6 +128,9 @@ typedef struct {
     int32_t profile;     /* nonzero: time the solve kernels with CUDA events (vgp_stats) */
     int32_t launch;      /* VGP_LAUNCH_BATCHED (0) or VGP_LAUNCH_PER_INSTANCE (1) */
     int32_t normal_steps;/* ray-cast testing points: voxels along each surface normal, each side */
+    double sigma_prop;   /* noise std of the surface-property GP (Eq. 6); default 0.1 */
+    int32_t n_props;     /* surface-property channels per point, 0..4; default 0 */
+    int32_t reserved;    /* must be 0 */
 } vgp_params;
 
 /* Counters of the most recent call on a map (host copy; informational). */
@@ -184,6 +187,20 @@ int vgp_build_frame(vgp_map* m, const float* pts_dev, int64_t n, const double* o
                     vgp_frame** out);
 
 /*
+ * vgp_build_frame with surface properties (Eq. 6).  props_dev [n][params.n_props] float32
+ * (device) holds each point's properties (e.g. intensity, colour channels); NULL behaves as
+ * vgp_build_frame.  Each occupied voxel's property is the mean over its points (FP64 sums, in
+ * an unspecified order); each leaf gets a second GP on the same training voxels with noise
+ * sigma_prop, and every testing voxel, through the same node as its distance, gets
+ *   c = k^T (K + sigma_prop^2 I)^-1 y     (Eq. 6, per channel, FP64)
+ *   w = 1 - k^T (K + sigma_prop^2 I)^-1 k (posterior variance, read as for Eq. 2, FP64)
+ * read with vgp_frame_props; c = NaN and w = +inf where the distance has no GP node or the
+ * factorisation failed.  VGP_ERR_ARG if props_dev is given and the map has n_props = 0.
+ */
+int vgp_build_frame_props(vgp_map* m, const float* pts_dev, const float* props_dev, int64_t n,
+                          const double* origin, vgp_stream stream, vgp_frame** out);
+
+/*
  * Views of a frame's testing-voxel results (device pointers, owned by the frame, valid until
  * vgp_frame_destroy).  Arrays have *n_test entries in one common (unspecified) order:
  *   keys    voxel key: ((i + 2^20) << 42) | ((j + 2^20) << 21) | (k + 2^20)
@@ -210,6 +227,13 @@ int vgp_frame_instances(const vgp_frame* f, int64_t* n_leaves, int64_t* n_train,
                         const uint64_t** leaf_key, const int32_t** n_occ,
                         const int64_t** inst_off, const double** X, const double** alpha);
 
+/*
+ * Surface-property results of a frame built by vgp_build_frame_props (device pointers owned
+ * by the frame, in the order of vgp_frame_results): c [n_test][n_props], w [n_test].
+ * *n_props = 0 (and NULL pointers) for a frame without properties.
+ */
+int vgp_frame_props(const vgp_frame* f, int32_t* n_props, const double** c, const double** w);
+
 /* Free a frame (waits for its stream).  NULL is a no-op. */
 int vgp_frame_destroy(vgp_frame* f);
 
@@ -220,6 +244,11 @@ int vgp_frame_destroy(vgp_frame* f);
  * b = v / (V + v), V = (1/V + 1/v)^-1) or Eq. 9.  Leaves that receive a voxel are marked
  * active (flag bit 0: touched by this fuse, bit 1: ever touched).  Grows the grid as needed
  * (may synchronise the stream).  The frame must come from the same map.
+ * Surface properties (a frame with properties on a map with n_props > 0; the last sentence
+ * of Sec. IV-C): where a voxel's distance is fused and its c is finite and w valid (finite,
+ * > 0, and < 1 for Eq. 9), the properties C (all channels) and their variance W are fused by
+ * the same rules with w in place of v; a voxel's first property takes C = c, W = w (Eq. 9:
+ * 1 - w).  Voxels without a fused property hold C = W = NaN.
  */
 int vgp_fuse(vgp_map* m, vgp_frame* f, vgp_stream stream);
 
@@ -231,6 +260,21 @@ int vgp_fuse(vgp_map* m, vgp_frame* f, vgp_stream stream);
  */
 int vgp_export_grid(vgp_map* m, int64_t* n, uint64_t* keys, double* D, double* V,
                     uint8_t* flags, vgp_stream stream);
+
+/*
+ * Fused surface properties in the order of vgp_export_grid: C [n][n_props], W [n] (NaN where
+ * none was fused).  Count query and capacity rules as for vgp_export_grid; *n = 0 when the
+ * map has n_props = 0.  Synchronises the stream.
+ */
+int vgp_export_props(vgp_map* m, int64_t* n, uint64_t* keys, double* C, double* W, vgp_stream stream);
+
+/*
+ * Set the fused surface properties of voxels already in the grid (after vgp_import_grid;
+ * host arrays in the export format).  Keys not in the grid are skipped.  VGP_ERR_STATE if the
+ * map has n_props = 0.  Synchronises the stream.
+ */
+int vgp_import_props(vgp_map* m, int64_t n, const uint64_t* keys, const double* C, const double* W,
+                     vgp_stream stream);
 
 /* Replace the global grid by host arrays in the export format (checkpoint / resume). */
 int vgp_import_grid(vgp_map* m, int64_t n, const uint64_t* keys, const double* D,
@@ -274,6 +318,15 @@ int vgp_mesh_crossings(const vgp_mesh* mesh, int64_t* n, const float** xyz_dev, 
 int vgp_mesh_triangles(const vgp_mesh* mesh, int64_t* n, const double** xyz_dev, const uint64_t** edge_key_dev,
                        const uint8_t** edge_axis_dev);
 void vgp_mesh_destroy(vgp_mesh* mesh);
+
+/*
+ * Surface properties on the mesh (Sec. IV-D: the reconstruction carries the fused properties):
+ * at each crossing the fused C of the edge's two ends interpolated with the crossing's t,
+ * C_a + t (C_b - C_a) (NaN unless both ends hold properties).  cross [n_crossings][n_props],
+ * vert [n_triangles][3][n_props], device, owned by the handle; *n_props = 0 (NULL pointers)
+ * when the map has none.
+ */
+int vgp_mesh_props(const vgp_mesh* mesh, int32_t* n_props, const double** cross_dev, const double** vert_dev);
 
 /*
  * Host copy of the marching-cubes table the kernels use (no device work): tab [256][16] cell

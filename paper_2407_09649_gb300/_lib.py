@@ -23,7 +23,8 @@ class VgpParams(C.Structure):
     _fields_ = [("voxel_size", C.c_double), ("lengthscale", C.c_double), ("sigma_occ", C.c_double),
                 ("d_max", C.c_double), ("d_var_floor", C.c_double), ("max_pts_leaf", C.c_int32),
                 ("max_pts_group", C.c_int32), ("max_leaf_search", C.c_int32), ("fusion", C.c_int32),
-                ("precision", C.c_int32), ("profile", C.c_int32), ("launch", C.c_int32), ("normal_steps", C.c_int32)]
+                ("precision", C.c_int32), ("profile", C.c_int32), ("launch", C.c_int32), ("normal_steps", C.c_int32),
+                ("sigma_prop", C.c_double), ("n_props", C.c_int32), ("reserved", C.c_int32)]
 
 
 class VgpStats(C.Structure):
@@ -45,6 +46,11 @@ SIGNATURES = [
     ("vgp_frame_results", _i32, [_vp, C.POINTER(C.c_int64), _PP, _PP, _PP, _PP, _PP]),
     ("vgp_frame_instances", _i32, [_vp, C.POINTER(C.c_int64), C.POINTER(C.c_int64), _PP, _PP, _PP, _PP, _PP]),
     ("vgp_frame_destroy", _i32, [_vp]),
+    ("vgp_build_frame_props", _i32, [_vp, _vp, _vp, _i64, _vp, _vp, _PP]),
+    ("vgp_frame_props", _i32, [_vp, C.POINTER(C.c_int32), _PP, _PP]),
+    ("vgp_export_props", _i32, [_vp, C.POINTER(C.c_int64), _vp, _vp, _vp, _vp]),
+    ("vgp_import_props", _i32, [_vp, _i64, _vp, _vp, _vp, _vp]),
+    ("vgp_mesh_props", _i32, [_vp, C.POINTER(C.c_int32), _PP, _PP]),
     ("vgp_fuse", _i32, [_vp, _vp, _vp]),
     ("vgp_export_grid", _i32, [_vp, C.POINTER(C.c_int64), _vp, _vp, _vp, _vp, _vp]),
     ("vgp_import_grid", _i32, [_vp, _i64, _vp, _vp, _vp, _vp, _vp]),

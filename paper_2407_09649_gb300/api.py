@@ -84,6 +84,21 @@ class Frame:
                     grad=_view(g.value, (n, 3), "<f8", torch.float64),
                     status=_view(s.value, (n,), "|u1", torch.uint8))
 
+    def props(self):
+        """Surface-property means (n_test, n_props) and variances (n_test,) of the testing
+        voxels, in the order of results(); None for a frame without properties."""
+        lib = L.load()
+        npr = C.c_int32()
+        c, w = C.c_void_p(), C.c_void_p()
+        L.check(lib.vgp_frame_props(self._h, C.byref(npr), C.byref(c), C.byref(w)))
+        if npr.value == 0:
+            return None
+        n = C.c_int64()
+        L.check(lib.vgp_frame_results(self._h, C.byref(n), None, None, None, None, None))
+        torch.cuda.current_stream().synchronize()
+        return (_view(c.value, (n.value, npr.value), "<f8", torch.float64),
+                _view(w.value, (n.value,), "<f8", torch.float64))
+
     def instances(self) -> dict:
         lib = L.load()
         nl, T = C.c_int64(), C.c_int64()
@@ -128,16 +143,45 @@ class Map:
         self._surface_key = None
 
     # -- L-GPDF ----------------------------------------------------------------------
-    def build_frame(self, pts, origin=None) -> Frame:
+    def build_frame(self, pts, origin=None, props=None) -> Frame:
         """L-GPDF of one frame; with the sensor ``origin`` (3 floats) the testing voxels are
-        the ray-cast set and distances are signed."""
+        the ray-cast set and distances are signed; ``props`` (n, n_props) float32 adds the
+        surface-property GP (Eq. 6)."""
         pts = _dev_f32(pts, "pts")
         h = C.c_void_p()
         o = None
         if origin is not None:
             o = (C.c_double * 3)(*[float(x) for x in origin])
-        L.check(L.load().vgp_build_frame(self._h, _ptr(pts), pts.shape[0], o, _stream(), C.byref(h)))
+        if props is None:
+            L.check(L.load().vgp_build_frame(self._h, _ptr(pts), pts.shape[0], o, _stream(), C.byref(h)))
+        else:
+            if isinstance(props, np.ndarray):
+                props = torch.from_numpy(np.ascontiguousarray(props, np.float32))
+            pr = props.to(device="cuda", dtype=torch.float32).reshape(pts.shape[0], -1).contiguous()
+            L.check(L.load().vgp_build_frame_props(self._h, _ptr(pts), _ptr(pr), pts.shape[0], o, _stream(),
+                                                   C.byref(h)))
         return Frame(self, h)
+
+    def export_props(self):
+        """Fused surface properties (n, n_props) and variances in the order of export_grid."""
+        lib = L.load()
+        n = C.c_int64(0)
+        L.check(lib.vgp_export_props(self._h, C.byref(n), None, None, None, _stream()))
+        npr = self.params.n_props
+        k = np.zeros(n.value, np.uint64)
+        Cp = np.zeros((n.value, npr))
+        W = np.zeros(n.value)
+        if n.value:
+            L.check(lib.vgp_export_props(self._h, C.byref(n), k.ctypes.data_as(C.c_void_p),
+                                         Cp.ctypes.data_as(C.c_void_p), W.ctypes.data_as(C.c_void_p), _stream()))
+        return k, Cp, W
+
+    def import_props(self, keys, Cp, W) -> None:
+        keys = np.ascontiguousarray(keys, np.uint64)
+        Cp = np.ascontiguousarray(Cp, np.float64)
+        W = np.ascontiguousarray(W, np.float64)
+        L.check(L.load().vgp_import_props(self._h, len(keys), keys.ctypes.data_as(C.c_void_p),
+                                          Cp.ctypes.data_as(C.c_void_p), W.ctypes.data_as(C.c_void_p), _stream()))
 
     def fuse(self, frame: Frame) -> None:
         L.check(L.load().vgp_fuse(self._h, frame._h, _stream()))
@@ -191,9 +235,16 @@ class Map:
             nt = nt.value
             tri = (_view(x.value, (nt, 3, 3), "<f8", torch.float64), _view(o.value, (nt, 3), "<u8", torch.uint64),
                    _view(sl.value, (nt, 3), "|u1", torch.uint8))
+            npr = C.c_int32()
+            L.check(lib.vgp_mesh_props(h, C.byref(npr), C.byref(x), C.byref(o)))
+            npr = npr.value
+            props = None
+            if npr:
+                props = (_view(x.value, (n, npr), "<f8", torch.float64),
+                         _view(o.value, (nt, 3, npr), "<f8", torch.float64))
         finally:
             lib.vgp_mesh_destroy(h)
-        return dict(crossings=cross, triangles=tri)
+        return dict(crossings=cross, triangles=tri, props=props)
 
     def update_surface(self) -> int:
         """Refresh the G-GPDF training set from the zero crossings of the leaves the latest

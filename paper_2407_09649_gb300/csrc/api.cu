@@ -105,6 +105,8 @@ struct vgp_map {
     double* g_D = nullptr;
     double* g_V = nullptr;
     int32_t* g_flags = nullptr;
+    double* g_C = nullptr;  // fused surface properties [pool][512][n_props] (Eq. 6, Sec. IV-C)
+    double* g_W = nullptr;  // their variances / weights [pool][512]; NaN: none fused
     int g_leaves = 0;
     // surface
     float* s_pts = nullptr;
@@ -138,6 +140,9 @@ struct vgp_frame {
     char4* Xi = nullptr;
     double* centre = nullptr;
     double* alpha = nullptr;
+    int nprop = 0;
+    double* c = nullptr;  // [ntest][nprop] surface-property means (Eq. 6)
+    double* w = nullptr;  // [ntest] their variances
     uint64_t* tkey = nullptr;
     double* d = nullptr;
     double* v = nullptr;
@@ -166,6 +171,8 @@ static DevParams expand(const vgp_params& p) {
     P.inv2l2_log2e = (float)(1.4426950408889634 / (2.0 * P.l2));
     P.cap_leaf = p.max_pts_leaf;
     P.cap_group = p.max_pts_group;
+    P.n_props = p.n_props;
+    P.s2p = p.sigma_prop * p.sigma_prop;
     P.search_r = p.max_leaf_search;
     P.fusion = p.fusion;
     P.precision = p.precision;
@@ -219,6 +226,8 @@ void vgp_default_params(vgp_params* p) {
     p->fusion = VGP_FUSE_INVVAR;
     p->precision = VGP_MIXED;
     p->normal_steps = 3;
+    p->sigma_prop = 0.1;
+    p->n_props = 0;
 }
 
 int vgp_create(const vgp_params* p, vgp_map** out) {
@@ -234,6 +243,8 @@ int vgp_create(const vgp_params* p, vgp_map** out) {
     if (p->fusion != VGP_FUSE_INVVAR && p->fusion != VGP_FUSE_TSDF) return fail(VGP_ERR_ARG, "unknown fusion rule");
     if (p->precision != VGP_FP64 && p->precision != VGP_MIXED) return fail(VGP_ERR_ARG, "unknown precision");
     if (p->normal_steps < 0 || p->normal_steps > 16) return fail(VGP_ERR_ARG, "normal_steps must be in [0, 16]");
+    if (p->n_props < 0 || p->n_props > 4) return fail(VGP_ERR_ARG, "n_props must be in [0, 4]");
+    if (!(p->sigma_prop > 0) || !std::isfinite(p->sigma_prop)) return fail(VGP_ERR_ARG, "sigma_prop must be > 0");
     if (p->launch != VGP_LAUNCH_BATCHED && p->launch != VGP_LAUNCH_PER_INSTANCE) return fail(VGP_ERR_ARG, "unknown launch mode");
     if (p->profile != 0 && p->profile != 1) return fail(VGP_ERR_ARG, "profile must be 0 or 1");
     vgp_map* m = new (std::nothrow) vgp_map();
@@ -298,6 +309,8 @@ int vgp_destroy(vgp_map* m) {
     cudaFree(m->g_D);
     cudaFree(m->g_V);
     cudaFree(m->g_flags);
+    cudaFree(m->g_C);
+    cudaFree(m->g_W);
     cudaFree(m->s_pts);
     cudaFree(m->s_tab.keys);
     cudaFree(m->s_slot2leaf);
@@ -325,7 +338,13 @@ int vgp_get_stats(const vgp_map* m, vgp_stats* out) {
 // ---------------------------------- frame ----------------------------------------------
 int vgp_build_frame(vgp_map* m, const float* pts, int64_t n, const double* origin, vgp_stream stream,
                     vgp_frame** out) {
+    return vgp_build_frame_props(m, pts, nullptr, n, origin, stream, out);
+}
+
+int vgp_build_frame_props(vgp_map* m, const float* pts, const float* props, int64_t n, const double* origin,
+                          vgp_stream stream, vgp_frame** out) {
     if (!m || !out || n < 0 || (n > 0 && !pts)) return fail(VGP_ERR_ARG, "vgp_build_frame: bad argument");
+    if (props && m->prm.n_props == 0) return fail(VGP_ERR_ARG, "vgp_build_frame_props: the map has n_props = 0");
     if (n > (1ll << 30)) return fail(VGP_ERR_ARG, "vgp_build_frame: n too large");
     *out = nullptr;
     cudaStream_t st = (cudaStream_t)stream;
@@ -511,6 +530,37 @@ int vgp_build_frame(vgp_map* m, const float* pts, int64_t n, const double* origi
     SolveStats ss;
     solve_batch(b, P, m->dev_words, st, m->ar, &ss, nullptr, m->prm.profile != 0, m->prm.launch, &m->cfg);
     if (origin) frame_orphans_and_sign(f->ntest, n_assigned, gsign, f->d, f->grad, f->v, f->status, st);
+    // 6. surface properties (Eq. 6): voxel-mean properties as targets of a second GP per leaf
+    // with noise sigma_prop, inferred at the same testing voxels through the same nodes
+    if (props && n > 0) {
+        const int nc = m->prm.n_props;
+        f->nprop = nc;
+        f->c = f->alloc<double>(f->ntest * nc, st);
+        f->w = f->alloc<double>(f->ntest, st);
+        double* y = (double*)m->ar.get(Arena::kPair5, sizeof(double) * std::max<int64_t>(T * nc, 1), st);
+        double* ycnt = (double*)m->ar.get(Arena::kPair6, sizeof(double) * std::max<int64_t>(T, 1), st);
+        if (!f->c || !f->w || !y || !ycnt) return bail(VGP_ERR_OOM, "allocation failed");
+        fill_u64(reinterpret_cast<uint64_t*>(f->c), 0x7ff8000000000000ull, f->ntest * nc, st);  // NaN
+        fill_u64(reinterpret_cast<uint64_t*>(f->w), 0x7ff0000000000000ull, f->ntest, st);       // +inf
+        cudaMemsetAsync(y, 0, sizeof(double) * T * nc, st);
+        cudaMemsetAsync(ycnt, 0, sizeof(double) * T, st);
+        frame_point_props(pts, props, n, nc, P, ft, fmasks, fslot2leaf, f->nocc, f->inst_off, y, ycnt, st);
+        frame_prop_means(y, ycnt, T, nc, st);
+        SolveBatch pb = b;
+        pb.d = nullptr;
+        pb.grad = nullptr;
+        pb.var = nullptr;
+        pb.status = nullptr;
+        pb.alpha_out = nullptr;
+        pb.nprop = nc;
+        pb.yprop = y;
+        pb.pc = f->c;
+        pb.pw = f->w;
+        pb.want_var = 1;
+        DevParams Pp = P;
+        Pp.s2 = P.s2p;
+        solve_batch(pb, Pp, m->dev_words, st, m->ar, nullptr, nullptr, false, m->prm.launch, &m->cfg);
+    }
     if (read_words(m, st) != VGP_OK) return bail(VGP_ERR_CUDA, "sync failed");
     if (!origin && m->host_words[4] != 0) return bail(VGP_ERR_STATE, "testing voxel without a neighbouring GP leaf");
     cudaError_t ce = cudaGetLastError();
@@ -547,6 +597,14 @@ int vgp_frame_results(const vgp_frame* f, int64_t* n_test, const uint64_t** keys
     return VGP_OK;
 }
 
+int vgp_frame_props(const vgp_frame* f, int32_t* n_props, const double** c, const double** w) {
+    if (!f) return fail(VGP_ERR_ARG, "null frame");
+    if (n_props) *n_props = f->nprop;
+    if (c) *c = f->c;
+    if (w) *w = f->w;
+    return VGP_OK;
+}
+
 int vgp_frame_instances(const vgp_frame* f, int64_t* n_leaves, int64_t* n_train, const uint64_t** leaf_key,
                         const int32_t** n_occ, const int64_t** inst_off, const double** X, const double** alpha) {
     if (!f) return fail(VGP_ERR_ARG, "null frame");
@@ -569,6 +627,16 @@ int vgp_frame_destroy(vgp_frame* f) {
 }
 
 // ---------------------------------- fusion ---------------------------------------------
+static PropGrid prop_grid(const vgp_map* m) {
+    PropGrid pg;
+    if (m->prm.n_props > 0 && m->g_C) {
+        pg.C = m->g_C;
+        pg.W = m->g_W;
+        pg.nc = m->prm.n_props;
+    }
+    return pg;
+}
+
 static int grid_reserve(vgp_map* m, int64_t extra_leaves, cudaStream_t st) {
     const int64_t need = m->g_leaves + extra_leaves;
     if (need > (1ll << 30)) return fail(VGP_ERR_OOM, "grid too large");
@@ -592,9 +660,26 @@ static int grid_reserve(vgp_map* m, int64_t extra_leaves, cudaStream_t st) {
             cudaMemcpyAsync(V, m->g_V, sizeof(double) * 512 * m->g_leaves, cudaMemcpyDeviceToDevice, st);
             cudaMemcpyAsync(flags, m->g_flags, sizeof(int32_t) * m->g_leaves, cudaMemcpyDeviceToDevice, st);
         }
+        const int np = m->prm.n_props;
+        double *Cp = nullptr, *Wp = nullptr;
+        if (np > 0) {
+            if (cudaMalloc(&Cp, sizeof(double) * 512 * np * nc) != cudaSuccess ||
+                cudaMalloc(&Wp, sizeof(double) * 512 * nc) != cudaSuccess) {
+                cudaGetLastError();
+                cudaStreamSynchronize(st);
+                cudaFree(known); cudaFree(D); cudaFree(V); cudaFree(flags); cudaFree(Cp); cudaFree(Wp);
+                return fail(VGP_ERR_OOM, "grid property pool allocation failed (%lld leaves)", (long long)nc);
+            }
+            if (m->g_leaves > 0) {
+                cudaMemcpyAsync(Cp, m->g_C, sizeof(double) * 512 * np * m->g_leaves, cudaMemcpyDeviceToDevice, st);
+                cudaMemcpyAsync(Wp, m->g_W, sizeof(double) * 512 * m->g_leaves, cudaMemcpyDeviceToDevice, st);
+            }
+        }
         CUDA_TRY(cudaStreamSynchronize(st));
         cudaFree(m->g_known); cudaFree(m->g_D); cudaFree(m->g_V); cudaFree(m->g_flags);
+        cudaFree(m->g_C); cudaFree(m->g_W);
         m->g_known = known; m->g_D = D; m->g_V = V; m->g_flags = flags;
+        m->g_C = Cp; m->g_W = Wp;
         m->pool_cap = (int)nc;
     }
     // hash table at load <= 1/2
@@ -628,9 +713,16 @@ int vgp_fuse(vgp_map* m, vgp_frame* f, vgp_stream stream) {
     CUDA_TRY(cudaMemcpyAsync(m->dev_words + 3, &m->g_leaves, sizeof(int), cudaMemcpyHostToDevice, st));
     fuse_clear_flags(m->g_flags, m->g_leaves, st);
     fuse_insert(f->tkey, f->d, f->v, f->status, f->ntest, m->prm.fusion, m->g, m->g_slot2pool, m->dev_words, st);
-    fuse_alloc(m->g_slot2pool, m->g, m->dev_words + 3, m->pool_cap, m->g_known, m->g_flags, m->dev_words, st);
+    const PropGrid pg = prop_grid(m);
+    PropIn pin;
+    if (pg.nc > 0 && f->nprop == pg.nc) {
+        pin.c = f->c;
+        pin.w = f->w;
+        pin.nc = f->nprop;
+    }
+    fuse_alloc(m->g_slot2pool, m->g, m->dev_words + 3, m->pool_cap, m->g_known, m->g_flags, m->dev_words, pg, st);
     fuse_update(f->tkey, f->d, f->v, f->status, f->ntest, m->prm.fusion, m->g, m->g_slot2pool, m->g_known, m->g_D,
-                m->g_V, m->g_flags, st);
+                m->g_V, m->g_flags, pin, pg, st);
     TRY(read_words(m, st));
     TRY(check_err(m, "vgp_fuse"));
     CUDA_TRY(cudaGetLastError());
@@ -703,10 +795,67 @@ int vgp_import_grid(vgp_map* m, int64_t n, const uint64_t* keys, const double* D
     CUDA_TRY(cudaMemcpyAsync(iV, V, sizeof(double) * n, cudaMemcpyHostToDevice, st));
     CUDA_TRY(cudaMemcpyAsync(ifl, flags, n, cudaMemcpyHostToDevice, st));
     grid_import(ik, iD, iV, ifl, n, m->g, m->g_slot2pool, m->dev_words + 3, m->pool_cap, m->g_known, m->g_D, m->g_V,
-                m->g_flags, m->dev_words, st);
+                m->g_flags, m->dev_words, prop_grid(m), st);
     TRY(read_words(m, st));
     TRY(check_err(m, "vgp_import_grid"));
     m->g_leaves = m->host_words[3];
+    return VGP_OK;
+}
+
+int vgp_export_props(vgp_map* m, int64_t* n, uint64_t* keys, double* C, double* W, vgp_stream stream) {
+    if (!m || !n) return fail(VGP_ERR_ARG, "vgp_export_props: bad argument");
+    cudaStream_t st = (cudaStream_t)stream;
+    const PropGrid pg = prop_grid(m);
+    if (m->g_leaves == 0 || pg.nc == 0) {
+        *n = 0;
+        return VGP_OK;
+    }
+    const int64_t cap_out = (int64_t)m->g_leaves * 512;
+    ARENA(okey, uint64_t, kTmp0, cap_out);
+    ARENA(oC, double, kTmp1, cap_out * pg.nc);
+    ARENA(oW, double, kTmp2, cap_out);
+    grid_export_props(m->g, m->g_slot2pool, m->g_known, pg, m->dev_words + 2, okey, oC, oW, st);
+    TRY(read_words(m, st));
+    const int64_t cnt = m->host_words[2];
+    if (!keys) {
+        *n = cnt;
+        return VGP_OK;
+    }
+    if (*n < cnt) return fail(VGP_ERR_ARG, "vgp_export_props: arrays hold %lld < %lld", (long long)*n, (long long)cnt);
+    std::vector<uint64_t> hk(cnt);
+    std::vector<double> hC(cnt * pg.nc), hW(cnt);
+    CUDA_TRY(cudaMemcpyAsync(hk.data(), okey, sizeof(uint64_t) * cnt, cudaMemcpyDeviceToHost, st));
+    CUDA_TRY(cudaMemcpyAsync(hC.data(), oC, sizeof(double) * cnt * pg.nc, cudaMemcpyDeviceToHost, st));
+    CUDA_TRY(cudaMemcpyAsync(hW.data(), oW, sizeof(double) * cnt, cudaMemcpyDeviceToHost, st));
+    CUDA_TRY(cudaStreamSynchronize(st));
+    std::vector<int64_t> ord(cnt);
+    for (int64_t i = 0; i < cnt; ++i) ord[i] = i;
+    std::sort(ord.begin(), ord.end(), [&](int64_t a, int64_t b) { return hk[a] < hk[b]; });
+    for (int64_t i = 0; i < cnt; ++i) {
+        keys[i] = hk[ord[i]];
+        if (C)
+            for (int ch = 0; ch < pg.nc; ++ch) C[i * pg.nc + ch] = hC[ord[i] * pg.nc + ch];
+        if (W) W[i] = hW[ord[i]];
+    }
+    *n = cnt;
+    return VGP_OK;
+}
+
+int vgp_import_props(vgp_map* m, int64_t n, const uint64_t* keys, const double* C, const double* W, vgp_stream stream) {
+    if (!m || n < 0 || (n > 0 && (!keys || !C || !W))) return fail(VGP_ERR_ARG, "vgp_import_props: bad argument");
+    const PropGrid pg = prop_grid(m);
+    if (n == 0) return VGP_OK;
+    if (pg.nc == 0) return fail(VGP_ERR_STATE, "vgp_import_props: the map holds no properties (n_props = 0 or empty grid)");
+    cudaStream_t st = (cudaStream_t)stream;
+    ARENA(ik, uint64_t, kTmp0, n);
+    ARENA(iC, double, kTmp1, n * pg.nc);
+    ARENA(iW, double, kTmp2, n);
+    CUDA_TRY(cudaMemcpyAsync(ik, keys, sizeof(uint64_t) * n, cudaMemcpyHostToDevice, st));
+    CUDA_TRY(cudaMemcpyAsync(iC, C, sizeof(double) * n * pg.nc, cudaMemcpyHostToDevice, st));
+    CUDA_TRY(cudaMemcpyAsync(iW, W, sizeof(double) * n, cudaMemcpyHostToDevice, st));
+    grid_import_props(ik, iC, iW, n, m->g, m->g_slot2pool, m->g_known, pg, st);
+    CUDA_TRY(cudaStreamSynchronize(st));
+    CUDA_TRY(cudaGetLastError());
     return VGP_OK;
 }
 
@@ -792,7 +941,12 @@ int vgp_set_surface(vgp_map* m, const float* pts, int64_t n, vgp_stream stream) 
 
 // ------------------------- zero crossings and marching cubes (Sec. IV-D) ----------------
 static GridView grid_view(const vgp_map* m) {
-    return GridView{m->g.keys, m->g.mask, m->g_slot2pool, m->g_known, m->g_D};
+    GridView g{m->g.keys, m->g.mask, m->g_slot2pool, m->g_known, m->g_D};
+    const PropGrid pg = prop_grid(m);
+    g.C = pg.C;
+    g.W = pg.W;
+    g.nc = pg.nc;
+    return g;
 }
 
 // leaves of the grid (all, or those the latest fusion touched), in arena slots kTmp5/kTmp6
@@ -825,6 +979,9 @@ struct vgp_mesh {
     double* txyz = nullptr;
     uint64_t* tkey = nullptr;
     uint8_t* taxis = nullptr;
+    int nprop = 0;
+    double* xprop = nullptr;  // [nx][nprop]
+    double* tprop = nullptr;  // [nt][3][nprop]
 };
 
 void vgp_mesh_destroy(vgp_mesh* h) {
@@ -835,6 +992,8 @@ void vgp_mesh_destroy(vgp_mesh* h) {
     cudaFree(h->txyz);
     cudaFree(h->tkey);
     cudaFree(h->taxis);
+    cudaFree(h->xprop);
+    cudaFree(h->tprop);
     delete h;
 }
 
@@ -848,28 +1007,33 @@ static int extract_into(vgp_map* m, int active_only, int want_triangles, cudaStr
     const GridView g = grid_view(m);
     ARENA(cnt, int64_t, kTmp7, nl + 1);
     ARENA(off, int64_t, kTmp8, nl + 1);
-    mesh_crossings(g, lp, lk, nl, vs, cnt, nullptr, 0, nullptr, nullptr, nullptr, false, st);
+    h->nprop = g.nc;
+    mesh_crossings(g, lp, lk, nl, vs, cnt, nullptr, 0, nullptr, nullptr, nullptr, nullptr, false, st);
     exclusive_scan_i64(cnt, off, nl, st, m->ar);
     TRY(read_total(off + nl, st, &h->nx));
     if (cudaMalloc(&h->xyz, sizeof(float) * 3 * std::max<int64_t>(h->nx, 1)) != cudaSuccess ||
         cudaMalloc(&h->owner, sizeof(uint64_t) * std::max<int64_t>(h->nx, 1)) != cudaSuccess ||
-        cudaMalloc(&h->slot, std::max<int64_t>(h->nx, 1)) != cudaSuccess) {
+        cudaMalloc(&h->slot, std::max<int64_t>(h->nx, 1)) != cudaSuccess ||
+        (g.nc > 0 && cudaMalloc(&h->xprop, sizeof(double) * g.nc * std::max<int64_t>(h->nx, 1)) != cudaSuccess)) {
         cudaGetLastError();
         return fail(VGP_ERR_OOM, "vgp_extract_mesh: crossing allocation failed");
     }
-    mesh_crossings(g, lp, lk, nl, vs, cnt, off, 0, h->xyz, h->owner, h->slot, true, st);
+    mesh_crossings(g, lp, lk, nl, vs, cnt, off, 0, h->xyz, h->owner, h->slot, h->xprop, true, st);
     if (want_triangles) {
         const uint8_t* tab = m->mc_tab;
-        mesh_triangles(g, lp, lk, nl, tab, tab + 256 * 16, vs, cnt, nullptr, nullptr, nullptr, nullptr, false, st);
+        mesh_triangles(g, lp, lk, nl, tab, tab + 256 * 16, vs, cnt, nullptr, nullptr, nullptr, nullptr, nullptr, false,
+                       st);
         exclusive_scan_i64(cnt, off, nl, st, m->ar);
         TRY(read_total(off + nl, st, &h->nt));
         if (cudaMalloc(&h->txyz, sizeof(double) * 9 * std::max<int64_t>(h->nt, 1)) != cudaSuccess ||
             cudaMalloc(&h->tkey, sizeof(uint64_t) * 3 * std::max<int64_t>(h->nt, 1)) != cudaSuccess ||
-            cudaMalloc(&h->taxis, 3 * std::max<int64_t>(h->nt, 1)) != cudaSuccess) {
+            cudaMalloc(&h->taxis, 3 * std::max<int64_t>(h->nt, 1)) != cudaSuccess ||
+            (g.nc > 0 && cudaMalloc(&h->tprop, sizeof(double) * 3 * g.nc * std::max<int64_t>(h->nt, 1)) != cudaSuccess)) {
             cudaGetLastError();
             return fail(VGP_ERR_OOM, "vgp_extract_mesh: triangle allocation failed");
         }
-        mesh_triangles(g, lp, lk, nl, tab, tab + 256 * 16, vs, cnt, off, h->txyz, h->tkey, h->taxis, true, st);
+        mesh_triangles(g, lp, lk, nl, tab, tab + 256 * 16, vs, cnt, off, h->txyz, h->tkey, h->taxis, h->tprop, true,
+                       st);
     }
     CUDA_TRY(cudaStreamSynchronize(st));
     CUDA_TRY(cudaGetLastError());
@@ -898,6 +1062,14 @@ int vgp_mesh_crossings(const vgp_mesh* h, int64_t* n, const float** xyz, const u
     if (xyz) *xyz = h->xyz;
     if (owner) *owner = h->owner;
     if (slot) *slot = h->slot;
+    return VGP_OK;
+}
+
+int vgp_mesh_props(const vgp_mesh* h, int32_t* n_props, const double** cross, const double** vert) {
+    if (!h) return fail(VGP_ERR_ARG, "vgp_mesh_props: null mesh");
+    if (n_props) *n_props = h->nprop;
+    if (cross) *cross = h->xprop;
+    if (vert) *vert = h->tprop;
     return VGP_OK;
 }
 
@@ -965,7 +1137,7 @@ int vgp_update_surface(vgp_map* m, vgp_stream stream) {
             ARENA(off_, int64_t, kTmp8, nl + 1);
             cnt = cnt_;
             off = off_;
-            mesh_crossings(g, lp, lk, nl, vs, cnt, nullptr, 0, nullptr, nullptr, nullptr, false, st);
+            mesh_crossings(g, lp, lk, nl, vs, cnt, nullptr, 0, nullptr, nullptr, nullptr, nullptr, false, st);
             exclusive_scan_i64(cnt, off, nl, st, m->ar);
             TRY(read_total(off + nl, st, &added));
         }
@@ -978,7 +1150,7 @@ int vgp_update_surface(vgp_map* m, vgp_stream stream) {
         store_compact(m->ps_pts, n0, keep, pos, m->ps_tmp, st);
     else if (n0 > 0)
         CUDA_TRY(cudaMemcpyAsync(m->ps_tmp, m->ps_pts, sizeof(float) * 3 * n0, cudaMemcpyDeviceToDevice, st));
-    if (added > 0) mesh_crossings(g, lp, lk, nl, vs, cnt, off, kept, m->ps_tmp, nullptr, nullptr, true, st);
+    if (added > 0) mesh_crossings(g, lp, lk, nl, vs, cnt, off, kept, m->ps_tmp, nullptr, nullptr, nullptr, true, st);
     std::swap(m->ps_pts, m->ps_tmp);
     std::swap(m->ps_cap, m->ps_tmp_cap);
     m->ps_n = n1;

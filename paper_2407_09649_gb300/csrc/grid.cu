@@ -378,6 +378,42 @@ void frame_scatter_tests(const uint64_t* tl_keys, int ntl, const Table& ft, cons
 // --------------------------------------------------------------------------------------
 namespace {
 // Warp per frame leaf: every occupied voxel (uncapped), in bit order, at soff[l].
+// Surface properties of a frame (Eq. 6): a training point's property is the mean over the
+// points in its voxel.  Each point finds its leaf's training index: rank r of its voxel bit in
+// the leaf mask; with n > cap occupied voxels the leaf keeps ranks floor(k n / cap), so r is
+// kept iff k = ceil(r cap / n) maps back to r.  Sums and counts in FP64 atomics.
+__global__ void k_point_props(const float* pts, const float* props, int64_t n, int nc, DevParams P, Table ft,
+                              const unsigned long long* masks, const int32_t* slot2leaf, const int32_t* nocc,
+                              const int64_t* inst_off, double* ysum, double* ycnt) {
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    int x, y, z;
+    if (!voxel_ijk(pts[3 * i], pts[3 * i + 1], pts[3 * i + 2], P.vs, x, y, z)) return;
+    const int64_t s = ht_find(ft.keys, ft.mask, pack_key(leaf_coord(x), leaf_coord(y), leaf_coord(z)));
+    if (s < 0) return;
+    const int li = slot2leaf[s];
+    if (li < 0) return;
+    const int bit = (x & 7) + 8 * (y & 7) + 64 * (z & 7);
+    const unsigned long long* mk = masks + s * 8;
+    int r = __popcll(mk[bit >> 6] & ((1ull << (bit & 63)) - 1ull));
+    for (int w = 0; w < (bit >> 6); ++w) r += __popcll(mk[w]);
+    const int no = nocc[li], cap = P.cap_leaf;
+    int k = r;
+    if (no > cap) {
+        k = (int)(((int64_t)r * cap + no - 1) / no);
+        if (k >= cap || (int)((int64_t)k * no / cap) != r) return;
+    }
+    const int64_t t = inst_off[li] + k;
+    for (int ch = 0; ch < nc; ++ch) atomicAdd(&ysum[t * nc + ch], (double)props[i * nc + ch]);
+    atomicAdd(&ycnt[t], 1.0);
+}
+
+__global__ void k_prop_means(double* y, const double* ycnt, int64_t T, int nc) {
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= T * nc) return;
+    y[i] = y[i] / ycnt[i / nc];
+}
+
 __global__ void k_surface_voxels(const int32_t* list, const uint64_t* lkeys, int nl, const unsigned long long* masks,
                                  const int64_t* soff, uint64_t* svox) {
     int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
@@ -638,6 +674,20 @@ __global__ void k_orphans_and_sign(int64_t nt, int64_t n_assigned, const int8_t*
     }
 }
 }  // namespace
+
+void frame_point_props(const float* pts, const float* props, int64_t n, int nc, const DevParams& P, const Table& ft,
+                       const unsigned long long* masks, const int32_t* slot2leaf, const int32_t* nocc,
+                       const int64_t* inst_off, double* ysum, double* ycnt, cudaStream_t st) {
+    if (n <= 0) return;
+    k_point_props<<<nblk(n), TB, 0, st>>>(pts, props, n, nc, P, ft, masks, slot2leaf, nocc, inst_off, ysum, ycnt);
+    note_launch();
+}
+
+void frame_prop_means(double* y, const double* ycnt, int64_t T, int nc, cudaStream_t st) {
+    if (T <= 0) return;
+    k_prop_means<<<nblk(T * nc), TB, 0, st>>>(y, ycnt, T, nc);
+    note_launch();
+}
 
 void frame_surface_voxels(const int32_t* list, const uint64_t* lkeys, int nl, const unsigned long long* masks,
                           const int64_t* soff, uint64_t* svox, cudaStream_t st) {
@@ -1323,7 +1373,7 @@ __global__ void k_fuse_insert(const uint64_t* vkey, const double* d, const doubl
 }
 
 __global__ void k_fuse_alloc(int32_t* slot2pool, int64_t cap, int* pool_count, int pool_cap,
-                             unsigned long long* known, int32_t* flags, int* err) {
+                             unsigned long long* known, int32_t* flags, int* err, PropGrid pg) {
     int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (s >= cap || slot2pool[s] != -2) return;
     int p = atomicAdd(pool_count, 1);
@@ -1335,11 +1385,38 @@ __global__ void k_fuse_alloc(int32_t* slot2pool, int64_t cap, int* pool_count, i
     slot2pool[s] = p;
     for (int w = 0; w < 8; ++w) known[(int64_t)p * 8 + w] = 0ull;
     flags[p] = 0;
+    if (pg.nc > 0)
+        for (int e = 0; e < 512; ++e) {
+            pg.W[(int64_t)p * 512 + e] = __longlong_as_double(0x7ff8000000000000ll);
+            for (int ch = 0; ch < pg.nc; ++ch) pg.C[((int64_t)p * 512 + e) * pg.nc + ch] = __longlong_as_double(0x7ff8000000000000ll);
+        }
+}
+
+// Surface-property fusion: the rules of the distance fusion (Eqs. 8-9) applied to every
+// channel with the shared variance (weight) W; W = NaN takes the first estimate.
+__device__ __forceinline__ void fuse_props(int mode, double* C, double* W, const double* c, double w, int nc) {
+    if (isnan(*W)) {
+        for (int ch = 0; ch < nc; ++ch) C[ch] = c[ch];
+        *W = mode == 0 ? w : 1.0 - w;
+        return;
+    }
+    if (mode == 0) {
+        const double Wp = *W;
+        const double a = Wp / (Wp + w), b = w / (Wp + w);
+        for (int ch = 0; ch < nc; ++ch) C[ch] = a * c[ch] + b * C[ch];
+        *W = 1.0 / (1.0 / Wp + 1.0 / w);
+    } else {
+        const double Wp = *W, ww = 1.0 - w;
+        const double a = ww / (Wp + ww), b = Wp / (Wp + ww);
+        for (int ch = 0; ch < nc; ++ch) C[ch] = a * c[ch] + b * C[ch];
+        *W = Wp + ww;
+    }
 }
 
 __global__ void k_fuse_update(const uint64_t* vkey, const double* d, const double* v, const uint8_t* st, int64_t n,
                               int mode, const uint64_t* gkeys, uint32_t gmask, const int32_t* slot2pool,
-                              unsigned long long* known, double* D, double* V, int32_t* flags) {
+                              unsigned long long* known, double* D, double* V, int32_t* flags, PropIn pin,
+                              PropGrid pg) {
     int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (i >= n || !fusable(mode, st[i], d[i], v[i])) return;
     int x, y, z;
@@ -1368,6 +1445,54 @@ __global__ void k_fuse_update(const uint64_t* vkey, const double* d, const doubl
         V[e] = Vp + w;
     }
     atomicOr(&flags[p], 3);
+    if (pg.nc > 0 && pin.c) {
+        // properties fuse where the distance fuses and their estimate is valid
+        const int nc = pg.nc;
+        const double wn = pin.w[i];
+        bool okp = isfinite(wn) && wn > 0.0 && (mode == 0 || wn < 1.0);
+        double cv[4];
+        for (int ch = 0; ch < nc; ++ch) {
+            cv[ch] = pin.c[i * nc + ch];
+            okp = okp && isfinite(cv[ch]);
+        }
+        if (okp) fuse_props(mode, pg.C + e * nc, pg.W + e, cv, wn, nc);
+    }
+}
+
+__global__ void k_export_props(const uint64_t* gkeys, int64_t cap, const int32_t* slot2pool,
+                               const unsigned long long* known, PropGrid pg, int* count, uint64_t* okey, double* oC,
+                               double* oW) {
+    int64_t s = blockIdx.x;
+    if (s >= cap || gkeys[s] == kEmpty) return;
+    int p = slot2pool[s];
+    if (p < 0) return;
+    int bit = threadIdx.x;
+    if (!((known[(int64_t)p * 8 + (bit >> 6)] >> (bit & 63)) & 1ull)) return;
+    int lx, ly, lz;
+    unpack_key(gkeys[s], lx, ly, lz);
+    int o = atomicAdd(count, 1);
+    okey[o] = pack_key(8 * lx + (bit & 7), 8 * ly + ((bit >> 3) & 7), 8 * lz + (bit >> 6));
+    const int64_t e = (int64_t)p * 512 + bit;
+    for (int ch = 0; ch < pg.nc; ++ch) oC[(int64_t)o * pg.nc + ch] = pg.C[e * pg.nc + ch];
+    oW[o] = pg.W[e];
+}
+
+__global__ void k_import_props(const uint64_t* vkey, const double* iC, const double* iW, int64_t n,
+                               const uint64_t* gkeys, uint32_t gmask, const int32_t* slot2pool,
+                               const unsigned long long* known, PropGrid pg) {
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    int x, y, z;
+    unpack_key(vkey[i], x, y, z);
+    int64_t s = ht_find(gkeys, gmask, pack_key(leaf_coord(x), leaf_coord(y), leaf_coord(z)));
+    if (s < 0) return;
+    int p = slot2pool[s];
+    if (p < 0) return;
+    int bit = (x & 7) + 8 * (y & 7) + 64 * (z & 7);
+    if (!((known[(int64_t)p * 8 + (bit >> 6)] >> (bit & 63)) & 1ull)) return;
+    const int64_t e = (int64_t)p * 512 + bit;
+    for (int ch = 0; ch < pg.nc; ++ch) pg.C[e * pg.nc + ch] = iC[i * pg.nc + ch];
+    pg.W[e] = iW[i];
 }
 
 __global__ void k_export(const uint64_t* gkeys, int64_t cap, const int32_t* slot2pool, const unsigned long long* known,
@@ -1443,18 +1568,35 @@ void fuse_insert(const uint64_t* vkey, const double* d, const double* v, const u
 }
 
 void fuse_alloc(int32_t* slot2pool, const Table& g, int* pool_count, int pool_cap, unsigned long long* known,
-                int32_t* flags, int* err, cudaStream_t st) {
-    k_fuse_alloc<<<nblk(g.cap()), TB, 0, st>>>(slot2pool, (int64_t)g.cap(), pool_count, pool_cap, known, flags, err);
+                int32_t* flags, int* err, const PropGrid& pg, cudaStream_t st) {
+    k_fuse_alloc<<<nblk(g.cap()), TB, 0, st>>>(slot2pool, (int64_t)g.cap(), pool_count, pool_cap, known, flags, err,
+                                               pg);
     note_launch();
 }
 
 void fuse_update(const uint64_t* vkey, const double* d, const double* v, const uint8_t* s, int64_t n, int mode,
                  const Table& g, const int32_t* slot2pool, unsigned long long* known, double* D, double* V,
-                 int32_t* flags, cudaStream_t st) {
+                 int32_t* flags, const PropIn& pin, const PropGrid& pg, cudaStream_t st) {
     if (n > 0) {
-        k_fuse_update<<<nblk(n), TB, 0, st>>>(vkey, d, v, s, n, mode, g.keys, g.mask, slot2pool, known, D, V, flags);
+        k_fuse_update<<<nblk(n), TB, 0, st>>>(vkey, d, v, s, n, mode, g.keys, g.mask, slot2pool, known, D, V, flags,
+                                              pin, pg);
         note_launch();
     }
+}
+
+void grid_export_props(const Table& g, const int32_t* slot2pool, const unsigned long long* known, const PropGrid& pg,
+                       int* count, uint64_t* okey, double* oC, double* oW, cudaStream_t st) {
+    cudaMemsetAsync(count, 0, sizeof(int), st);
+    k_export_props<<<(unsigned)g.cap(), 512, 0, st>>>(g.keys, (int64_t)g.cap(), slot2pool, known, pg, count, okey, oC,
+                                                      oW);
+    note_launch();
+}
+
+void grid_import_props(const uint64_t* vkey, const double* iC, const double* iW, int64_t n, const Table& g,
+                       const int32_t* slot2pool, const unsigned long long* known, const PropGrid& pg, cudaStream_t st) {
+    if (n <= 0 || pg.nc <= 0) return;
+    k_import_props<<<nblk(n), TB, 0, st>>>(vkey, iC, iW, n, g.keys, g.mask, slot2pool, known, pg);
+    note_launch();
 }
 
 void grid_export(const Table& g, const int32_t* slot2pool, const unsigned long long* known, const double* D,
@@ -1468,11 +1610,11 @@ void grid_export(const Table& g, const int32_t* slot2pool, const unsigned long l
 
 void grid_import(const uint64_t* vkey, const double* iD, const double* iV, const uint8_t* ifl, int64_t n, const Table& g,
                  int32_t* slot2pool, int* pool_count, int pool_cap, unsigned long long* known, double* D, double* V,
-                 int32_t* flags, int* err, cudaStream_t st) {
+                 int32_t* flags, int* err, const PropGrid& pg, cudaStream_t st) {
     if (n <= 0) return;
     k_import_insert<<<nblk(n), TB, 0, st>>>(vkey, n, g.keys, g.mask, slot2pool, err);
     note_launch();
-    fuse_alloc(slot2pool, g, pool_count, pool_cap, known, flags, err, st);
+    fuse_alloc(slot2pool, g, pool_count, pool_cap, known, flags, err, pg, st);
     k_import_set<<<nblk(n), TB, 0, st>>>(vkey, iD, iV, ifl, n, g.keys, g.mask, slot2pool, known, D, V, flags);
     note_launch();
 }

@@ -11,6 +11,20 @@ struct Table {
     size_t cap() const { return keys ? (size_t)mask + 1 : 0; }
 };
 
+// fused surface properties of the global grid (Eq. 6, Sec. IV-C): per pool voxel nc channels
+// and one variance (weight for Eq. 9); W = NaN: no property fused yet
+struct PropGrid {
+    double* C = nullptr;
+    double* W = nullptr;
+    int nc = 0;
+};
+// one frame's property estimates by testing voxel
+struct PropIn {
+    const double* c = nullptr;
+    const double* w = nullptr;
+    int nc = 0;
+};
+
 void collect_table(const Table& t, int32_t* slot2idx, int32_t* list, uint64_t* keys_out, int* count_dev,
                    int64_t list_cap, int* err, cudaStream_t st);
 
@@ -83,17 +97,28 @@ void query_scatter(const int32_t* q_inst, int64_t n, const int64_t* q_off, int64
 void fuse_clear_flags(int32_t* flags, int n, cudaStream_t st);
 void fuse_insert(const uint64_t* vkey, const double* d, const double* v, const uint8_t* s, int64_t n, int mode,
                  const Table& g, int32_t* slot2pool, int* err, cudaStream_t st);
+// frame surface properties: per training point the mean of its voxel's point properties
+void frame_point_props(const float* pts, const float* props, int64_t n, int nc, const DevParams& P, const Table& ft,
+                       const unsigned long long* masks, const int32_t* slot2leaf, const int32_t* nocc,
+                       const int64_t* inst_off, double* ysum, double* ycnt, cudaStream_t st);
+void frame_prop_means(double* y, const double* ycnt, int64_t T, int nc, cudaStream_t st);
+
 void fuse_alloc(int32_t* slot2pool, const Table& g, int* pool_count, int pool_cap, unsigned long long* known,
-                int32_t* flags, int* err, cudaStream_t st);
+                int32_t* flags, int* err, const PropGrid& pg, cudaStream_t st);
 void fuse_update(const uint64_t* vkey, const double* d, const double* v, const uint8_t* s, int64_t n, int mode,
                  const Table& g, const int32_t* slot2pool, unsigned long long* known, double* D, double* V,
-                 int32_t* flags, cudaStream_t st);
+                 int32_t* flags, const PropIn& pin, const PropGrid& pg, cudaStream_t st);
+// properties of every known voxel (key order unspecified), and setting them for given keys
+void grid_export_props(const Table& g, const int32_t* slot2pool, const unsigned long long* known, const PropGrid& pg,
+                       int* count, uint64_t* okey, double* oC, double* oW, cudaStream_t st);
+void grid_import_props(const uint64_t* vkey, const double* iC, const double* iW, int64_t n, const Table& g,
+                       const int32_t* slot2pool, const unsigned long long* known, const PropGrid& pg, cudaStream_t st);
 void grid_export(const Table& g, const int32_t* slot2pool, const unsigned long long* known, const double* D,
                  const double* V, const int32_t* flags, int* count, uint64_t* okey, double* oD, double* oV,
                  uint8_t* ofl, cudaStream_t st);
 void grid_import(const uint64_t* vkey, const double* iD, const double* iV, const uint8_t* ifl, int64_t n, const Table& g,
                  int32_t* slot2pool, int* pool_count, int pool_cap, unsigned long long* known, double* D, double* V,
-                 int32_t* flags, int* err, cudaStream_t st);
+                 int32_t* flags, int* err, const PropGrid& pg, cudaStream_t st);
 void grid_rehash(const Table& o, const int32_t* oslot2pool, const Table& nt, int32_t* nslot2pool, int* err,
                  cudaStream_t st);
 

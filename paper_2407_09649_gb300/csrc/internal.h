@@ -50,6 +50,12 @@ struct SolveBatch {
     uint8_t* status = nullptr;
     double* alpha_out = nullptr;        // [T] optional
     int want_var = 0;
+    // surface-property mode (Eq. 6): nprop > 0 replaces the right-hand side 1 by the nprop
+    // columns of yprop and writes property means / variances instead of distances
+    int nprop = 0;
+    const double* yprop = nullptr;      // [T][nprop]
+    double* pc = nullptr;               // [n_queries][nprop] by query id
+    double* pw = nullptr;               // [n_queries] by query id
 };
 
 // Backward-pass extras (G-GPDF only).

@@ -42,6 +42,18 @@ __device__ __forceinline__ void crossing_point(const int a[3], int axis, double 
     p[axis] = __dmul_rn(__dadd_rn((double)a[axis], t), vs);
 }
 
+// fused properties at a crossing: C_a + t (C_b - C_a) per channel with the crossing's t, NaN
+// unless both ends hold properties (round-to-nearest, no contraction)
+__device__ __forceinline__ void crossing_props(const GridView& g, int64_t ea, int64_t eb, double Da, double Db,
+                                               double* out) {
+    const double t = __ddiv_rn(Da, __dsub_rn(Da, Db));
+    const bool ok = !isnan(g.W[ea]) && !isnan(g.W[eb]);
+    for (int ch = 0; ch < g.nc; ++ch) {
+        const double ca = g.C[ea * g.nc + ch], cb = g.C[eb * g.nc + ch];
+        out[ch] = ok ? __dadd_rn(ca, __dmul_rn(t, __dsub_rn(cb, ca))) : __longlong_as_double(0x7ff8000000000000ll);
+    }
+}
+
 // Block-wide exclusive prefix sum of small non-negative counts.
 __device__ __forceinline__ int block_excl_sum(int v, int* wsum, int& total) {
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
@@ -85,7 +97,7 @@ struct VoxCtx {
 };
 
 __device__ __forceinline__ bool slot_crossing(const GridView& g, const int* nb, const VoxCtx& c, int s, double vs,
-                                              float out[3]) {
+                                              float out[3], double* prop = nullptr) {
     const int axis = s >> 1, dir = (s & 1) ? 1 : -1;
     const int stride = axis == 0 ? 1 : (axis == 1 ? 8 : 64);
     int lc = c.l[axis] + dir, q = c.p;
@@ -107,13 +119,18 @@ __device__ __forceinline__ bool slot_crossing(const GridView& g, const int* nb, 
     out[2] = __double2float_rn(pd[2]);
     int i, j, k;
     if (!voxel_ijk(out[0], out[1], out[2], vs, i, j, k)) return false;
-    return i == c.v[0] && j == c.v[1] && k == c.v[2];
+    if (!(i == c.v[0] && j == c.v[1] && k == c.v[2])) return false;
+    if (prop) {
+        const int64_t ev = (int64_t)c.p * 512 + c.bit, en = (int64_t)q * 512 + nbit;
+        crossing_props(g, dir > 0 ? ev : en, dir > 0 ? en : ev, Dlo, Dhi, prop);
+    }
+    return true;
 }
 
 template <bool kEmit>
 __global__ void __launch_bounds__(512) k_crossings(GridView g, const int32_t* lpool, const uint64_t* lkey, double vs,
                                                    int64_t* cnt, const int64_t* off, int64_t base, float* xyz,
-                                                   uint64_t* owner, uint8_t* slot) {
+                                                   uint64_t* owner, uint8_t* slot, double* xprop) {
     __shared__ int nb[6];
     __shared__ int wsum[16];
     const int li = blockIdx.x;
@@ -150,7 +167,7 @@ __global__ void __launch_bounds__(512) k_crossings(GridView g, const int32_t* lp
     int64_t w = base + off[li] + o;
     const uint64_t okey = pack_key(c.v[0], c.v[1], c.v[2]);
     for (int s = 0; s < 6; ++s) {
-        if (!slot_crossing(g, nb, c, s, vs, tmp)) continue;
+        if (!slot_crossing(g, nb, c, s, vs, tmp, xprop ? xprop + w * g.nc : nullptr)) continue;
         xyz[3 * w] = tmp[0];
         xyz[3 * w + 1] = tmp[1];
         xyz[3 * w + 2] = tmp[2];
@@ -163,7 +180,8 @@ __global__ void __launch_bounds__(512) k_crossings(GridView g, const int32_t* lp
 template <bool kEmit>
 __global__ void __launch_bounds__(512) k_mesh(GridView g, const int32_t* lpool, const uint64_t* lkey,
                                               const uint8_t* tab, const uint8_t* ntri, double vs, int64_t* cnt,
-                                              const int64_t* off, double* xyz, uint64_t* ekey, uint8_t* eaxis) {
+                                              const int64_t* off, double* xyz, uint64_t* ekey, uint8_t* eaxis,
+                                              double* vprop) {
     __shared__ int nb[8];
     __shared__ int wsum[16];
     const int li = blockIdx.x, b = threadIdx.x;
@@ -173,6 +191,7 @@ __global__ void __launch_bounds__(512) k_mesh(GridView g, const int32_t* lpool, 
     __syncthreads();
     const int l0 = b & 7, l1 = (b >> 3) & 7, l2 = b >> 6;
     double D[8];
+    int64_t E[8];  // pool element of each corner
     int mask = 0;
     bool ok = true;
 #pragma unroll
@@ -180,6 +199,7 @@ __global__ void __launch_bounds__(512) k_mesh(GridView g, const int32_t* lpool, 
         const int cx = l0 + (c & 1), cy = l1 + ((c >> 1) & 1), cz = l2 + (c >> 2);
         const int q = nb[(cx >> 3) + 2 * (cy >> 3) + 4 * (cz >> 3)];
         const int cb = (cx & 7) + 8 * (cy & 7) + 64 * (cz & 7);
+        E[c] = (int64_t)q * 512 + cb;
         D[c] = 0.0;
         if (ok && vox_known(g, q, cb)) {
             D[c] = g.D[(int64_t)q * 512 + cb];
@@ -211,6 +231,7 @@ __global__ void __launch_bounds__(512) k_mesh(GridView g, const int32_t* lpool, 
             xyz[9 * w + 3 * j + 2] = p[2];
             ekey[3 * w + j] = pack_key(a[0], a[1], a[2]);
             eaxis[3 * w + j] = (uint8_t)axis;
+            if (vprop) crossing_props(g, E[lc], E[uc], D[lc], D[uc], vprop + (3 * w + j) * g.nc);
         }
     }
 }
@@ -314,24 +335,24 @@ void mesh_leaf_list(const GridView& g, const int32_t* flags, int active_only, in
 }
 
 void mesh_crossings(const GridView& g, const int32_t* lpool, const uint64_t* lkey, int nl, double vs, int64_t* cnt,
-                    const int64_t* off, int64_t base, float* xyz, uint64_t* owner, uint8_t* slot, bool emit,
-                    cudaStream_t st) {
+                    const int64_t* off, int64_t base, float* xyz, uint64_t* owner, uint8_t* slot, double* xprop,
+                    bool emit, cudaStream_t st) {
     if (nl <= 0) return;
     if (emit)
-        k_crossings<true><<<nl, 512, 0, st>>>(g, lpool, lkey, vs, cnt, off, base, xyz, owner, slot);
+        k_crossings<true><<<nl, 512, 0, st>>>(g, lpool, lkey, vs, cnt, off, base, xyz, owner, slot, xprop);
     else
-        k_crossings<false><<<nl, 512, 0, st>>>(g, lpool, lkey, vs, cnt, off, base, xyz, owner, slot);
+        k_crossings<false><<<nl, 512, 0, st>>>(g, lpool, lkey, vs, cnt, off, base, xyz, owner, slot, nullptr);
     note_launch();
 }
 
 void mesh_triangles(const GridView& g, const int32_t* lpool, const uint64_t* lkey, int nl, const uint8_t* tab,
                     const uint8_t* ntri, double vs, int64_t* cnt, const int64_t* off, double* xyz, uint64_t* ekey,
-                    uint8_t* eaxis, bool emit, cudaStream_t st) {
+                    uint8_t* eaxis, double* vprop, bool emit, cudaStream_t st) {
     if (nl <= 0) return;
     if (emit)
-        k_mesh<true><<<nl, 512, 0, st>>>(g, lpool, lkey, tab, ntri, vs, cnt, off, xyz, ekey, eaxis);
+        k_mesh<true><<<nl, 512, 0, st>>>(g, lpool, lkey, tab, ntri, vs, cnt, off, xyz, ekey, eaxis, vprop);
     else
-        k_mesh<false><<<nl, 512, 0, st>>>(g, lpool, lkey, tab, ntri, vs, cnt, off, xyz, ekey, eaxis);
+        k_mesh<false><<<nl, 512, 0, st>>>(g, lpool, lkey, tab, ntri, vs, cnt, off, xyz, ekey, eaxis, nullptr);
     note_launch();
 }
 

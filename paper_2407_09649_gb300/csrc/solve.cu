@@ -79,9 +79,11 @@ struct Shared {
     float* alf;     // [npad] alpha rounded to FP32
     float* alf_lo;  // [npad] alpha - alf, rounded to FP32
     int* xi;        // [npad] lattice offsets x | y << 8 | z << 16 (lattice instances)
+    double* pa[4];  // property weights per channel (property mode): channels 0 and 1 reuse the
+                    // distance alpha and its FP32 copies, which that mode does not use
 };
 
-__device__ Shared carve(double* sm, int npad, int a_in_smem, double* ws_a) {
+__device__ Shared carve(double* sm, int npad, int a_in_smem, double* ws_a, int nprop) {
     Shared s;
     s.X = sm;
     s.alpha = s.X + 3 * npad;
@@ -104,12 +106,18 @@ __device__ Shared carve(double* sm, int npad, int a_in_smem, double* ws_a) {
     s.alf = s.Xf + 3 * npad;
     s.alf_lo = s.alf + npad;
     s.xi = reinterpret_cast<int*>(s.alf_lo + npad);
+    double* extra = reinterpret_cast<double*>(s.xi + npad);  // 4 npad bytes: 8-byte aligned
+    s.pa[0] = s.alpha;
+    s.pa[1] = reinterpret_cast<double*>(s.alf);  // alf, alf_lo: 2 npad floats, 8-byte aligned
+    s.pa[2] = nprop > 2 ? extra : nullptr;
+    s.pa[3] = nprop > 3 ? extra + npad : nullptr;
     return s;
 }
 
-__host__ size_t smem_bytes(int npad, int a_in_smem) {
+__host__ size_t smem_bytes(int npad, int a_in_smem, int nprop = 0) {
     size_t d = (size_t)7 * npad + 64 + 256 + (a_in_smem ? (size_t)n_tiles(npad / 8) * 64 : (size_t)(npad / 8) * 64);
-    return d * sizeof(double) + (size_t)5 * npad * sizeof(float) + (size_t)npad * sizeof(int);
+    return d * sizeof(double) + (size_t)5 * npad * sizeof(float) + (size_t)npad * sizeof(int) +
+           (size_t)std::max(nprop - 2, 0) * npad * sizeof(double);
 }
 
 __device__ __forceinline__ int lat_m(int a, int b) {
@@ -321,6 +329,15 @@ __device__ bool fit_instance(const SolveCtx& c, const Shared& s, int N, int64_t 
         __syncthreads();
     }
     if (s_fail) return false;
+    if (c.b.nprop > 0) {
+        // property weights alpha_c = A^-1 y_c, one right-hand side per channel (Eq. 6)
+        for (int ch = 0; ch < c.b.nprop; ++ch) {
+            for (int i = tid; i < Np; i += nt) s.z[i] = i < N ? c.b.yprop[(base + i) * c.b.nprop + ch] : 0.0;
+            __syncthreads();
+            chol_solve(s, A, Nt, s.pa[ch]);
+        }
+        return true;
+    }
     // alpha = A^-1 1 (Eq. 1)
     for (int i = tid; i < Np; i += nt) s.z[i] = i < N ? 1.0 : 0.0;
     __syncthreads();
@@ -510,6 +527,27 @@ __device__ __forceinline__ double latent_var(const DevParams& P, const Shared& s
     return fmax(0.0, 1.0 - acc);
 }
 
+// Property means c_ch = sum_j alpha_ch,j k_j (Eq. 6) in FP64 with FP64 kernel values.
+__device__ __forceinline__ void property_mean(const DevParams& P, const Shared& s, int N, int nprop,
+                                              bool lattice, int qi, const double xl[3], double* out) {
+    double acc[4] = {0.0, 0.0, 0.0, 0.0};
+    for (int j = 0; j < N; ++j) {
+        double k;
+        if (lattice) {
+            k = P.lat_tab[lat_m(s.xi[j], qi)];
+        } else {
+            double dx = s.X[3 * j] - xl[0], dy = s.X[3 * j + 1] - xl[1], dz = s.X[3 * j + 2] - xl[2];
+            k = exp(-(dx * dx + dy * dy + dz * dz) * P.inv2l2);
+        }
+#pragma unroll
+        for (int ch = 0; ch < 4; ++ch)
+            if (ch < nprop) acc[ch] += s.pa[ch][j] * k;
+    }
+#pragma unroll
+    for (int ch = 0; ch < 4; ++ch)
+        if (ch < nprop) out[ch] = acc[ch];
+}
+
 __device__ __forceinline__ void invalid(EvalOut& r, int status) {
     r.status = status;
     r.d = INFINITY;
@@ -522,7 +560,7 @@ __global__ void k_solve(SolveCtx c) {
     __shared__ int s_w;
     const int tid = threadIdx.x, nt = blockDim.x;
     double* ws_a = c.a_in_smem ? nullptr : c.ws_a + (int64_t)blockIdx.x * c.ws_a_stride;
-    Shared s = carve(sm, c.npad, c.a_in_smem, ws_a);
+    Shared s = carve(sm, c.npad, c.a_in_smem, ws_a, c.b.nprop);
     double* V = c.ws_v ? c.ws_v + (int64_t)blockIdx.x * c.ws_v_stride + tid : nullptr;
     const bool lattice = c.b.Xi != nullptr;
     for (int j = tid; j < 256; j += nt) s.T256[j] = c.P.exp_tab[j];
@@ -537,6 +575,27 @@ __global__ void k_solve(SolveCtx c) {
         const int N = (int)(c.b.inst_off[I + 1] - base);
         const int64_t q0 = c.b.q_off[I], q1 = c.b.q_off[I + 1];
         const bool ok = N > 0 && fit_instance(c, s, N, base);
+        if (c.b.nprop > 0) {
+            // property mode: means and variance (Eq. 6, variance read as for Eq. 2)
+            const int np = c.b.nprop;
+            for (int64_t p = q0 + tid; p < q1; p += nt) {
+                const int64_t qid = c.b.qidx ? c.b.qidx[p] : p;
+                double xl[3], cm[4] = {NAN, NAN, NAN, NAN}, w = INFINITY;
+                int qi = 0;
+                if (ok) {
+                    query_local(c, I, p, qid, xl, &qi);
+                    if (isfinite(xl[0]) && isfinite(xl[1]) && isfinite(xl[2])) {
+                        property_mean(c.P, s, N, np, lattice, qi, xl, cm);
+                        w = latent_var(c.P, s, N, lattice, qi, xl, V, nt);
+                    }
+                }
+                for (int ch = 0; ch < np; ++ch) c.b.pc[qid * np + ch] = cm[ch];
+                c.b.pw[qid] = w;
+            }
+            if (!ok && N > 0 && tid == 0) atomicOr(c.err, kErrFactor);
+            __syncthreads();
+            continue;
+        }
         if (c.b.alpha_out)
             for (int j = tid; j < N; j += nt) c.b.alpha_out[base + j] = ok ? s.alpha[j] : NAN;
         for (int64_t p = q0 + tid; p < q1; p += nt) {
@@ -573,7 +632,7 @@ __global__ void k_backward(SolveCtx c) {
     __shared__ int s_w;
     const int tid = threadIdx.x, nt = blockDim.x;
     double* ws_a = c.a_in_smem ? nullptr : c.ws_a + (int64_t)blockIdx.x * c.ws_a_stride;
-    Shared s = carve(sm, c.npad, c.a_in_smem, ws_a);
+    Shared s = carve(sm, c.npad, c.a_in_smem, ws_a, 0);
     const double l2 = c.P.l2;
     SolveCtx cc = c;
     cc.P.precision = VGP_FP64;
@@ -780,7 +839,7 @@ void solve_batch(const SolveBatch& b, const DevParams& P, int* err_dev, cudaStre
             c.npad = std::max((N + 7) & ~7, 8);
             c.a_in_smem = c.npad <= 224;
             const int threads = c.npad <= 32 ? 64 : c.npad <= 64 ? 128 : c.npad <= 128 ? 256 : 512;
-            const size_t shm = smem_bytes(c.npad, c.a_in_smem);
+            const size_t shm = smem_bytes(c.npad, c.a_in_smem, b.nprop);
             cudaFuncSetAttribute(k_solve, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm);
             c.ws_a_stride = c.a_in_smem ? 0 : n_tiles(c.npad / 8) * 64;
             c.ws_a = c.a_in_smem ? nullptr : (double*)ar.get(Arena::kWs0, sizeof(double) * n_tiles(128) * 64, st);
@@ -825,7 +884,7 @@ void solve_batch(const SolveBatch& b, const DevParams& P, int* err_dev, cudaStre
         c.npad = std::max((nmax + 7) & ~7, 8);
         c.a_in_smem = bk.smem_a;
         if (bw) c.bw = *bw;
-        const size_t shm = smem_bytes(c.npad, c.a_in_smem);
+        const size_t shm = smem_bytes(c.npad, c.a_in_smem, bw ? 0 : b.nprop);
         auto kern = bw ? k_backward : k_solve;
         cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm);
         int per_sm = 0;

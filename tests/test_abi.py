@@ -48,7 +48,8 @@ def test_param_struct_layout_matches_header(lib):
     assert abs(p.voxel_size - 0.1) < 1e-15 and abs(p.lengthscale - 0.3) < 1e-15
     assert p.max_pts_leaf == 64 and p.max_pts_group == 1024 and p.max_leaf_search == 8
     assert p.precision == _lib.VGP_MIXED and p.fusion == _lib.VGP_FUSE_INVVAR
-    assert C.sizeof(_lib.VgpParams) == 5 * 8 + 8 * 4 and p.profile == 0 and p.normal_steps == 3
+    assert C.sizeof(_lib.VgpParams) == 5 * 8 + 8 * 4 + 8 + 2 * 4 and p.profile == 0 and p.normal_steps == 3
+    assert abs(p.sigma_prop - 0.1) < 1e-15 and p.n_props == 0
 
 
 def test_create_rejects_bad_params_without_touching_the_gpu(lib):
