@@ -349,6 +349,21 @@ def comparisons(S, Q, S_h, args):
     mesh = mp.extract_mesh(active_only=False, triangles=True)
     b.record()
     torch.cuda.synchronize()
+    # the same mapping step with three colour channels per point (Eq. 6 properties, fused)
+    mc = Map(precision="mixed", max_pts_leaf=512, n_props=3)
+    cols = [torch.rand((fr.shape[0], 3), device="cuda", generator=torch.Generator("cuda").manual_seed(k))
+            for k, fr in enumerate(frames)]
+    mc.fuse(mc.build_frame(frames[0], origin=poses[0], props=cols[0]))
+    torch.cuda.synchronize()
+    a2, b2 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a2.record()
+    for fr, o, col in zip(frames, poses, cols):
+        mc.fuse(mc.build_frame(fr, origin=o, props=col))
+        mc.update_surface()
+    b2.record()
+    torch.cuda.synchronize()
+    out["room_mapping_step_rgb"] = {"ms_per_frame": a2.elapsed_time(b2) / len(frames), "frames": len(frames),
+                                    "n_props": 3, "precision": "mixed"}
     out["room_mapping_step"] = {"ms_per_frame": 1e3 * sec / len(frames), "frames": len(frames),
                                 "training_points": int(mp.surface_points().shape[0]),
                                 "mesh_ms": a.elapsed_time(b), "mesh_triangles": int(mesh["triangles"][0].shape[0]),
