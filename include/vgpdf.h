@@ -150,6 +150,9 @@ typedef struct {
     int32_t cfg_per_sm[5];   /* ... and cap on CTAs per SM (0: occupancy limit) */
     int64_t grid_leaves;  /* leaves in the global grid */
     int64_t grid_capacity_leaves;
+    int32_t cfg_stage_panel; /* N > 224 bucket: panel column staged in shared memory (1) or read
+                                through L1/L2, leaving room for two CTAs per SM (0) */
+    int32_t reserved;
 } vgp_stats;
 
 /* Fill *p with the defaults listed above. */
@@ -395,6 +398,15 @@ int vgp_query_smooth(vgp_map* m, const float* q_dev, int64_t n, int32_t n_nodes,
  * times appear in vgp_stats.  VGP_ERR_STATE before vgp_set_surface.  Synchronises the stream.
  */
 int vgp_autotune(vgp_map* m, const float* q_dev, int64_t n, vgp_stream stream);
+
+/*
+ * Set the GP solve launch shapes by hand (what vgp_autotune chooses): threads[5] per CTA for
+ * the size buckets N > 224, 129..224, 65..128, 33..64, <= 32 (multiples of 32 in [32, 1024]),
+ * per_sm[5] caps on CTAs per SM (0: the occupancy limit), stage_panel 1 or 0 for the N > 224
+ * bucket (panel column staged in shared memory, or read through L1/L2 with room for two
+ * CTAs per SM).  VGP_ERR_ARG on a bad value.  Results do not depend on the shapes.
+ */
+int vgp_set_launch(vgp_map* m, const int32_t* threads, const int32_t* per_sm, int32_t stage_panel);
 
 /*
  * Backward pass of a scalar loss L through vgp_query_distance_gradient, with the discrete

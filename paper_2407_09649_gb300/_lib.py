@@ -32,7 +32,8 @@ class VgpStats(C.Structure):
                 ("n_train", C.c_int64), ("n_queries", C.c_int64), ("n_groups", C.c_int64),
                 ("bucket_count", C.c_int64 * 5), ("sum_n3", C.c_double), ("sum_n2", C.c_double),
                 ("t_solve_ms", C.c_double), ("t_bucket_ms", C.c_double * 5),
-                ("cfg_threads", C.c_int32 * 5), ("cfg_per_sm", C.c_int32 * 5), ("grid_leaves", C.c_int64), ("grid_capacity_leaves", C.c_int64)]
+                ("cfg_threads", C.c_int32 * 5), ("cfg_per_sm", C.c_int32 * 5), ("grid_leaves", C.c_int64), ("grid_capacity_leaves", C.c_int64),
+                ("cfg_stage_panel", C.c_int32), ("reserved", C.c_int32)]
 
 
 # (name, restype, argtypes)
@@ -58,6 +59,7 @@ SIGNATURES = [
     ("vgp_query_distance_gradient", _i32, [_vp, _vp, _i64, _vp, _vp, _vp, _vp, _vp]),
     ("vgp_query_backward", _i32, [_vp, _vp, _i64, _vp, _vp, _vp, _vp]),
     ("vgp_autotune", _i32, [_vp, _vp, _i64, _vp]),
+    ("vgp_set_launch", _i32, [_vp, _vp, _vp, C.c_int32]),
     ("vgp_query_smooth", _i32, [_vp, _vp, _i64, C.c_int32, C.c_double, _vp, _vp, _vp, _vp, _vp]),
     ("vgp_extract_mesh", _i32, [_vp, _i32, _i32, _vp, _PP]),
     ("vgp_mesh_crossings", _i32, [_vp, C.POINTER(C.c_int64), _PP, _PP, _PP]),

@@ -294,7 +294,13 @@ class Map:
         L.check(L.load().vgp_autotune(self._h, _ptr(q), q.shape[0], _stream()))
         st = self.stats()
         return {"threads": list(st["cfg_threads"]), "per_sm": list(st["cfg_per_sm"]),
-                "bucket_ms": list(st["t_bucket_ms"])}
+                "stage_panel": int(st["cfg_stage_panel"]), "bucket_ms": list(st["t_bucket_ms"])}
+
+    def set_launch(self, threads, per_sm, stage_panel: int = 1) -> None:
+        """Pin the GP solve launch shapes per size bucket (vgp_set_launch)."""
+        t = (C.c_int32 * 5)(*[int(x) for x in threads])
+        p = (C.c_int32 * 5)(*[int(x) for x in per_sm])
+        L.check(L.load().vgp_set_launch(self._h, t, p, int(stage_panel)))
 
     def query_backward(self, q, dL_dd, want_dq: bool = True, want_dX: bool = True):
         q = _dev_f32(q, "q")

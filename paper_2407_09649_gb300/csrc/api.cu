@@ -578,6 +578,7 @@ int vgp_build_frame_props(vgp_map* m, const float* pts, const float* props, int6
         S.cfg_threads[i] = m->cfg.threads[i];
         S.cfg_per_sm[i] = m->cfg.per_sm[i];
     }
+    S.cfg_stage_panel = m->cfg.stage_panel;
     S.grid_leaves = m->g_leaves;
     S.grid_capacity_leaves = m->pool_cap;
     m->stats = S;
@@ -1324,6 +1325,7 @@ int vgp_query_distance_gradient(vgp_map* m, const float* q, int64_t n, double* d
         S.cfg_threads[i] = m->cfg.threads[i];
         S.cfg_per_sm[i] = m->cfg.per_sm[i];
     }
+    S.cfg_stage_panel = m->cfg.stage_panel;
     S.grid_leaves = m->g_leaves;
     S.grid_capacity_leaves = m->pool_cap;
     m->stats = S;
@@ -1425,6 +1427,7 @@ int vgp_query_smooth(vgp_map* m, const float* q, int64_t n, int32_t n_nodes, dou
         S.cfg_threads[i] = m->cfg.threads[i];
         S.cfg_per_sm[i] = m->cfg.per_sm[i];
     }
+    S.cfg_stage_panel = m->cfg.stage_panel;
     S.sum_n3 = ss.sum_n3;
     S.sum_n2 = ss.sum_n2;
     S.t_solve_ms = ss.t_solve_ms;
@@ -1455,17 +1458,22 @@ int vgp_autotune(vgp_map* m, const float* q, int64_t n, vgp_stream stream) {
     b.qxyz = q;
     b.d = dtmp;
     // candidate launch shapes (threads per CTA, CTAs per SM cap) per size bucket
-    const int cand_t[4][5] = {{512, 512, 256, 128, 64}, {256, 256, 128, 64, 32},
-                              {256, 384, 512, 256, 128}, {128, 128, 64, 32, 256}};
-    const int cand_p[4][5] = {{1, 0, 0, 0, 0}, {2, 0, 0, 0, 0}, {1, 0, 0, 0, 0}, {4, 0, 0, 0, 0}};
+    // (the last three: N > 224 without panel staging, two or three CTAs per SM)
+    const int cand_t[7][5] = {{512, 512, 256, 128, 64}, {256, 256, 128, 64, 32}, {256, 384, 512, 256, 128},
+                              {128, 128, 64, 32, 256},  {384, 512, 256, 128, 64}, {256, 512, 256, 128, 64},
+                              {256, 512, 256, 128, 64}};
+    const int cand_p[7][5] = {{1, 0, 0, 0, 0}, {2, 0, 0, 0, 0}, {1, 0, 0, 0, 0}, {4, 0, 0, 0, 0},
+                              {2, 0, 0, 0, 0}, {2, 0, 0, 0, 0}, {3, 0, 0, 0, 0}};
+    const int cand_s[7] = {1, 1, 1, 1, 0, 0, 0};
     double best[5] = {1e300, 1e300, 1e300, 1e300, 1e300};
     SolveConfig chosen = m->cfg;
-    for (int c = 0; c < 4; ++c) {
+    for (int c = 0; c < 7; ++c) {
         SolveConfig cfg;
         for (int i = 0; i < 5; ++i) {
             cfg.threads[i] = cand_t[c][i];
             cfg.per_sm[i] = cand_p[c][i];
         }
+        cfg.stage_panel = cand_s[c];
         SolveStats ss;
         solve_batch(b, m->P, m->dev_words, st, m->ar, &ss, nullptr, true, 0, &cfg);
         CUDA_TRY(cudaGetLastError());
@@ -1474,6 +1482,7 @@ int vgp_autotune(vgp_map* m, const float* q, int64_t n, vgp_stream stream) {
                 best[i] = ss.t_bucket_ms[i];
                 chosen.threads[i] = cfg.threads[i];
                 chosen.per_sm[i] = cfg.per_sm[i];
+                if (i == 0) chosen.stage_panel = cfg.stage_panel;
             }
     }
     m->cfg = chosen;
@@ -1482,6 +1491,23 @@ int vgp_autotune(vgp_map* m, const float* q, int64_t n, vgp_stream stream) {
         m->stats.cfg_per_sm[i] = chosen.per_sm[i];
         m->stats.t_bucket_ms[i] = best[i] < 1e299 ? best[i] : 0.0;
     }
+    m->stats.cfg_stage_panel = chosen.stage_panel;
+    return VGP_OK;
+}
+
+int vgp_set_launch(vgp_map* m, const int32_t* threads, const int32_t* per_sm, int32_t stage_panel) {
+    if (!m || !threads || !per_sm || (stage_panel != 0 && stage_panel != 1))
+        return fail(VGP_ERR_ARG, "vgp_set_launch: bad argument");
+    for (int i = 0; i < 5; ++i) {
+        if (threads[i] < 32 || threads[i] > 1024 || threads[i] % 32 != 0)
+            return fail(VGP_ERR_ARG, "vgp_set_launch: threads must be multiples of 32 in [32, 1024]");
+        if (per_sm[i] < 0 || per_sm[i] > 32) return fail(VGP_ERR_ARG, "vgp_set_launch: per_sm must be in [0, 32]");
+    }
+    for (int i = 0; i < 5; ++i) {
+        m->cfg.threads[i] = threads[i];
+        m->cfg.per_sm[i] = per_sm[i];
+    }
+    m->cfg.stage_panel = stage_panel;
     return VGP_OK;
 }
 
@@ -1629,6 +1655,7 @@ extern "C" int vgp_gp_batch(vgp_map* m, int64_t n_inst, const int64_t* inst_off,
         S.cfg_threads[i] = m->cfg.threads[i];
         S.cfg_per_sm[i] = m->cfg.per_sm[i];
     }
+    S.cfg_stage_panel = m->cfg.stage_panel;
     m->stats = S;
     return VGP_OK;
 }

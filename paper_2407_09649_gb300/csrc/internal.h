@@ -73,6 +73,10 @@ struct BackwardBatch {
 struct SolveConfig {
     int threads[5] = {512, 512, 256, 128, 64};
     int per_sm[5] = {1, 0, 0, 0, 0};
+    // N > 224 (A in global memory): stage the current panel column in shared memory (1), or
+    // read it from the global tile-packed matrix through L1/L2 (0), which leaves room for two
+    // CTAs per SM
+    int stage_panel = 1;
 };
 
 struct SolveStats {

@@ -58,6 +58,7 @@ struct SolveCtx {
     int n_work;
     int npad;              // largest N in this launch, rounded up to 8
     int a_in_smem;
+    int stage_panel;       // A global: current panel column staged in shared memory
     double* ws_a;          // per-CTA tile-packed A when not in shared memory
     int64_t ws_a_stride;
     double* ws_v;          // per-CTA variance columns [npad][blockDim]
@@ -70,7 +71,7 @@ struct Shared {
     double* alpha;  // [npad]
     double* invd;   // [npad] 1 / L_ii
     double* z;      // [npad] scratch
-    double* w;      // [npad] scratch
+    double* w;      // [npad] scratch (backward pass only)
     double* Tinv;   // [64] inverse of the current diagonal tile
     double* T256;   // [256] 2^(j/256) for exp_neg
     double* A;      // tile-packed lower triangle
@@ -83,14 +84,15 @@ struct Shared {
                     // distance alpha and its FP32 copies, which that mode does not use
 };
 
-__device__ Shared carve(double* sm, int npad, int a_in_smem, double* ws_a, int nprop) {
+__device__ Shared carve(double* sm, int npad, int a_in_smem, double* ws_a, int nprop, int stage_panel,
+                        bool lattice, bool with_w) {
     Shared s;
     s.X = sm;
     s.alpha = s.X + 3 * npad;
     s.invd = s.alpha + npad;
     s.z = s.invd + npad;
-    s.w = s.z + npad;
-    s.Tinv = s.w + npad;
+    s.w = with_w ? s.z + npad : nullptr;
+    s.Tinv = s.z + (with_w ? 2 : 1) * npad;
     s.T256 = s.Tinv + 64;
     double* end = s.T256 + 256;
     if (a_in_smem) {
@@ -99,14 +101,15 @@ __device__ Shared carve(double* sm, int npad, int a_in_smem, double* ws_a, int n
         s.panel = nullptr;
     } else {
         s.A = ws_a;
-        s.panel = end;
-        end += (int64_t)(npad / 8) * 64;
+        s.panel = stage_panel ? end : nullptr;
+        if (stage_panel) end += (int64_t)(npad / 8) * 64;
     }
     s.Xf = reinterpret_cast<float*>(end);
     s.alf = s.Xf + 3 * npad;
     s.alf_lo = s.alf + npad;
-    s.xi = reinterpret_cast<int*>(s.alf_lo + npad);
-    double* extra = reinterpret_cast<double*>(s.xi + npad);  // 4 npad bytes: 8-byte aligned
+    s.xi = lattice ? reinterpret_cast<int*>(s.alf_lo + npad) : nullptr;
+    double* extra = reinterpret_cast<double*>(reinterpret_cast<int*>(s.alf_lo + npad) + (lattice ? npad : 0));
+    // (4 npad bytes of xi keep 8-byte alignment: npad is a multiple of 8)
     s.pa[0] = s.alpha;
     s.pa[1] = reinterpret_cast<double*>(s.alf);  // alf, alf_lo: 2 npad floats, 8-byte aligned
     s.pa[2] = nprop > 2 ? extra : nullptr;
@@ -114,9 +117,10 @@ __device__ Shared carve(double* sm, int npad, int a_in_smem, double* ws_a, int n
     return s;
 }
 
-__host__ size_t smem_bytes(int npad, int a_in_smem, int nprop = 0) {
-    size_t d = (size_t)7 * npad + 64 + 256 + (a_in_smem ? (size_t)n_tiles(npad / 8) * 64 : (size_t)(npad / 8) * 64);
-    return d * sizeof(double) + (size_t)5 * npad * sizeof(float) + (size_t)npad * sizeof(int) +
+__host__ size_t smem_bytes(int npad, int a_in_smem, int nprop, int stage_panel, bool lattice, bool with_w = false) {
+    size_t d = (size_t)(with_w ? 7 : 6) * npad + 64 + 256 +
+               (a_in_smem ? (size_t)n_tiles(npad / 8) * 64 : (stage_panel ? (size_t)(npad / 8) * 64 : 0));
+    return d * sizeof(double) + (size_t)5 * npad * sizeof(float) + (lattice ? (size_t)npad * sizeof(int) : 0) +
            (size_t)std::max(nprop - 2, 0) * npad * sizeof(double);
 }
 
@@ -560,7 +564,7 @@ __global__ void k_solve(SolveCtx c) {
     __shared__ int s_w;
     const int tid = threadIdx.x, nt = blockDim.x;
     double* ws_a = c.a_in_smem ? nullptr : c.ws_a + (int64_t)blockIdx.x * c.ws_a_stride;
-    Shared s = carve(sm, c.npad, c.a_in_smem, ws_a, c.b.nprop);
+    Shared s = carve(sm, c.npad, c.a_in_smem, ws_a, c.b.nprop, c.stage_panel, c.b.Xi != nullptr, false);
     double* V = c.ws_v ? c.ws_v + (int64_t)blockIdx.x * c.ws_v_stride + tid : nullptr;
     const bool lattice = c.b.Xi != nullptr;
     for (int j = tid; j < 256; j += nt) s.T256[j] = c.P.exp_tab[j];
@@ -632,7 +636,7 @@ __global__ void k_backward(SolveCtx c) {
     __shared__ int s_w;
     const int tid = threadIdx.x, nt = blockDim.x;
     double* ws_a = c.a_in_smem ? nullptr : c.ws_a + (int64_t)blockIdx.x * c.ws_a_stride;
-    Shared s = carve(sm, c.npad, c.a_in_smem, ws_a, 0);
+    Shared s = carve(sm, c.npad, c.a_in_smem, ws_a, 0, c.stage_panel, c.b.Xi != nullptr, true);
     const double l2 = c.P.l2;
     SolveCtx cc = c;
     cc.P.precision = VGP_FP64;
@@ -754,9 +758,10 @@ int solve_launch_static(const SolveBatch& b, const DevParams& P, int* err_dev, i
     c.n_work = (int)b.n_inst;
     c.npad = npad;
     c.a_in_smem = 1;
+    c.stage_panel = 1;
     c.ws_a = nullptr;
     c.ws_a_stride = 0;
-    const size_t shm = smem_bytes(npad, 1);
+    const size_t shm = smem_bytes(npad, 1, 0, 1, b.Xi != nullptr);
     if (cudaFuncSetAttribute(k_solve, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm) != cudaSuccess) return -1;
     int dev = 0, n_sm = 0, per_sm = 0;
     cudaGetDevice(&dev);
@@ -838,8 +843,9 @@ void solve_batch(const SolveBatch& b, const DevParams& P, int* err_dev, cudaStre
             c.n_work = 1;
             c.npad = std::max((N + 7) & ~7, 8);
             c.a_in_smem = c.npad <= 224;
+            c.stage_panel = 1;
             const int threads = c.npad <= 32 ? 64 : c.npad <= 64 ? 128 : c.npad <= 128 ? 256 : 512;
-            const size_t shm = smem_bytes(c.npad, c.a_in_smem, b.nprop);
+            const size_t shm = smem_bytes(c.npad, c.a_in_smem, b.nprop, 1, b.Xi != nullptr);
             cudaFuncSetAttribute(k_solve, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm);
             c.ws_a_stride = c.a_in_smem ? 0 : n_tiles(c.npad / 8) * 64;
             c.ws_a = c.a_in_smem ? nullptr : (double*)ar.get(Arena::kWs0, sizeof(double) * n_tiles(128) * 64, st);
@@ -883,8 +889,9 @@ void solve_batch(const SolveBatch& b, const DevParams& P, int* err_dev, cudaStre
         c.n_work = cnt;
         c.npad = std::max((nmax + 7) & ~7, 8);
         c.a_in_smem = bk.smem_a;
+        c.stage_panel = bk.smem_a ? 1 : cfg->stage_panel;
         if (bw) c.bw = *bw;
-        const size_t shm = smem_bytes(c.npad, c.a_in_smem, bw ? 0 : b.nprop);
+        const size_t shm = smem_bytes(c.npad, c.a_in_smem, bw ? 0 : b.nprop, c.stage_panel, b.Xi != nullptr, bw != nullptr);
         auto kern = bw ? k_backward : k_solve;
         cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm);
         int per_sm = 0;

@@ -410,3 +410,26 @@ def test_raycast_frames_and_fusion(vg, orc, precision):
             # precision those carry ~1e-3 relative error, which moves an average by that fraction
             # of the spread between the fused frames' distances.
             assert np.mean(err <= tol) >= 0.999 and err.max() <= 5 * tol
+
+
+def test_launch_shapes_give_identical_results(vg):
+    """Large neighbourhoods (N up to 1024, A in global memory): every launch shape of the
+    solve, with the panel staged in shared memory or read through L1/L2 with two CTAs per SM,
+    gives bit-identical distances, gradients and variances."""
+    rng = np.random.default_rng(8)
+    u = rng.normal(size=(150000, 3))
+    surf = (1.3 * u / np.linalg.norm(u, axis=1, keepdims=True)).astype(np.float32)
+    q = (surf[rng.integers(0, len(surf), 20000)] * rng.uniform(0.6, 1.4, (20000, 1))).astype(np.float32)
+    m = vg.Map(precision="mixed")
+    m.set_surface(torch.from_numpy(surf).cuda())
+    qt = torch.from_numpy(q).cuda()
+    ref = {k: v.cpu().numpy() for k, v in m.query(qt, grad=True, var=True).items()}
+    assert m.stats()["bucket_count"][4] > 50  # instances with N > 256
+    for threads, per_sm, stage in [((384, 512, 256, 128, 64), (2, 0, 0, 0, 0), 0),
+                                   ((256, 256, 128, 64, 32), (2, 0, 0, 0, 0), 0),
+                                   ((256, 512, 256, 128, 64), (3, 0, 0, 0, 0), 0),
+                                   ((512, 512, 256, 128, 64), (1, 0, 0, 0, 0), 1)]:
+        m.set_launch(threads, per_sm, stage)
+        out = {k: v.cpu().numpy() for k, v in m.query(qt, grad=True, var=True).items()}
+        for k in ("d", "grad", "var", "status"):
+            assert np.array_equal(out[k].view(np.uint8), ref[k].view(np.uint8)), k
