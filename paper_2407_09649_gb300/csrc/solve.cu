@@ -187,6 +187,7 @@ __device__ void chol_solve(const Shared& s, const double* A, int Nt, double* out
 }
 
 // Assemble A, factorise, solve alpha.  Returns false if a pivot was not positive.
+template <bool kProps>
 __device__ bool fit_instance(const SolveCtx& c, const Shared& s, int N, int64_t base) {
     const int tid = threadIdx.x, nt = blockDim.x;
     const int lane = tid & 31, warp = tid >> 5, nwarps = nt >> 5;
@@ -333,7 +334,7 @@ __device__ bool fit_instance(const SolveCtx& c, const Shared& s, int N, int64_t 
         __syncthreads();
     }
     if (s_fail) return false;
-    if (c.b.nprop > 0) {
+    if (kProps) {
         // property weights alpha_c = A^-1 y_c, one right-hand side per channel (Eq. 6)
         for (int ch = 0; ch < c.b.nprop; ++ch) {
             for (int i = tid; i < Np; i += nt) s.z[i] = i < N ? c.b.yprop[(base + i) * c.b.nprop + ch] : 0.0;
@@ -559,6 +560,9 @@ __device__ __forceinline__ void invalid(EvalOut& r, int status) {
     r.v = INFINITY;
 }
 
+// kProps: surface-property mode (Eq. 6), a separate instantiation so that the distance path
+// keeps its register budget
+template <bool kProps>
 __global__ void k_solve(SolveCtx c) {
     extern __shared__ double sm[];
     __shared__ int s_w;
@@ -578,8 +582,8 @@ __global__ void k_solve(SolveCtx c) {
         const int64_t base = c.b.inst_off[I];
         const int N = (int)(c.b.inst_off[I + 1] - base);
         const int64_t q0 = c.b.q_off[I], q1 = c.b.q_off[I + 1];
-        const bool ok = N > 0 && fit_instance(c, s, N, base);
-        if (c.b.nprop > 0) {
+        const bool ok = N > 0 && fit_instance<kProps>(c, s, N, base);
+        if (kProps) {
             // property mode: means and variance (Eq. 6, variance read as for Eq. 2)
             const int np = c.b.nprop;
             for (int64_t p = q0 + tid; p < q1; p += nt) {
@@ -652,7 +656,7 @@ __global__ void k_backward(SolveCtx c) {
         const int N = (int)(c.b.inst_off[I + 1] - base);
         const int Nt = (N + 7) >> 3;
         const int64_t q0 = c.b.q_off[I], q1 = c.b.q_off[I + 1];
-        const bool ok = N > 0 && fit_instance(cc, s, N, base);
+        const bool ok = N > 0 && fit_instance<false>(cc, s, N, base);
         for (int64_t p = q0 + tid; p < q1; p += nt) {
             const int64_t qid = c.b.qidx ? c.b.qidx[p] : p;
             double ob = 0.0, gq[3] = {0.0, 0.0, 0.0};
@@ -762,15 +766,16 @@ int solve_launch_static(const SolveBatch& b, const DevParams& P, int* err_dev, i
     c.ws_a = nullptr;
     c.ws_a_stride = 0;
     const size_t shm = smem_bytes(npad, 1, 0, 1, b.Xi != nullptr);
-    if (cudaFuncSetAttribute(k_solve, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm) != cudaSuccess) return -1;
+    if (cudaFuncSetAttribute(k_solve<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm) != cudaSuccess)
+        return -1;
     int dev = 0, n_sm = 0, per_sm = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_solve, threads, shm);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_solve<false>, threads, shm);
     const int grid = (int)std::min<int64_t>(std::min<int64_t>(b.n_inst, (int64_t)n_sm * std::max(per_sm, 1)), max_grid);
     c.ws_v_stride = (int64_t)npad * threads;
     c.ws_v = ws_v;
-    k_solve<<<grid, threads, shm, st>>>(c);
+    k_solve<false><<<grid, threads, shm, st>>>(c);
     note_launch();
     return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }
@@ -846,12 +851,13 @@ void solve_batch(const SolveBatch& b, const DevParams& P, int* err_dev, cudaStre
             c.stage_panel = 1;
             const int threads = c.npad <= 32 ? 64 : c.npad <= 64 ? 128 : c.npad <= 128 ? 256 : 512;
             const size_t shm = smem_bytes(c.npad, c.a_in_smem, b.nprop, 1, b.Xi != nullptr);
-            cudaFuncSetAttribute(k_solve, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm);
+            auto ks = b.nprop > 0 ? k_solve<true> : k_solve<false>;
+            cudaFuncSetAttribute(ks, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm);
             c.ws_a_stride = c.a_in_smem ? 0 : n_tiles(c.npad / 8) * 64;
             c.ws_a = c.a_in_smem ? nullptr : (double*)ar.get(Arena::kWs0, sizeof(double) * n_tiles(128) * 64, st);
             c.ws_v_stride = (int64_t)c.npad * threads;
             c.ws_v = b.want_var ? (double*)ar.get(Arena::kWs1, sizeof(double) * 1024 * 512, st) : nullptr;
-            k_solve<<<1, threads, shm, st>>>(c);
+            ks<<<1, threads, shm, st>>>(c);
             note_launch();
         }
         if (profile) {
@@ -892,7 +898,7 @@ void solve_batch(const SolveBatch& b, const DevParams& P, int* err_dev, cudaStre
         c.stage_panel = bk.smem_a ? 1 : cfg->stage_panel;
         if (bw) c.bw = *bw;
         const size_t shm = smem_bytes(c.npad, c.a_in_smem, bw ? 0 : b.nprop, c.stage_panel, b.Xi != nullptr, bw != nullptr);
-        auto kern = bw ? k_backward : k_solve;
+        auto kern = bw ? k_backward : (b.nprop > 0 ? k_solve<true> : k_solve<false>);
         cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm);
         int per_sm = 0;
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, bk.threads, shm);
