@@ -319,6 +319,23 @@ def comparisons(S, Q, S_h, args):
         out.setdefault("lgpdf_room", {})[prec] = {"voxels_per_s": nvox / sec, "frames": len(frames),
                                                  "ms_per_frame": 1e3 * sec / len(frames),
                                                  "testing_voxels_per_frame": nvox / len(frames)}
+    # the plain FP64 per-instance form of the L-GPDF (one launch per leaf GP) on two frames
+    mq = Map(precision="fp64", max_pts_leaf=512, launch="per_instance")
+    mq.fuse(mq.build_frame(frames[0]))
+    torch.cuda.synchronize()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    nvox = 0
+    a.record()
+    for fr in frames[1:3]:
+        f = mq.build_frame(fr)
+        nvox += f.n_test
+        mq.fuse(f)
+    b.record()
+    torch.cuda.synchronize()
+    sec = a.elapsed_time(b) / 1e3
+    out["lgpdf_room"]["per_instance_fp64"] = {"voxels_per_s": nvox / sec, "frames": 2,
+                                              "ms_per_frame": 1e3 * sec / 2,
+                                              "speedup_batched_mixed": out["lgpdf_room"]["mixed"]["voxels_per_s"] / (nvox / sec)}
     # L-GPDF with the paper's testing points: ray-cast from the sensor origin, signed distances
     poses = [room.camera_pose(k)[0] for k in range(args.room_frames)]
     mr = Map(precision="mixed", max_pts_leaf=512)
@@ -369,6 +386,23 @@ def comparisons(S, Q, S_h, args):
     torch.cuda.synchronize()
     out["room_mapping_step_rgb"] = {"ms_per_frame": a2.elapsed_time(b2) / len(frames), "frames": len(frames),
                                     "n_props": 3, "precision": "mixed"}
+    # the same mapping step with every GP solve replayed as a CUDA graph (VGP_LAUNCH_GRAPH)
+    mg = Map(precision="mixed", max_pts_leaf=512, launch="graph")
+    mg.fuse(mg.build_frame(frames[0], origin=poses[0]))
+    mg.update_surface()
+    torch.cuda.synchronize()
+    a3, b3 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a3.record()
+    for fr, o in zip(frames, poses):
+        mg.fuse(mg.build_frame(fr, origin=o))
+        mg.update_surface()
+    b3.record()
+    torch.cuda.synchronize()
+    gst = mg.stats()
+    out["room_mapping_step_graph"] = {"ms_per_frame": a3.elapsed_time(b3) / len(frames), "frames": len(frames),
+                                      "graph_replays": int(gst["graph_replays"]),
+                                      "graph_instantiations": int(gst["graph_instantiations"]),
+                                      "precision": "mixed"}
     out["room_mapping_step"] = {"ms_per_frame": 1e3 * sec / len(frames), "frames": len(frames),
                                 "training_points": int(mp.surface_points().shape[0]),
                                 "mesh_ms": a.elapsed_time(b), "mesh_triangles": int(mesh["triangles"][0].shape[0]),
@@ -447,7 +481,7 @@ def main():
     ap.add_argument("--n-sub", type=int, default=1_000_000, help="queries of the precision comparison subset")
     ap.add_argument("--n-per-instance", type=int, default=5_000, help="queries of the per-instance comparison")
     ap.add_argument("--room-frames", type=int, default=10)
-    ap.add_argument("--n-tune", type=int, default=1_000_000, help="queries the autotuner times")
+    ap.add_argument("--n-tune", type=int, default=2_000_000, help="queries the autotuner times")
     ap.add_argument("--sweep-inst", type=int, default=20_000)
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     args = ap.parse_args()

@@ -70,7 +70,7 @@ enum {
 
 enum { VGP_FP64 = 0, VGP_MIXED = 1 };          /* precision */
 enum { VGP_FUSE_INVVAR = 0, VGP_FUSE_TSDF = 1 }; /* fusion rule: Eq. 8 or Eq. 9 */
-enum { VGP_LAUNCH_BATCHED = 0, VGP_LAUNCH_PER_INSTANCE = 1 };
+enum { VGP_LAUNCH_BATCHED = 0, VGP_LAUNCH_PER_INSTANCE = 1, VGP_LAUNCH_GRAPH = 2 };
 enum {
     VGP_ST_OK = 0,
     VGP_ST_NO_SUPPORT = 1,
@@ -113,6 +113,15 @@ enum {
  *                    persistent launches, one per size bucket, largest first.
  *                    VGP_LAUNCH_PER_INSTANCE: one kernel launch per instance, in instance
  *                    order (the plain comparison form; same arithmetic, no batching).
+ *                    VGP_LAUNCH_GRAPH: the batched form with the size histogram, bucket
+ *                    plan and ordering computed on the device, so that the whole solve of a
+ *                    call (eight kernels) is captured as a CUDA graph on a stream the map
+ *                    owns and replayed through a cached executable graph, updated in place
+ *                    from call to call; the launch shapes are sized for the largest
+ *                    instance the call can hold (max_pts_leaf for frames, max_pts_group for
+ *                    queries).  Same arithmetic and results as VGP_LAUNCH_BATCHED; the caller's
+ *                    stream waits on the map's stream through events.  The backward pass and
+ *                    the autotuner always launch directly.
  */
 typedef struct {
     double voxel_size;
@@ -126,7 +135,7 @@ typedef struct {
     int32_t fusion;
     int32_t precision;
     int32_t profile;     /* nonzero: time the solve kernels with CUDA events (vgp_stats) */
-    int32_t launch;      /* VGP_LAUNCH_BATCHED (0) or VGP_LAUNCH_PER_INSTANCE (1) */
+    int32_t launch;      /* VGP_LAUNCH_BATCHED (0), VGP_LAUNCH_PER_INSTANCE (1) or VGP_LAUNCH_GRAPH (2) */
     int32_t normal_steps;/* ray-cast testing points: voxels along each surface normal, each side */
     double sigma_prop;   /* noise std of the surface-property GP (Eq. 6); default 0.1 */
     int32_t n_props;     /* surface-property channels per point, 0..4; default 0 */
@@ -153,6 +162,8 @@ typedef struct {
     int32_t cfg_stage_panel; /* N > 224 bucket: panel column staged in shared memory (1) or read
                                 through L1/L2, leaving room for two CTAs per SM (0) */
     int32_t reserved;
+    int64_t graph_replays;        /* VGP_LAUNCH_GRAPH: executable-graph launches on this map ... */
+    int64_t graph_instantiations; /* ... and graph instantiations (the rest were updates in place) */
 } vgp_stats;
 
 /* Fill *p with the defaults listed above. */
@@ -391,10 +402,10 @@ int vgp_query_smooth(vgp_map* m, const float* q_dev, int64_t n, int32_t n_nodes,
 
 /*
  * Autotuner of the GP solve launch shapes: plans the given queries against the current
- * surface (as vgp_query_distance_gradient does), then solves the batch once with each of four
- * candidate launch shapes (threads per CTA, CTAs per SM) for every size bucket, times each
- * bucket with CUDA events, and keeps the fastest shape per bucket for later calls on this map
- * (L-GPDF frames, queries, batches).  Outputs nothing else; the chosen shapes and bucket
+ * surface (as vgp_query_distance_gradient does), then solves the batch twice with each of
+ * seven candidate launch shapes (threads per CTA, CTAs per SM, panel staging for N > 224),
+ * times each bucket with CUDA events (the faster of the two runs counts), and keeps the
+ * fastest shape per bucket for later calls on this map (L-GPDF frames, queries, batches).  Outputs nothing else; the chosen shapes and bucket
  * times appear in vgp_stats.  VGP_ERR_STATE before vgp_set_surface.  Synchronises the stream.
  */
 int vgp_autotune(vgp_map* m, const float* q_dev, int64_t n, vgp_stream stream);

@@ -15,7 +15,7 @@ ERRORS = {-1: "VGP_ERR_ARG", -2: "VGP_ERR_OOM", -3: "VGP_ERR_CUDA", -4: "VGP_ERR
           -5: "VGP_ERR_TIMEOUT", -6: "VGP_ERR_STATE"}
 VGP_FP64, VGP_MIXED = 0, 1
 VGP_FUSE_INVVAR, VGP_FUSE_TSDF = 0, 1
-VGP_LAUNCH_BATCHED, VGP_LAUNCH_PER_INSTANCE = 0, 1
+VGP_LAUNCH_BATCHED, VGP_LAUNCH_PER_INSTANCE, VGP_LAUNCH_GRAPH = 0, 1, 2
 ST_OK, ST_NO_SUPPORT, ST_CLAMPED, ST_BAD_INPUT, ST_FACTOR_FAIL = 0, 1, 2, 3, 4
 
 
@@ -33,7 +33,8 @@ class VgpStats(C.Structure):
                 ("bucket_count", C.c_int64 * 5), ("sum_n3", C.c_double), ("sum_n2", C.c_double),
                 ("t_solve_ms", C.c_double), ("t_bucket_ms", C.c_double * 5),
                 ("cfg_threads", C.c_int32 * 5), ("cfg_per_sm", C.c_int32 * 5), ("grid_leaves", C.c_int64), ("grid_capacity_leaves", C.c_int64),
-                ("cfg_stage_panel", C.c_int32), ("reserved", C.c_int32)]
+                ("cfg_stage_panel", C.c_int32), ("reserved", C.c_int32),
+                ("graph_replays", C.c_int64), ("graph_instantiations", C.c_int64)]
 
 
 # (name, restype, argtypes)

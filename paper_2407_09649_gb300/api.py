@@ -55,7 +55,8 @@ def make_params(**kw) -> L.VgpParams:
         if k == "precision" and isinstance(v, str):
             v = {"fp64": L.VGP_FP64, "mixed": L.VGP_MIXED}[v]
         if k == "launch" and isinstance(v, str):
-            v = {"batched": L.VGP_LAUNCH_BATCHED, "per_instance": L.VGP_LAUNCH_PER_INSTANCE}[v]
+            v = {"batched": L.VGP_LAUNCH_BATCHED, "per_instance": L.VGP_LAUNCH_PER_INSTANCE,
+                 "graph": L.VGP_LAUNCH_GRAPH}[v]
         if k == "fusion" and isinstance(v, str):
             v = {"invvar": L.VGP_FUSE_INVVAR, "tsdf": L.VGP_FUSE_TSDF}[v]
         if not hasattr(p, k):

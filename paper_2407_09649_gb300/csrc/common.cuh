@@ -20,7 +20,8 @@ enum : int {
     kErrTableFull = 1,
     kErrTimeout = 2,
     kErrCapacity = 4,   // an internal buffer bound was exceeded
-    kErrFactor = 8
+    kErrFactor = 8,
+    kErrLaunch = 16     // a graph capture, instantiation or launch failed
 };
 
 // Run-time parameters, expanded once on the host.

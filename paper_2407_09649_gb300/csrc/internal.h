@@ -53,6 +53,7 @@ struct SolveBatch {
     // surface-property mode (Eq. 6): nprop > 0 replaces the right-hand side 1 by the nprop
     // columns of yprop and writes property means / variances instead of distances
     int nprop = 0;
+    int max_n = 1024;                   // largest N the batch can hold (sizes graph-mode buffers)
     const double* yprop = nullptr;      // [T][nprop]
     double* pc = nullptr;               // [n_queries][nprop] by query id
     double* pw = nullptr;               // [n_queries] by query id
@@ -97,11 +98,22 @@ void fill_u64(uint64_t* p, uint64_t v, int64_t n, cudaStream_t st);
 void fill_i32(int32_t* p, int32_t v, int64_t n, cudaStream_t st);
 void widen_i32(const int32_t* in, int64_t* out, int64_t n, cudaStream_t st);
 
+// CUDA-graph state of a map (launch mode VGP_LAUNCH_GRAPH): a private capture stream, two
+// events joining it to the caller's stream, and one executable graph per solve kind.
+struct GraphCache {
+    cudaStream_t gs = nullptr;
+    cudaEvent_t e0 = nullptr, e1 = nullptr, t0 = nullptr, t1 = nullptr;
+    cudaGraphExec_t exec[2] = {nullptr, nullptr};  // distance, surface property
+    int64_t replays = 0, instantiations = 0;
+};
+void graph_cache_destroy(GraphCache& gc);
+
 // Solve every instance of the batch (factorise, alpha, evaluate its queries).  Returns
-// error bits through *err_dev.  Synchronises once to read the size histogram.
+// error bits through *err_dev.  Synchronises once to read the size histogram (in graph mode
+// the histogram is planned on the device and read once at the end, for the statistics).
 void solve_batch(const SolveBatch& b, const DevParams& P, int* err_dev, cudaStream_t st,
                  Arena& ar, SolveStats* stats, const BackwardBatch* bw = nullptr, bool profile = false,
-                 int launch = 0, const SolveConfig* cfg = nullptr);
+                 int launch = 0, const SolveConfig* cfg = nullptr, GraphCache* gc = nullptr);
 
 // Set the thread-local message returned by vgp_last_error().
 void set_last_error(const char* msg);

@@ -56,6 +56,8 @@ struct SolveCtx {
     const int32_t* order;  // instance ids, decreasing N (null: inst_base + work index)
     int inst_base;
     int n_work;
+    const int* plan;       // device bucket plan (graph mode): counts [5], then offsets [5]
+    int bucket;
     int npad;              // largest N in this launch, rounded up to 8
     int a_in_smem;
     int stage_panel;       // A global: current panel column staged in shared memory
@@ -572,13 +574,19 @@ __global__ void k_solve(SolveCtx c) {
     double* V = c.ws_v ? c.ws_v + (int64_t)blockIdx.x * c.ws_v_stride + tid : nullptr;
     const bool lattice = c.b.Xi != nullptr;
     for (int j = tid; j < 256; j += nt) s.T256[j] = c.P.exp_tab[j];
+    int n_work = c.n_work;
+    const int32_t* order = c.order;
+    if (c.plan) {  // graph mode: this bucket's share of the order, planned on the device
+        n_work = c.plan[c.bucket];
+        order = c.order + c.plan[5 + c.bucket];
+    }
     for (;;) {
         if (tid == 0) s_w = atomicAdd(c.counter, 1);
         __syncthreads();
         const int w = s_w;
         __syncthreads();
-        if (w >= c.n_work) break;
-        const int I = c.order ? c.order[w] : c.inst_base + w;
+        if (w >= n_work) break;
+        const int I = order ? order[w] : c.inst_base + w;
         const int64_t base = c.b.inst_off[I];
         const int N = (int)(c.b.inst_off[I + 1] - base);
         const int64_t q0 = c.b.q_off[I], q1 = c.b.q_off[I + 1];
@@ -740,6 +748,28 @@ __global__ void k_order_n(const int64_t* inst_off, int64_t n, int* cursor, int32
     order[pos] = (int32_t)i;
 }
 
+__global__ void k_or_err(int* err, int bits) { atomicOr(err, bits); }
+
+// Device bucket plan (graph mode): cursor[N] = first position of size N in decreasing-N
+// order; plan[b] = instances of bucket b, plan[5 + b] = its first position.
+__global__ void k_plan_buckets(const int* hist, int* cursor, int* plan) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    int run = 0;
+    for (int N = 1024; N >= 0; --N) {
+        cursor[N] = run;
+        run += hist[N];
+    }
+    const int lo[5] = {225, 129, 65, 33, 0}, hi[5] = {1024, 224, 128, 64, 32};
+    int off = 0;
+    for (int b = 0; b < 5; ++b) {
+        int cnt = 0;
+        for (int N = lo[b]; N <= hi[b]; ++N) cnt += hist[N];
+        plan[b] = cnt;
+        plan[5 + b] = off;
+        off += cnt;
+    }
+}
+
 __global__ void k_reverse_i32(const int32_t* in, int32_t* out, int n) {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i < n) out[i] = in[n - 1 - i];
@@ -753,6 +783,8 @@ __global__ void k_reverse_i32(const int32_t* in, int32_t* out, int n) {
 int solve_launch_static(const SolveBatch& b, const DevParams& P, int* err_dev, int npad, int threads, int max_grid,
                         int* counter, const int32_t* order, double* ws_v, cudaStream_t st) {
     SolveCtx c;
+    c.plan = nullptr;
+    c.bucket = 0;
     c.b = b;
     c.P = P;
     c.err = err_dev;
@@ -780,12 +812,186 @@ int solve_launch_static(const SolveBatch& b, const DevParams& P, int* err_dev, i
     return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }
 
+void graph_cache_destroy(GraphCache& gc) {
+    for (auto& e : gc.exec)
+        if (e) cudaGraphExecDestroy(e);
+    if (gc.e0) cudaEventDestroy(gc.e0);
+    if (gc.e1) cudaEventDestroy(gc.e1);
+    if (gc.t0) cudaEventDestroy(gc.t0);
+    if (gc.t1) cudaEventDestroy(gc.t1);
+    if (gc.gs) cudaStreamDestroy(gc.gs);
+    gc = GraphCache{};
+}
+
+namespace {
+
+void add_stats(SolveStats* stats, const std::vector<int>& h) {
+    if (!stats) return;
+    for (int N = 0; N <= 1024; ++N) {
+        int bk = N <= 32 ? 0 : N <= 64 ? 1 : N <= 128 ? 2 : N <= 256 ? 3 : 4;
+        stats->bucket_count[bk] += h[N];
+        stats->sum_n3 += (double)h[N] * N * N * N;
+        stats->sum_n2 += (double)h[N] * N * N;
+    }
+}
+
+// Graph mode: the whole solve -- size histogram, bucket plan, decreasing-size order and one
+// persistent launch per size bucket -- is planned on the device, captured as a CUDA graph on
+// the map's private stream and replayed through a cached executable graph (updated in place
+// when only the arguments changed).  Launch shapes come from the map's configuration, sized
+// for the largest N the batch can hold; CTAs of a bucket with no work exit at once.  Returns
+// false when a CUDA call failed (the caller reports it through cudaGetLastError).
+bool solve_batch_graph(const SolveBatch& b, const DevParams& P, int* err_dev, cudaStream_t st, Arena& ar,
+                       SolveStats* stats, bool profile, const SolveConfig* cfg, GraphCache* gc) {
+    const int64_t n = b.n_inst;
+    if (!gc->gs) {
+        if (cudaStreamCreateWithFlags(&gc->gs, cudaStreamNonBlocking) != cudaSuccess ||
+            cudaEventCreateWithFlags(&gc->e0, cudaEventDisableTiming) != cudaSuccess ||
+            cudaEventCreateWithFlags(&gc->e1, cudaEventDisableTiming) != cudaSuccess ||
+            cudaEventCreate(&gc->t0) != cudaSuccess || cudaEventCreate(&gc->t1) != cudaSuccess)
+            return false;
+    }
+    const bool props = b.nprop > 0;
+    auto kern = props ? k_solve<true> : k_solve<false>;
+    const int T = 256;
+    int dev = 0, n_sm = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev);
+    const int maxn = std::min(std::max(b.max_n, 1), 1024);
+    const int lo[5] = {225, 129, 65, 33, 0}, hi[5] = {1024, 224, 128, 64, 32};
+    struct Shape {
+        int npad, smem_a, stage, threads, grid;
+        size_t shm;
+        bool live;
+    } sh[5];
+    size_t shm_max = 0;
+    for (int i = 0; i < 5; ++i) {
+        Shape& s = sh[i];
+        s.live = maxn >= lo[i];
+        s.npad = std::max((std::min(hi[i], maxn) + 7) & ~7, 8);
+        s.smem_a = i > 0;
+        s.stage = s.smem_a ? 1 : cfg->stage_panel;
+        s.threads = cfg->threads[i];
+        s.shm = smem_bytes(s.npad, s.smem_a, b.nprop, s.stage, b.Xi != nullptr, false);
+        if (s.live) shm_max = std::max(shm_max, s.shm);
+    }
+    if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm_max) != cudaSuccess)
+        return false;
+    int64_t ws_a_need = 0, ws_v_need = 0;
+    for (int i = 0; i < 5; ++i) {
+        Shape& s = sh[i];
+        if (!s.live) continue;
+        int per_sm = 0;
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, s.threads, s.shm);
+        per_sm = std::max(per_sm, 1);
+        if (cfg->per_sm[i] > 0) per_sm = std::min(per_sm, cfg->per_sm[i]);
+        s.grid = (int)std::min<int64_t>(n, (int64_t)n_sm * per_sm);
+        if (!s.smem_a) ws_a_need = std::max<int64_t>(ws_a_need, n_tiles(s.npad / 8) * 64 * s.grid);
+        if (b.want_var) ws_v_need = std::max<int64_t>(ws_v_need, (int64_t)s.npad * s.threads * s.grid);
+    }
+    // every buffer exists before the capture starts (allocation is not captured)
+    int* hist = (int*)ar.get(Arena::kHist, sizeof(int) * 2 * 1025, st);
+    int32_t* order = (int32_t*)ar.get(Arena::kOrder, sizeof(int32_t) * n, st);
+    int* counters = (int*)ar.get(Arena::kCounters, sizeof(int) * 16, st);
+    double* ws_a = ws_a_need ? (double*)ar.get(Arena::kWs0, sizeof(double) * ws_a_need, st) : nullptr;
+    double* ws_v = ws_v_need ? (double*)ar.get(Arena::kWs1, sizeof(double) * ws_v_need, st) : nullptr;
+    if (!hist || !order || !counters || (ws_a_need && !ws_a) || (ws_v_need && !ws_v)) return false;
+    int* cursor = hist + 1025;
+    int* plan = counters + 5;
+    cudaStream_t gs = gc->gs;
+    if (cudaEventRecord(gc->e0, st) != cudaSuccess || cudaStreamWaitEvent(gs, gc->e0, 0) != cudaSuccess) return false;
+    if (cudaStreamBeginCapture(gs, cudaStreamCaptureModeThreadLocal) != cudaSuccess) return false;
+    fill_i32(hist, 0, 1025, gs);
+    fill_i32(counters, 0, 5, gs);
+    k_hist_n<<<(unsigned)((n + T - 1) / T), T, 0, gs>>>(b.inst_off, n, hist);
+    note_launch();
+    k_plan_buckets<<<1, 32, 0, gs>>>(hist, cursor, plan);
+    note_launch();
+    k_order_n<<<(unsigned)((n + T - 1) / T), T, 0, gs>>>(b.inst_off, n, cursor, order);
+    note_launch();
+    for (int i = 0; i < 5; ++i) {
+        const Shape& s = sh[i];
+        if (!s.live) continue;
+        SolveCtx c;
+        c.b = b;
+        c.P = P;
+        c.err = err_dev;
+        c.counter = counters + i;
+        c.order = order;
+        c.inst_base = 0;
+        c.n_work = 0;
+        c.plan = plan;
+        c.bucket = i;
+        c.npad = s.npad;
+        c.a_in_smem = s.smem_a;
+        c.stage_panel = s.stage;
+        c.ws_a_stride = s.smem_a ? 0 : n_tiles(s.npad / 8) * 64;
+        c.ws_a = s.smem_a ? nullptr : ws_a;
+        c.ws_v_stride = (int64_t)s.npad * s.threads;
+        c.ws_v = ws_v;
+        kern<<<s.grid, s.threads, s.shm, gs>>>(c);
+        note_launch();
+    }
+    cudaGraph_t graph = nullptr;
+    if (cudaStreamEndCapture(gs, &graph) != cudaSuccess || !graph) return false;
+    cudaGraphExec_t& ex = gc->exec[props ? 1 : 0];
+    if (ex) {
+        cudaGraphExecUpdateResultInfo info;
+        if (cudaGraphExecUpdate(ex, graph, &info) != cudaSuccess) {
+            cudaGetLastError();
+            cudaGraphExecDestroy(ex);
+            ex = nullptr;
+        }
+    }
+    if (!ex) {
+        if (cudaGraphInstantiate(&ex, graph, 0) != cudaSuccess) {
+            ex = nullptr;
+            cudaGraphDestroy(graph);
+            return false;
+        }
+        ++gc->instantiations;
+    }
+    cudaGraphDestroy(graph);
+    if (profile) cudaEventRecord(gc->t0, gs);
+    if (cudaGraphLaunch(ex, gs) != cudaSuccess) return false;
+    ++gc->replays;
+    if (profile) cudaEventRecord(gc->t1, gs);
+    if (cudaEventRecord(gc->e1, gs) != cudaSuccess || cudaStreamWaitEvent(st, gc->e1, 0) != cudaSuccess) return false;
+    // statistics: the size histogram, read once after the solve
+    std::vector<int> h(1025);
+    cudaMemcpyAsync(h.data(), hist, sizeof(int) * 1025, cudaMemcpyDeviceToHost, st);
+    if (cudaStreamSynchronize(st) != cudaSuccess) return false;
+    add_stats(stats, h);
+    if (profile && stats) {
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, gc->t0, gc->t1);
+        stats->t_solve_ms += ms;
+    }
+    return true;
+}
+
+}  // namespace
+
 void solve_batch(const SolveBatch& b, const DevParams& P, int* err_dev, cudaStream_t st, Arena& ar, SolveStats* stats,
-                 const BackwardBatch* bw, bool profile, int launch, const SolveConfig* cfg) {
+                 const BackwardBatch* bw, bool profile, int launch, const SolveConfig* cfg, GraphCache* gc) {
     const SolveConfig dflt;
     if (!cfg) cfg = &dflt;
     const int64_t n = b.n_inst;
     if (n <= 0) return;
+    if (launch == VGP_LAUNCH_GRAPH && !bw && gc) {
+        if (!solve_batch_graph(b, P, err_dev, st, ar, stats, profile, cfg, gc)) {
+            // leave the capture stream usable and the error visible to the caller
+            cudaGraph_t g = nullptr;
+            cudaStreamCaptureStatus cs;
+            if (gc->gs && cudaStreamIsCapturing(gc->gs, &cs) == cudaSuccess && cs != cudaStreamCaptureStatusNone)
+                cudaStreamEndCapture(gc->gs, &g);
+            if (g) cudaGraphDestroy(g);
+            cudaGetLastError();
+            k_or_err<<<1, 1, 0, st>>>(err_dev, kErrLaunch);
+            note_launch();
+        }
+        return;
+    }
     // size histogram and decreasing-size order
     int* hist = (int*)ar.get(Arena::kHist, sizeof(int) * 2 * 1025, st);
     int* cursor = hist + 1025;
@@ -805,14 +1011,7 @@ void solve_batch(const SolveBatch& b, const DevParams& P, int* err_dev, cudaStre
     note_launch();
     k_reverse_i32<<<(unsigned)((n + T - 1) / T), T, 0, st>>>(order_inc, order, (int)n);
     note_launch();
-    if (stats) {
-        for (int N = 0; N <= 1024; ++N) {
-            int bk = N <= 32 ? 0 : N <= 64 ? 1 : N <= 128 ? 2 : N <= 256 ? 3 : 4;
-            stats->bucket_count[bk] += h[N];
-            stats->sum_n3 += (double)h[N] * N * N * N;
-            stats->sum_n2 += (double)h[N] * N * N;
-        }
-    }
+    add_stats(stats, h);
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
     if (profile) {
         cudaEventCreate(&ev0);
@@ -839,6 +1038,8 @@ void solve_batch(const SolveBatch& b, const DevParams& P, int* err_dev, cudaStre
         for (int64_t I = 0; I < n; ++I) {
             const int N = (int)(off[I + 1] - off[I]);
             SolveCtx c;
+            c.plan = nullptr;
+            c.bucket = 0;
             c.b = b;
             c.P = P;
             c.err = err_dev;
@@ -886,6 +1087,8 @@ void solve_batch(const SolveBatch& b, const DevParams& P, int* err_dev, cudaStre
             continue;
         }
         SolveCtx c;
+        c.plan = nullptr;
+        c.bucket = 0;
         c.b = b;
         c.P = P;
         c.err = err_dev;

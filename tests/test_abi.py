@@ -61,6 +61,10 @@ def test_create_rejects_bad_params_without_touching_the_gpu(lib):
     h = C.c_void_p()
     assert lib.vgp_create(C.byref(p), C.byref(h)) == -1
     assert b"max_pts_group" in lib.vgp_last_error()
+    lib.vgp_default_params(C.byref(p))
+    p.launch = 3
+    assert lib.vgp_create(C.byref(p), C.byref(h)) == -1
+    assert b"launch" in lib.vgp_last_error()
     assert lib.vgp_destroy(None) == 0
 
 

@@ -433,3 +433,48 @@ def test_launch_shapes_give_identical_results(vg):
         out = {k: v.cpu().numpy() for k, v in m.query(qt, grad=True, var=True).items()}
         for k in ("d", "grad", "var", "status"):
             assert np.array_equal(out[k].view(np.uint8), ref[k].view(np.uint8)), k
+
+
+def test_graph_launch_mode_matches_direct(vg):
+    """VGP_LAUNCH_GRAPH (device-planned buckets, the solve replayed as a CUDA graph) gives
+    bit-identical frames (with surface properties), fused grids and G-GPDF queries to the
+    direct batched launches, and updates its executable graph in place between calls."""
+    from paper_2407_09649_gb300 import scenes
+    room = scenes.Room(0)
+    frames = [torch.from_numpy(room.frame(k, seed=0)[::2]).cuda() for k in range(4)]
+    props = [torch.rand((f.shape[0], 2), device="cuda", generator=torch.Generator("cuda").manual_seed(k))
+             for k, f in enumerate(frames)]
+    for precision in ("mixed", "fp64"):
+        maps = {mode: vg.Map(precision=precision, max_pts_leaf=256, n_props=2, launch=mode)
+                for mode in ("batched", "graph")}
+        res = {}
+        for mode, m in maps.items():
+            out = []
+            for k, (f, p) in enumerate(zip(frames, props)):
+                fr = m.build_frame(f, origin=room.camera_pose(k)[0], props=p)
+                r = {kk: v.cpu().numpy() for kk, v in fr.results().items()}
+                c, w = (t.cpu().numpy() for t in fr.props())
+                o = np.argsort(r["keys"])  # result order is unspecified; keys are unique
+                out.append(({kk: v[o] for kk, v in r.items()}, c[o], w[o]))
+                m.fuse(fr)
+            m.update_surface()
+            ss = room.surface_samples(seed=3)
+            rng = np.random.default_rng(3)
+            q = torch.from_numpy((ss[rng.integers(0, len(ss), 20000)]
+                                  + rng.normal(0, 0.2, (20000, 3))).astype(np.float32)).cuda()
+            qo = {kk: v.cpu().numpy() for kk, v in m.query(q, grad=True, var=True).items()}
+            so = {kk: v.cpu().numpy() for kk, v in m.query_smooth(q, n_nodes=8, var=True).items()}
+            res[mode] = (out, m.export_grid(), qo, so, m.stats())
+        a, b = res["batched"], res["graph"]
+        for (ra, ca, wa), (rb, cb, wb) in zip(a[0], b[0]):
+            for k in ("keys", "d", "v", "grad", "status"):
+                assert np.array_equal(ra[k].view(np.uint8), rb[k].view(np.uint8)), k
+            assert np.array_equal(ca.view(np.uint8), cb.view(np.uint8))
+            assert np.array_equal(wa.view(np.uint8), wb.view(np.uint8))
+        for x, y in zip(a[1], b[1]):
+            assert np.array_equal(np.asarray(x).view(np.uint8), np.asarray(y).view(np.uint8))
+        for k in ("d", "grad", "var", "status"):
+            assert np.array_equal(a[2][k].view(np.uint8), b[2][k].view(np.uint8)), k
+            assert np.array_equal(a[3][k].view(np.uint8), b[3][k].view(np.uint8)), k
+        st = b[4]
+        assert st["graph_replays"] >= 10 and st["graph_instantiations"] <= 4
