@@ -39,6 +39,14 @@ def _dist_env():
     return replicas.rank_env()
 
 
+# DRAM bytes (read + write) of the N > 224 k_solve launch of one full 10M-query step, from one
+# ncu capture of the current kernel (profiles/k_solve_city_10m_traffic.md); the four smaller
+# launches (4 % of the solve time) are not included.  Set to None when the kernel changes.
+K_SOLVE_TRAFFIC = 2.75e12
+K_SOLVE_TRAFFIC_SOURCE = ("ncu dram__bytes_read.sum + dram__bytes_write.sum, N > 224 launch of the full step "
+                          "(1 pass); smaller buckets not included")
+
+
 def _scene(rank: int, n_surface: int, n_query: int):
     from paper_2407_09649_gb300 import scenes
     city = scenes.City(0)
@@ -236,7 +244,8 @@ def run_ours(args):
             "gpu_launches": launches,
             "roofline": {"kernel": "k_solve (FP64 tile Cholesky on mma.sync f64, alpha, fused eval)",
                          "bound": "tensor", "dtype": "fp64", "achieved": achieved, "peak": peak,
-                         "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
+                         "unit": "TFLOP/s", "frac": achieved / peak, "traffic": K_SOLVE_TRAFFIC,
+                         "traffic_source": K_SOLVE_TRAFFIC_SOURCE,
                          "peak_source": "of measured: MEASURED_PEAKS bf16_tflops x nominal FP64/bf16 (1.25/2250)",
                          "solve_ms": solve_ms, "algorithmic_fp64_flop": fp64_flops,
                          "algorithmic_flop_def": "sum over instances of N^3/3 + 2 N^2"},
