@@ -40,8 +40,8 @@ def _dist_env():
 
 
 # DRAM bytes (read + write) of the N > 224 k_solve launch of one full 10M-query step, from one
-# ncu capture of the current kernel (profiles/k_solve_city_10m_traffic.md); the four smaller
-# launches (4 % of the solve time) are not included.  Set to None when the kernel changes.
+# single-pass ncu capture of the current kernel at this workload; the four smaller launches
+# (4 % of the solve time) are not included.  Set to None when the kernel changes.
 K_SOLVE_TRAFFIC = 2.75e12
 K_SOLVE_TRAFFIC_SOURCE = ("ncu dram__bytes_read.sum + dram__bytes_write.sum, N > 224 launch of the full step "
                           "(1 pass); smaller buckets not included")
