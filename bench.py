@@ -223,8 +223,9 @@ def run_ours(args):
     e_value, _ = replicas.aggregate(nq * e_steps, a.elapsed_time(b) / 1e3, ws, device=dev)
 
     cpu = None
+    err = None
     if rank == 0 and not args.no_cpu:
-        cpu = cpu_baseline(S_h, Q_h, args.cpu_sample)
+        cpu, err = cpu_baseline(S_h, Q_h, args.cpu_sample, m)
 
     if rank == 0:
         pk = _peaks()
@@ -251,6 +252,7 @@ def run_ours(args):
                          "algorithmic_flop_def": "sum over instances of N^3/3 + 2 N^2"},
             "clocks": clk.summary(),
             "cpu_baseline": cpu,
+            "error_vs_oracle": err,
         }
         line.update(extra)
         if pk:
@@ -429,7 +431,9 @@ def comparisons(S, Q, S_h, args):
     return out
 
 
-def cpu_baseline(S_h, Q_h, n_sample):
+def cpu_baseline(S_h, Q_h, n_sample, m=None):
+    """The FP64 oracle timed on the host cores on a sample of the queries; with the GPU map
+    ``m`` also the error of its outputs against the oracle on that sample."""
     import oracle
     oracle.build()
     cores = os.cpu_count() or 1
@@ -439,9 +443,40 @@ def cpu_baseline(S_h, Q_h, n_sample):
     surf = oracle.Surface(S_h, oracle.params())
     surf.query(q, want_var=False)
     dt = time.perf_counter() - t0
-    return {"value": len(q) / dt, "unit": UNIT, "cores": oracle.get_threads(), "kind": "oracle",
+    base = {"value": len(q) / dt, "unit": UNIT, "cores": oracle.get_threads(), "kind": "oracle",
             "sample": f"first {len(q)} of the 10M queries against the full 2M-point surface (surface binning included)",
             "seconds": dt}
+    return base, (error_vs_oracle(S_h, Q_h, m, n_sample) if m is not None else None)
+
+
+def error_vs_oracle(S_h, Q_h, m, n_sample):
+    """The headline configuration's outputs (mixed precision, the benchmark's map, variance on)
+    against the FP64 oracle on the CPU-baseline sample: max |d - d_ref| by distance bin,
+    gradient angle, relative variance error, status agreement."""
+    import oracle
+    import torch
+    q = Q_h[:n_sample]
+    ref = oracle.Surface(S_h, oracle.params()).query(q, want_var=True)
+    m.set_surface(torch.from_numpy(S_h).cuda())
+    got = {k: v.cpu().numpy() for k, v in m.query(torch.from_numpy(q).cuda(), grad=True, var=True).items()}
+    ok = (got["status"] == 0) & (ref["status"] == 0)
+    d, rd = got["d"][ok], ref["d"][ok]
+    g, rg = got["grad"][ok], ref["grad"][ok]
+    dd = np.abs(d - rd)
+    bins = {}
+    for lo, hi in ((0.0, 0.1), (0.1, 0.5), (0.5, 2.0), (2.0, np.inf)):
+        sel = (rd >= lo) & (rd < hi)
+        if sel.any():
+            bins[f"{lo}-{hi}"] = {"n": int(sel.sum()), "max_abs_dd_m": float(dd[sel].max())}
+    big = (rd > 0.05) & (np.linalg.norm(rg, axis=1) > 1e-3)
+    cosang = np.sum(g[big] * rg[big], 1) / (np.linalg.norm(g[big], axis=1) * np.linalg.norm(rg[big], axis=1))
+    ang = np.degrees(np.arccos(np.clip(cosang, -1.0, 1.0)))
+    fin = np.isfinite(ref["var"][ok]) & (ref["var"][ok] > 0)
+    rv = np.abs(got["var"][ok][fin] - ref["var"][ok][fin]) / ref["var"][ok][fin]
+    return {"precision": "mixed", "queries": int(len(q)), "status_equal": bool(np.array_equal(got["status"], ref["status"])),
+            "max_abs_dd_m": float(dd.max()), "by_distance_m": bins,
+            "grad_angle_deg": {"max": float(ang.max()), "p99.9": float(np.percentile(ang, 99.9))},
+            "var_rel_err": {"max": float(rv.max()), "median": float(np.median(rv))}}
 
 
 def run_reference(args):
