@@ -574,19 +574,15 @@ __global__ void k_solve(SolveCtx c) {
     double* V = c.ws_v ? c.ws_v + (int64_t)blockIdx.x * c.ws_v_stride + tid : nullptr;
     const bool lattice = c.b.Xi != nullptr;
     for (int j = tid; j < 256; j += nt) s.T256[j] = c.P.exp_tab[j];
-    int n_work = c.n_work;
-    const int32_t* order = c.order;
-    if (c.plan) {  // graph mode: this bucket's share of the order, planned on the device
-        n_work = c.plan[c.bucket];
-        order = c.order + c.plan[5 + c.bucket];
-    }
     for (;;) {
         if (tid == 0) s_w = atomicAdd(c.counter, 1);
         __syncthreads();
         const int w = s_w;
         __syncthreads();
-        if (w >= n_work) break;
-        const int I = order ? order[w] : c.inst_base + w;
+        // graph mode: this bucket's count and share of the order, planned on the device (read
+        // per work item rather than held in registers across the loop)
+        if (w >= (c.plan ? c.plan[c.bucket] : c.n_work)) break;
+        const int I = c.order ? c.order[(c.plan ? c.plan[5 + c.bucket] : 0) + w] : c.inst_base + w;
         const int64_t base = c.b.inst_off[I];
         const int N = (int)(c.b.inst_off[I + 1] - base);
         const int64_t q0 = c.b.q_off[I], q1 = c.b.q_off[I + 1];
