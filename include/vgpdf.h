@@ -109,6 +109,13 @@ enum {
  *                    report their time in vgp_stats.t_solve_ms (adds one stream sync per call).
  *   normal_steps     K in [0, 16] (default 3): with a sensor origin, vgp_build_frame also tests
  *                    the voxels round(s + k n), k = +-1..+-K, along each surface voxel's normal.
+ *   emulate_fp64     1: instances with N > 224 (A in global memory) are factorised in blocks of
+ *                    64 columns whose trailing updates run on the bf16 tensor cores to FP64
+ *                    accuracy: each row of the block is split exactly into eight 7-bit integer
+ *                    slices under a power-of-two row scale, the slice products accumulate
+ *                    exactly in FP32 and are recombined in FP64 (error below the FP64 rounding of
+ *                    the update).  Same results up to rounding; 0 keeps every update on the
+ *                    FP64 tensor path.
  *   launch           VGP_LAUNCH_BATCHED (default): all GP instances of a call run in a few
  *                    persistent launches, one per size bucket, largest first.
  *                    VGP_LAUNCH_PER_INSTANCE: one kernel launch per instance, in instance
@@ -139,7 +146,7 @@ typedef struct {
     int32_t normal_steps;/* ray-cast testing points: voxels along each surface normal, each side */
     double sigma_prop;   /* noise std of the surface-property GP (Eq. 6); default 0.1 */
     int32_t n_props;     /* surface-property channels per point, 0..4; default 0 */
-    int32_t reserved;    /* must be 0 */
+    int32_t emulate_fp64;/* 0 (default) or 1: see below */
 } vgp_params;
 
 /* Counters of the most recent call on a map (host copy; informational). */

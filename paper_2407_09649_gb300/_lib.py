@@ -24,7 +24,7 @@ class VgpParams(C.Structure):
                 ("d_max", C.c_double), ("d_var_floor", C.c_double), ("max_pts_leaf", C.c_int32),
                 ("max_pts_group", C.c_int32), ("max_leaf_search", C.c_int32), ("fusion", C.c_int32),
                 ("precision", C.c_int32), ("profile", C.c_int32), ("launch", C.c_int32), ("normal_steps", C.c_int32),
-                ("sigma_prop", C.c_double), ("n_props", C.c_int32), ("reserved", C.c_int32)]
+                ("sigma_prop", C.c_double), ("n_props", C.c_int32), ("emulate_fp64", C.c_int32)]
 
 
 class VgpStats(C.Structure):

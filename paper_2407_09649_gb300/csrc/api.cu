@@ -173,6 +173,7 @@ static DevParams expand(const vgp_params& p) {
     P.cap_leaf = p.max_pts_leaf;
     P.cap_group = p.max_pts_group;
     P.n_props = p.n_props;
+    P.emulate = p.emulate_fp64;
     P.s2p = p.sigma_prop * p.sigma_prop;
     P.search_r = p.max_leaf_search;
     P.fusion = p.fusion;
@@ -246,6 +247,7 @@ int vgp_create(const vgp_params* p, vgp_map** out) {
     if (p->precision != VGP_FP64 && p->precision != VGP_MIXED) return fail(VGP_ERR_ARG, "unknown precision");
     if (p->normal_steps < 0 || p->normal_steps > 16) return fail(VGP_ERR_ARG, "normal_steps must be in [0, 16]");
     if (p->n_props < 0 || p->n_props > 4) return fail(VGP_ERR_ARG, "n_props must be in [0, 4]");
+    if (p->emulate_fp64 != 0 && p->emulate_fp64 != 1) return fail(VGP_ERR_ARG, "emulate_fp64 must be 0 or 1");
     if (!(p->sigma_prop > 0) || !std::isfinite(p->sigma_prop)) return fail(VGP_ERR_ARG, "sigma_prop must be > 0");
     if (p->launch != VGP_LAUNCH_BATCHED && p->launch != VGP_LAUNCH_PER_INSTANCE && p->launch != VGP_LAUNCH_GRAPH)
         return fail(VGP_ERR_ARG, "unknown launch mode");

@@ -18,7 +18,7 @@ public:
     enum Slot {
         kScan0, kScan1, kScan2, kHist, kOrder, kTmp0, kTmp1, kTmp2, kTmp3, kTmp4, kTmp5, kTmp6,
         kTmp7, kTmp8, kTmp9, kTmp10, kTmp11, kTmp12, kTmp13, kTmp14, kTmp15, kTmp16, kTmp17,
-        kWs0, kWs1, kWs2, kBw0, kBw1, kPair0, kPair1, kPair2, kPair3, kPair4, kPair5, kPair6, kPair7,
+        kWs0, kWs1, kWs2, kWs3, kBw0, kBw1, kPair0, kPair1, kPair2, kPair3, kPair4, kPair5, kPair6, kPair7,
         kCounters, kNumSlots
     };
     void* get(Slot s, size_t bytes, cudaStream_t st);

@@ -48,6 +48,8 @@ __device__ __forceinline__ void dmma(double& c0, double& c1, double a, double b)
                  : "d"(a), "d"(b));
 }
 
+constexpr int kEmuThreads = 256;  // CTA size of the emulated-update kernels (two CTAs per SM)
+
 struct SolveCtx {
     SolveBatch b;
     DevParams P;
@@ -65,6 +67,8 @@ struct SolveCtx {
     int64_t ws_a_stride;
     double* ws_v;          // per-CTA variance columns [npad][blockDim]
     int64_t ws_v_stride;
+    uint8_t* ws_e;         // per-CTA bf16 slices and row scales (emulated trailing updates)
+    int64_t ws_e_stride;
     BackwardBatch bw;
 };
 
@@ -188,8 +192,218 @@ __device__ void chol_solve(const Shared& s, const double* A, int Nt, double* out
     }
 }
 
+// One thread: 8x8 Cholesky of diagonal tile kt in place, 1 / L_jj into invd and the inverse
+// of the tile's factor into Tinv (FP64 pipe).  False on a non-positive pivot.  (The plain
+// factorisation loop keeps the same steps inline, which the compiler fits in fewer registers.)
+__device__ bool diag_tile(double* A, int kt, const Shared& s) {
+    double* D = A + tix(kt, kt);
+    double* W = s.Tinv;
+    for (int j = 0; j < 8; ++j) {
+        double v = D[te(j, j)];
+        for (int k = 0; k < j; ++k) v -= D[te(j, k)] * D[te(j, k)];
+        if (!(v > 0.0)) return false;
+        const double d = sqrt(v), inv = 1.0 / d;
+        D[te(j, j)] = d;
+        s.invd[8 * kt + j] = inv;
+        for (int i = j + 1; i < 8; ++i) {
+            double u = D[te(i, j)];
+            for (int k = 0; k < j; ++k) u -= D[te(i, k)] * D[te(j, k)];
+            D[te(i, j)] = u * inv;
+        }
+    }
+    for (int j = 0; j < 8; ++j) {
+        for (int i = 0; i < j; ++i) W[te(i, j)] = 0.0;
+        W[te(j, j)] = s.invd[8 * kt + j];
+        for (int i = j + 1; i < 8; ++i) {
+            double u = 0.0;
+            for (int k = j; k < i; ++k) u += D[te(i, k)] * W[te(k, j)];
+            W[te(i, j)] = -u * s.invd[8 * kt + i];
+        }
+    }
+    return true;
+}
+
+// Panel column kt: L_it,kt = A_it,kt Tinv^T for it > kt, one tile per warp.
+__device__ void panel_column(double* A, int kt, int Nt, const Shared& s) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+    const int g = lane >> 2, t = lane & 3;
+    for (int it = kt + 1 + warp; it < Nt; it += nwarps) {
+        double* T = A + tix(it, kt);
+        const double a0 = T[te(g, t)], a1 = T[te(g, 4 + t)];
+        const double b0 = s.Tinv[te(g, t)], b1 = s.Tinv[te(g, 4 + t)];
+        double c0 = 0.0, c1 = 0.0;
+        dmma(c0, c1, a0, b0);
+        dmma(c0, c1, a1, b1);
+        __syncwarp();
+        T[te(g, 2 * t)] = c0;
+        T[te(g, 2 * t + 1)] = c1;
+    }
+}
+
+// D += A B on the bf16 tensor path (m16n8k16, FP32 accumulation)
+__device__ __forceinline__ void mma_bf16(float* d, const uint32_t* a, const uint32_t* b) {
+    asm volatile(
+        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+        "{%0,%1,%2,%3};\n"
+        : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
+}
+
+// Right-looking Cholesky of a global-memory instance in blocks of 64 columns, with every
+// trailing update C -= P P^T (P: the block's 64 columns below it) done on the bf16 tensor
+// cores to FP64 accuracy.  Each row r of P is written exactly as
+//     P_r = 2^(e_r - 1022) sum_{s=1..8} q_rs 2^(-7 s),   q_rs integer, |q_rs| <= 127,
+// from the bits of its FP64 values aligned to the row's largest biased exponent e_r (bits
+// below 2^-56 of the row maximum are dropped).  A slice product Q_s Q_t^T sums 64 products
+// below 2^14, so every group G_g = sum_{s+t=g} Q_s Q_t^T (g <= 9, at most 8 terms) is an
+// integer below 2^23 and accumulates exactly in FP32; groups g >= 10 are below 2^-63 relative
+// and dropped.  The FP64 update is
+//     C_rc -= 2^(e_r + e_c - 2044) sum_g 2^(-7 g) G_g,rc,
+// with groups 7-9 first combined in FP32 (error below 2^-56 of the largest possible term).
+// Within a block the columns are factorised as in the plain loop (8x8 tiles, FP64 tensor path).
+__device__ bool factor_emulated(const SolveCtx& c, const Shared& s, double* A, int Nt, int* s_fail) {
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarps = blockDim.x >> 5;
+    const int g = lane >> 2, t = lane & 3;
+    // per CTA: 8 slices of [npad rows][64] bf16, then npad row scales
+    uint16_t* sl = reinterpret_cast<uint16_t*>(c.ws_e + (int64_t)blockIdx.x * c.ws_e_stride);
+    const int64_t sstride = (int64_t)c.npad * 64;
+    double* sr = reinterpret_cast<double*>(sl + 8 * sstride);
+    for (int K0 = 0; K0 < Nt; K0 += 8) {
+        const int K1 = min(K0 + 8, Nt);
+        for (int kt = K0; kt < K1; ++kt) {
+            if (tid == 0 && !diag_tile(A, kt, s)) *s_fail = 1;
+            __syncthreads();
+            if (*s_fail) return false;
+            panel_column(A, kt, Nt, s);
+            __syncthreads();
+            // the rest of the block: tiles (it, jt) with kt < jt < K1, jt <= it < Nt
+            const int nj = K1 - kt - 1;
+            for (int p = warp;; p += nwarps) {
+                int q = 0, rem = p;
+                while (q < nj && rem >= Nt - (kt + 1 + q)) {
+                    rem -= Nt - (kt + 1 + q);
+                    ++q;
+                }
+                if (q >= nj) break;
+                const int jt = kt + 1 + q, it = jt + rem;
+                double* C = A + tix(it, jt);
+                const double* Li = A + tix(it, kt);
+                const double* Lj = A + tix(jt, kt);
+                double c0 = C[te(g, 2 * t)], c1 = C[te(g, 2 * t + 1)];
+                dmma(c0, c1, neg(Li[te(g, t)]), Lj[te(g, t)]);
+                dmma(c0, c1, neg(Li[te(g, 4 + t)]), Lj[te(g, 4 + t)]);
+                C[te(g, 2 * t)] = c0;
+                C[te(g, 2 * t + 1)] = c1;
+            }
+            __syncthreads();
+        }
+        if (K1 >= Nt) break;
+        // slices of the rows below the block over the block's columns (zero beyond them)
+        const int rows = 8 * (Nt - K1), kcols = 8 * (K1 - K0);
+        for (int rr = warp; rr < rows; rr += nwarps) {
+            const int r = 8 * K1 + rr, it = r >> 3, ri = r & 7;
+            unsigned long long bits[2];
+            int E[2];
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const int col = 2 * lane + h;
+                const double x = col < kcols ? A[tix(it, K0 + (col >> 3)) + te(ri, col & 7)] : 0.0;
+                bits[h] = (unsigned long long)__double_as_longlong(x);
+                E[h] = (int)((bits[h] >> 52) & 0x7FF);
+            }
+            int em = max(E[0], E[1]);
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) em = max(em, __shfl_xor_sync(0xffffffffu, em, o));
+            uint32_t q32[8];
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                unsigned long long Y = 0;  // |x| 2^(1078 - em), a 56-bit integer
+                if (E[h] > 0 && E[h] < 0x7FF) {  // zero and subnormals slice to zero
+                    const unsigned long long m53 = (bits[h] & 0xFFFFFFFFFFFFFull) | (1ull << 52);
+                    const int sh = em - E[h];
+                    Y = sh >= 56 ? 0ull : ((m53 << 3) >> sh);
+                }
+                const bool negx = (bits[h] >> 63) != 0;
+#pragma unroll
+                for (int ss = 0; ss < 8; ++ss) {
+                    int qv = (int)((Y >> (49 - 7 * ss)) & 127ull);
+                    if (negx) qv = -qv;
+                    const uint32_t b16 = __float_as_uint((float)qv) >> 16;  // exact: |qv| < 2^7
+                    q32[ss] = h ? (q32[ss] | (b16 << 16)) : b16;
+                }
+            }
+#pragma unroll
+            for (int ss = 0; ss < 8; ++ss) reinterpret_cast<uint32_t*>(sl + ss * sstride + (int64_t)rr * 64)[lane] = q32[ss];
+            if (lane == 0) sr[rr] = em > 0 ? __longlong_as_double((long long)(em + 1) << 52) : 0.0;
+        }
+        __syncthreads();
+        // trailing update, warp item = 16 rows (tiles i0, i0 + 1) x 8 columns (tile jt),
+        // K1 <= jt <= i0 + 1; items ordered by row pair bi, with bi (bi + 1) items before bi
+        const int M = Nt - K1, MB = (M + 1) >> 1;
+        const int total = (MB - 1) * MB + min(2 * MB, M);
+        for (int p = warp; p < total; p += nwarps) {
+            int bi = (int)((sqrtf(4.f * (float)p + 1.f) - 1.f) * 0.5f);
+            while (bi > 0 && bi * (bi + 1) > p) --bi;
+            while (bi + 1 < MB && (bi + 1) * (bi + 2) <= p) ++bi;
+            const int jt = K1 + (p - bi * (bi + 1));
+            const int i0 = K1 + 2 * bi, i1 = i0 + 1;
+            const bool has1 = i1 < Nt;
+            const int ra = 16 * bi + g, rb = ra + 8, rj = 8 * (jt - K1) + g;
+            float acc[8][4];
+#pragma unroll
+            for (int q = 0; q < 8; ++q) acc[q][0] = acc[q][1] = acc[q][2] = acc[q][3] = 0.f;
+#pragma unroll
+            for (int kk = 0; kk < 4; ++kk) {
+                const int k0 = 16 * kk + 2 * t;
+                uint32_t bf[8][2];
+#pragma unroll
+                for (int tt = 0; tt < 8; ++tt) {
+                    const uint16_t* bp = sl + tt * sstride + (int64_t)rj * 64;
+                    bf[tt][0] = *reinterpret_cast<const uint32_t*>(bp + k0);
+                    bf[tt][1] = *reinterpret_cast<const uint32_t*>(bp + k0 + 8);
+                }
+#pragma unroll
+                for (int ss = 0; ss < 8; ++ss) {
+                    const uint16_t* pa = sl + ss * sstride + (int64_t)ra * 64;
+                    const uint16_t* pb = sl + ss * sstride + (int64_t)rb * 64;
+                    uint32_t af[4];
+                    af[0] = *reinterpret_cast<const uint32_t*>(pa + k0);
+                    af[1] = has1 ? *reinterpret_cast<const uint32_t*>(pb + k0) : 0u;
+                    af[2] = *reinterpret_cast<const uint32_t*>(pa + k0 + 8);
+                    af[3] = has1 ? *reinterpret_cast<const uint32_t*>(pb + k0 + 8) : 0u;
+#pragma unroll
+                    for (int tt = 0; tt + ss < 8; ++tt) mma_bf16(acc[ss + tt], af, bf[tt]);
+                }
+            }
+#pragma unroll
+            for (int half = 0; half < 2; ++half) {
+                const int it = half ? i1 : i0;
+                if (it >= Nt || it < jt) continue;  // past the end, or above the diagonal
+                double* C = A + tix(it, jt);
+                const double srow = sr[half ? rb : ra];
+#pragma unroll
+                for (int e = 0; e < 2; ++e) {
+                    const int ai = 2 * half + e, col = 2 * t + e;
+                    const double sc = srow * sr[8 * (jt - K1) + col];
+                    const float lo = fmaf(acc[7][ai], 0x1p-14f, fmaf(acc[6][ai], 0x1p-7f, acc[5][ai]));
+                    double v = (double)lo * 0x1p-49;
+                    v = fma((double)acc[4][ai], 0x1p-42, v);
+                    v = fma((double)acc[3][ai], 0x1p-35, v);
+                    v = fma((double)acc[2][ai], 0x1p-28, v);
+                    v = fma((double)acc[1][ai], 0x1p-21, v);
+                    v = fma((double)acc[0][ai], 0x1p-14, v);
+                    double* cp = C + te(g, col);
+                    *cp = fma(-sc, v, *cp);
+                }
+            }
+        }
+        __syncthreads();
+    }
+    return true;
+}
+
 // Assemble A, factorise, solve alpha.  Returns false if a pivot was not positive.
-template <bool kProps>
+template <bool kProps, bool kEmu = false>
 __device__ bool fit_instance(const SolveCtx& c, const Shared& s, int N, int64_t base) {
     const int tid = threadIdx.x, nt = blockDim.x;
     const int lane = tid & 31, warp = tid >> 5, nwarps = nt >> 5;
@@ -226,6 +440,9 @@ __device__ bool fit_instance(const SolveCtx& c, const Shared& s, int N, int64_t 
         }
     }
     __syncthreads();
+    if (kEmu) {
+        if (!factor_emulated(c, s, A, Nt, &s_fail)) return false;
+    } else
     for (int kt = 0; kt < Nt; ++kt) {
         // diagonal tile: 8x8 Cholesky and the inverse of its factor (FP64 pipe)
         if (tid == 0) {
@@ -562,10 +779,9 @@ __device__ __forceinline__ void invalid(EvalOut& r, int status) {
     r.v = INFINITY;
 }
 
-// kProps: surface-property mode (Eq. 6), a separate instantiation so that the distance path
-// keeps its register budget
-template <bool kProps>
-__global__ void k_solve(SolveCtx c) {
+// The body of the GP solve kernels (see k_solve below).
+template <bool kProps, bool kEmu>
+__device__ __forceinline__ void solve_body(const SolveCtx& c) {
     extern __shared__ double sm[];
     __shared__ int s_w;
     const int tid = threadIdx.x, nt = blockDim.x;
@@ -586,7 +802,7 @@ __global__ void k_solve(SolveCtx c) {
         const int64_t base = c.b.inst_off[I];
         const int N = (int)(c.b.inst_off[I + 1] - base);
         const int64_t q0 = c.b.q_off[I], q1 = c.b.q_off[I + 1];
-        const bool ok = N > 0 && fit_instance<kProps>(c, s, N, base);
+        const bool ok = N > 0 && fit_instance<kProps, kEmu>(c, s, N, base);
         if (kProps) {
             // property mode: means and variance (Eq. 6, variance read as for Eq. 2)
             const int np = c.b.nprop;
@@ -632,6 +848,19 @@ __global__ void k_solve(SolveCtx c) {
         if (!ok && N > 0 && tid == 0) atomicOr(c.err, kErrFactor);
         __syncthreads();
     }
+}
+
+// kProps: surface-property mode (Eq. 6); the emulated kernels run the trailing updates of
+// N > 224 instances on the bf16 tensor cores (256 threads, two CTAs per SM).  Separate
+// kernels, so that the plain distance kernel keeps its register budget.
+template <bool kProps>
+__global__ void k_solve(SolveCtx c) {
+    solve_body<kProps, false>(c);
+}
+
+template <bool kProps>
+__global__ void __launch_bounds__(kEmuThreads, 2) k_solve_emu(SolveCtx c) {
+    solve_body<kProps, true>(c);
 }
 
 // Backward pass (derived from Eq. 1 and Eq. 3): per instance,
@@ -781,6 +1010,8 @@ int solve_launch_static(const SolveBatch& b, const DevParams& P, int* err_dev, i
     SolveCtx c;
     c.plan = nullptr;
     c.bucket = 0;
+    c.ws_e = nullptr;
+    c.ws_e_stride = 0;
     c.b = b;
     c.P = P;
     c.err = err_dev;
@@ -807,6 +1038,19 @@ int solve_launch_static(const SolveBatch& b, const DevParams& P, int* err_dev, i
     note_launch();
     return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }
+
+namespace {
+
+using SolveKernel = void (*)(SolveCtx);
+
+SolveKernel pick_solve(bool props, bool emu) {
+    if (props) return emu ? k_solve_emu<true> : k_solve<true>;
+    return emu ? k_solve_emu<false> : k_solve<false>;
+}
+
+constexpr int64_t kEmuBytesPerRow = 8 * 64 * 2 + 8;  // eight bf16 slices of 64 columns + row scale
+
+}  // namespace
 
 void graph_cache_destroy(GraphCache& gc) {
     for (auto& e : gc.exec)
@@ -848,7 +1092,6 @@ bool solve_batch_graph(const SolveBatch& b, const DevParams& P, int* err_dev, cu
             return false;
     }
     const bool props = b.nprop > 0;
-    auto kern = props ? k_solve<true> : k_solve<false>;
     const int T = 256;
     int dev = 0, n_sm = 0;
     cudaGetDevice(&dev);
@@ -858,32 +1101,34 @@ bool solve_batch_graph(const SolveBatch& b, const DevParams& P, int* err_dev, cu
     struct Shape {
         int npad, smem_a, stage, threads, grid;
         size_t shm;
-        bool live;
+        bool live, emu;
+        SolveKernel kern;
     } sh[5];
-    size_t shm_max = 0;
     for (int i = 0; i < 5; ++i) {
         Shape& s = sh[i];
         s.live = maxn >= lo[i];
         s.npad = std::max((std::min(hi[i], maxn) + 7) & ~7, 8);
         s.smem_a = i > 0;
-        s.stage = s.smem_a ? 1 : cfg->stage_panel;
-        s.threads = cfg->threads[i];
+        s.emu = !s.smem_a && P.emulate;
+        s.stage = s.smem_a ? 1 : (s.emu ? 0 : cfg->stage_panel);
+        s.threads = s.emu ? kEmuThreads : cfg->threads[i];
         s.shm = smem_bytes(s.npad, s.smem_a, b.nprop, s.stage, b.Xi != nullptr, false);
-        if (s.live) shm_max = std::max(shm_max, s.shm);
+        s.kern = pick_solve(props, s.emu);
     }
-    if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm_max) != cudaSuccess)
-        return false;
-    int64_t ws_a_need = 0, ws_v_need = 0;
+    int64_t ws_a_need = 0, ws_v_need = 0, ws_e_need = 0;
     for (int i = 0; i < 5; ++i) {
         Shape& s = sh[i];
         if (!s.live) continue;
+        if (cudaFuncSetAttribute(s.kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)s.shm) != cudaSuccess)
+            return false;
         int per_sm = 0;
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, s.threads, s.shm);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, s.kern, s.threads, s.shm);
         per_sm = std::max(per_sm, 1);
         if (cfg->per_sm[i] > 0) per_sm = std::min(per_sm, cfg->per_sm[i]);
         s.grid = (int)std::min<int64_t>(n, (int64_t)n_sm * per_sm);
         if (!s.smem_a) ws_a_need = std::max<int64_t>(ws_a_need, n_tiles(s.npad / 8) * 64 * s.grid);
         if (b.want_var) ws_v_need = std::max<int64_t>(ws_v_need, (int64_t)s.npad * s.threads * s.grid);
+        if (s.emu) ws_e_need = std::max<int64_t>(ws_e_need, (int64_t)s.npad * kEmuBytesPerRow * s.grid);
     }
     // every buffer exists before the capture starts (allocation is not captured)
     int* hist = (int*)ar.get(Arena::kHist, sizeof(int) * 2 * 1025, st);
@@ -891,7 +1136,9 @@ bool solve_batch_graph(const SolveBatch& b, const DevParams& P, int* err_dev, cu
     int* counters = (int*)ar.get(Arena::kCounters, sizeof(int) * 16, st);
     double* ws_a = ws_a_need ? (double*)ar.get(Arena::kWs0, sizeof(double) * ws_a_need, st) : nullptr;
     double* ws_v = ws_v_need ? (double*)ar.get(Arena::kWs1, sizeof(double) * ws_v_need, st) : nullptr;
-    if (!hist || !order || !counters || (ws_a_need && !ws_a) || (ws_v_need && !ws_v)) return false;
+    uint8_t* ws_e = ws_e_need ? (uint8_t*)ar.get(Arena::kWs3, ws_e_need, st) : nullptr;
+    if (!hist || !order || !counters || (ws_a_need && !ws_a) || (ws_v_need && !ws_v) || (ws_e_need && !ws_e))
+        return false;
     int* cursor = hist + 1025;
     int* plan = counters + 5;
     cudaStream_t gs = gc->gs;
@@ -925,7 +1172,9 @@ bool solve_batch_graph(const SolveBatch& b, const DevParams& P, int* err_dev, cu
         c.ws_a = s.smem_a ? nullptr : ws_a;
         c.ws_v_stride = (int64_t)s.npad * s.threads;
         c.ws_v = ws_v;
-        kern<<<s.grid, s.threads, s.shm, gs>>>(c);
+        c.ws_e_stride = s.emu ? (int64_t)s.npad * kEmuBytesPerRow : 0;
+        c.ws_e = s.emu ? ws_e : nullptr;
+        s.kern<<<s.grid, s.threads, s.shm, gs>>>(c);
         note_launch();
     }
     cudaGraph_t graph = nullptr;
@@ -1036,6 +1285,8 @@ void solve_batch(const SolveBatch& b, const DevParams& P, int* err_dev, cudaStre
             SolveCtx c;
             c.plan = nullptr;
             c.bucket = 0;
+            c.ws_e = nullptr;
+            c.ws_e_stride = 0;
             c.b = b;
             c.P = P;
             c.err = err_dev;
@@ -1045,10 +1296,13 @@ void solve_batch(const SolveBatch& b, const DevParams& P, int* err_dev, cudaStre
             c.n_work = 1;
             c.npad = std::max((N + 7) & ~7, 8);
             c.a_in_smem = c.npad <= 224;
-            c.stage_panel = 1;
-            const int threads = c.npad <= 32 ? 64 : c.npad <= 64 ? 128 : c.npad <= 128 ? 256 : 512;
-            const size_t shm = smem_bytes(c.npad, c.a_in_smem, b.nprop, 1, b.Xi != nullptr);
-            auto ks = b.nprop > 0 ? k_solve<true> : k_solve<false>;
+            const bool emu = !c.a_in_smem && P.emulate;
+            c.stage_panel = emu ? 0 : 1;
+            const int threads = emu ? kEmuThreads : c.npad <= 32 ? 64 : c.npad <= 64 ? 128 : c.npad <= 128 ? 256 : 512;
+            const size_t shm = smem_bytes(c.npad, c.a_in_smem, b.nprop, c.stage_panel, b.Xi != nullptr);
+            auto ks = pick_solve(b.nprop > 0, emu);
+            c.ws_e_stride = emu ? (int64_t)c.npad * kEmuBytesPerRow : 0;
+            c.ws_e = emu ? (uint8_t*)ar.get(Arena::kWs3, 1024 * kEmuBytesPerRow, st) : nullptr;
             cudaFuncSetAttribute(ks, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm);
             c.ws_a_stride = c.a_in_smem ? 0 : n_tiles(c.npad / 8) * 64;
             c.ws_a = c.a_in_smem ? nullptr : (double*)ar.get(Arena::kWs0, sizeof(double) * n_tiles(128) * 64, st);
@@ -1085,6 +1339,8 @@ void solve_batch(const SolveBatch& b, const DevParams& P, int* err_dev, cudaStre
         SolveCtx c;
         c.plan = nullptr;
         c.bucket = 0;
+        c.ws_e = nullptr;
+        c.ws_e_stride = 0;
         c.b = b;
         c.P = P;
         c.err = err_dev;
@@ -1094,27 +1350,31 @@ void solve_batch(const SolveBatch& b, const DevParams& P, int* err_dev, cudaStre
         c.n_work = cnt;
         c.npad = std::max((nmax + 7) & ~7, 8);
         c.a_in_smem = bk.smem_a;
-        c.stage_panel = bk.smem_a ? 1 : cfg->stage_panel;
+        const bool emu = !bw && !bk.smem_a && P.emulate;
+        const int threads = emu ? kEmuThreads : bk.threads;
+        c.stage_panel = bk.smem_a ? 1 : (emu ? 0 : cfg->stage_panel);
         if (bw) c.bw = *bw;
         const size_t shm = smem_bytes(c.npad, c.a_in_smem, bw ? 0 : b.nprop, c.stage_panel, b.Xi != nullptr, bw != nullptr);
-        auto kern = bw ? k_backward : (b.nprop > 0 ? k_solve<true> : k_solve<false>);
+        auto kern = bw ? k_backward : pick_solve(b.nprop > 0, emu);
         cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm);
         int per_sm = 0;
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, bk.threads, shm);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, threads, shm);
         per_sm = std::max(per_sm, 1);
         if (cfg->per_sm[bi] > 0) per_sm = std::min(per_sm, cfg->per_sm[bi]);
         const int grid = (int)std::min<int64_t>(cnt, (int64_t)n_sm * per_sm);
         c.ws_a_stride = c.a_in_smem ? 0 : n_tiles(c.npad / 8) * 64;
         c.ws_a = c.a_in_smem ? nullptr : (double*)ar.get(Arena::kWs0, sizeof(double) * c.ws_a_stride * grid, st);
-        c.ws_v_stride = (int64_t)c.npad * bk.threads;
+        c.ws_v_stride = (int64_t)c.npad * threads;
         c.ws_v = (b.want_var && !bw) ? (double*)ar.get(Arena::kWs1, sizeof(double) * c.ws_v_stride * grid, st) : nullptr;
+        c.ws_e_stride = emu ? (int64_t)c.npad * kEmuBytesPerRow : 0;
+        c.ws_e = emu ? (uint8_t*)ar.get(Arena::kWs3, c.ws_e_stride * grid, st) : nullptr;
         cudaEvent_t b0 = nullptr, b1 = nullptr;
         if (profile) {
             cudaEventCreate(&b0);
             cudaEventCreate(&b1);
             cudaEventRecord(b0, st);
         }
-        kern<<<grid, bk.threads, shm, st>>>(c);
+        kern<<<grid, threads, shm, st>>>(c);
         note_launch();
         if (profile) {
             cudaEventRecord(b1, st);

@@ -478,3 +478,50 @@ def test_graph_launch_mode_matches_direct(vg):
             assert np.array_equal(a[3][k].view(np.uint8), b[3][k].view(np.uint8)), k
         st = b[4]
         assert st["graph_replays"] >= 10 and st["graph_instantiations"] <= 4
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_emulated_trailing_updates(vg, orc, precision):
+    """emulate_fp64 = 1 (trailing updates of N > 224 instances on the bf16 tensor cores with
+    exact slice products) agrees with the FP64 tensor path to rounding on large
+    neighbourhoods and on full L-GPDF leaves, and the FP64 map stays within the FP64 contract
+    against the oracle.  In mixed precision the gradient is an FP32 sum whose own error
+    (well inside the mixed tolerance) follows last-bit changes of alpha, so it is compared at
+    that scale."""
+    rng = np.random.default_rng(8)
+    u = rng.normal(size=(150000, 3))
+    surf = (1.3 * u / np.linalg.norm(u, axis=1, keepdims=True)).astype(np.float32)
+    q = (surf[rng.integers(0, len(surf), 20000)] * rng.uniform(0.6, 1.4, (20000, 1))).astype(np.float32)
+    qt = torch.from_numpy(q).cuda()
+    out = {}
+    for emu in (0, 1):
+        m = vg.Map(precision=precision, emulate_fp64=emu)
+        m.set_surface(torch.from_numpy(surf).cuda())
+        out[emu] = {k: v.cpu().numpy() for k, v in m.query(qt, grad=True, var=True).items()}
+        assert m.stats()["bucket_count"][4] > 50
+    a, b = out[0], out[1]
+    assert np.array_equal(a["status"], b["status"])
+    ok = a["status"] == 0
+    g_tol = 1e-5 if precision == "fp64" else 5e-3
+    assert np.abs(a["d"][ok] - b["d"][ok]).max() <= (1e-7 if precision == "fp64" else 1e-5)
+    assert np.abs(a["grad"][ok] - b["grad"][ok]).max() <= g_tol
+    fin = ok & np.isfinite(a["var"]) & (a["var"] > 1e-12)
+    assert np.median(np.abs(a["var"][fin] - b["var"][fin]) / a["var"][fin]) <= 1e-6
+    if precision == "fp64":
+        sel = rng.choice(np.flatnonzero(ok), 300, replace=False)
+        ref = orc.Surface(surf, orc.params()).query(q[sel], want_var=False)
+        assert np.array_equal(ref["status"], b["status"][sel])
+        assert np.abs(b["d"][sel] - ref["d"]).max() <= D_TOL
+    # full L-GPDF leaves: a volume, every leaf holds 512 occupied voxels
+    pts = torch.from_numpy(rng.uniform(0.0, 2.4, (200000, 3)).astype(np.float32)).cuda()
+    fr = {}
+    for emu in (0, 1):
+        m = vg.Map(precision=precision, max_pts_leaf=512, emulate_fp64=emu)
+        f = m.build_frame(pts)
+        assert m.stats()["bucket_count"][4] >= 27
+        r = {k: v.cpu().numpy() for k, v in f.results().items()}
+        o = np.argsort(r["keys"])
+        fr[emu] = {k: v[o] for k, v in r.items()}
+    assert np.array_equal(fr[0]["keys"], fr[1]["keys"]) and np.array_equal(fr[0]["status"], fr[1]["status"])
+    ok = fr[0]["status"] == 0
+    assert np.abs(fr[0]["d"][ok] - fr[1]["d"][ok]).max() <= (1e-7 if precision == "fp64" else 1e-5)
