@@ -259,7 +259,8 @@ __device__ __forceinline__ void mma_bf16(float* d, const uint32_t* a, const uint
 // integer below 2^23 and accumulates exactly in FP32; groups g >= 10 are below 2^-63 relative
 // and dropped.  The FP64 update is
 //     C_rc -= 2^(e_r + e_c - 2044) sum_g 2^(-7 g) G_g,rc,
-// with groups 7-9 first combined in FP32 (error below 2^-56 of the largest possible term).
+// with the groups packed exactly into two 64-bit integers (g = 2..5 and 6..9, each below
+// 2^45), so that one FP64 rounding is left.
 // Within a block the columns are factorised as in the plain loop (8x8 tiles, FP64 tensor path).
 __device__ bool factor_emulated(const SolveCtx& c, const Shared& s, double* A, int Nt, int* s_fail) {
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarps = blockDim.x >> 5;
@@ -380,20 +381,18 @@ __device__ bool factor_emulated(const SolveCtx& c, const Shared& s, double* A, i
                 const int it = half ? i1 : i0;
                 if (it >= Nt || it < jt) continue;  // past the end, or above the diagonal
                 double* C = A + tix(it, jt);
-                const double srow = sr[half ? rb : ra];
+                const double srow = sr[half ? rb : ra] * 0x1p-35;  // exact: powers of two
 #pragma unroll
                 for (int e = 0; e < 2; ++e) {
                     const int ai = 2 * half + e, col = 2 * t + e;
-                    const double sc = srow * sr[8 * (jt - K1) + col];
-                    const float lo = fmaf(acc[7][ai], 0x1p-14f, fmaf(acc[6][ai], 0x1p-7f, acc[5][ai]));
-                    double v = (double)lo * 0x1p-49;
-                    v = fma((double)acc[4][ai], 0x1p-42, v);
-                    v = fma((double)acc[3][ai], 0x1p-35, v);
-                    v = fma((double)acc[2][ai], 0x1p-28, v);
-                    v = fma((double)acc[1][ai], 0x1p-21, v);
-                    v = fma((double)acc[0][ai], 0x1p-14, v);
+                    long long gq[8];
+#pragma unroll
+                    for (int q = 0; q < 8; ++q) gq[q] = __float2int_rn(acc[q][ai]);  // exact integers
+                    const long long hi = gq[0] * (1ll << 21) + gq[1] * (1ll << 14) + gq[2] * 128 + gq[3];
+                    const long long lo = gq[4] * (1ll << 21) + gq[5] * (1ll << 14) + gq[6] * 128 + gq[7];
+                    const double v = fma((double)lo, 0x1p-28, (double)hi);  // x 2^-35 is in srow
                     double* cp = C + te(g, col);
-                    *cp = fma(-sc, v, *cp);
+                    *cp = fma(-(srow * sr[8 * (jt - K1) + col]), v, *cp);
                 }
             }
         }
@@ -1124,7 +1123,7 @@ bool solve_batch_graph(const SolveBatch& b, const DevParams& P, int* err_dev, cu
         int per_sm = 0;
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, s.kern, s.threads, s.shm);
         per_sm = std::max(per_sm, 1);
-        if (cfg->per_sm[i] > 0) per_sm = std::min(per_sm, cfg->per_sm[i]);
+        if (cfg->per_sm[i] > 0 && !s.emu) per_sm = std::min(per_sm, cfg->per_sm[i]);
         s.grid = (int)std::min<int64_t>(n, (int64_t)n_sm * per_sm);
         if (!s.smem_a) ws_a_need = std::max<int64_t>(ws_a_need, n_tiles(s.npad / 8) * 64 * s.grid);
         if (b.want_var) ws_v_need = std::max<int64_t>(ws_v_need, (int64_t)s.npad * s.threads * s.grid);
@@ -1360,7 +1359,7 @@ void solve_batch(const SolveBatch& b, const DevParams& P, int* err_dev, cudaStre
         int per_sm = 0;
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, threads, shm);
         per_sm = std::max(per_sm, 1);
-        if (cfg->per_sm[bi] > 0) per_sm = std::min(per_sm, cfg->per_sm[bi]);
+        if (cfg->per_sm[bi] > 0 && !emu) per_sm = std::min(per_sm, cfg->per_sm[bi]);  // emulated: occupancy limit
         const int grid = (int)std::min<int64_t>(cnt, (int64_t)n_sm * per_sm);
         c.ws_a_stride = c.a_in_smem ? 0 : n_tiles(c.npad / 8) * 64;
         c.ws_a = c.a_in_smem ? nullptr : (double*)ar.get(Arena::kWs0, sizeof(double) * c.ws_a_stride * grid, st);
