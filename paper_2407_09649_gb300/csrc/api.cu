@@ -572,6 +572,12 @@ int vgp_build_frame_props(vgp_map* m, const float* pts, const float* props, int6
         solve_batch(pb, Pp, m->dev_words, st, m->ar, nullptr, nullptr, false, m->prm.launch, &m->cfg, &m->gcache);
     }
     if (read_words(m, st) != VGP_OK) return bail(VGP_ERR_CUDA, "sync failed");
+    if (check_err(m, "vgp_build_frame") != VGP_OK) {
+        std::string msg = g_last_error;
+        vgp_frame_destroy(f);
+        g_last_error = msg;
+        return VGP_ERR_CUDA;
+    }
     if (!origin && m->host_words[4] != 0) return bail(VGP_ERR_STATE, "testing voxel without a neighbouring GP leaf");
     cudaError_t ce = cudaGetLastError();
     if (ce != cudaSuccess) return bail(VGP_ERR_CUDA, cudaGetErrorString(ce));
@@ -1320,7 +1326,9 @@ int vgp_query_distance_gradient(vgp_map* m, const float* q, int64_t n, double* d
     b.want_var = var != nullptr;
     SolveStats ss;
     b.max_n = m->P.cap_group;
-    solve_batch(b, m->P, m->dev_words, st, m->ar, &ss, nullptr, m->prm.profile != 0, m->prm.launch, &m->cfg, &m->gcache);
+    if (solve_batch(b, m->P, m->dev_words, st, m->ar, &ss, nullptr, m->prm.profile != 0, m->prm.launch, &m->cfg,
+                    &m->gcache) != 0)
+        return fail(VGP_ERR_CUDA, "query: CUDA graph capture, instantiation or launch failed");
     CUDA_TRY(cudaGetLastError());
     vgp_stats S{};
     S.n_points = m->s_n;
@@ -1427,7 +1435,9 @@ int vgp_query_smooth(vgp_map* m, const float* q, int64_t n, int32_t n_nodes, dou
     b.want_var = var != nullptr;
     SolveStats ss;
     b.max_n = P.cap_leaf;
-    solve_batch(b, P, m->dev_words, st, m->ar, &ss, nullptr, m->prm.profile != 0, m->prm.launch, &m->cfg, &m->gcache);
+    if (solve_batch(b, P, m->dev_words, st, m->ar, &ss, nullptr, m->prm.profile != 0, m->prm.launch, &m->cfg,
+                    &m->gcache) != 0)
+        return fail(VGP_ERR_CUDA, "vgp_query_smooth: CUDA graph capture, instantiation or launch failed");
     smooth_blend(n, n_nodes, G.q_slot, nn, pd, pg, pv, ps, lambda, P, d, grad, var, status, st);
     CUDA_TRY(cudaGetLastError());
     vgp_stats S{};
@@ -1662,7 +1672,9 @@ extern "C" int vgp_gp_batch(vgp_map* m, int64_t n_inst, const int64_t* inst_off,
     b.status = status;
     b.want_var = var != nullptr;
     SolveStats ss;
-    solve_batch(b, m->P, m->dev_words, st, m->ar, &ss, nullptr, m->prm.profile != 0, m->prm.launch, &m->cfg, &m->gcache);
+    if (solve_batch(b, m->P, m->dev_words, st, m->ar, &ss, nullptr, m->prm.profile != 0, m->prm.launch, &m->cfg,
+                    &m->gcache) != 0)
+        return fail(VGP_ERR_CUDA, "vgp_gp_batch: CUDA graph capture, instantiation or launch failed");
     CUDA_TRY(cudaGetLastError());
     vgp_stats S{};
     S.n_instances = n_inst;

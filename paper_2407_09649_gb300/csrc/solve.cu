@@ -252,23 +252,25 @@ __device__ __forceinline__ void mma_bf16(float* d, const uint32_t* a, const uint
 // Right-looking Cholesky of a global-memory instance in blocks of 64 columns, with every
 // trailing update C -= P P^T (P: the block's 64 columns below it) done on the bf16 tensor
 // cores to FP64 accuracy.  Each row r of P is written exactly as
-//     P_r = 2^(e_r - 1022) sum_{s=1..8} q_rs 2^(-7 s),   q_rs integer, |q_rs| <= 127,
+//     P_r = 2^(e_r - 1021) sum_{s=1..7} q_rs 2^(-8 s),   q_rs integer, |q_rs| <= 128,
 // from the bits of its FP64 values aligned to the row's largest biased exponent e_r (bits
-// below 2^-56 of the row maximum are dropped).  A slice product Q_s Q_t^T sums 64 products
-// below 2^14, so every group G_g = sum_{s+t=g} Q_s Q_t^T (g <= 9, at most 8 terms) is an
-// integer below 2^23 and accumulates exactly in FP32; groups g >= 10 are below 2^-63 relative
-// and dropped.  The FP64 update is
-//     C_rc -= 2^(e_r + e_c - 2044) sum_g 2^(-7 g) G_g,rc,
+// below 2^-55 of the row maximum are dropped): a 55-bit integer per value, cut into seven
+// balanced base-256 digits (the lower six in [-128, 127], the top one in [0, 128]), each
+// exact in bf16.  A slice product Q_s Q_t^T sums 64 products of at most 2^14, so every group
+// G_g = sum_{s+t=g} Q_s Q_t^T with g <= 9 (at most 7 terms) is an integer below 2^23 and
+// accumulates exactly in FP32; groups g >= 10 are below 2^-64 relative and dropped.  The
+// FP64 update is
+//     C_rc -= 2^(e_r + e_c - 2042) sum_g 2^(-8 g) G_g,rc,
 // with the groups packed exactly into two 64-bit integers (g = 2..5 and 6..9, each below
-// 2^45), so that one FP64 rounding is left.
+// 2^48), so that one FP64 rounding is left.
 // Within a block the columns are factorised as in the plain loop (8x8 tiles, FP64 tensor path).
 __device__ bool factor_emulated(const SolveCtx& c, const Shared& s, double* A, int Nt, int* s_fail) {
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarps = blockDim.x >> 5;
     const int g = lane >> 2, t = lane & 3;
-    // per CTA: 8 slices of [npad rows][64] bf16, then npad row scales
+    // per CTA: 7 slices of [npad rows][64] bf16, then npad row scales
     uint16_t* sl = reinterpret_cast<uint16_t*>(c.ws_e + (int64_t)blockIdx.x * c.ws_e_stride);
     const int64_t sstride = (int64_t)c.npad * 64;
-    double* sr = reinterpret_cast<double*>(sl + 8 * sstride);
+    double* sr = reinterpret_cast<double*>(sl + 7 * sstride);
     for (int K0 = 0; K0 < Nt; K0 += 8) {
         const int K1 = min(K0 + 8, Nt);
         for (int kt = K0; kt < K1; ++kt) {
@@ -315,27 +317,30 @@ __device__ bool factor_emulated(const SolveCtx& c, const Shared& s, double* A, i
             int em = max(E[0], E[1]);
 #pragma unroll
             for (int o = 16; o > 0; o >>= 1) em = max(em, __shfl_xor_sync(0xffffffffu, em, o));
-            uint32_t q32[8];
+            uint32_t q32[7];
 #pragma unroll
             for (int h = 0; h < 2; ++h) {
-                unsigned long long Y = 0;  // |x| 2^(1078 - em), a 56-bit integer
+                unsigned long long Y = 0;  // |x| 2^(1077 - em), a 55-bit integer
                 if (E[h] > 0 && E[h] < 0x7FF) {  // zero and subnormals slice to zero
                     const unsigned long long m53 = (bits[h] & 0xFFFFFFFFFFFFFull) | (1ull << 52);
                     const int sh = em - E[h];
-                    Y = sh >= 56 ? 0ull : ((m53 << 3) >> sh);
+                    Y = sh >= 55 ? 0ull : ((m53 << 2) >> sh);
                 }
+                // balanced digits: adding 128 to each of the six lower digits lets every digit
+                // be read as a byte minus 128; the top digit keeps the rest (0 .. 128)
+                const unsigned long long Yb = Y + 0x808080808080ull;
                 const bool negx = (bits[h] >> 63) != 0;
 #pragma unroll
-                for (int ss = 0; ss < 8; ++ss) {
-                    int qv = (int)((Y >> (49 - 7 * ss)) & 127ull);
+                for (int ss = 0; ss < 7; ++ss) {  // ss = 0: the most significant digit
+                    int qv = ss == 0 ? (int)(Yb >> 48) : (int)((Yb >> (48 - 8 * ss)) & 255ull) - 128;
                     if (negx) qv = -qv;
-                    const uint32_t b16 = __float_as_uint((float)qv) >> 16;  // exact: |qv| < 2^7
+                    const uint32_t b16 = __float_as_uint((float)qv) >> 16;  // exact: |qv| <= 2^7
                     q32[ss] = h ? (q32[ss] | (b16 << 16)) : b16;
                 }
             }
 #pragma unroll
-            for (int ss = 0; ss < 8; ++ss) reinterpret_cast<uint32_t*>(sl + ss * sstride + (int64_t)rr * 64)[lane] = q32[ss];
-            if (lane == 0) sr[rr] = em > 0 ? __longlong_as_double((long long)(em + 1) << 52) : 0.0;
+            for (int ss = 0; ss < 7; ++ss) reinterpret_cast<uint32_t*>(sl + ss * sstride + (int64_t)rr * 64)[lane] = q32[ss];
+            if (lane == 0) sr[rr] = em > 0 ? __longlong_as_double((long long)(em + 2) << 52) : 0.0;
         }
         __syncthreads();
         // trailing update, warp item = 16 rows (tiles i0, i0 + 1) x 8 columns (tile jt),
@@ -356,15 +361,15 @@ __device__ bool factor_emulated(const SolveCtx& c, const Shared& s, double* A, i
 #pragma unroll
             for (int kk = 0; kk < 4; ++kk) {
                 const int k0 = 16 * kk + 2 * t;
-                uint32_t bf[8][2];
+                uint32_t bf[7][2];
 #pragma unroll
-                for (int tt = 0; tt < 8; ++tt) {
+                for (int tt = 0; tt < 7; ++tt) {
                     const uint16_t* bp = sl + tt * sstride + (int64_t)rj * 64;
                     bf[tt][0] = *reinterpret_cast<const uint32_t*>(bp + k0);
                     bf[tt][1] = *reinterpret_cast<const uint32_t*>(bp + k0 + 8);
                 }
 #pragma unroll
-                for (int ss = 0; ss < 8; ++ss) {
+                for (int ss = 0; ss < 7; ++ss) {
                     const uint16_t* pa = sl + ss * sstride + (int64_t)ra * 64;
                     const uint16_t* pb = sl + ss * sstride + (int64_t)rb * 64;
                     uint32_t af[4];
@@ -373,7 +378,7 @@ __device__ bool factor_emulated(const SolveCtx& c, const Shared& s, double* A, i
                     af[2] = *reinterpret_cast<const uint32_t*>(pa + k0 + 8);
                     af[3] = has1 ? *reinterpret_cast<const uint32_t*>(pb + k0 + 8) : 0u;
 #pragma unroll
-                    for (int tt = 0; tt + ss < 8; ++tt) mma_bf16(acc[ss + tt], af, bf[tt]);
+                    for (int tt = 0; tt < 7 && tt + ss < 8; ++tt) mma_bf16(acc[ss + tt], af, bf[tt]);
                 }
             }
 #pragma unroll
@@ -381,16 +386,16 @@ __device__ bool factor_emulated(const SolveCtx& c, const Shared& s, double* A, i
                 const int it = half ? i1 : i0;
                 if (it >= Nt || it < jt) continue;  // past the end, or above the diagonal
                 double* C = A + tix(it, jt);
-                const double srow = sr[half ? rb : ra] * 0x1p-35;  // exact: powers of two
+                const double srow = sr[half ? rb : ra] * 0x1p-40;  // exact: powers of two
 #pragma unroll
                 for (int e = 0; e < 2; ++e) {
                     const int ai = 2 * half + e, col = 2 * t + e;
                     long long gq[8];
 #pragma unroll
                     for (int q = 0; q < 8; ++q) gq[q] = __float2int_rn(acc[q][ai]);  // exact integers
-                    const long long hi = gq[0] * (1ll << 21) + gq[1] * (1ll << 14) + gq[2] * 128 + gq[3];
-                    const long long lo = gq[4] * (1ll << 21) + gq[5] * (1ll << 14) + gq[6] * 128 + gq[7];
-                    const double v = fma((double)lo, 0x1p-28, (double)hi);  // x 2^-35 is in srow
+                    const long long hi = gq[0] * (1ll << 24) + gq[1] * (1ll << 16) + gq[2] * 256 + gq[3];
+                    const long long lo = gq[4] * (1ll << 24) + gq[5] * (1ll << 16) + gq[6] * 256 + gq[7];
+                    const double v = fma((double)lo, 0x1p-32, (double)hi);  // x 2^-40 is in srow
                     double* cp = C + te(g, col);
                     *cp = fma(-(srow * sr[8 * (jt - K1) + col]), v, *cp);
                 }
@@ -1047,7 +1052,7 @@ SolveKernel pick_solve(bool props, bool emu) {
     return emu ? k_solve_emu<false> : k_solve<false>;
 }
 
-constexpr int64_t kEmuBytesPerRow = 8 * 64 * 2 + 8;  // eight bf16 slices of 64 columns + row scale
+constexpr int64_t kEmuBytesPerRow = 7 * 64 * 2 + 8;  // seven bf16 slices of 64 columns + row scale
 
 }  // namespace
 
@@ -1114,12 +1119,20 @@ bool solve_batch_graph(const SolveBatch& b, const DevParams& P, int* err_dev, cu
         s.shm = smem_bytes(s.npad, s.smem_a, b.nprop, s.stage, b.Xi != nullptr, false);
         s.kern = pick_solve(props, s.emu);
     }
+    // buckets share a kernel: its shared-memory limit is the largest of the live buckets that
+    // launch it, set before any occupancy query or captured launch
+    for (int i = 0; i < 5; ++i) {
+        if (!sh[i].live) continue;
+        size_t shm_max = 0;
+        for (int j = 0; j < 5; ++j)
+            if (sh[j].live && sh[j].kern == sh[i].kern) shm_max = std::max(shm_max, sh[j].shm);
+        if (cudaFuncSetAttribute(sh[i].kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm_max) != cudaSuccess)
+            return false;
+    }
     int64_t ws_a_need = 0, ws_v_need = 0, ws_e_need = 0;
     for (int i = 0; i < 5; ++i) {
         Shape& s = sh[i];
         if (!s.live) continue;
-        if (cudaFuncSetAttribute(s.kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)s.shm) != cudaSuccess)
-            return false;
         int per_sm = 0;
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, s.kern, s.threads, s.shm);
         per_sm = std::max(per_sm, 1);
@@ -1216,12 +1229,12 @@ bool solve_batch_graph(const SolveBatch& b, const DevParams& P, int* err_dev, cu
 
 }  // namespace
 
-void solve_batch(const SolveBatch& b, const DevParams& P, int* err_dev, cudaStream_t st, Arena& ar, SolveStats* stats,
+int solve_batch(const SolveBatch& b, const DevParams& P, int* err_dev, cudaStream_t st, Arena& ar, SolveStats* stats,
                  const BackwardBatch* bw, bool profile, int launch, const SolveConfig* cfg, GraphCache* gc) {
     const SolveConfig dflt;
     if (!cfg) cfg = &dflt;
     const int64_t n = b.n_inst;
-    if (n <= 0) return;
+    if (n <= 0) return 0;
     if (launch == VGP_LAUNCH_GRAPH && !bw && gc) {
         if (!solve_batch_graph(b, P, err_dev, st, ar, stats, profile, cfg, gc)) {
             // leave the capture stream usable and the error visible to the caller
@@ -1233,8 +1246,9 @@ void solve_batch(const SolveBatch& b, const DevParams& P, int* err_dev, cudaStre
             cudaGetLastError();
             k_or_err<<<1, 1, 0, st>>>(err_dev, kErrLaunch);
             note_launch();
+            return -1;
         }
-        return;
+        return 0;
     }
     // size histogram and decreasing-size order
     int* hist = (int*)ar.get(Arena::kHist, sizeof(int) * 2 * 1025, st);
@@ -1319,7 +1333,7 @@ void solve_batch(const SolveBatch& b, const DevParams& P, int* err_dev, cudaStre
             cudaEventDestroy(ev0);
             cudaEventDestroy(ev1);
         }
-        return;
+        return 0;
     }
     int* counters = (int*)ar.get(Arena::kCounters, sizeof(int) * 8, st);
     cudaMemsetAsync(counters, 0, sizeof(int) * 8, st);
@@ -1396,6 +1410,7 @@ void solve_batch(const SolveBatch& b, const DevParams& P, int* err_dev, cudaStre
         cudaEventDestroy(ev0);
         cudaEventDestroy(ev1);
     }
+    return 0;
 }
 
 }  // namespace vgp

@@ -98,6 +98,7 @@ def test_graph_mode_on_empty_and_tiny_batches(vg):
     one = torch.tensor([[0.31, 0.22, -0.14]], device="cuda")
     f = m.build_frame(one)
     r = f.results()
+    assert m.stats()["graph_replays"] > 0  # the solve ran as a graph, not skipped
     assert r["keys"].shape[0] == 27 * 512
     mb = vg.Map(precision="mixed")
     rb = mb.build_frame(one).results()
