@@ -267,10 +267,12 @@ __device__ __forceinline__ void mma_bf16(float* d, const uint32_t* a, const uint
 __device__ bool factor_emulated(const SolveCtx& c, const Shared& s, double* A, int Nt, int* s_fail) {
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarps = blockDim.x >> 5;
     const int g = lane >> 2, t = lane & 3;
-    // per CTA: 7 slices of [npad rows][64] bf16, then npad row scales
-    uint16_t* sl = reinterpret_cast<uint16_t*>(c.ws_e + (int64_t)blockIdx.x * c.ws_e_stride);
-    const int64_t sstride = (int64_t)c.npad * 64;
-    double* sr = reinterpret_cast<double*>(sl + 7 * sstride);
+    // per CTA: the slices in mma fragment order, [row tile][slice][16-column step kk][lane]
+    // [2 x u32] (lane = 4 g + t holds columns 16 kk + 2t, +1 and 16 kk + 8 + 2t, +1 of row g
+    // of the tile), so that every A or B fragment is one coalesced 8-byte load per lane; then
+    // npad row scales
+    uint2* sl = reinterpret_cast<uint2*>(c.ws_e + (int64_t)blockIdx.x * c.ws_e_stride);
+    double* sr = reinterpret_cast<double*>(sl + (int64_t)c.npad * 7 * 16);
     for (int K0 = 0; K0 < Nt; K0 += 8) {
         const int K1 = min(K0 + 8, Nt);
         for (int kt = K0; kt < K1; ++kt) {
@@ -339,7 +341,14 @@ __device__ bool factor_emulated(const SolveCtx& c, const Shared& s, double* A, i
                 }
             }
 #pragma unroll
-            for (int ss = 0; ss < 7; ++ss) reinterpret_cast<uint32_t*>(sl + ss * sstride + (int64_t)rr * 64)[lane] = q32[ss];
+            {
+                // columns 2 lane, 2 lane + 1: step kk = lane / 8, half (lane / 4) % 2, t = lane % 4
+                uint32_t* dst = reinterpret_cast<uint32_t*>(sl + ((int64_t)(rr >> 3) * 7 * 4 + (lane >> 3)) * 32 +
+                                                            4 * (rr & 7) + (lane & 3)) +
+                                ((lane >> 2) & 1);
+#pragma unroll
+                for (int ss = 0; ss < 7; ++ss) dst[ss * 4 * 32 * 2] = q32[ss];
+            }
             if (lane == 0) sr[rr] = em > 0 ? __longlong_as_double((long long)(em + 2) << 52) : 0.0;
         }
         __syncthreads();
@@ -354,29 +363,30 @@ __device__ bool factor_emulated(const SolveCtx& c, const Shared& s, double* A, i
             const int jt = K1 + (p - bi * (bi + 1));
             const int i0 = K1 + 2 * bi, i1 = i0 + 1;
             const bool has1 = i1 < Nt;
-            const int ra = 16 * bi + g, rb = ra + 8, rj = 8 * (jt - K1) + g;
+            const int ra = 16 * bi + g, rb = ra + 8;
+            const uint2* fa = sl + (int64_t)(2 * bi) * 7 * 4 * 32 + lane;  // row tiles i0, i1
+            const uint2* fb = sl + (int64_t)(jt - K1) * 7 * 4 * 32 + lane;  // column tile jt
             float acc[8][4];
 #pragma unroll
             for (int q = 0; q < 8; ++q) acc[q][0] = acc[q][1] = acc[q][2] = acc[q][3] = 0.f;
 #pragma unroll
             for (int kk = 0; kk < 4; ++kk) {
-                const int k0 = 16 * kk + 2 * t;
                 uint32_t bf[7][2];
 #pragma unroll
                 for (int tt = 0; tt < 7; ++tt) {
-                    const uint16_t* bp = sl + tt * sstride + (int64_t)rj * 64;
-                    bf[tt][0] = *reinterpret_cast<const uint32_t*>(bp + k0);
-                    bf[tt][1] = *reinterpret_cast<const uint32_t*>(bp + k0 + 8);
+                    const uint2 v = fb[(tt * 4 + kk) * 32];
+                    bf[tt][0] = v.x;
+                    bf[tt][1] = v.y;
                 }
 #pragma unroll
                 for (int ss = 0; ss < 7; ++ss) {
-                    const uint16_t* pa = sl + ss * sstride + (int64_t)ra * 64;
-                    const uint16_t* pb = sl + ss * sstride + (int64_t)rb * 64;
+                    const uint2 va = fa[(ss * 4 + kk) * 32];
+                    const uint2 vb = has1 ? fa[(7 * 4 + ss * 4 + kk) * 32] : make_uint2(0u, 0u);
                     uint32_t af[4];
-                    af[0] = *reinterpret_cast<const uint32_t*>(pa + k0);
-                    af[1] = has1 ? *reinterpret_cast<const uint32_t*>(pb + k0) : 0u;
-                    af[2] = *reinterpret_cast<const uint32_t*>(pa + k0 + 8);
-                    af[3] = has1 ? *reinterpret_cast<const uint32_t*>(pb + k0 + 8) : 0u;
+                    af[0] = va.x;
+                    af[1] = vb.x;
+                    af[2] = va.y;
+                    af[3] = vb.y;
 #pragma unroll
                     for (int tt = 0; tt < 7 && tt + ss < 8; ++tt) mma_bf16(acc[ss + tt], af, bf[tt]);
                 }
