@@ -49,6 +49,8 @@ __device__ __forceinline__ void dmma(double& c0, double& c1, double a, double b)
 }
 
 constexpr int kEmuThreads = 256;  // CTA size of the emulated-update kernels (two CTAs per SM)
+constexpr int kEB = 4;            // tiles (of 8 columns) per block of the emulated factorisation
+constexpr int kEK = kEB / 2;      // 16-column mma steps per block
 
 struct SolveCtx {
     SolveBatch b;
@@ -88,10 +90,14 @@ struct Shared {
     int* xi;        // [npad] lattice offsets x | y << 8 | z << 16 (lattice instances)
     double* pa[4];  // property weights per channel (property mode): channels 0 and 1 reuse the
                     // distance alpha and its FP32 copies, which that mode does not use
+    double* Tblk;   // [kEB][64] inverses of the diagonal tiles of the current block
+    double* Wsc;    // [warps][64] per-warp tile scratch (layout changes between mma operands)
 };
 
+constexpr int kEmuSmemDoubles = 8 * 64 + 8 * 64;  // Tblk + Wsc for the 8 warps of an emulated CTA
+
 __device__ Shared carve(double* sm, int npad, int a_in_smem, double* ws_a, int nprop, int stage_panel,
-                        bool lattice, bool with_w) {
+                        bool lattice, bool with_w, bool emu = false) {
     Shared s;
     s.X = sm;
     s.alpha = s.X + 3 * npad;
@@ -101,6 +107,9 @@ __device__ Shared carve(double* sm, int npad, int a_in_smem, double* ws_a, int n
     s.Tinv = s.z + (with_w ? 2 : 1) * npad;
     s.T256 = s.Tinv + 64;
     double* end = s.T256 + 256;
+    s.Tblk = emu ? end : nullptr;
+    s.Wsc = emu ? end + 8 * 64 : nullptr;
+    if (emu) end += kEmuSmemDoubles;
     if (a_in_smem) {
         s.A = end;
         end += n_tiles(npad / 8) * 64;
@@ -123,8 +132,9 @@ __device__ Shared carve(double* sm, int npad, int a_in_smem, double* ws_a, int n
     return s;
 }
 
-__host__ size_t smem_bytes(int npad, int a_in_smem, int nprop, int stage_panel, bool lattice, bool with_w = false) {
-    size_t d = (size_t)(with_w ? 7 : 6) * npad + 64 + 256 +
+__host__ size_t smem_bytes(int npad, int a_in_smem, int nprop, int stage_panel, bool lattice, bool with_w = false,
+                          bool emu = false) {
+    size_t d = (size_t)(with_w ? 7 : 6) * npad + 64 + 256 + (emu ? kEmuSmemDoubles : 0) +
                (a_in_smem ? (size_t)n_tiles(npad / 8) * 64 : (stage_panel ? (size_t)(npad / 8) * 64 : 0));
     return d * sizeof(double) + (size_t)5 * npad * sizeof(float) + (lattice ? (size_t)npad * sizeof(int) : 0) +
            (size_t)std::max(nprop - 2, 0) * npad * sizeof(double);
@@ -192,45 +202,57 @@ __device__ void chol_solve(const Shared& s, const double* A, int Nt, double* out
     }
 }
 
-// One thread: 8x8 Cholesky of diagonal tile kt in place, 1 / L_jj into invd and the inverse
-// of the tile's factor into Tinv (FP64 pipe).  False on a non-positive pivot.  (The plain
-// factorisation loop keeps the same steps inline, which the compiler fits in fewer registers.)
-__device__ bool diag_tile(double* A, int kt, const Shared& s) {
+// One warp: the 8x8 Cholesky of diagonal tile kt in place (right-looking, the column scaling
+// and rank-1 updates spread over the lanes, 1 / L_jj from rsqrt), 1 / L_jj into invd and the
+// inverse of the tile's factor into Ti (rows by forward substitution, one lane per column).
+// S: 64 doubles of scratch.  False on a non-positive pivot (the same on every lane).
+__device__ bool diag_tile_warp(double* A, int kt, const Shared& s, double* Ti, double* S) {
+    const int lane = threadIdx.x & 31;
     double* D = A + tix(kt, kt);
-    double* W = s.Tinv;
+    S[lane] = D[lane];
+    S[lane + 32] = D[lane + 32];
+    __syncwarp();
     for (int j = 0; j < 8; ++j) {
-        double v = D[te(j, j)];
-        for (int k = 0; k < j; ++k) v -= D[te(j, k)] * D[te(j, k)];
+        const double v = S[te(j, j)];
         if (!(v > 0.0)) return false;
-        const double d = sqrt(v), inv = 1.0 / d;
-        D[te(j, j)] = d;
-        s.invd[8 * kt + j] = inv;
-        for (int i = j + 1; i < 8; ++i) {
-            double u = D[te(i, j)];
-            for (int k = 0; k < j; ++k) u -= D[te(i, k)] * D[te(j, k)];
-            D[te(i, j)] = u * inv;
+        const double r = rsqrt(v);
+        __syncwarp();
+        if (lane > j && lane < 8) S[te(lane, j)] *= r;
+        if (lane == 0) {
+            S[te(j, j)] = v * r;
+            s.invd[8 * kt + j] = r;
         }
+        __syncwarp();
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {  // entries (rr, cc), j < cc <= rr
+            const int e = lane + 32 * h, rr = e >> 3, cc = e & 7;
+            if (cc > j && rr >= cc) S[te(rr, cc)] -= S[te(rr, j)] * S[te(cc, j)];
+        }
+        __syncwarp();
     }
-    for (int j = 0; j < 8; ++j) {
-        for (int i = 0; i < j; ++i) W[te(i, j)] = 0.0;
-        W[te(j, j)] = s.invd[8 * kt + j];
-        for (int i = j + 1; i < 8; ++i) {
-            double u = 0.0;
-            for (int k = j; k < i; ++k) u += D[te(i, k)] * W[te(k, j)];
-            W[te(i, j)] = -u * s.invd[8 * kt + i];
+    D[lane] = S[lane];
+    D[lane + 32] = S[lane + 32];
+    // Ti = L^-1: Ti_ii = 1 / L_ii, Ti_ic = -(sum_{c <= k < i} L_ik Ti_kc) / L_ii for c < i
+    for (int i = 0; i < 8; ++i) {
+        if (lane < 8) {
+            double u = lane == i ? 1.0 : 0.0;
+            for (int k = lane; k < i; ++k) u -= S[te(i, k)] * Ti[te(k, lane)];
+            Ti[te(i, lane)] = lane <= i ? u * s.invd[8 * kt + i] : 0.0;
         }
+        __syncwarp();
     }
     return true;
 }
 
-// Panel column kt: L_it,kt = A_it,kt Tinv^T for it > kt, one tile per warp.
-__device__ void panel_column(double* A, int kt, int Nt, const Shared& s) {
+// Panel column kt: L_it,kt = A_it,kt Ti^T for kt < it < it_end (Ti: inverse of the diagonal
+// tile's factor), one tile per warp.
+__device__ void panel_column(double* A, int kt, int it_end, const double* Ti) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
     const int g = lane >> 2, t = lane & 3;
-    for (int it = kt + 1 + warp; it < Nt; it += nwarps) {
+    for (int it = kt + 1 + warp; it < it_end; it += nwarps) {
         double* T = A + tix(it, kt);
         const double a0 = T[te(g, t)], a1 = T[te(g, 4 + t)];
-        const double b0 = s.Tinv[te(g, t)], b1 = s.Tinv[te(g, 4 + t)];
+        const double b0 = Ti[te(g, t)], b1 = Ti[te(g, 4 + t)];
         double c0 = 0.0, c1 = 0.0;
         dmma(c0, c1, a0, b0);
         dmma(c0, c1, a1, b1);
@@ -249,21 +271,119 @@ __device__ __forceinline__ void mma_bf16(float* d, const uint32_t* a, const uint
         : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
 }
 
-// Right-looking Cholesky of a global-memory instance in blocks of 64 columns, with every
-// trailing update C -= P P^T (P: the block's 64 columns below it) done on the bf16 tensor
-// cores to FP64 accuracy.  Each row r of P is written exactly as
+// Balanced base-256 digits of row g of an 8-row tile over one block (the FP64 values
+// x[0 .. 2 kEB - 1] held by the four lanes t of the row: columns 8 j + 2t and 8 j + 2t + 1 in
+// x[2j], x[2j + 1]), written as bf16 pairs in mma fragment order to F ([slice][16-column step]
+// [lane] uint2), and the row scale 2^(em - 1021) to *scale (lane t = 0).  The digit scheme is
+// described at factor_emulated.
+__device__ __forceinline__ void slice_row(const double (&x)[2 * kEB], uint2* F, double* scale) {
+    const int lane = threadIdx.x & 31;
+    int em = 0;
+#pragma unroll
+    for (int i = 0; i < 2 * kEB; ++i) em = max(em, (int)((__double_as_longlong(x[i]) >> 52) & 0x7FF));
+    em = max(em, __shfl_xor_sync(0xffffffffu, em, 1));
+    em = max(em, __shfl_xor_sync(0xffffffffu, em, 2));
+#pragma unroll
+    for (int kk = 0; kk < kEK; ++kk) {
+        unsigned long long Yb[4];
+        bool negx[4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {  // columns 16 kk + {2t, 2t + 1, 8 + 2t, 8 + 2t + 1}
+            const unsigned long long bits = (unsigned long long)__double_as_longlong(x[4 * kk + i]);
+            const int E = (int)((bits >> 52) & 0x7FF);
+            unsigned long long Y = 0;  // |x| 2^(1077 - em), a 55-bit integer
+            if (E > 0 && E < 0x7FF) {  // zero and subnormals slice to zero
+                const int sh = em - E;
+                Y = sh >= 55 ? 0ull : ((((bits & 0xFFFFFFFFFFFFFull) | (1ull << 52)) << 2) >> sh);
+            }
+            // adding 128 to each of the six lower digits lets every digit be read as a byte
+            // minus 128; the top digit keeps the rest (0 .. 128)
+            Yb[i] = Y + 0x808080808080ull;
+            negx[i] = (bits >> 63) != 0;
+        }
+#pragma unroll
+        for (int ss = 0; ss < 7; ++ss) {  // ss = 0: the most significant digit
+            uint32_t h16[4];
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                int qv = ss == 0 ? (int)(Yb[i] >> 48) : (int)((Yb[i] >> (48 - 8 * ss)) & 255ull) - 128;
+                if (negx[i]) qv = -qv;
+                h16[i] = __float_as_uint((float)qv) >> 16;  // exact: |qv| <= 2^7
+            }
+            F[(ss * kEK + kk) * 32 + lane] = make_uint2(h16[0] | (h16[1] << 16), h16[2] | (h16[3] << 16));
+        }
+    }
+    if ((lane & 3) == 0) *scale = em > 0 ? __longlong_as_double((long long)(em + 2) << 52) : 0.0;
+}
+
+// Row tile it below the factorised diagonal block of tile columns K0 .. K0 + kEB - 1 (inverses
+// of its diagonal tiles in Tblk): L_it,K0+j = (A_it,K0+j - sum_{k<j} L_it,K0+k L_K0+j,K0+k^T)
+// Ti_j^T for j < kEB on the FP64 tensor path, one warp, the row's tiles in registers.  The warp's
+// scratch tile W turns each result from the accumulator into the operand layout.  The
+// results are stored to A and sliced for the trailing update (F, scale: this tile's slices
+// and row scales).
+__device__ void block_rows(double* A, int it, int K0, const double* Tblk, double* W, uint2* F, double* scale) {
+    const int lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
+    double* R = A + tix(it, K0);  // tiles (it, K0 .. K0 + kEB - 1), contiguous
+    double x[2 * kEB];            // accumulator layout: tile j holds columns 2t, 2t + 1 of row g
+#pragma unroll
+    for (int j = 0; j < kEB; ++j) {
+        x[2 * j] = R[64 * j + te(g, 2 * t)];
+        x[2 * j + 1] = R[64 * j + te(g, 2 * t + 1)];
+    }
+    double xa[kEB - 1][2];  // operand layout of the solved tiles: columns t and 4 + t of row g
+#pragma unroll
+    for (int j = 0; j < kEB; ++j) {
+        double a0 = x[2 * j], a1 = x[2 * j + 1];
+        const double* Lj = A + tix(K0 + j, K0);  // tiles (K0 + j, K0 .. K0 + j), contiguous
+#pragma unroll
+        for (int k = 0; k < j; ++k) {
+            dmma(a0, a1, neg(xa[k][0]), Lj[64 * k + te(g, t)]);
+            dmma(a0, a1, neg(xa[k][1]), Lj[64 * k + te(g, 4 + t)]);
+        }
+        W[te(g, 2 * t)] = a0;
+        W[te(g, 2 * t + 1)] = a1;
+        __syncwarp();
+        const double p0 = W[te(g, t)], p1 = W[te(g, 4 + t)];
+        __syncwarp();
+        const double* Ti = Tblk + 64 * j;
+        double y0 = 0.0, y1 = 0.0;
+        dmma(y0, y1, p0, Ti[te(g, t)]);
+        dmma(y0, y1, p1, Ti[te(g, 4 + t)]);
+        R[64 * j + te(g, 2 * t)] = y0;
+        R[64 * j + te(g, 2 * t + 1)] = y1;
+        x[2 * j] = y0;
+        x[2 * j + 1] = y1;
+        if (j < kEB - 1) {
+            W[te(g, 2 * t)] = y0;
+            W[te(g, 2 * t + 1)] = y1;
+            __syncwarp();
+            xa[j][0] = W[te(g, t)];
+            xa[j][1] = W[te(g, 4 + t)];
+            __syncwarp();
+        }
+    }
+    slice_row(x, F, scale + g);
+}
+
+// Right-looking Cholesky of a global-memory instance in blocks of W = 8 kEB columns, with
+// every trailing update C -= P P^T (P: the block's W columns below it) done on the bf16
+// tensor cores to FP64 accuracy.  Each row r of P is written exactly as
 //     P_r = 2^(e_r - 1021) sum_{s=1..7} q_rs 2^(-8 s),   q_rs integer, |q_rs| <= 128,
 // from the bits of its FP64 values aligned to the row's largest biased exponent e_r (bits
 // below 2^-55 of the row maximum are dropped): a 55-bit integer per value, cut into seven
 // balanced base-256 digits (the lower six in [-128, 127], the top one in [0, 128]), each
-// exact in bf16.  A slice product Q_s Q_t^T sums 64 products of at most 2^14, so every group
-// G_g = sum_{s+t=g} Q_s Q_t^T with g <= 9 (at most 7 terms) is an integer below 2^23 and
-// accumulates exactly in FP32; groups g >= 10 are below 2^-64 relative and dropped.  The
+// exact in bf16.  A slice product Q_s Q_t^T sums W <= 64 products of at most 2^14, so every
+// group G_g = sum_{s+t=g} Q_s Q_t^T with g <= 9 (at most 7 terms) is an integer below 2^23
+// and accumulates exactly in FP32; groups g >= 10 are below 2^-64 relative and dropped.  The
 // FP64 update is
-//     C_rc -= 2^(e_r + e_c - 2042) sum_g 2^(-8 g) G_g,rc,
-// with the groups packed exactly into two 64-bit integers (g = 2..5 and 6..9, each below
-// 2^48), so that one FP64 rounding is left.
-// Within a block the columns are factorised as in the plain loop (8x8 tiles, FP64 tensor path).
+//     C_rc -= 2^(e_r + e_c - 2042) sum_g 2^(-8 g) G_g,rc.
+// The groups are packed exactly into two 64-bit integers, hi (g = 2..5) and lo (g = 6..9),
+// each below 2^48, and joined as w = 2^14 hi + floor(lo / 2^18), below 2^62: the dropped
+// part of lo is below 2^-54 of the scale 2^(e_r + e_c - 2042), under the slicing error.  The
+// update is then one conversion of w and one FMA.
+// Within a block the diagonal block is factorised as in the plain loop (8x8 tiles, FP64 tensor
+// path); the rows below it are solved one row tile per warp (block_rows).
 __device__ bool factor_emulated(const SolveCtx& c, const Shared& s, double* A, int Nt, int* s_fail) {
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarps = blockDim.x >> 5;
     const int g = lane >> 2, t = lane & 3;
@@ -272,25 +392,21 @@ __device__ bool factor_emulated(const SolveCtx& c, const Shared& s, double* A, i
     // of the tile), so that every A or B fragment is one coalesced 8-byte load per lane; then
     // npad row scales
     uint2* sl = reinterpret_cast<uint2*>(c.ws_e + (int64_t)blockIdx.x * c.ws_e_stride);
-    double* sr = reinterpret_cast<double*>(sl + (int64_t)c.npad * 7 * 16);
-    for (int K0 = 0; K0 < Nt; K0 += 8) {
-        const int K1 = min(K0 + 8, Nt);
+    constexpr int kTS = 7 * kEK * 32;  // uint2 per row tile
+    double* sr = reinterpret_cast<double*>(sl + (int64_t)(c.npad / 8) * kTS);
+    for (int K0 = 0; K0 < Nt; K0 += kEB) {
+        const int K1 = min(K0 + kEB, Nt);
+        // the diagonal block: tiles (it, jt), K0 <= jt <= it < K1, right-looking by 8 columns
         for (int kt = K0; kt < K1; ++kt) {
-            if (tid == 0 && !diag_tile(A, kt, s)) *s_fail = 1;
+            double* Ti = s.Tblk + 64 * (kt - K0);
+            if (warp == 0 && !diag_tile_warp(A, kt, s, Ti, s.Wsc) && lane == 0) *s_fail = 1;
             __syncthreads();
             if (*s_fail) return false;
-            panel_column(A, kt, Nt, s);
+            panel_column(A, kt, K1, Ti);
             __syncthreads();
-            // the rest of the block: tiles (it, jt) with kt < jt < K1, jt <= it < Nt
             const int nj = K1 - kt - 1;
-            for (int p = warp;; p += nwarps) {
-                int q = 0, rem = p;
-                while (q < nj && rem >= Nt - (kt + 1 + q)) {
-                    rem -= Nt - (kt + 1 + q);
-                    ++q;
-                }
-                if (q >= nj) break;
-                const int jt = kt + 1 + q, it = jt + rem;
+            for (int p = warp; p < nj * (nj + 1) / 2; p += nwarps) {
+                const int ir = tri_row(p), it = kt + 1 + ir, jt = kt + 1 + (p - ir * (ir + 1) / 2);
                 double* C = A + tix(it, jt);
                 const double* Li = A + tix(it, kt);
                 const double* Lj = A + tix(jt, kt);
@@ -303,54 +419,10 @@ __device__ bool factor_emulated(const SolveCtx& c, const Shared& s, double* A, i
             __syncthreads();
         }
         if (K1 >= Nt) break;
-        // slices of the rows below the block over the block's columns (zero beyond them)
-        const int rows = 8 * (Nt - K1), kcols = 8 * (K1 - K0);
-        for (int rr = warp; rr < rows; rr += nwarps) {
-            const int r = 8 * K1 + rr, it = r >> 3, ri = r & 7;
-            unsigned long long bits[2];
-            int E[2];
-#pragma unroll
-            for (int h = 0; h < 2; ++h) {
-                const int col = 2 * lane + h;
-                const double x = col < kcols ? A[tix(it, K0 + (col >> 3)) + te(ri, col & 7)] : 0.0;
-                bits[h] = (unsigned long long)__double_as_longlong(x);
-                E[h] = (int)((bits[h] >> 52) & 0x7FF);
-            }
-            int em = max(E[0], E[1]);
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) em = max(em, __shfl_xor_sync(0xffffffffu, em, o));
-            uint32_t q32[7];
-#pragma unroll
-            for (int h = 0; h < 2; ++h) {
-                unsigned long long Y = 0;  // |x| 2^(1077 - em), a 55-bit integer
-                if (E[h] > 0 && E[h] < 0x7FF) {  // zero and subnormals slice to zero
-                    const unsigned long long m53 = (bits[h] & 0xFFFFFFFFFFFFFull) | (1ull << 52);
-                    const int sh = em - E[h];
-                    Y = sh >= 55 ? 0ull : ((m53 << 2) >> sh);
-                }
-                // balanced digits: adding 128 to each of the six lower digits lets every digit
-                // be read as a byte minus 128; the top digit keeps the rest (0 .. 128)
-                const unsigned long long Yb = Y + 0x808080808080ull;
-                const bool negx = (bits[h] >> 63) != 0;
-#pragma unroll
-                for (int ss = 0; ss < 7; ++ss) {  // ss = 0: the most significant digit
-                    int qv = ss == 0 ? (int)(Yb >> 48) : (int)((Yb >> (48 - 8 * ss)) & 255ull) - 128;
-                    if (negx) qv = -qv;
-                    const uint32_t b16 = __float_as_uint((float)qv) >> 16;  // exact: |qv| <= 2^7
-                    q32[ss] = h ? (q32[ss] | (b16 << 16)) : b16;
-                }
-            }
-#pragma unroll
-            {
-                // columns 2 lane, 2 lane + 1: step kk = lane / 8, half (lane / 4) % 2, t = lane % 4
-                uint32_t* dst = reinterpret_cast<uint32_t*>(sl + ((int64_t)(rr >> 3) * 7 * 4 + (lane >> 3)) * 32 +
-                                                            4 * (rr & 7) + (lane & 3)) +
-                                ((lane >> 2) & 1);
-#pragma unroll
-                for (int ss = 0; ss < 7; ++ss) dst[ss * 4 * 32 * 2] = q32[ss];
-            }
-            if (lane == 0) sr[rr] = em > 0 ? __longlong_as_double((long long)(em + 2) << 52) : 0.0;
-        }
+        // the rows below: one warp per row tile solves its eight tiles against the diagonal
+        // block and writes their slices and row scales
+        for (int it = K1 + warp; it < Nt; it += nwarps)
+            block_rows(A, it, K0, s.Tblk, s.Wsc + 64 * warp, sl + (int64_t)(it - K1) * kTS, sr + 8 * (it - K1));
         __syncthreads();
         // trailing update, warp item = 16 rows (tiles i0, i0 + 1) x 8 columns (tile jt),
         // K1 <= jt <= i0 + 1; items ordered by row pair bi, with bi (bi + 1) items before bi
@@ -364,24 +436,24 @@ __device__ bool factor_emulated(const SolveCtx& c, const Shared& s, double* A, i
             const int i0 = K1 + 2 * bi, i1 = i0 + 1;
             const bool has1 = i1 < Nt;
             const int ra = 16 * bi + g, rb = ra + 8;
-            const uint2* fa = sl + (int64_t)(2 * bi) * 7 * 4 * 32 + lane;  // row tiles i0, i1
-            const uint2* fb = sl + (int64_t)(jt - K1) * 7 * 4 * 32 + lane;  // column tile jt
+            const uint2* fa = sl + (int64_t)(2 * bi) * kTS + lane;  // row tiles i0, i1
+            const uint2* fb = sl + (int64_t)(jt - K1) * kTS + lane;  // column tile jt
             float acc[8][4];
 #pragma unroll
             for (int q = 0; q < 8; ++q) acc[q][0] = acc[q][1] = acc[q][2] = acc[q][3] = 0.f;
 #pragma unroll
-            for (int kk = 0; kk < 4; ++kk) {
+            for (int kk = 0; kk < kEK; ++kk) {
                 uint32_t bf[7][2];
 #pragma unroll
                 for (int tt = 0; tt < 7; ++tt) {
-                    const uint2 v = fb[(tt * 4 + kk) * 32];
+                    const uint2 v = fb[(tt * kEK + kk) * 32];
                     bf[tt][0] = v.x;
                     bf[tt][1] = v.y;
                 }
 #pragma unroll
                 for (int ss = 0; ss < 7; ++ss) {
-                    const uint2 va = fa[(ss * 4 + kk) * 32];
-                    const uint2 vb = has1 ? fa[(7 * 4 + ss * 4 + kk) * 32] : make_uint2(0u, 0u);
+                    const uint2 va = fa[(ss * kEK + kk) * 32];
+                    const uint2 vb = has1 ? fa[kTS + (ss * kEK + kk) * 32] : make_uint2(0u, 0u);
                     uint32_t af[4];
                     af[0] = va.x;
                     af[1] = vb.x;
@@ -396,7 +468,7 @@ __device__ bool factor_emulated(const SolveCtx& c, const Shared& s, double* A, i
                 const int it = half ? i1 : i0;
                 if (it >= Nt || it < jt) continue;  // past the end, or above the diagonal
                 double* C = A + tix(it, jt);
-                const double srow = sr[half ? rb : ra] * 0x1p-40;  // exact: powers of two
+                const double srow = sr[half ? rb : ra] * 0x1p-54;  // exact: powers of two
 #pragma unroll
                 for (int e = 0; e < 2; ++e) {
                     const int ai = 2 * half + e, col = 2 * t + e;
@@ -405,7 +477,7 @@ __device__ bool factor_emulated(const SolveCtx& c, const Shared& s, double* A, i
                     for (int q = 0; q < 8; ++q) gq[q] = __float2int_rn(acc[q][ai]);  // exact integers
                     const long long hi = gq[0] * (1ll << 24) + gq[1] * (1ll << 16) + gq[2] * 256 + gq[3];
                     const long long lo = gq[4] * (1ll << 24) + gq[5] * (1ll << 16) + gq[6] * 256 + gq[7];
-                    const double v = fma((double)lo, 0x1p-32, (double)hi);  // x 2^-40 is in srow
+                    const double v = (double)(hi * (1ll << 14) + (lo >> 18));  // x 2^-54 is in srow
                     double* cp = C + te(g, col);
                     *cp = fma(-(srow * sr[8 * (jt - K1) + col]), v, *cp);
                 }
@@ -800,7 +872,7 @@ __device__ __forceinline__ void solve_body(const SolveCtx& c) {
     __shared__ int s_w;
     const int tid = threadIdx.x, nt = blockDim.x;
     double* ws_a = c.a_in_smem ? nullptr : c.ws_a + (int64_t)blockIdx.x * c.ws_a_stride;
-    Shared s = carve(sm, c.npad, c.a_in_smem, ws_a, c.b.nprop, c.stage_panel, c.b.Xi != nullptr, false);
+    Shared s = carve(sm, c.npad, c.a_in_smem, ws_a, c.b.nprop, c.stage_panel, c.b.Xi != nullptr, false, kEmu);
     double* V = c.ws_v ? c.ws_v + (int64_t)blockIdx.x * c.ws_v_stride + tid : nullptr;
     const bool lattice = c.b.Xi != nullptr;
     for (int j = tid; j < 256; j += nt) s.T256[j] = c.P.exp_tab[j];
@@ -1062,7 +1134,7 @@ SolveKernel pick_solve(bool props, bool emu) {
     return emu ? k_solve_emu<false> : k_solve<false>;
 }
 
-constexpr int64_t kEmuBytesPerRow = 7 * 64 * 2 + 8;  // seven bf16 slices of 64 columns + row scale
+constexpr int64_t kEmuBytesPerRow = 7 * 8 * kEB * 2 + 8;  // seven bf16 slices of a block's columns + row scale
 
 }  // namespace
 
@@ -1126,7 +1198,7 @@ bool solve_batch_graph(const SolveBatch& b, const DevParams& P, int* err_dev, cu
         s.emu = !s.smem_a && P.emulate;
         s.stage = s.smem_a ? 1 : (s.emu ? 0 : cfg->stage_panel);
         s.threads = s.emu ? kEmuThreads : cfg->threads[i];
-        s.shm = smem_bytes(s.npad, s.smem_a, b.nprop, s.stage, b.Xi != nullptr, false);
+        s.shm = smem_bytes(s.npad, s.smem_a, b.nprop, s.stage, b.Xi != nullptr, false, s.emu);
         s.kern = pick_solve(props, s.emu);
     }
     // buckets share a kernel: its shared-memory limit is the largest of the live buckets that
@@ -1322,7 +1394,7 @@ int solve_batch(const SolveBatch& b, const DevParams& P, int* err_dev, cudaStrea
             const bool emu = !c.a_in_smem && P.emulate;
             c.stage_panel = emu ? 0 : 1;
             const int threads = emu ? kEmuThreads : c.npad <= 32 ? 64 : c.npad <= 64 ? 128 : c.npad <= 128 ? 256 : 512;
-            const size_t shm = smem_bytes(c.npad, c.a_in_smem, b.nprop, c.stage_panel, b.Xi != nullptr);
+            const size_t shm = smem_bytes(c.npad, c.a_in_smem, b.nprop, c.stage_panel, b.Xi != nullptr, false, emu);
             auto ks = pick_solve(b.nprop > 0, emu);
             c.ws_e_stride = emu ? (int64_t)c.npad * kEmuBytesPerRow : 0;
             c.ws_e = emu ? (uint8_t*)ar.get(Arena::kWs3, 1024 * kEmuBytesPerRow, st) : nullptr;
@@ -1377,7 +1449,8 @@ int solve_batch(const SolveBatch& b, const DevParams& P, int* err_dev, cudaStrea
         const int threads = emu ? kEmuThreads : bk.threads;
         c.stage_panel = bk.smem_a ? 1 : (emu ? 0 : cfg->stage_panel);
         if (bw) c.bw = *bw;
-        const size_t shm = smem_bytes(c.npad, c.a_in_smem, bw ? 0 : b.nprop, c.stage_panel, b.Xi != nullptr, bw != nullptr);
+        const size_t shm =
+            smem_bytes(c.npad, c.a_in_smem, bw ? 0 : b.nprop, c.stage_panel, b.Xi != nullptr, bw != nullptr, emu);
         auto kern = bw ? k_backward : pick_solve(b.nprop > 0, emu);
         cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm);
         int per_sm = 0;
