@@ -262,6 +262,31 @@ __device__ void panel_column(double* A, int kt, int it_end, const double* Ti) {
     }
 }
 
+// w 2^(e - 1023) as an FP64 value for a 64-bit integer w, |w| < 2^62, and a biased exponent e,
+// built on the integer pipe: the leading bit of |w| gives the exponent, the significand is
+// rounded to 53 bits (ties away from zero).  0 when w = 0 or the result would not be normal
+// (below 2^-1022, far under any entry it is added to).
+__device__ __forceinline__ double scaled_int(long long w, int e) {
+    if (w == 0) return 0.0;
+    const unsigned long long a = (unsigned long long)(w < 0 ? -w : w);
+    const int p = 63 - __clzll((long long)a);  // |w| in [2^p, 2^(p+1))
+    int E = p + e;
+    unsigned long long m;
+    if (p > 52) {
+        const int sh = p - 52;
+        m = (a + (1ull << (sh - 1))) >> sh;
+        if (m >> 53) {
+            m >>= 1;
+            ++E;
+        }
+    } else {
+        m = a << (52 - p);
+    }
+    if (E <= 0) return 0.0;
+    return __longlong_as_double((long long)(((unsigned long long)(w < 0) << 63) | ((unsigned long long)E << 52) |
+                                            (m & 0xFFFFFFFFFFFFFull)));
+}
+
 // D += A B on the bf16 tensor path (m16n8k16, FP32 accumulation)
 __device__ __forceinline__ void mma_bf16(float* d, const uint32_t* a, const uint32_t* b) {
     asm volatile(
@@ -381,7 +406,10 @@ __device__ void block_rows(double* A, int it, int K0, const double* Tblk, double
 // The groups are packed exactly into two 64-bit integers, hi (g = 2..5) and lo (g = 6..9),
 // each below 2^48, and joined as w = 2^14 hi + floor(lo / 2^18), below 2^62: the dropped
 // part of lo is below 2^-54 of the scale 2^(e_r + e_c - 2042), under the slicing error.  The
-// update is then one conversion of w and one FMA.
+// scaled w is built as an FP64 value on the integer pipe (scaled_int) and subtracted: one
+// FP64 operation per updated entry.  With W = 32 every partial group sum stays below 2^22,
+// so the accumulators start at 1.5 * 2^23, where FP32 holds every integer, and the group is
+// read from the accumulator's bits (no float-to-integer conversion).
 // Within a block the diagonal block is factorised as in the plain loop (8x8 tiles, FP64 tensor
 // path); the rows below it are solved one row tile per warp (block_rows).
 __device__ bool factor_emulated(const SolveCtx& c, const Shared& s, double* A, int Nt, int* s_fail) {
@@ -438,9 +466,11 @@ __device__ bool factor_emulated(const SolveCtx& c, const Shared& s, double* A, i
             const int ra = 16 * bi + g, rb = ra + 8;
             const uint2* fa = sl + (int64_t)(2 * bi) * kTS + lane;  // row tiles i0, i1
             const uint2* fb = sl + (int64_t)(jt - K1) * kTS + lane;  // column tile jt
+            static_assert(7 * 8 * kEB * 128 * 128 < (1 << 22), "group sums must stay below 2^22");
+            constexpr float kOff = 12582912.0f;  // 1.5 * 2^23, bits 0x4B400000
             float acc[8][4];
 #pragma unroll
-            for (int q = 0; q < 8; ++q) acc[q][0] = acc[q][1] = acc[q][2] = acc[q][3] = 0.f;
+            for (int q = 0; q < 8; ++q) acc[q][0] = acc[q][1] = acc[q][2] = acc[q][3] = kOff;
 #pragma unroll
             for (int kk = 0; kk < kEK; ++kk) {
                 uint32_t bf[7][2];
@@ -468,18 +498,21 @@ __device__ bool factor_emulated(const SolveCtx& c, const Shared& s, double* A, i
                 const int it = half ? i1 : i0;
                 if (it >= Nt || it < jt) continue;  // past the end, or above the diagonal
                 double* C = A + tix(it, jt);
-                const double srow = sr[half ? rb : ra] * 0x1p-54;  // exact: powers of two
+                // biased exponents of the row scales (0 for a zero row, whose w is 0)
+                const int er = (int)(__double_as_longlong(sr[half ? rb : ra]) >> 52);
 #pragma unroll
                 for (int e = 0; e < 2; ++e) {
                     const int ai = 2 * half + e, col = 2 * t + e;
-                    long long gq[8];
+                    const int ec = (int)(__double_as_longlong(sr[8 * (jt - K1) + col]) >> 52);
+                    long long gq[8];  // G + 0x4B400000: the accumulator bits
 #pragma unroll
-                    for (int q = 0; q < 8; ++q) gq[q] = __float2int_rn(acc[q][ai]);  // exact integers
-                    const long long hi = gq[0] * (1ll << 24) + gq[1] * (1ll << 16) + gq[2] * 256 + gq[3];
-                    const long long lo = gq[4] * (1ll << 24) + gq[5] * (1ll << 16) + gq[6] * 256 + gq[7];
-                    const double v = (double)(hi * (1ll << 14) + (lo >> 18));  // x 2^-54 is in srow
+                    for (int q = 0; q < 8; ++q) gq[q] = __float_as_int(acc[q][ai]);
+                    constexpr long long kOffBits = 0x4B400000ll * 0x01010101ll;
+                    const long long hi = gq[0] * (1ll << 24) + gq[1] * (1ll << 16) + gq[2] * 256 + gq[3] - kOffBits;
+                    const long long lo = gq[4] * (1ll << 24) + gq[5] * (1ll << 16) + gq[6] * 256 + gq[7] - kOffBits;
+                    // scale 2^(er + ec - 2046) 2^-54 = 2^(eS - 1023)
                     double* cp = C + te(g, col);
-                    *cp = fma(-(srow * sr[8 * (jt - K1) + col]), v, *cp);
+                    *cp -= scaled_int(hi * (1ll << 14) + (lo >> 18), er + ec - 1077);
                 }
             }
         }
