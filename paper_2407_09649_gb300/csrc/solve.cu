@@ -202,6 +202,89 @@ __device__ void chol_solve(const Shared& s, const double* A, int Nt, double* out
     }
 }
 
+// Solve (L L^T) x = rhs in place on s.z (x written to out) with the inverses of every diagonal
+// tile in Tall ([Nt][64], tile layout); rows >= N of rhs must be zero.  Blocks of four tiles:
+// inside a block warp 0 alone takes each tile (its inverse times the right-hand side, eight
+// lanes) and updates the rest of the block; the rows outside the block are then updated by
+// the whole CTA, two barriers per block and side.
+__device__ void chol_solve_inv(const Shared& s, const double* A, int Nt, double* out, const double* Tall) {
+    const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31;
+    const int Np = Nt * 8;
+    double* z = s.z;
+    for (int B0 = 0; B0 < Nt; B0 += 4) {
+        const int B1 = min(B0 + 4, Nt);
+        if (tid < 32) {
+            for (int kt = B0; kt < B1; ++kt) {
+                const double* Ti = Tall + 64 * kt;
+                double v = 0.0;
+                if (lane < 8)
+                    for (int c2 = 0; c2 <= lane; ++c2) v += Ti[te(lane, c2)] * z[8 * kt + c2];
+                __syncwarp();
+                if (lane < 8) z[8 * kt + lane] = v;
+                __syncwarp();
+                const int i = 8 * (kt + 1) + lane;  // rows of the block below tile kt
+                if (i < 8 * B1) {
+                    const double* T = A + tix(i >> 3, kt);
+                    const int r = i & 7;
+                    double u = z[i];
+#pragma unroll
+                    for (int c2 = 0; c2 < 8; ++c2) u -= T[te(r, c2)] * z[8 * kt + c2];
+                    z[i] = u;
+                }
+                __syncwarp();
+            }
+        }
+        __syncthreads();
+        for (int i = 8 * B1 + tid; i < Np; i += nt) {
+            const int r = i & 7;
+            double u = z[i];
+            for (int kt = B0; kt < B1; ++kt) {
+                const double* T = A + tix(i >> 3, kt);
+#pragma unroll
+                for (int c2 = 0; c2 < 8; ++c2) u -= T[te(r, c2)] * z[8 * kt + c2];
+            }
+            z[i] = u;
+        }
+        __syncthreads();
+    }
+    for (int B1 = Nt; B1 > 0; B1 -= 4) {
+        const int B0 = max(B1 - 4, 0);
+        if (tid < 32) {
+            for (int kt = B1 - 1; kt >= B0; --kt) {
+                const double* Ti = Tall + 64 * kt;
+                double v = 0.0;
+                if (lane < 8)
+                    for (int r = lane; r < 8; ++r) v += Ti[te(r, lane)] * z[8 * kt + r];
+                __syncwarp();
+                if (lane < 8) out[8 * kt + lane] = v;
+                __syncwarp();
+                const int j = 8 * B0 + lane;  // columns of the block left of tile kt
+                if (j < 8 * kt) {
+                    const double* T = A + tix(kt, j >> 3);
+                    const int cj = j & 7;
+                    double u = z[j];
+#pragma unroll
+                    for (int c2 = 0; c2 < 8; ++c2) u -= T[te(c2, cj)] * out[8 * kt + c2];
+                    z[j] = u;
+                }
+                __syncwarp();
+            }
+        }
+        __syncthreads();
+        for (int j = tid; j < 8 * B0; j += nt) {
+            const int cj = j & 7;
+            double u = z[j];
+            for (int kt = B0; kt < B1; ++kt) {
+                const double* T = A + tix(kt, j >> 3);
+#pragma unroll
+                for (int c2 = 0; c2 < 8; ++c2) u -= T[te(c2, cj)] * out[8 * kt + c2];
+            }
+            z[j] = u;
+        }
+        __syncthreads();
+    }
+}
+
 // One warp: the 8x8 Cholesky of diagonal tile kt in place (right-looking, the column scaling
 // and rank-1 updates spread over the lanes, 1 / L_jj from rsqrt), 1 / L_jj into invd and the
 // inverse of the tile's factor into Ti (rows by forward substitution, one lane per column).
@@ -391,6 +474,14 @@ __device__ void block_rows(double* A, int it, int K0, const double* Tblk, double
     slice_row(x, F, scale + g);
 }
 
+// Per-CTA workspace of the emulated factorisation: the slices of the rows below the current
+// block ([row tile][7 slices][kEK steps][lane] uint2), npad row scales, then the inverses of all
+// diagonal tiles ([npad / 8][64] doubles).
+__device__ __forceinline__ double* emu_tile_inverses(const SolveCtx& c) {
+    const uint2* sl = reinterpret_cast<const uint2*>(c.ws_e + (int64_t)blockIdx.x * c.ws_e_stride);
+    return const_cast<double*>(reinterpret_cast<const double*>(sl + (int64_t)(c.npad / 8) * 7 * kEK * 32)) + c.npad;
+}
+
 // Right-looking Cholesky of a global-memory instance in blocks of W = 8 kEB columns, with
 // every trailing update C -= P P^T (P: the block's W columns below it) done on the bf16
 // tensor cores to FP64 accuracy.  Each row r of P is written exactly as
@@ -422,12 +513,20 @@ __device__ bool factor_emulated(const SolveCtx& c, const Shared& s, double* A, i
     uint2* sl = reinterpret_cast<uint2*>(c.ws_e + (int64_t)blockIdx.x * c.ws_e_stride);
     constexpr int kTS = 7 * kEK * 32;  // uint2 per row tile
     double* sr = reinterpret_cast<double*>(sl + (int64_t)(c.npad / 8) * kTS);
+    double* Tall = emu_tile_inverses(c);  // inverses of all diagonal tiles, for the solves
     for (int K0 = 0; K0 < Nt; K0 += kEB) {
         const int K1 = min(K0 + kEB, Nt);
         // the diagonal block: tiles (it, jt), K0 <= jt <= it < K1, right-looking by 8 columns
         for (int kt = K0; kt < K1; ++kt) {
             double* Ti = s.Tblk + 64 * (kt - K0);
-            if (warp == 0 && !diag_tile_warp(A, kt, s, Ti, s.Wsc) && lane == 0) *s_fail = 1;
+            if (warp == 0) {
+                if (diag_tile_warp(A, kt, s, Ti, s.Wsc)) {
+                    Tall[64 * kt + lane] = Ti[lane];
+                    Tall[64 * kt + lane + 32] = Ti[lane + 32];
+                } else if (lane == 0) {
+                    *s_fail = 1;
+                }
+            }
             __syncthreads();
             if (*s_fail) return false;
             panel_column(A, kt, K1, Ti);
@@ -677,14 +776,20 @@ __device__ bool fit_instance(const SolveCtx& c, const Shared& s, int N, int64_t 
         for (int ch = 0; ch < c.b.nprop; ++ch) {
             for (int i = tid; i < Np; i += nt) s.z[i] = i < N ? c.b.yprop[(base + i) * c.b.nprop + ch] : 0.0;
             __syncthreads();
-            chol_solve(s, A, Nt, s.pa[ch]);
+            if (kEmu)
+                chol_solve_inv(s, A, Nt, s.pa[ch], emu_tile_inverses(c));
+            else
+                chol_solve(s, A, Nt, s.pa[ch]);
         }
         return true;
     }
     // alpha = A^-1 1 (Eq. 1)
     for (int i = tid; i < Np; i += nt) s.z[i] = i < N ? 1.0 : 0.0;
     __syncthreads();
-    chol_solve(s, A, Nt, s.alpha);
+    if (kEmu)
+        chol_solve_inv(s, A, Nt, s.alpha, emu_tile_inverses(c));
+    else
+        chol_solve(s, A, Nt, s.alpha);
     for (int j = tid; j < Np; j += nt) {
         const float hi = (float)s.alpha[j];
         s.alf[j] = hi;
@@ -1167,7 +1272,8 @@ SolveKernel pick_solve(bool props, bool emu) {
     return emu ? k_solve_emu<false> : k_solve<false>;
 }
 
-constexpr int64_t kEmuBytesPerRow = 7 * 8 * kEB * 2 + 8;  // seven bf16 slices of a block's columns + row scale
+// seven bf16 slices of a block's columns, the row scale, and one row of diagonal-tile inverses
+constexpr int64_t kEmuBytesPerRow = 7 * 8 * kEB * 2 + 8 + 64;
 
 }  // namespace
 
