@@ -238,10 +238,9 @@ def run_ours(args):
             "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic (seeded city scene)",
             "config": {"workload": WORKLOAD, "n_surface": int(S.shape[0]), "n_queries": int(nq),
-                       "precision": ("mixed: FP32 evaluation; FP64-accurate Cholesky whose block updates "
+                       "precision": ("mixed: FP32 evaluation; FP64-accurate Cholesky whose trailing updates "
                                      "for N > 224 run as exact bf16 slice products on the tensor cores, "
-                                     "summed exactly in integers and converted to FP64; FP64 K entries, panels, "
-                                     "solves, variance and reverting"),
+                                     "recombined in FP64; FP64 K entries, panels, solves, variance and reverting"),
                        "variance": False, "l2": "inputs+outputs (~460 MB) larger than L2",
                        "parallelism": f"replicas x{ws}" if ws > 1 else "single GPU",
                        "instances": st["n_instances"], "query_leaves": st["n_groups"],
@@ -249,9 +248,9 @@ def run_ours(args):
             "e2e": {"value": e_value, "unit": UNIT,
                     "h2d_bytes_per_step": int(S_h.nbytes + Q_h.nbytes), "d2h_bytes_per_step": int(nq * 32)},
             "gpu_launches": launches,
-            "roofline": {"kernel": ("k_solve_emu (N > 224: FP64-accurate left-looking Cholesky, the updates "
-                                    "from earlier 32-column blocks as exact bf16 slice products) + k_solve "
-                                    "(N <= 224: FP64 tile Cholesky on mma.sync f64); alpha, fused eval"),
+            "roofline": {"kernel": ("k_solve_emu (N > 224: FP64-accurate Cholesky, trailing updates as bf16 "
+                                    "slice products) + k_solve (N <= 224: FP64 tile Cholesky on mma.sync f64); "
+                                    "alpha, fused eval"),
                          "bound": "tensor", "dtype": "fp64 (FP64-equivalent work)", "achieved": achieved,
                          "peak": peak,
                          "frac_note": ("achieved counts the FP64 Cholesky flops the method needs; the emulated "

@@ -381,12 +381,16 @@ __device__ __forceinline__ void mma_bf16(float* d, const uint32_t* a, const uint
 
 // Balanced base-256 digits of row g of an 8-row tile over one block (the FP64 values
 // x[0 .. 2 kEB - 1] held by the four lanes t of the row: columns 8 j + 2t and 8 j + 2t + 1 in
-// x[2j], x[2j + 1]) under the common scale 2^(em - 1021), written as bf16 pairs in mma fragment
-// order to F ([slice][16-column step][lane] uint2).  Each value becomes the 55-bit integer
-// |x| 2^(1077 - em), rounded to nearest.  A value with an exponent above em (outside the bound
-// the scale comes from) sets *bad.  The digit scheme is described at factor_emulated.
-__device__ __forceinline__ void slice_row(const double (&x)[2 * kEB], uint2* F, int em, int* bad) {
+// x[2j], x[2j + 1]), written as bf16 pairs in mma fragment order to F ([slice][16-column step]
+// [lane] uint2), and the row scale 2^(em - 1021) to *scale (lane t = 0).  The digit scheme is
+// described at factor_emulated.
+__device__ __forceinline__ void slice_row(const double (&x)[2 * kEB], uint2* F, double* scale) {
     const int lane = threadIdx.x & 31;
+    int em = 0;
+#pragma unroll
+    for (int i = 0; i < 2 * kEB; ++i) em = max(em, (int)((__double_as_longlong(x[i]) >> 52) & 0x7FF));
+    em = max(em, __shfl_xor_sync(0xffffffffu, em, 1));
+    em = max(em, __shfl_xor_sync(0xffffffffu, em, 2));
 #pragma unroll
     for (int kk = 0; kk < kEK; ++kk) {
         unsigned long long Yb[4];
@@ -395,13 +399,10 @@ __device__ __forceinline__ void slice_row(const double (&x)[2 * kEB], uint2* F, 
         for (int i = 0; i < 4; ++i) {  // columns 16 kk + {2t, 2t + 1, 8 + 2t, 8 + 2t + 1}
             const unsigned long long bits = (unsigned long long)__double_as_longlong(x[4 * kk + i]);
             const int E = (int)((bits >> 52) & 0x7FF);
-            unsigned long long Y = 0;
-            if (E > em) {
-                *bad = 1;
-            } else if (E > 0) {  // zero and subnormals slice to zero
+            unsigned long long Y = 0;  // |x| 2^(1077 - em), a 55-bit integer
+            if (E > 0 && E < 0x7FF) {  // zero and subnormals slice to zero
                 const int sh = em - E;
-                const unsigned long long M = ((bits & 0xFFFFFFFFFFFFFull) | (1ull << 52)) << 2;
-                Y = sh == 0 ? M : sh >= 56 ? 0ull : ((M >> (sh - 1)) + 1) >> 1;
+                Y = sh >= 55 ? 0ull : ((((bits & 0xFFFFFFFFFFFFFull) | (1ull << 52)) << 2) >> sh);
             }
             // adding 128 to each of the six lower digits lets every digit be read as a byte
             // minus 128; the top digit keeps the rest (0 .. 128)
@@ -420,15 +421,16 @@ __device__ __forceinline__ void slice_row(const double (&x)[2 * kEB], uint2* F, 
             F[(ss * kEK + kk) * 32 + lane] = make_uint2(h16[0] | (h16[1] << 16), h16[2] | (h16[3] << 16));
         }
     }
+    if ((lane & 3) == 0) *scale = em > 0 ? __longlong_as_double((long long)(em + 2) << 52) : 0.0;
 }
 
 // Row tile it below the factorised diagonal block of tile columns K0 .. K0 + kEB - 1 (inverses
 // of its diagonal tiles in Tblk): L_it,K0+j = (A_it,K0+j - sum_{k<j} L_it,K0+k L_K0+j,K0+k^T)
 // Ti_j^T for j < kEB on the FP64 tensor path, one warp, the row's tiles in registers.  The warp's
 // scratch tile W turns each result from the accumulator into the operand layout.  The
-// results are stored to A and sliced for the later updates (F: this tile's slices, em: the
-// common scale, bad: set when a value is outside it).
-__device__ void block_rows(double* A, int it, int K0, const double* Tblk, double* W, uint2* F, int em, int* bad) {
+// results are stored to A and sliced for the trailing update (F, scale: this tile's slices
+// and row scales).
+__device__ void block_rows(double* A, int it, int K0, const double* Tblk, double* W, uint2* F, double* scale) {
     const int lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
     double* R = A + tix(it, K0);  // tiles (it, K0 .. K0 + kEB - 1), contiguous
     double x[2 * kEB];            // accumulator layout: tile j holds columns 2t, 2t + 1 of row g
@@ -469,135 +471,51 @@ __device__ void block_rows(double* A, int it, int K0, const double* Tblk, double
             __syncwarp();
         }
     }
-    slice_row(x, F, em, bad);
+    slice_row(x, F, scale + g);
 }
 
-// Row tiles sliced over all blocks of an instance with nt tiles: block b keeps the tiles below
-// it, nt - kEB (b + 1) of them.
-__host__ __device__ __forceinline__ int64_t emu_slice_tiles(int nt) {
-    int64_t n = 0;
-    for (int k1 = kEB; k1 < nt; k1 += kEB) n += nt - k1;
-    return n;
-}
-
-constexpr int kTS = 7 * kEK * 32;  // uint2 of slices per row tile and block
-
-// Per-CTA workspace of the emulated factorisation: the slices of every block's rows below it
-// (block b from tile b nt - kEB b (b + 1) / 2 on, [row tile][7 slices][kEK steps][lane] uint2),
-// then the inverses of all diagonal tiles ([npad / 8][64] doubles).
+// Per-CTA workspace of the emulated factorisation: the slices of the rows below the current
+// block ([row tile][7 slices][kEK steps][lane] uint2), npad row scales, then the inverses of all
+// diagonal tiles ([npad / 8][64] doubles).
 __device__ __forceinline__ double* emu_tile_inverses(const SolveCtx& c) {
     const uint2* sl = reinterpret_cast<const uint2*>(c.ws_e + (int64_t)blockIdx.x * c.ws_e_stride);
-    return const_cast<double*>(reinterpret_cast<const double*>(sl + emu_slice_tiles(c.npad / 8) * kTS));
+    return const_cast<double*>(reinterpret_cast<const double*>(sl + (int64_t)(c.npad / 8) * 7 * kEK * 32)) + c.npad;
 }
 
-// Left-looking Cholesky of a global-memory instance in blocks of W = 8 kEB columns, with the
-// updates of each block column from all earlier blocks (A_:,b -= sum_{b' < b} P_b' P_b'^T over
-// the block's columns, P_b': block b' of L below it) done on the bf16 tensor cores to FP64
-// accuracy.  Every entry of L obeys |L_ij| <= sqrt(A_ii) (the rows of L have the norms
-// sqrt(A_ii)), so one scale serves all rows: r = 2^(em - 1021), em the biased exponent of
-// sqrt(max_i A_ii) plus one.  Each row of P is written exactly as
-//     P_r = r sum_{s=1..7} q_rs 2^(-8 s),   q_rs integer, |q_rs| <= 128,
-// from its FP64 values as 55-bit integers below r (rounded), cut into seven balanced base-256
-// digits (the lower six in [-128, 127], the top one in [0, 128]), each exact in bf16.  A slice
-// product Q_s Q_t^T sums W = 32 products of at most 2^14, so every group
-// G_g = sum_{s+t=g} Q_s Q_t^T with g <= 9 (at most 7 terms) is an integer below 2^22 and
-// accumulates exactly in FP32; groups g >= 10 are below 2^-64 of r^2 and dropped.  The
-// accumulators start at 1.5 * 2^23, where FP32 holds every integer, and each group is read from
-// the accumulator's bits.  Per block b' the groups are packed exactly into two 64-bit integers,
-// hi (g = 2..5) and lo (g = 6..9), and summed over the earlier blocks (below 2^53), so the update
-//     C_rc -= r^2 (2^-40 hi + 2^-72 lo)
-// is converted to FP64 once per entry and block column: both terms are built as FP64 values on
-// the integer pipe (scaled_int) and subtracted.  The rounding of the slices, below 2^-56 r per
-// value, gives an error of the order of FP64 Cholesky's backward error bound
-// (n u sum_k |L_ik||L_jk|, with sum_k |L_ik||L_jk| <= sqrt(A_ii A_jj)).
-// The diagonal block is then factorised as in the plain loop (8x8 tiles, FP64 tensor path) and
-// the rows below it are solved one row tile per warp and sliced (block_rows).
+// Right-looking Cholesky of a global-memory instance in blocks of W = 8 kEB columns, with
+// every trailing update C -= P P^T (P: the block's W columns below it) done on the bf16
+// tensor cores to FP64 accuracy.  Each row r of P is written exactly as
+//     P_r = 2^(e_r - 1021) sum_{s=1..7} q_rs 2^(-8 s),   q_rs integer, |q_rs| <= 128,
+// from the bits of its FP64 values aligned to the row's largest biased exponent e_r (bits
+// below 2^-55 of the row maximum are dropped): a 55-bit integer per value, cut into seven
+// balanced base-256 digits (the lower six in [-128, 127], the top one in [0, 128]), each
+// exact in bf16.  A slice product Q_s Q_t^T sums W <= 64 products of at most 2^14, so every
+// group G_g = sum_{s+t=g} Q_s Q_t^T with g <= 9 (at most 7 terms) is an integer below 2^23
+// and accumulates exactly in FP32; groups g >= 10 are below 2^-64 relative and dropped.  The
+// FP64 update is
+//     C_rc -= 2^(e_r + e_c - 2042) sum_g 2^(-8 g) G_g,rc.
+// The groups are packed exactly into two 64-bit integers, hi (g = 2..5) and lo (g = 6..9),
+// each below 2^48, and joined as w = 2^14 hi + floor(lo / 2^18), below 2^62: the dropped
+// part of lo is below 2^-54 of the scale 2^(e_r + e_c - 2042), under the slicing error.  The
+// scaled w is built as an FP64 value on the integer pipe (scaled_int) and subtracted: one
+// FP64 operation per updated entry.  With W = 32 every partial group sum stays below 2^22,
+// so the accumulators start at 1.5 * 2^23, where FP32 holds every integer, and the group is
+// read from the accumulator's bits (no float-to-integer conversion).
+// Within a block the diagonal block is factorised as in the plain loop (8x8 tiles, FP64 tensor
+// path); the rows below it are solved one row tile per warp (block_rows).
 __device__ bool factor_emulated(const SolveCtx& c, const Shared& s, double* A, int Nt, int* s_fail) {
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarps = blockDim.x >> 5;
     const int g = lane >> 2, t = lane & 3;
+    // per CTA: the slices in mma fragment order, [row tile][slice][16-column step kk][lane]
+    // [2 x u32] (lane = 4 g + t holds columns 16 kk + 2t, +1 and 16 kk + 8 + 2t, +1 of row g
+    // of the tile), so that every A or B fragment is one coalesced 8-byte load per lane; then
+    // npad row scales
     uint2* sl = reinterpret_cast<uint2*>(c.ws_e + (int64_t)blockIdx.x * c.ws_e_stride);
+    constexpr int kTS = 7 * kEK * 32;  // uint2 per row tile
+    double* sr = reinterpret_cast<double*>(sl + (int64_t)(c.npad / 8) * kTS);
     double* Tall = emu_tile_inverses(c);  // inverses of all diagonal tiles, for the solves
-    // A_ii = 1 + sigma^2 (padding rows: 1)
-    const int em = (int)((__double_as_longlong(sqrt(fmax(1.0 + c.P.s2, 1.0))) >> 52) & 0x7FF) + 1;
-    const int er = em + 2;  // biased exponent of r
-    static_assert(7 * 8 * kEB * 128 * 128 < (1 << 22), "group sums must stay below 2^22");
-    constexpr float kOff = 12582912.0f;  // 1.5 * 2^23, bits 0x4B400000
-    constexpr long long kOffBits = 0x4B400000ll * 0x01010101ll;
     for (int K0 = 0; K0 < Nt; K0 += kEB) {
-        const int K1 = min(K0 + kEB, Nt), nb = K1 - K0, b = K0 / kEB;
-        if (b > 0) {
-            // updates of tiles (it, jt), K0 <= jt < K1, jt <= it < Nt from blocks 0 .. b - 1; warp
-            // item = 16 rows (tiles i0, i0 + 1, i0 = K0 + 2 bi) x 8 columns (tile jt); row pair 0
-            // has min(nb, 2) items, every later pair nb
-            const int MB = (Nt - K0 + 1) >> 1, c0 = min(nb, 2);
-            const int total = c0 + nb * (MB - 1);
-            for (int p = warp; p < total; p += nwarps) {
-                int bi, jq;
-                if (p < c0) {
-                    bi = 0;
-                    jq = p;
-                } else {
-                    bi = 1 + (p - c0) / nb;
-                    jq = (p - c0) % nb;
-                }
-                const int jt = K0 + jq, i0 = K0 + 2 * bi, i1 = i0 + 1;
-                const bool has1 = i1 < Nt;
-                long long hs[4] = {0, 0, 0, 0}, ls[4] = {0, 0, 0, 0};
-                for (int bp = 0; bp < b; ++bp) {
-                    const int K1p = kEB * (bp + 1);
-                    const uint2* Fp = sl + ((int64_t)bp * Nt - (int64_t)kEB * bp * (bp + 1) / 2) * kTS + lane;
-                    const uint2* fa = Fp + (int64_t)(i0 - K1p) * kTS;  // row tiles i0, i1
-                    const uint2* fb = Fp + (int64_t)(jt - K1p) * kTS;  // column tile jt
-                    float acc[8][4];
-#pragma unroll
-                    for (int q = 0; q < 8; ++q) acc[q][0] = acc[q][1] = acc[q][2] = acc[q][3] = kOff;
-#pragma unroll
-                    for (int kk = 0; kk < kEK; ++kk) {
-                        uint32_t bf[7][2];
-#pragma unroll
-                        for (int tt = 0; tt < 7; ++tt) {
-                            const uint2 v = fb[(tt * kEK + kk) * 32];
-                            bf[tt][0] = v.x;
-                            bf[tt][1] = v.y;
-                        }
-#pragma unroll
-                        for (int ss = 0; ss < 7; ++ss) {
-                            const uint2 va = fa[(ss * kEK + kk) * 32];
-                            const uint2 vb = has1 ? fa[kTS + (ss * kEK + kk) * 32] : make_uint2(0u, 0u);
-                            uint32_t af[4];
-                            af[0] = va.x;
-                            af[1] = vb.x;
-                            af[2] = va.y;
-                            af[3] = vb.y;
-#pragma unroll
-                            for (int tt = 0; tt < 7 && tt + ss < 8; ++tt) mma_bf16(acc[ss + tt], af, bf[tt]);
-                        }
-                    }
-#pragma unroll
-                    for (int ai = 0; ai < 4; ++ai) {  // accumulator bits = G + 0x4B400000
-                        long long gq[8];
-#pragma unroll
-                        for (int q = 0; q < 8; ++q) gq[q] = __float_as_int(acc[q][ai]);
-                        hs[ai] += gq[0] * (1ll << 24) + gq[1] * (1ll << 16) + gq[2] * 256 + gq[3] - kOffBits;
-                        ls[ai] += gq[4] * (1ll << 24) + gq[5] * (1ll << 16) + gq[6] * 256 + gq[7] - kOffBits;
-                    }
-                }
-#pragma unroll
-                for (int half = 0; half < 2; ++half) {
-                    const int it = half ? i1 : i0;
-                    if (it >= Nt || it < jt) continue;  // past the end, or above the diagonal
-                    double* C = A + tix(it, jt);
-#pragma unroll
-                    for (int e = 0; e < 2; ++e) {
-                        const int ai = 2 * half + e;
-                        double* cp = C + te(g, 2 * t + e);
-                        // r^2 2^-40 = 2^(2 er - 1063 - 1023), r^2 2^-72 = 2^(2 er - 1095 - 1023)
-                        *cp = (*cp - scaled_int(hs[ai], 2 * er - 1063)) - scaled_int(ls[ai], 2 * er - 1095);
-                    }
-                }
-            }
-            __syncthreads();
-        }
+        const int K1 = min(K0 + kEB, Nt);
         // the diagonal block: tiles (it, jt), K0 <= jt <= it < K1, right-looking by 8 columns
         for (int kt = K0; kt < K1; ++kt) {
             double* Ti = s.Tblk + 64 * (kt - K0);
@@ -628,13 +546,76 @@ __device__ bool factor_emulated(const SolveCtx& c, const Shared& s, double* A, i
             __syncthreads();
         }
         if (K1 >= Nt) break;
-        // the rows below: one warp per row tile solves its tiles against the diagonal block and
-        // writes their slices (block b's region)
-        uint2* Fb = sl + ((int64_t)b * Nt - (int64_t)kEB * b * (b + 1) / 2) * kTS;
+        // the rows below: one warp per row tile solves its eight tiles against the diagonal
+        // block and writes their slices and row scales
         for (int it = K1 + warp; it < Nt; it += nwarps)
-            block_rows(A, it, K0, s.Tblk, s.Wsc + 64 * warp, Fb + (int64_t)(it - K1) * kTS, em, s_fail);
+            block_rows(A, it, K0, s.Tblk, s.Wsc + 64 * warp, sl + (int64_t)(it - K1) * kTS, sr + 8 * (it - K1));
         __syncthreads();
-        if (*s_fail) return false;
+        // trailing update, warp item = 16 rows (tiles i0, i0 + 1) x 8 columns (tile jt),
+        // K1 <= jt <= i0 + 1; items ordered by row pair bi, with bi (bi + 1) items before bi
+        const int M = Nt - K1, MB = (M + 1) >> 1;
+        const int total = (MB - 1) * MB + min(2 * MB, M);
+        for (int p = warp; p < total; p += nwarps) {
+            int bi = (int)((sqrtf(4.f * (float)p + 1.f) - 1.f) * 0.5f);
+            while (bi > 0 && bi * (bi + 1) > p) --bi;
+            while (bi + 1 < MB && (bi + 1) * (bi + 2) <= p) ++bi;
+            const int jt = K1 + (p - bi * (bi + 1));
+            const int i0 = K1 + 2 * bi, i1 = i0 + 1;
+            const bool has1 = i1 < Nt;
+            const int ra = 16 * bi + g, rb = ra + 8;
+            const uint2* fa = sl + (int64_t)(2 * bi) * kTS + lane;  // row tiles i0, i1
+            const uint2* fb = sl + (int64_t)(jt - K1) * kTS + lane;  // column tile jt
+            static_assert(7 * 8 * kEB * 128 * 128 < (1 << 22), "group sums must stay below 2^22");
+            constexpr float kOff = 12582912.0f;  // 1.5 * 2^23, bits 0x4B400000
+            float acc[8][4];
+#pragma unroll
+            for (int q = 0; q < 8; ++q) acc[q][0] = acc[q][1] = acc[q][2] = acc[q][3] = kOff;
+#pragma unroll
+            for (int kk = 0; kk < kEK; ++kk) {
+                uint32_t bf[7][2];
+#pragma unroll
+                for (int tt = 0; tt < 7; ++tt) {
+                    const uint2 v = fb[(tt * kEK + kk) * 32];
+                    bf[tt][0] = v.x;
+                    bf[tt][1] = v.y;
+                }
+#pragma unroll
+                for (int ss = 0; ss < 7; ++ss) {
+                    const uint2 va = fa[(ss * kEK + kk) * 32];
+                    const uint2 vb = has1 ? fa[kTS + (ss * kEK + kk) * 32] : make_uint2(0u, 0u);
+                    uint32_t af[4];
+                    af[0] = va.x;
+                    af[1] = vb.x;
+                    af[2] = va.y;
+                    af[3] = vb.y;
+#pragma unroll
+                    for (int tt = 0; tt < 7 && tt + ss < 8; ++tt) mma_bf16(acc[ss + tt], af, bf[tt]);
+                }
+            }
+#pragma unroll
+            for (int half = 0; half < 2; ++half) {
+                const int it = half ? i1 : i0;
+                if (it >= Nt || it < jt) continue;  // past the end, or above the diagonal
+                double* C = A + tix(it, jt);
+                // biased exponents of the row scales (0 for a zero row, whose w is 0)
+                const int er = (int)(__double_as_longlong(sr[half ? rb : ra]) >> 52);
+#pragma unroll
+                for (int e = 0; e < 2; ++e) {
+                    const int ai = 2 * half + e, col = 2 * t + e;
+                    const int ec = (int)(__double_as_longlong(sr[8 * (jt - K1) + col]) >> 52);
+                    long long gq[8];  // G + 0x4B400000: the accumulator bits
+#pragma unroll
+                    for (int q = 0; q < 8; ++q) gq[q] = __float_as_int(acc[q][ai]);
+                    constexpr long long kOffBits = 0x4B400000ll * 0x01010101ll;
+                    const long long hi = gq[0] * (1ll << 24) + gq[1] * (1ll << 16) + gq[2] * 256 + gq[3] - kOffBits;
+                    const long long lo = gq[4] * (1ll << 24) + gq[5] * (1ll << 16) + gq[6] * 256 + gq[7] - kOffBits;
+                    // scale 2^(er + ec - 2046) 2^-54 = 2^(eS - 1023)
+                    double* cp = C + te(g, col);
+                    *cp -= scaled_int(hi * (1ll << 14) + (lo >> 18), er + ec - 1077);
+                }
+            }
+        }
+        __syncthreads();
     }
     return true;
 }
@@ -1291,8 +1272,8 @@ SolveKernel pick_solve(bool props, bool emu) {
     return emu ? k_solve_emu<false> : k_solve<false>;
 }
 
-// per-CTA workspace of the emulated factorisation for instances of up to npad points
-int64_t emu_ws_bytes(int npad) { return emu_slice_tiles(npad / 8) * kTS * 8 + (int64_t)(npad / 8) * 64 * 8; }
+// seven bf16 slices of a block's columns, the row scale, and one row of diagonal-tile inverses
+constexpr int64_t kEmuBytesPerRow = 7 * 8 * kEB * 2 + 8 + 64;
 
 }  // namespace
 
@@ -1380,7 +1361,7 @@ bool solve_batch_graph(const SolveBatch& b, const DevParams& P, int* err_dev, cu
         s.grid = (int)std::min<int64_t>(n, (int64_t)n_sm * per_sm);
         if (!s.smem_a) ws_a_need = std::max<int64_t>(ws_a_need, n_tiles(s.npad / 8) * 64 * s.grid);
         if (b.want_var) ws_v_need = std::max<int64_t>(ws_v_need, (int64_t)s.npad * s.threads * s.grid);
-        if (s.emu) ws_e_need = std::max<int64_t>(ws_e_need, emu_ws_bytes(s.npad) * s.grid);
+        if (s.emu) ws_e_need = std::max<int64_t>(ws_e_need, (int64_t)s.npad * kEmuBytesPerRow * s.grid);
     }
     // every buffer exists before the capture starts (allocation is not captured)
     int* hist = (int*)ar.get(Arena::kHist, sizeof(int) * 2 * 1025, st);
@@ -1424,7 +1405,7 @@ bool solve_batch_graph(const SolveBatch& b, const DevParams& P, int* err_dev, cu
         c.ws_a = s.smem_a ? nullptr : ws_a;
         c.ws_v_stride = (int64_t)s.npad * s.threads;
         c.ws_v = ws_v;
-        c.ws_e_stride = s.emu ? emu_ws_bytes(s.npad) : 0;
+        c.ws_e_stride = s.emu ? (int64_t)s.npad * kEmuBytesPerRow : 0;
         c.ws_e = s.emu ? ws_e : nullptr;
         s.kern<<<s.grid, s.threads, s.shm, gs>>>(c);
         note_launch();
@@ -1554,8 +1535,8 @@ int solve_batch(const SolveBatch& b, const DevParams& P, int* err_dev, cudaStrea
             const int threads = emu ? kEmuThreads : c.npad <= 32 ? 64 : c.npad <= 64 ? 128 : c.npad <= 128 ? 256 : 512;
             const size_t shm = smem_bytes(c.npad, c.a_in_smem, b.nprop, c.stage_panel, b.Xi != nullptr, false, emu);
             auto ks = pick_solve(b.nprop > 0, emu);
-            c.ws_e_stride = emu ? emu_ws_bytes(c.npad) : 0;
-            c.ws_e = emu ? (uint8_t*)ar.get(Arena::kWs3, emu_ws_bytes(1024), st) : nullptr;
+            c.ws_e_stride = emu ? (int64_t)c.npad * kEmuBytesPerRow : 0;
+            c.ws_e = emu ? (uint8_t*)ar.get(Arena::kWs3, 1024 * kEmuBytesPerRow, st) : nullptr;
             cudaFuncSetAttribute(ks, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm);
             c.ws_a_stride = c.a_in_smem ? 0 : n_tiles(c.npad / 8) * 64;
             c.ws_a = c.a_in_smem ? nullptr : (double*)ar.get(Arena::kWs0, sizeof(double) * n_tiles(128) * 64, st);
@@ -1620,7 +1601,7 @@ int solve_batch(const SolveBatch& b, const DevParams& P, int* err_dev, cudaStrea
         c.ws_a = c.a_in_smem ? nullptr : (double*)ar.get(Arena::kWs0, sizeof(double) * c.ws_a_stride * grid, st);
         c.ws_v_stride = (int64_t)c.npad * threads;
         c.ws_v = (b.want_var && !bw) ? (double*)ar.get(Arena::kWs1, sizeof(double) * c.ws_v_stride * grid, st) : nullptr;
-        c.ws_e_stride = emu ? emu_ws_bytes(c.npad) : 0;
+        c.ws_e_stride = emu ? (int64_t)c.npad * kEmuBytesPerRow : 0;
         c.ws_e = emu ? (uint8_t*)ar.get(Arena::kWs3, c.ws_e_stride * grid, st) : nullptr;
         cudaEvent_t b0 = nullptr, b1 = nullptr;
         if (profile) {
