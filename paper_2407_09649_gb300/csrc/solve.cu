@@ -399,10 +399,11 @@ __device__ __forceinline__ void slice_row(const double (&x)[2 * kEB], uint2* F, 
         for (int i = 0; i < 4; ++i) {  // columns 16 kk + {2t, 2t + 1, 8 + 2t, 8 + 2t + 1}
             const unsigned long long bits = (unsigned long long)__double_as_longlong(x[4 * kk + i]);
             const int E = (int)((bits >> 52) & 0x7FF);
-            unsigned long long Y = 0;  // |x| 2^(1077 - em), a 55-bit integer
+            unsigned long long Y = 0;  // |x| 2^(1077 - em) rounded to nearest, below 2^55
             if (E > 0 && E < 0x7FF) {  // zero and subnormals slice to zero
                 const int sh = em - E;
-                Y = sh >= 55 ? 0ull : ((((bits & 0xFFFFFFFFFFFFFull) | (1ull << 52)) << 2) >> sh);
+                const unsigned long long M = ((bits & 0xFFFFFFFFFFFFFull) | (1ull << 52)) << 2;
+                Y = sh == 0 ? M : sh >= 56 ? 0ull : ((M >> (sh - 1)) + 1) >> 1;
             }
             // adding 128 to each of the six lower digits lets every digit be read as a byte
             // minus 128; the top digit keeps the rest (0 .. 128)
@@ -486,8 +487,8 @@ __device__ __forceinline__ double* emu_tile_inverses(const SolveCtx& c) {
 // every trailing update C -= P P^T (P: the block's W columns below it) done on the bf16
 // tensor cores to FP64 accuracy.  Each row r of P is written exactly as
 //     P_r = 2^(e_r - 1021) sum_{s=1..7} q_rs 2^(-8 s),   q_rs integer, |q_rs| <= 128,
-// from the bits of its FP64 values aligned to the row's largest biased exponent e_r (bits
-// below 2^-55 of the row maximum are dropped): a 55-bit integer per value, cut into seven
+// from the bits of its FP64 values aligned to the row's largest biased exponent e_r (rounded
+// to nearest at 2^-55 of the row maximum): a 55-bit integer per value, cut into seven
 // balanced base-256 digits (the lower six in [-128, 127], the top one in [0, 128]), each
 // exact in bf16.  A slice product Q_s Q_t^T sums W <= 64 products of at most 2^14, so every
 // group G_g = sum_{s+t=g} Q_s Q_t^T with g <= 9 (at most 7 terms) is an integer below 2^23
@@ -495,8 +496,8 @@ __device__ __forceinline__ double* emu_tile_inverses(const SolveCtx& c) {
 // FP64 update is
 //     C_rc -= 2^(e_r + e_c - 2042) sum_g 2^(-8 g) G_g,rc.
 // The groups are packed exactly into two 64-bit integers, hi (g = 2..5) and lo (g = 6..9),
-// each below 2^48, and joined as w = 2^14 hi + floor(lo / 2^18), below 2^62: the dropped
-// part of lo is below 2^-54 of the scale 2^(e_r + e_c - 2042), under the slicing error.  The
+// and joined as w = 2^16 hi + round(lo / 2^16), below 2^63 because every group stays below
+// 2^22 with W = 32: the rounding of lo is below 2^-57 of the scale 2^(e_r + e_c - 2042).  The
 // scaled w is built as an FP64 value on the integer pipe (scaled_int) and subtracted: one
 // FP64 operation per updated entry.  With W = 32 every partial group sum stays below 2^22,
 // so the accumulators start at 1.5 * 2^23, where FP32 holds every integer, and the group is
@@ -609,9 +610,9 @@ __device__ bool factor_emulated(const SolveCtx& c, const Shared& s, double* A, i
                     constexpr long long kOffBits = 0x4B400000ll * 0x01010101ll;
                     const long long hi = gq[0] * (1ll << 24) + gq[1] * (1ll << 16) + gq[2] * 256 + gq[3] - kOffBits;
                     const long long lo = gq[4] * (1ll << 24) + gq[5] * (1ll << 16) + gq[6] * 256 + gq[7] - kOffBits;
-                    // scale 2^(er + ec - 2046) 2^-54 = 2^(eS - 1023)
+                    // scale 2^(er + ec - 2046) 2^-56 = 2^(eS - 1023)
                     double* cp = C + te(g, col);
-                    *cp -= scaled_int(hi * (1ll << 14) + (lo >> 18), er + ec - 1077);
+                    *cp -= scaled_int(hi * (1ll << 16) + ((lo + (1ll << 15)) >> 16), er + ec - 1079);
                 }
             }
         }
