@@ -43,7 +43,7 @@ def _dist_env():
 # DRAM bytes (read + write) of the N > 224 solve launch of one full 10M-query step, from one
 # single-pass ncu capture of the current kernel at this workload; the four smaller launches
 # (3 % of the solve time) are not included.  Set to None when the kernel changes.
-K_SOLVE_TRAFFIC = None
+K_SOLVE_TRAFFIC = 1.01459e12
 K_SOLVE_TRAFFIC_SOURCE = ("ncu dram__bytes_read.sum + dram__bytes_write.sum, N > 224 launch (k_solve_emu) of the "
                           "full step (1 pass); smaller buckets not included")
 
