@@ -131,3 +131,27 @@ def test_properties_need_n_props(vg):
     pts = torch.zeros((10, 3), device="cuda")
     with pytest.raises(Exception, match="n_props"):
         m.build_frame(pts, props=torch.zeros((10, 1), device="cuda"))
+
+
+def test_properties_with_emulated_updates(vg):
+    """Full leaves (512 occupied voxels each) with two property channels: the property GP
+    factorised with the emulated FP64-accurate updates (N > 224) agrees with the FP64
+    tensor path to the FP64 tolerance."""
+    rng = np.random.default_rng(9)
+    pts = rng.uniform(0.0, 1.6, (60000, 3)).astype(np.float32)
+    props = _props(pts, 2, seed=3)
+    out = {}
+    for emu in (0, 1):
+        m = vg.Map(precision="fp64", max_pts_leaf=512, n_props=2, emulate_fp64=emu)
+        f = m.build_frame(torch.from_numpy(pts).cuda(), props=torch.from_numpy(props).cuda())
+        assert m.stats()["bucket_count"][4] >= 8
+        r = {k: v.cpu().numpy() for k, v in f.results().items()}
+        c, w = (t.cpu().numpy() for t in f.props())
+        out[emu] = _by_key(r["keys"], c, w, r["status"])
+    k0, c0, w0, s0 = out[0]
+    k1, c1, w1, s1 = out[1]
+    assert np.array_equal(k0, k1) and np.array_equal(s0, s1)
+    fin = np.isfinite(w0)
+    assert np.array_equal(np.isfinite(w1), fin) and fin.mean() > 0.9
+    assert np.abs(c1[fin] - c0[fin]).max() <= C_TOL
+    assert np.abs(w1[fin] - w0[fin]).max() <= C_TOL
