@@ -468,8 +468,13 @@ int vgp_gp_batch(vgp_map* m, int64_t n_inst, const int64_t* inst_off_dev, const 
  * before any result is written): at most 65536 instances and 262144 training points per call,
  * at most 64 points per instance.
  *
- * The first call on each device looks up the array's device address and writes a constant
- * table into it with a synchronous copy: make that first call before any stream capture.
+ * The first call on each device looks up the array's device address (cudaGetSymbolAddress,
+ * with that device current) and keeps it for the life of the process: make that first call
+ * before any stream capture, and do not call this entry point on a device after a
+ * cudaDeviceReset of it in the same process (the kept address no longer names the array).
+ * Each call writes a 2 KB constant table into the array on the caller's stream (an
+ * asynchronous copy from host memory, ordered before the kernels that read it).
+ * VGP_ERR_ARG also for offsets that are negative, decrease, or run past the maximum.
  * The call reads two words back from the GPU, so it synchronises the stream.  Every call on a
  * device shares the same array and it keeps the last call's contents; the call clears what
  * must start at zero.  Calls whose GPU work overlaps (several streams or host threads at once)
@@ -479,6 +484,38 @@ int vgp_gp_batch(vgp_map* m, int64_t n_inst, const int64_t* inst_off_dev, const 
 int vgp_gp_batch_static(const vgp_params* p, int64_t n_inst, const int64_t* inst_off_dev, const float* X_dev,
                         const int64_t* q_off_dev, const float* Q_dev, double* d_dev, double* grad_dev,
                         double* var_dev, uint8_t* status_dev, vgp_stream stream);
+
+/*
+ * Diagnostic view of the neighbourhood selection of vgp_query_distance_gradient (Sec. IV-D
+ * with the cap and fallback rules of max_pts_group and max_leaf_search): plans the n queries
+ * exactly as that call does (query leaves, centre leaves, capped 27-leaf neighbourhoods),
+ * solves nothing, and copies the plan to HOST arrays.  Call it once with the four arrays NULL
+ * to get *n_inst and *n_train, then again with arrays of those sizes (the plan is recomputed
+ * and is the same):
+ *   inst_key   [n_inst] centre leaf key of each instance (order unspecified)
+ *   inst_off   [n_inst + 1] offsets of each instance's points in point_idx
+ *   point_idx  [n_train] indices into the points of the last vgp_set_surface (order within an
+ *              instance unspecified)
+ *   q_inst     [n] instance of each query, negative when it has none (bad input or no
+ *              support)
+ * VGP_ERR_STATE before vgp_set_surface.  Synchronises the stream.
+ */
+int vgp_debug_query_plan(vgp_map* m, const float* q_dev, int64_t n, vgp_stream stream, int64_t* n_inst,
+                         int64_t* n_train, uint64_t* inst_key, int64_t* inst_off, int64_t* point_idx,
+                         int32_t* q_inst);
+
+/*
+ * Diagnostic view of the node selection of vgp_query_smooth (Sec. IV-D, Eq. 10): the node GPs
+ * (occupied leaves around the queries' centre leaves, each capped to the max_pts_leaf points
+ * nearest its centre) and the nodes each query blends, copied to HOST arrays; same two-call
+ * protocol and array meanings as vgp_debug_query_plan, with
+ *   node_key   [n_inst] leaf key of each node GP (order unspecified)
+ *   pair_inst  [n][n_nodes] node of each query by rank (nearest first), -1 past the last node
+ * n_nodes in [1, 27].  Synchronises the stream.
+ */
+int vgp_debug_smooth_plan(vgp_map* m, const float* q_dev, int64_t n, int32_t n_nodes, vgp_stream stream,
+                          int64_t* n_inst, int64_t* n_train, uint64_t* node_key, int64_t* inst_off,
+                          int64_t* point_idx, int32_t* pair_inst);
 
 /* Counters of the most recent build_frame / set_surface / query / batch call. */
 int vgp_get_stats(const vgp_map* m, vgp_stats* out);

@@ -98,6 +98,10 @@ def lib():
         L.or_surface_leaves.restype = i64
         L.or_surface_instance.argtypes = [vp, C.c_uint64, vp]
         L.or_surface_instance.restype = i64
+        L.or_query_smooth_nodes.argtypes = [vp, vp, i64, C.c_int, vp]
+        L.or_query_smooth_nodes.restype = C.c_int
+        L.or_surface_leaf_capped.argtypes = [vp, C.c_uint64, C.c_int, vp]
+        L.or_surface_leaf_capped.restype = i64
         L.or_query.argtypes = [vp, vp, i64, C.c_int, vp, vp, vp, vp, vp, vp]
         L.or_query_backward.argtypes = [vp, vp, i64, vp, vp, vp]
         L.or_query_smooth.argtypes = [vp, vp, i64, C.c_int, C.c_double, C.c_int, vp, vp, vp, vp, vp]
@@ -402,6 +406,23 @@ class Surface:
         iN = np.zeros(n, np.int32)
         lib().or_query(self.h, _p(q), n, int(want_var), _p(d), _p(g), _p(v), _p(st), _p(ik), _p(iN))
         return dict(d=d, grad=g, var=v if want_var else None, status=st, inst_key=ik, inst_n=iN)
+
+    def smooth_nodes(self, q, n_nodes: int = 8) -> np.ndarray:
+        """Leaf keys of the nodes each query blends in query_smooth, nearest first, 0 past the
+        last node: (n, n_nodes) uint64."""
+        q = _f32(q)
+        keys = np.zeros((len(q), int(n_nodes)), np.uint64)
+        lib().or_query_smooth_nodes(self.h, _p(q), len(q), int(n_nodes), _p(keys))
+        return keys
+
+    def leaf_capped(self, key: int, cap: int) -> np.ndarray:
+        """Sorted point indices of the node GP of leaf ``key`` (at most ``cap`` points, those
+        nearest the leaf centre)."""
+        L = lib()
+        n = L.or_surface_leaf_capped(self.h, C.c_uint64(int(key)), int(cap), None)
+        out = np.zeros(max(n, 1), np.int64)
+        L.or_surface_leaf_capped(self.h, C.c_uint64(int(key)), int(cap), _p(out))
+        return out[:n]
 
     def query_smooth(self, q, n_nodes: int = 8, lam: float = 100.0, want_var: bool = True):
         """G-GPDF as per-leaf GPs blended by the smooth minimum of Eq. 10."""

@@ -1720,6 +1720,62 @@ static int cmp_node(const void* a, const void* b) {
     return (x->key > y->key) - (x->key < y->key);
 }
 
+/* The nodes of query point xs whose centre leaf is C: the occupied leaves of C's 27-leaf
+ * neighbourhood, nearest first (FP64 squared distance to the leaf centre, ties to the
+ * smaller key), at most Qmax of them, in nc[0 .. return value). */
+static int smooth_select(const or_surface* S, const double xs[3], const int64_t C[3], int Qmax, node_c nc[27]) {
+    int nn = 0;
+    for (int dz = -1; dz <= 1; ++dz)
+        for (int dy = -1; dy <= 1; ++dy)
+            for (int dx = -1; dx <= 1; ++dx) {
+                int64_t F[3] = {C[0] + dx, C[1] + dy, C[2] + dz};
+                uint64_t k = pack_key(F[0], F[1], F[2]);
+                int64_t l = find_key(S->lkey, S->nl, k);
+                if (l < 0) continue;
+                double e2 = 0.0;
+                for (int a = 0; a < 3; ++a) {
+                    double c = ((double)(8 * F[a]) + 3.5) * S->P.voxel_size;
+                    double e = xs[a] - c;
+                    e2 += e * e;
+                }
+                nc[nn].d2 = e2; nc[nn].key = k; nc[nn].l = l; ++nn;
+            }
+    qsort(nc, (size_t)nn, sizeof(node_c), cmp_node);
+    return nn > Qmax ? Qmax : nn;
+}
+
+/* Node choice of or_query_smooth for each query: keys[i * Qmax + t] = leaf key of its node of
+ * rank t, 0 past the last node (and for queries without a centre leaf). */
+int or_query_smooth_nodes(const or_surface* S, const float* q, int64_t n, int Qmax, uint64_t* keys) {
+    for (int64_t i = 0; i < n; ++i) {
+        for (int t = 0; t < Qmax; ++t) keys[i * Qmax + t] = 0;
+        double p[3] = {(double)q[3 * i], (double)q[3 * i + 1], (double)q[3 * i + 2]};
+        int64_t ijk[3], M[3], C[3];
+        int32_t bit;
+        if (!voxel_ijk(p, S->P.voxel_size, ijk)) continue;
+        leaf_of(ijk, M, &bit);
+        if (!centre_leaf(S, M, C)) continue;
+        node_c nc[27];
+        int nn = smooth_select(S, p, C, Qmax, nc);
+        for (int t = 0; t < nn; ++t) keys[i * Qmax + t] = nc[t].key;
+    }
+    return 0;
+}
+
+/* Training points of the node GP of leaf `key` (the leaf's points, at most cap of them, those
+ * nearest the leaf centre), as sorted point indices in out (may be NULL); returns their count,
+ * 0 for an unoccupied leaf. */
+int64_t or_surface_leaf_capped(const or_surface* S, uint64_t key, int cap, int64_t* out) {
+    int64_t l = find_key(S->lkey, S->nl, key);
+    if (l < 0) return 0;
+    int64_t n = S->off[l + 1] - S->off[l];
+    int64_t* tmp = (int64_t*)malloc(sizeof(int64_t) * (n + 1));
+    int64_t m = leaf_points_capped(S, l, cap, tmp);
+    if (out) memcpy(out, tmp, sizeof(int64_t) * m);
+    free(tmp);
+    return m;
+}
+
 int or_query_smooth(const or_surface* S, const float* q, int64_t n, int Qmax, double lambda, int want_var,
                     double* d, double* grad, double* var, uint8_t* status, int32_t* n_nodes) {
     const or_params* P = &S->P;
@@ -1778,25 +1834,7 @@ int or_query_smooth(const or_surface* S, const float* q, int64_t n, int Qmax, do
         }
         double xs[3] = {(double)q[3 * i], (double)q[3 * i + 1], (double)q[3 * i + 2]};
         node_c nc[27];
-        int nn = 0;
-        const int64_t* C = q_c + 3 * i;
-        for (int dz = -1; dz <= 1; ++dz)
-            for (int dy = -1; dy <= 1; ++dy)
-                for (int dx = -1; dx <= 1; ++dx) {
-                    int64_t F[3] = {C[0] + dx, C[1] + dy, C[2] + dz};
-                    uint64_t k = pack_key(F[0], F[1], F[2]);
-                    int64_t l = find_key(S->lkey, S->nl, k);
-                    if (l < 0) continue;
-                    double e2 = 0.0;
-                    for (int a = 0; a < 3; ++a) {
-                        double c = ((double)(8 * F[a]) + 3.5) * P->voxel_size;
-                        double e = xs[a] - c;
-                        e2 += e * e;
-                    }
-                    nc[nn].d2 = e2; nc[nn].key = k; nc[nn].l = l; ++nn;
-                }
-        qsort(nc, (size_t)nn, sizeof(node_c), cmp_node);
-        if (nn > Qmax) nn = Qmax;
+        int nn = smooth_select(S, xs, q_c + 3 * i, Qmax, nc);
         double dq[27], vq[27], gq[27][3];
         int stq[27];
         int n_ok = 0, first_status = ST_NO_SUPPORT;

@@ -289,6 +289,42 @@ class Map:
                                           _ptr(s), _stream()))
         return dict(d=d, grad=g, var=v, status=s)
 
+    def debug_query_plan(self, q) -> dict:
+        """Selection of vgp_query_distance_gradient for these queries (vgp_debug_query_plan):
+        ``inst_key`` (centre leaf per instance), ``inst_off`` / ``point_idx`` (surface point
+        indices per instance) and ``q_inst`` (instance per query, negative if none)."""
+        q = _dev_f32(q, "q")
+        lib = L.load()
+        ni, T = C.c_int64(), C.c_int64()
+        L.check(lib.vgp_debug_query_plan(self._h, _ptr(q), q.shape[0], _stream(), C.byref(ni), C.byref(T),
+                                         None, None, None, None))
+        key = np.zeros(ni.value, np.uint64)
+        off = np.zeros(ni.value + 1, np.int64)
+        idx = np.zeros(T.value, np.int64)
+        qi = np.zeros(q.shape[0], np.int32)
+        h = lambda a: a.ctypes.data_as(C.c_void_p)  # noqa: E731
+        L.check(lib.vgp_debug_query_plan(self._h, _ptr(q), q.shape[0], _stream(), C.byref(ni), C.byref(T), h(key),
+                                         h(off), h(idx), h(qi)))
+        return dict(inst_key=key, inst_off=off, point_idx=idx, q_inst=qi)
+
+    def debug_smooth_plan(self, q, n_nodes: int = 8) -> dict:
+        """Node selection of vgp_query_smooth (vgp_debug_smooth_plan): ``node_key``,
+        ``inst_off`` / ``point_idx`` per node GP, and ``pair_inst`` (n, n_nodes) nodes of each
+        query nearest first, -1 past the last."""
+        q = _dev_f32(q, "q")
+        lib = L.load()
+        ni, T = C.c_int64(), C.c_int64()
+        L.check(lib.vgp_debug_smooth_plan(self._h, _ptr(q), q.shape[0], int(n_nodes), _stream(), C.byref(ni),
+                                          C.byref(T), None, None, None, None))
+        key = np.zeros(ni.value, np.uint64)
+        off = np.zeros(ni.value + 1, np.int64)
+        idx = np.zeros(T.value, np.int64)
+        pi = np.zeros((q.shape[0], int(n_nodes)), np.int32)
+        h = lambda a: a.ctypes.data_as(C.c_void_p)  # noqa: E731
+        L.check(lib.vgp_debug_smooth_plan(self._h, _ptr(q), q.shape[0], int(n_nodes), _stream(), C.byref(ni),
+                                          C.byref(T), h(key), h(off), h(idx), h(pi)))
+        return dict(node_key=key, inst_off=off, point_idx=idx, pair_inst=pi)
+
     def autotune(self, q) -> dict:
         """Pick the fastest launch shape per size bucket on these queries (vgp_autotune)."""
         q = _dev_f32(q, "q")

@@ -192,8 +192,16 @@ static int check_err(vgp_map* m, const char* where) {
     if (e & kErrTableFull) return fail(VGP_ERR_TABLE_FULL, "%s: hash table full", where);
     if (e & kErrTimeout) return fail(VGP_ERR_TIMEOUT, "%s: device loop limit reached", where);
     if (e & kErrCapacity) return fail(VGP_ERR_OOM, "%s: internal buffer bound exceeded", where);
+    if (e & kErrAlloc) return fail(VGP_ERR_OOM, "%s: device allocation of a solve workspace failed", where);
     if (e & kErrLaunch) return fail(VGP_ERR_CUDA, "%s: CUDA graph capture, instantiation or launch failed", where);
     return VGP_OK;
+}
+
+// The ABI error code of a solve_batch return value.
+static int solve_status(int rc, const char* where) {
+    if (rc == 0) return VGP_OK;
+    if (rc == -2) return fail(VGP_ERR_OOM, "%s: device allocation of a solve workspace failed", where);
+    return fail(VGP_ERR_CUDA, "%s: CUDA graph capture, instantiation or launch failed", where);
 }
 
 #define TRY(expr)                 \
@@ -537,7 +545,9 @@ int vgp_build_frame_props(vgp_map* m, const float* pts, const float* props, int6
     b.want_var = 1;
     SolveStats ss;
     b.max_n = P.cap_leaf;
-    solve_batch(b, P, m->dev_words, st, m->ar, &ss, nullptr, m->prm.profile != 0, m->prm.launch, &m->cfg, &m->gcache);
+    if (solve_batch(b, P, m->dev_words, st, m->ar, &ss, nullptr, m->prm.profile != 0, m->prm.launch, &m->cfg,
+                    &m->gcache) == -2)
+        return bail(VGP_ERR_OOM, "device allocation of a solve workspace failed");
     if (origin) frame_orphans_and_sign(f->ntest, n_assigned, gsign, f->d, f->grad, f->v, f->status, st);
     // 6. surface properties (Eq. 6): voxel-mean properties as targets of a second GP per leaf
     // with noise sigma_prop, inferred at the same testing voxels through the same nodes
@@ -569,7 +579,9 @@ int vgp_build_frame_props(vgp_map* m, const float* pts, const float* props, int6
         DevParams Pp = P;
         Pp.s2 = P.s2p;
         pb.max_n = P.cap_leaf;
-        solve_batch(pb, Pp, m->dev_words, st, m->ar, nullptr, nullptr, false, m->prm.launch, &m->cfg, &m->gcache);
+        if (solve_batch(pb, Pp, m->dev_words, st, m->ar, nullptr, nullptr, false, m->prm.launch, &m->cfg,
+                        &m->gcache) == -2)
+            return bail(VGP_ERR_OOM, "device allocation of a solve workspace failed");
     }
     if (read_words(m, st) != VGP_OK) return bail(VGP_ERR_CUDA, "sync failed");
     if (check_err(m, "vgp_build_frame") != VGP_OK) {
@@ -1189,6 +1201,8 @@ struct QueryPlan {
     int64_t n = 0;
     int ni = 0, ng = 0;
     int64_t T = 0;
+    uint64_t* ikeys = nullptr;   // centre leaf key of each instance
+    int32_t* q_inst = nullptr;   // instance of each query (< 0: none)
     int64_t* inst_off = nullptr;
     double* Xl = nullptr;
     float* Xf = nullptr;
@@ -1291,6 +1305,8 @@ static int plan_queries(vgp_map* m, const float* q, int64_t n, double* d, double
     int64_t* qidx = (int64_t*)m->ar.get(Arena::kWs2, sizeof(int64_t) * std::max<int64_t>(n, 1), st);
     if (!qidx) return fail(VGP_ERR_OOM, "query index allocation failed");
     query_scatter(q_inst, n, q_off, inst_qcnt, qidx, d, grad, var, status, st);
+    Q.ikeys = ikeys;
+    Q.q_inst = q_inst;
     Q.inst_off = inst_off;
     Q.Xl = Xl;
     Q.Xf = Xf;
@@ -1301,71 +1317,28 @@ static int plan_queries(vgp_map* m, const float* q, int64_t n, double* d, double
     return VGP_OK;
 }
 
-int vgp_query_distance_gradient(vgp_map* m, const float* q, int64_t n, double* d, double* grad, double* var,
-                                uint8_t* status, vgp_stream stream) {
-    if (!m || n < 0 || (n > 0 && (!q || !d))) return fail(VGP_ERR_ARG, "vgp_query_distance_gradient: bad argument");
-    if (!m->has_surface) return fail(VGP_ERR_STATE, "vgp_query_distance_gradient before vgp_set_surface");
-    if (n >= (1ll << 31)) return fail(VGP_ERR_ARG, "at most 2^31 - 1 queries per call");
-    if (n == 0) return VGP_OK;
-    cudaStream_t st = (cudaStream_t)stream;
-    QueryPlan Q;
-    TRY(plan_queries(m, q, n, d, grad, var, status, st, Q));
-    SolveBatch b;
-    b.n_inst = Q.ni;
-    b.inst_off = Q.inst_off;
-    b.Xl = Q.Xl;
-    b.Xf = Q.Xf;
-    b.centre = Q.centre;
-    b.q_off = Q.q_off;
-    b.qidx = Q.qidx;
-    b.qxyz = q;
-    b.d = d;
-    b.grad = grad;
-    b.var = var;
-    b.status = status;
-    b.want_var = var != nullptr;
-    SolveStats ss;
-    b.max_n = m->P.cap_group;
-    if (solve_batch(b, m->P, m->dev_words, st, m->ar, &ss, nullptr, m->prm.profile != 0, m->prm.launch, &m->cfg,
-                    &m->gcache) != 0)
-        return fail(VGP_ERR_CUDA, "query: CUDA graph capture, instantiation or launch failed");
-    CUDA_TRY(cudaGetLastError());
-    vgp_stats S{};
-    S.n_points = m->s_n;
-    S.n_leaves = m->s_nl;
-    S.n_instances = Q.ni;
-    S.n_train = Q.T;
-    S.n_queries = n;
-    S.n_groups = Q.ng;
-    for (int i = 0; i < 5; ++i) S.bucket_count[i] = ss.bucket_count[i];
-    S.sum_n3 = ss.sum_n3;
-    S.sum_n2 = ss.sum_n2;
-    S.t_solve_ms = ss.t_solve_ms;
-    for (int i = 0; i < 5; ++i) {
-        S.t_bucket_ms[i] = ss.t_bucket_ms[i];
-        S.cfg_threads[i] = m->cfg.threads[i];
-        S.cfg_per_sm[i] = m->cfg.per_sm[i];
-    }
-    S.cfg_stage_panel = m->cfg.stage_panel;
-    S.graph_replays = m->gcache.replays;
-    S.graph_instantiations = m->gcache.instantiations;
-    S.grid_leaves = m->g_leaves;
-    S.grid_capacity_leaves = m->pool_cap;
-    m->stats = S;
-    return VGP_OK;
-}
-
-int vgp_query_smooth(vgp_map* m, const float* q, int64_t n, int32_t n_nodes, double lambda, double* d, double* grad,
-                     double* var, uint8_t* status, vgp_stream stream) {
-    if (!m || n < 0 || (n > 0 && (!q || !d))) return fail(VGP_ERR_ARG, "vgp_query_smooth: bad argument");
-    if (n_nodes < 1 || n_nodes > 27) return fail(VGP_ERR_ARG, "vgp_query_smooth: n_nodes must be in [1, 27]");
-    if (!(lambda > 0.0) || !std::isfinite(lambda)) return fail(VGP_ERR_ARG, "vgp_query_smooth: lambda must be > 0");
-    if (!m->has_surface) return fail(VGP_ERR_STATE, "vgp_query_smooth before vgp_set_surface");
-    if (n == 0) return VGP_OK;
-    if (n * n_nodes >= (1ll << 31)) return fail(VGP_ERR_ARG, "vgp_query_smooth: queries x nodes must be < 2^31");
-    cudaStream_t st = (cudaStream_t)stream;
-    const DevParams& P = m->P;
+// Plan of a blended per-leaf G-GPDF call (Eq. 10): the node GPs (one per occupied leaf around
+// the groups' centre leaves, capped to the points nearest the leaf centre) and the (query,
+// node) pairs, pair id = query * n_nodes + rank, grouped by node.
+struct SmoothPlan {
     GroupPlan G;
+    int ni = 0;
+    int64_t T = 0;
+    uint64_t* ikeys = nullptr;     // node leaf key per instance
+    int64_t* inst_off = nullptr;
+    double* Xl = nullptr;
+    float* Xf = nullptr;
+    double* centre = nullptr;
+    int64_t* gidx = nullptr;
+    int32_t* pair_inst = nullptr;  // [n * n_nodes] node instance per (query, rank), -1 if none
+    uint8_t* nn = nullptr;         // [n] nodes per query
+    int64_t* q_off = nullptr;
+    int64_t* qidx = nullptr;
+};
+
+static int plan_smooth(vgp_map* m, const float* q, int64_t n, int n_nodes, cudaStream_t st, SmoothPlan& SP) {
+    const DevParams& P = m->P;
+    GroupPlan& G = SP.G;
     TRY(plan_groups(m, q, n, st, G));
     // nodes: every occupied leaf around each group's centre leaf
     Table it;
@@ -1404,6 +1377,109 @@ int vgp_query_smooth(vgp_map* m, const float* q, int64_t n, int32_t n_nodes, dou
     ARENA(q_off, int64_t, kTmp16, ni + 1);
     ARENA(cursor, int64_t, kTmp17, ni + 1);
     ARENA(qidx, int64_t, kPair2, np);
+    CUDA_TRY(cudaMemsetAsync(cnt, 0, sizeof(int64_t) * (ni + 1), st));
+    CUDA_TRY(cudaMemsetAsync(cursor, 0, sizeof(int64_t) * (ni + 1), st));
+    smooth_pairs(q, n, G.q_slot, G.slot2group, G.gcen, m->s_tab, it, islot2inst, P, n_nodes, pair_inst, nn, cnt, st);
+    exclusive_scan_i64(cnt, q_off, ni, st, m->ar);
+    smooth_scatter(pair_inst, np, q_off, cursor, qidx, st);
+    SP.ni = ni;
+    SP.T = T;
+    SP.ikeys = ikeys;
+    SP.inst_off = inst_off;
+    SP.Xl = Xl;
+    SP.Xf = Xf;
+    SP.centre = centre;
+    SP.gidx = gidx;
+    SP.pair_inst = pair_inst;
+    SP.nn = nn;
+    SP.q_off = q_off;
+    SP.qidx = qidx;
+    return VGP_OK;
+}
+
+// Copy an instance table (keys, CSR offsets, global point indices) and a per-query int32 array
+// to host memory (any pointer may be null), then wait for the copies.
+static int copy_plan_out(const uint64_t* ikeys, const int64_t* inst_off, const int64_t* gidx, int64_t ni, int64_t T,
+                         const int32_t* qa, int64_t nqa, uint64_t* key_h, int64_t* off_h, int64_t* idx_h,
+                         int32_t* qa_h, cudaStream_t st) {
+    if (key_h && ni) CUDA_TRY(cudaMemcpyAsync(key_h, ikeys, sizeof(uint64_t) * ni, cudaMemcpyDeviceToHost, st));
+    if (off_h) CUDA_TRY(cudaMemcpyAsync(off_h, inst_off, sizeof(int64_t) * (ni + 1), cudaMemcpyDeviceToHost, st));
+    if (idx_h && T) CUDA_TRY(cudaMemcpyAsync(idx_h, gidx, sizeof(int64_t) * T, cudaMemcpyDeviceToHost, st));
+    if (qa_h && nqa) CUDA_TRY(cudaMemcpyAsync(qa_h, qa, sizeof(int32_t) * nqa, cudaMemcpyDeviceToHost, st));
+    CUDA_TRY(cudaStreamSynchronize(st));
+    return VGP_OK;
+}
+
+int vgp_query_distance_gradient(vgp_map* m, const float* q, int64_t n, double* d, double* grad, double* var,
+                                uint8_t* status, vgp_stream stream) {
+    if (!m || n < 0 || (n > 0 && (!q || !d))) return fail(VGP_ERR_ARG, "vgp_query_distance_gradient: bad argument");
+    if (!m->has_surface) return fail(VGP_ERR_STATE, "vgp_query_distance_gradient before vgp_set_surface");
+    if (n >= (1ll << 31)) return fail(VGP_ERR_ARG, "at most 2^31 - 1 queries per call");
+    if (n == 0) return VGP_OK;
+    cudaStream_t st = (cudaStream_t)stream;
+    QueryPlan Q;
+    TRY(plan_queries(m, q, n, d, grad, var, status, st, Q));
+    SolveBatch b;
+    b.n_inst = Q.ni;
+    b.inst_off = Q.inst_off;
+    b.Xl = Q.Xl;
+    b.Xf = Q.Xf;
+    b.centre = Q.centre;
+    b.q_off = Q.q_off;
+    b.qidx = Q.qidx;
+    b.qxyz = q;
+    b.d = d;
+    b.grad = grad;
+    b.var = var;
+    b.status = status;
+    b.want_var = var != nullptr;
+    SolveStats ss;
+    b.max_n = m->P.cap_group;
+    TRY(solve_status(solve_batch(b, m->P, m->dev_words, st, m->ar, &ss, nullptr, m->prm.profile != 0,
+                                 m->prm.launch, &m->cfg, &m->gcache),
+                     "query"));
+    CUDA_TRY(cudaGetLastError());
+    vgp_stats S{};
+    S.n_points = m->s_n;
+    S.n_leaves = m->s_nl;
+    S.n_instances = Q.ni;
+    S.n_train = Q.T;
+    S.n_queries = n;
+    S.n_groups = Q.ng;
+    for (int i = 0; i < 5; ++i) S.bucket_count[i] = ss.bucket_count[i];
+    S.sum_n3 = ss.sum_n3;
+    S.sum_n2 = ss.sum_n2;
+    S.t_solve_ms = ss.t_solve_ms;
+    for (int i = 0; i < 5; ++i) {
+        S.t_bucket_ms[i] = ss.t_bucket_ms[i];
+        S.cfg_threads[i] = m->cfg.threads[i];
+        S.cfg_per_sm[i] = m->cfg.per_sm[i];
+    }
+    S.cfg_stage_panel = m->cfg.stage_panel;
+    S.graph_replays = m->gcache.replays;
+    S.graph_instantiations = m->gcache.instantiations;
+    S.grid_leaves = m->g_leaves;
+    S.grid_capacity_leaves = m->pool_cap;
+    m->stats = S;
+    return VGP_OK;
+}
+
+int vgp_query_smooth(vgp_map* m, const float* q, int64_t n, int32_t n_nodes, double lambda, double* d, double* grad,
+                     double* var, uint8_t* status, vgp_stream stream) {
+    if (!m || n < 0 || (n > 0 && (!q || !d))) return fail(VGP_ERR_ARG, "vgp_query_smooth: bad argument");
+    if (n_nodes < 1 || n_nodes > 27) return fail(VGP_ERR_ARG, "vgp_query_smooth: n_nodes must be in [1, 27]");
+    if (!(lambda > 0.0) || !std::isfinite(lambda)) return fail(VGP_ERR_ARG, "vgp_query_smooth: lambda must be > 0");
+    if (!m->has_surface) return fail(VGP_ERR_STATE, "vgp_query_smooth before vgp_set_surface");
+    if (n == 0) return VGP_OK;
+    if (n * n_nodes >= (1ll << 31)) return fail(VGP_ERR_ARG, "vgp_query_smooth: queries x nodes must be < 2^31");
+    cudaStream_t st = (cudaStream_t)stream;
+    const DevParams& P = m->P;
+    SmoothPlan SP;
+    TRY(plan_smooth(m, q, n, n_nodes, st, SP));
+    const GroupPlan& G = SP.G;
+    const int ni = SP.ni;
+    const int64_t T = SP.T;
+    const int64_t np = n * n_nodes;
     ARENA(pd, double, kPair3, np);
     ARENA(pg, double, kPair4, 3 * np);
     ARENA(ps, uint8_t, kPair5, np);
@@ -1412,20 +1488,15 @@ int vgp_query_smooth(vgp_map* m, const float* q, int64_t n, int32_t n_nodes, dou
         pv = (double*)m->ar.get(Arena::kPair6, sizeof(double) * np, st);
         if (!pv) return fail(VGP_ERR_OOM, "device allocation failed");
     }
-    CUDA_TRY(cudaMemsetAsync(cnt, 0, sizeof(int64_t) * (ni + 1), st));
-    CUDA_TRY(cudaMemsetAsync(cursor, 0, sizeof(int64_t) * (ni + 1), st));
-    smooth_pairs(q, n, G.q_slot, G.slot2group, G.gcen, m->s_tab, it, islot2inst, P, n_nodes, pair_inst, nn, cnt, st);
-    exclusive_scan_i64(cnt, q_off, ni, st, m->ar);
-    smooth_scatter(pair_inst, np, q_off, cursor, qidx, st);
     CUDA_TRY(cudaMemsetAsync(ps, 0xFF, np, st));
     SolveBatch b;
     b.n_inst = ni;
-    b.inst_off = inst_off;
-    b.Xl = Xl;
-    b.Xf = Xf;
-    b.centre = centre;
-    b.q_off = q_off;
-    b.qidx = qidx;
+    b.inst_off = SP.inst_off;
+    b.Xl = SP.Xl;
+    b.Xf = SP.Xf;
+    b.centre = SP.centre;
+    b.q_off = SP.q_off;
+    b.qidx = SP.qidx;
     b.qdiv = n_nodes;
     b.qxyz = q;
     b.d = pd;
@@ -1435,10 +1506,10 @@ int vgp_query_smooth(vgp_map* m, const float* q, int64_t n, int32_t n_nodes, dou
     b.want_var = var != nullptr;
     SolveStats ss;
     b.max_n = P.cap_leaf;
-    if (solve_batch(b, P, m->dev_words, st, m->ar, &ss, nullptr, m->prm.profile != 0, m->prm.launch, &m->cfg,
-                    &m->gcache) != 0)
-        return fail(VGP_ERR_CUDA, "vgp_query_smooth: CUDA graph capture, instantiation or launch failed");
-    smooth_blend(n, n_nodes, G.q_slot, nn, pd, pg, pv, ps, lambda, P, d, grad, var, status, st);
+    TRY(solve_status(solve_batch(b, P, m->dev_words, st, m->ar, &ss, nullptr, m->prm.profile != 0, m->prm.launch,
+                                 &m->cfg, &m->gcache),
+                     "vgp_query_smooth"));
+    smooth_blend(n, n_nodes, G.q_slot, SP.nn, pd, pg, pv, ps, lambda, P, d, grad, var, status, st);
     CUDA_TRY(cudaGetLastError());
     vgp_stats S{};
     S.n_points = m->s_n;
@@ -1463,6 +1534,43 @@ int vgp_query_smooth(vgp_map* m, const float* q, int64_t n, int32_t n_nodes, dou
     S.grid_capacity_leaves = m->pool_cap;
     m->stats = S;
     return VGP_OK;
+}
+
+int vgp_debug_query_plan(vgp_map* m, const float* q, int64_t n, vgp_stream stream, int64_t* n_inst, int64_t* n_train,
+                         uint64_t* inst_key, int64_t* inst_off, int64_t* point_idx, int32_t* q_inst) {
+    if (!m || n < 0 || (n > 0 && !q) || !n_inst || !n_train) return fail(VGP_ERR_ARG, "vgp_debug_query_plan: bad argument");
+    if (!m->has_surface) return fail(VGP_ERR_STATE, "vgp_debug_query_plan before vgp_set_surface");
+    if (n >= (1ll << 31)) return fail(VGP_ERR_ARG, "at most 2^31 - 1 queries per call");
+    *n_inst = 0;
+    *n_train = 0;
+    if (n == 0) return VGP_OK;
+    cudaStream_t st = (cudaStream_t)stream;
+    double* dtmp = (double*)m->ar.get(Arena::kBw0, sizeof(double) * n, st);
+    if (!dtmp) return fail(VGP_ERR_OOM, "allocation failed");
+    QueryPlan Q;
+    TRY(plan_queries(m, q, n, dtmp, nullptr, nullptr, nullptr, st, Q));
+    *n_inst = Q.ni;
+    *n_train = Q.T;
+    return copy_plan_out(Q.ikeys, Q.inst_off, Q.gidx, Q.ni, Q.T, Q.q_inst, n, inst_key, inst_off, point_idx, q_inst, st);
+}
+
+int vgp_debug_smooth_plan(vgp_map* m, const float* q, int64_t n, int32_t n_nodes, vgp_stream stream, int64_t* n_inst,
+                          int64_t* n_train, uint64_t* node_key, int64_t* inst_off, int64_t* point_idx,
+                          int32_t* pair_inst) {
+    if (!m || n < 0 || (n > 0 && !q) || !n_inst || !n_train) return fail(VGP_ERR_ARG, "vgp_debug_smooth_plan: bad argument");
+    if (n_nodes < 1 || n_nodes > 27) return fail(VGP_ERR_ARG, "vgp_debug_smooth_plan: n_nodes must be in [1, 27]");
+    if (!m->has_surface) return fail(VGP_ERR_STATE, "vgp_debug_smooth_plan before vgp_set_surface");
+    if (n * n_nodes >= (1ll << 31)) return fail(VGP_ERR_ARG, "vgp_debug_smooth_plan: queries x nodes must be < 2^31");
+    *n_inst = 0;
+    *n_train = 0;
+    if (n == 0) return VGP_OK;
+    cudaStream_t st = (cudaStream_t)stream;
+    SmoothPlan SP;
+    TRY(plan_smooth(m, q, n, n_nodes, st, SP));
+    *n_inst = SP.ni;
+    *n_train = SP.T;
+    return copy_plan_out(SP.ikeys, SP.inst_off, SP.gidx, SP.ni, SP.T, SP.pair_inst, n * n_nodes, node_key, inst_off,
+                         point_idx, pair_inst, st);
 }
 
 int vgp_autotune(vgp_map* m, const float* q, int64_t n, vgp_stream stream) {
@@ -1504,8 +1612,8 @@ int vgp_autotune(vgp_map* m, const float* q, int64_t n, vgp_stream stream) {
         cfg.stage_panel = cand_s[c];
         // each candidate twice, the faster run counts
         SolveStats s1, s2;
-        solve_batch(b, m->P, m->dev_words, st, m->ar, &s1, nullptr, true, 0, &cfg);
-        solve_batch(b, m->P, m->dev_words, st, m->ar, &s2, nullptr, true, 0, &cfg);
+        TRY(solve_status(solve_batch(b, m->P, m->dev_words, st, m->ar, &s1, nullptr, true, 0, &cfg), "vgp_autotune"));
+        TRY(solve_status(solve_batch(b, m->P, m->dev_words, st, m->ar, &s2, nullptr, true, 0, &cfg), "vgp_autotune"));
         CUDA_TRY(cudaGetLastError());
         SolveStats ss = s1;
         for (int i = 0; i < 5; ++i) ss.t_bucket_ms[i] = std::min(s1.t_bucket_ms[i], s2.t_bucket_ms[i]);
@@ -1574,7 +1682,8 @@ int vgp_query_backward(vgp_map* m, const float* q, int64_t n, const double* dL_d
     bw.dL_dq = dL_dq;
     bw.dL_dX = dL_dX;
     bw.obar = obar;
-    solve_batch(b, m->P, m->dev_words, st, m->ar, nullptr, &bw, false, 0, &m->cfg);
+    TRY(solve_status(solve_batch(b, m->P, m->dev_words, st, m->ar, nullptr, &bw, false, 0, &m->cfg),
+                     "vgp_query_backward"));
     CUDA_TRY(cudaStreamSynchronize(st));
     CUDA_TRY(cudaGetLastError());
     return VGP_OK;
@@ -1672,9 +1781,9 @@ extern "C" int vgp_gp_batch(vgp_map* m, int64_t n_inst, const int64_t* inst_off,
     b.status = status;
     b.want_var = var != nullptr;
     SolveStats ss;
-    if (solve_batch(b, m->P, m->dev_words, st, m->ar, &ss, nullptr, m->prm.profile != 0, m->prm.launch, &m->cfg,
-                    &m->gcache) != 0)
-        return fail(VGP_ERR_CUDA, "vgp_gp_batch: CUDA graph capture, instantiation or launch failed");
+    TRY(solve_status(solve_batch(b, m->P, m->dev_words, st, m->ar, &ss, nullptr, m->prm.profile != 0,
+                                 m->prm.launch, &m->cfg, &m->gcache),
+                     "vgp_gp_batch"));
     CUDA_TRY(cudaGetLastError());
     vgp_stats S{};
     S.n_instances = n_inst;

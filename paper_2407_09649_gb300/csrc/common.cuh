@@ -21,7 +21,8 @@ enum : int {
     kErrTimeout = 2,
     kErrCapacity = 4,   // an internal buffer bound was exceeded
     kErrFactor = 8,
-    kErrLaunch = 16     // a graph capture, instantiation or launch failed
+    kErrLaunch = 16,    // a graph capture, instantiation or launch failed
+    kErrAlloc = 32      // a solve workspace could not be allocated (nothing was launched)
 };
 
 // Run-time parameters, expanded once on the host.

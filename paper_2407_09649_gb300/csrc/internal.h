@@ -111,8 +111,9 @@ void graph_cache_destroy(GraphCache& gc);
 // Solve every instance of the batch (factorise, alpha, evaluate its queries).  Returns
 // error bits through *err_dev.  Synchronises once to read the size histogram (in graph mode
 // the histogram is planned on the device and read once at the end, for the statistics).
-// Returns 0, or -1 when graph capture, instantiation or launch failed (kErrLaunch is then
-// also set in *err_dev).
+// Returns 0; -1 when graph capture, instantiation or launch failed (kErrLaunch is then also
+// set in *err_dev); -2 when a workspace could not be allocated (kErrAlloc is set in *err_dev
+// and no solve kernel was launched).
 int solve_batch(const SolveBatch& b, const DevParams& P, int* err_dev, cudaStream_t st,
                  Arena& ar, SolveStats* stats, const BackwardBatch* bw = nullptr, bool profile = false,
                  int launch = 0, const SolveConfig* cfg = nullptr, GraphCache* gc = nullptr);

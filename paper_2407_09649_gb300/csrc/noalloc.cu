@@ -51,8 +51,18 @@ int fail(int code, const char* fmt, ...) {
     return code;
 }
 
-// Device address of the scratch array on the current device; the first call on a device also
-// writes the constant table into it (a synchronous copy).
+// 2^(j/256), j = 0..255, for the FP64 table exponential; written into the scratch array on the
+// caller's stream by every call (stream-ordered, so no stream can read it half written).
+struct ExpTable {
+    double v[256];
+    ExpTable() {
+        for (int j = 0; j < 256; ++j) v[j] = (double)exp2l((long double)j / 256.0L);
+    }
+};
+const ExpTable g_tab;
+
+// Device address of the scratch array on the current device, looked up once per device (the
+// first call on that device) with that device current.
 int scratch_address(unsigned char** out) {
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
@@ -64,17 +74,18 @@ int scratch_address(unsigned char** out) {
         e = cudaGetSymbolAddress(&p, g_scratch);
         if (e != cudaSuccess || !p)
             return fail(VGP_ERR_CUDA, "vgp_gp_batch_static: cudaGetSymbolAddress: %s", cudaGetErrorString(e));
-        double tab[256];
-        for (int j = 0; j < 256; ++j) tab[j] = (double)exp2l((long double)j / 256.0L);
-        e = cudaMemcpy((unsigned char*)p + kOffTab, tab, sizeof(tab), cudaMemcpyHostToDevice);
-        if (e != cudaSuccess) return fail(VGP_ERR_CUDA, "vgp_gp_batch_static: table copy: %s", cudaGetErrorString(e));
         g_ptr[dev] = (unsigned char*)p;
     }
     *out = g_ptr[dev];
     return VGP_OK;
 }
 
-// Warp per instance: size check, bounding-box centre, local coordinates, identity order.
+// error bits of k_static_prep
+constexpr int kBadOffsets = 1;  // inst_off[I] < 0, inst_off[I+1] < inst_off[I], or beyond kMaxPoints
+constexpr int kTooLarge = 2;    // an instance with more than kMaxN points
+
+// Warp per instance: offset and size checks, bounding-box centre, local coordinates, identity
+// order.  A rejected instance writes nothing into the scratch array.
 __global__ void k_static_prep(const int64_t* inst_off, int64_t n_inst, const float* X, double* Xl, float* Xf,
                               double* centre, int32_t* order, int* err) {
     const int64_t I = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
@@ -82,8 +93,12 @@ __global__ void k_static_prep(const int64_t* inst_off, int64_t n_inst, const flo
     if (I >= n_inst) return;
     const int64_t b = inst_off[I], e = inst_off[I + 1];
     if (lane == 0) order[I] = (int32_t)I;
-    if (e < b || e - b > kMaxN || e > kMaxPoints) {
-        if (lane == 0) atomicOr(err, 1);
+    if (b < 0 || e < b || e > kMaxPoints) {
+        if (lane == 0) atomicOr(err, kBadOffsets);
+        return;
+    }
+    if (e - b > kMaxN) {
+        if (lane == 0) atomicOr(err, kTooLarge);
         return;
     }
     float lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
@@ -145,6 +160,8 @@ extern "C" int vgp_gp_batch_static(const vgp_params* p, int64_t n_inst, const in
     int32_t* order = (int32_t*)(base + kOffOrder);
     double* V = (double*)(base + kOffV);
     e = cudaMemsetAsync(words, 0, 2 * sizeof(int), st);  // work counter and error word start at zero
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(base + kOffTab, g_tab.v, sizeof(g_tab.v), cudaMemcpyHostToDevice, st);
     if (e != cudaSuccess) return fail(VGP_ERR_CUDA, "vgp_gp_batch_static: %s", cudaGetErrorString(e));
     k_static_prep<<<(unsigned)((n_inst * 32 + 255) / 256), 256, 0, st>>>(inst_off, n_inst, X, Xl, Xf, centre, order,
                                                                           words + 1);
@@ -153,6 +170,9 @@ extern "C" int vgp_gp_batch_static(const vgp_params* p, int64_t n_inst, const in
     e = cudaMemcpyAsync(&h_err, words + 1, sizeof(int), cudaMemcpyDeviceToHost, st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     if (e != cudaSuccess) return fail(VGP_ERR_CUDA, "vgp_gp_batch_static: %s", cudaGetErrorString(e));
+    if (h_err & kBadOffsets)
+        return fail(VGP_ERR_ARG, "vgp_gp_batch_static: inst_off is negative, decreasing or beyond %lld points",
+                    (long long)kMaxPoints);
     if (h_err) return fail(VGP_ERR_ARG, "vgp_gp_batch_static: an instance has more than %d points", kMaxN);
     DevParams P{};
     P.vs = p->voxel_size;

@@ -1225,6 +1225,14 @@ __global__ void k_reverse_i32(const int32_t* in, int32_t* out, int n) {
     if (i < n) out[i] = in[n - 1 - i];
 }
 
+// A workspace allocation failed: record it in the error word and launch nothing else.
+int alloc_failed(int* err_dev, cudaStream_t st) {
+    cudaGetLastError();
+    k_or_err<<<1, 1, 0, st>>>(err_dev, kErrAlloc);
+    note_launch();
+    return -2;
+}
+
 }  // namespace
 
 // One persistent launch of k_solve over instances in the given order with caller-provided
@@ -1306,16 +1314,17 @@ void add_stats(SolveStats* stats, const std::vector<int>& h) {
 // the map's private stream and replayed through a cached executable graph (updated in place
 // when only the arguments changed).  Launch shapes come from the map's configuration, sized
 // for the largest N the batch can hold; CTAs of a bucket with no work exit at once.  Returns
-// false when a CUDA call failed (the caller reports it through cudaGetLastError).
-bool solve_batch_graph(const SolveBatch& b, const DevParams& P, int* err_dev, cudaStream_t st, Arena& ar,
-                       SolveStats* stats, bool profile, const SolveConfig* cfg, GraphCache* gc) {
+// 0, -1 when a CUDA call failed, or -2 when a workspace could not be allocated (nothing was
+// launched; kErrAlloc is set in *err_dev).
+int solve_batch_graph(const SolveBatch& b, const DevParams& P, int* err_dev, cudaStream_t st, Arena& ar,
+                      SolveStats* stats, bool profile, const SolveConfig* cfg, GraphCache* gc) {
     const int64_t n = b.n_inst;
     if (!gc->gs) {
         if (cudaStreamCreateWithFlags(&gc->gs, cudaStreamNonBlocking) != cudaSuccess ||
             cudaEventCreateWithFlags(&gc->e0, cudaEventDisableTiming) != cudaSuccess ||
             cudaEventCreateWithFlags(&gc->e1, cudaEventDisableTiming) != cudaSuccess ||
             cudaEventCreate(&gc->t0) != cudaSuccess || cudaEventCreate(&gc->t1) != cudaSuccess)
-            return false;
+            return -1;
     }
     const bool props = b.nprop > 0;
     const int T = 256;
@@ -1349,7 +1358,7 @@ bool solve_batch_graph(const SolveBatch& b, const DevParams& P, int* err_dev, cu
         for (int j = 0; j < 5; ++j)
             if (sh[j].live && sh[j].kern == sh[i].kern) shm_max = std::max(shm_max, sh[j].shm);
         if (cudaFuncSetAttribute(sh[i].kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm_max) != cudaSuccess)
-            return false;
+            return -1;
     }
     int64_t ws_a_need = 0, ws_v_need = 0, ws_e_need = 0;
     for (int i = 0; i < 5; ++i) {
@@ -1372,12 +1381,12 @@ bool solve_batch_graph(const SolveBatch& b, const DevParams& P, int* err_dev, cu
     double* ws_v = ws_v_need ? (double*)ar.get(Arena::kWs1, sizeof(double) * ws_v_need, st) : nullptr;
     uint8_t* ws_e = ws_e_need ? (uint8_t*)ar.get(Arena::kWs3, ws_e_need, st) : nullptr;
     if (!hist || !order || !counters || (ws_a_need && !ws_a) || (ws_v_need && !ws_v) || (ws_e_need && !ws_e))
-        return false;
+        return alloc_failed(err_dev, st);
     int* cursor = hist + 1025;
     int* plan = counters + 5;
     cudaStream_t gs = gc->gs;
-    if (cudaEventRecord(gc->e0, st) != cudaSuccess || cudaStreamWaitEvent(gs, gc->e0, 0) != cudaSuccess) return false;
-    if (cudaStreamBeginCapture(gs, cudaStreamCaptureModeThreadLocal) != cudaSuccess) return false;
+    if (cudaEventRecord(gc->e0, st) != cudaSuccess || cudaStreamWaitEvent(gs, gc->e0, 0) != cudaSuccess) return -1;
+    if (cudaStreamBeginCapture(gs, cudaStreamCaptureModeThreadLocal) != cudaSuccess) return -1;
     fill_i32(hist, 0, 1025, gs);
     fill_i32(counters, 0, 5, gs);
     k_hist_n<<<(unsigned)((n + T - 1) / T), T, 0, gs>>>(b.inst_off, n, hist);
@@ -1412,7 +1421,7 @@ bool solve_batch_graph(const SolveBatch& b, const DevParams& P, int* err_dev, cu
         note_launch();
     }
     cudaGraph_t graph = nullptr;
-    if (cudaStreamEndCapture(gs, &graph) != cudaSuccess || !graph) return false;
+    if (cudaStreamEndCapture(gs, &graph) != cudaSuccess || !graph) return -1;
     cudaGraphExec_t& ex = gc->exec[props ? 1 : 0];
     if (ex) {
         cudaGraphExecUpdateResultInfo info;
@@ -1426,27 +1435,27 @@ bool solve_batch_graph(const SolveBatch& b, const DevParams& P, int* err_dev, cu
         if (cudaGraphInstantiate(&ex, graph, 0) != cudaSuccess) {
             ex = nullptr;
             cudaGraphDestroy(graph);
-            return false;
+            return -1;
         }
         ++gc->instantiations;
     }
     cudaGraphDestroy(graph);
     if (profile) cudaEventRecord(gc->t0, gs);
-    if (cudaGraphLaunch(ex, gs) != cudaSuccess) return false;
+    if (cudaGraphLaunch(ex, gs) != cudaSuccess) return -1;
     ++gc->replays;
     if (profile) cudaEventRecord(gc->t1, gs);
-    if (cudaEventRecord(gc->e1, gs) != cudaSuccess || cudaStreamWaitEvent(st, gc->e1, 0) != cudaSuccess) return false;
+    if (cudaEventRecord(gc->e1, gs) != cudaSuccess || cudaStreamWaitEvent(st, gc->e1, 0) != cudaSuccess) return -1;
     // statistics: the size histogram, read once after the solve
     std::vector<int> h(1025);
     cudaMemcpyAsync(h.data(), hist, sizeof(int) * 1025, cudaMemcpyDeviceToHost, st);
-    if (cudaStreamSynchronize(st) != cudaSuccess) return false;
+    if (cudaStreamSynchronize(st) != cudaSuccess) return -1;
     add_stats(stats, h);
     if (profile && stats) {
         float ms = 0.f;
         cudaEventElapsedTime(&ms, gc->t0, gc->t1);
         stats->t_solve_ms += ms;
     }
-    return true;
+    return 0;
 }
 
 }  // namespace
@@ -1458,7 +1467,9 @@ int solve_batch(const SolveBatch& b, const DevParams& P, int* err_dev, cudaStrea
     const int64_t n = b.n_inst;
     if (n <= 0) return 0;
     if (launch == VGP_LAUNCH_GRAPH && !bw && gc) {
-        if (!solve_batch_graph(b, P, err_dev, st, ar, stats, profile, cfg, gc)) {
+        const int rc = solve_batch_graph(b, P, err_dev, st, ar, stats, profile, cfg, gc);
+        if (rc == -2) return rc;
+        if (rc != 0) {
             // leave the capture stream usable and the error visible to the caller
             cudaGraph_t g = nullptr;
             cudaStreamCaptureStatus cs;
@@ -1474,6 +1485,7 @@ int solve_batch(const SolveBatch& b, const DevParams& P, int* err_dev, cudaStrea
     }
     // size histogram and decreasing-size order
     int* hist = (int*)ar.get(Arena::kHist, sizeof(int) * 2 * 1025, st);
+    if (!hist) return alloc_failed(err_dev, st);
     int* cursor = hist + 1025;
     cudaMemsetAsync(hist, 0, sizeof(int) * 1025, st);
     const int T = 256;
@@ -1486,6 +1498,7 @@ int solve_batch(const SolveBatch& b, const DevParams& P, int* err_dev, cudaStrea
     for (int i = 0; i < 1025; ++i) start[i + 1] = start[i] + h[i];
     cudaMemcpyAsync(cursor, start.data(), sizeof(int) * 1025, cudaMemcpyHostToDevice, st);
     int32_t* order_inc = (int32_t*)ar.get(Arena::kOrder, sizeof(int32_t) * 2 * n, st);
+    if (!order_inc) return alloc_failed(err_dev, st);
     int32_t* order = order_inc + n;
     k_order_n<<<(unsigned)((n + T - 1) / T), T, 0, st>>>(b.inst_off, n, cursor, order_inc);
     note_launch();
@@ -1510,7 +1523,18 @@ int solve_batch(const SolveBatch& b, const DevParams& P, int* err_dev, cudaStrea
     cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev);
     if (launch == VGP_LAUNCH_PER_INSTANCE && !bw) {
         // the plain comparison form: one launch per instance, in instance order, one CTA each
+        // workspaces sized for the largest instance (N <= 1024, at most 512 threads)
         int* ctr = (int*)ar.get(Arena::kCounters, sizeof(int) * n, st);
+        uint8_t* ws_e = P.emulate ? (uint8_t*)ar.get(Arena::kWs3, 1024 * kEmuBytesPerRow, st) : nullptr;
+        double* ws_a = (double*)ar.get(Arena::kWs0, sizeof(double) * n_tiles(128) * 64, st);
+        double* ws_v = b.want_var ? (double*)ar.get(Arena::kWs1, sizeof(double) * 1024 * 512, st) : nullptr;
+        if (!ctr || !ws_a || (P.emulate && !ws_e) || (b.want_var && !ws_v)) {
+            if (profile) {
+                cudaEventDestroy(ev0);
+                cudaEventDestroy(ev1);
+            }
+            return alloc_failed(err_dev, st);
+        }
         cudaMemsetAsync(ctr, 0, sizeof(int) * n, st);
         std::vector<int64_t> off(n + 1);
         cudaMemcpyAsync(off.data(), b.inst_off, sizeof(int64_t) * (n + 1), cudaMemcpyDeviceToHost, st);
@@ -1537,12 +1561,12 @@ int solve_batch(const SolveBatch& b, const DevParams& P, int* err_dev, cudaStrea
             const size_t shm = smem_bytes(c.npad, c.a_in_smem, b.nprop, c.stage_panel, b.Xi != nullptr, false, emu);
             auto ks = pick_solve(b.nprop > 0, emu);
             c.ws_e_stride = emu ? (int64_t)c.npad * kEmuBytesPerRow : 0;
-            c.ws_e = emu ? (uint8_t*)ar.get(Arena::kWs3, 1024 * kEmuBytesPerRow, st) : nullptr;
+            c.ws_e = emu ? ws_e : nullptr;
             cudaFuncSetAttribute(ks, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm);
             c.ws_a_stride = c.a_in_smem ? 0 : n_tiles(c.npad / 8) * 64;
-            c.ws_a = c.a_in_smem ? nullptr : (double*)ar.get(Arena::kWs0, sizeof(double) * n_tiles(128) * 64, st);
+            c.ws_a = c.a_in_smem ? nullptr : ws_a;
             c.ws_v_stride = (int64_t)c.npad * threads;
-            c.ws_v = b.want_var ? (double*)ar.get(Arena::kWs1, sizeof(double) * 1024 * 512, st) : nullptr;
+            c.ws_v = ws_v;
             ks<<<1, threads, shm, st>>>(c);
             note_launch();
         }
@@ -1558,6 +1582,13 @@ int solve_batch(const SolveBatch& b, const DevParams& P, int* err_dev, cudaStrea
         return 0;
     }
     int* counters = (int*)ar.get(Arena::kCounters, sizeof(int) * 8, st);
+    if (!counters) {
+        if (profile) {
+            cudaEventDestroy(ev0);
+            cudaEventDestroy(ev1);
+        }
+        return alloc_failed(err_dev, st);
+    }
     cudaMemsetAsync(counters, 0, sizeof(int) * 8, st);
     int done = 0;  // instances already assigned (from the large end)
     int bi = 0;
@@ -1604,6 +1635,13 @@ int solve_batch(const SolveBatch& b, const DevParams& P, int* err_dev, cudaStrea
         c.ws_v = (b.want_var && !bw) ? (double*)ar.get(Arena::kWs1, sizeof(double) * c.ws_v_stride * grid, st) : nullptr;
         c.ws_e_stride = emu ? (int64_t)c.npad * kEmuBytesPerRow : 0;
         c.ws_e = emu ? (uint8_t*)ar.get(Arena::kWs3, c.ws_e_stride * grid, st) : nullptr;
+        if ((!c.a_in_smem && !c.ws_a) || (b.want_var && !bw && !c.ws_v) || (emu && !c.ws_e)) {
+            if (profile) {
+                cudaEventDestroy(ev0);
+                cudaEventDestroy(ev1);
+            }
+            return alloc_failed(err_dev, st);
+        }
         cudaEvent_t b0 = nullptr, b1 = nullptr;
         if (profile) {
             cudaEventCreate(&b0);

@@ -76,6 +76,72 @@ def test_city_query_full_size_sampled(api, orc):
     assert np.array_equal(s[far], ref["status"][far])
 
 
+def test_city_headline_map_full_size_sampled(api, orc):
+    """The benchmark's headline configuration exactly: mixed precision with the emulated
+    FP64-accurate trailing updates (emulate_fp64 = 1), launch shapes chosen by the autotuner on
+    2M queries, the 2M-point city surface and all 10M queries in one call.  2000 seeded sampled
+    queries against the FP64 oracle: status bit-exact (every sampled query, OK or not),
+    |dd| <= 1e-3 m (the mixed-precision bound) with the error reported by distance bin,
+    gradient angle, and the instance and capped point set of each sampled query bit-exact.  The
+    sample is then queried again with variance on: distances bit-identical to the full call
+    (a query's result depends only on its own instance) and the variance within the
+    mixed-precision bound against the oracle."""
+    from paper_2407_09649_gb300 import scenes
+    city = scenes.City(0)
+    S_h = city.surface(n=2_000_000, seed=0)
+    Q_h = city.queries(n=10_000_000, seed=1)
+    m = api.Map(precision="mixed", emulate_fp64=1)
+    S = torch.from_numpy(S_h).cuda()
+    Q = torch.from_numpy(Q_h).cuda()
+    m.set_surface(S)
+    m.autotune(Q[:2_000_000].contiguous())
+    out = m.query(Q, grad=True, var=False)
+    st = m.stats()
+    assert st["bucket_count"][4] > 10000  # the emulated N > 224 bucket carries the workload
+    rng = np.random.default_rng(11)
+    idx = np.sort(rng.choice(len(Q_h), 2000, replace=False))
+    orc.set_threads(0)
+    surf = orc.Surface(S_h, orc.params())
+    ref = surf.query(Q_h[idx], want_var=True)
+    d = out["d"].cpu().numpy()[idx]
+    s = out["status"].cpu().numpy()[idx]
+    g = out["grad"].cpu().numpy()[idx]
+    assert np.array_equal(s, ref["status"])
+    ok = (ref["status"] == 0) & (ref["d"] > 2e-3) & (ref["d"] < 9.0)
+    assert ok.sum() > 1500
+    dd = np.abs(d[ok] - ref["d"][ok])
+    bins = {}
+    for lo, hi in ((0.0, 0.1), (0.1, 0.5), (0.5, 2.0), (2.0, np.inf)):
+        sel = (ref["d"][ok] >= lo) & (ref["d"][ok] < hi)
+        if sel.any():
+            bins[f"{lo}-{hi} m"] = (int(sel.sum()), float(dd[sel].max()))
+    print("headline map |dd| by distance bin (n, max):", bins)
+    assert dd.max() <= 1e-3
+    big = ok & (np.linalg.norm(ref["grad"], axis=1) > 0.5)
+    ang = _angle_deg(g[big], ref["grad"][big])
+    print("headline map gradient angle (deg): p99 %.2e, max %.2e" % (np.percentile(ang, 99), ang.max()))
+    assert np.percentile(ang, 99) <= 1.0
+    # selection of the sampled queries
+    qs = torch.from_numpy(Q_h[idx]).cuda()
+    plan = m.debug_query_plan(qs)
+    qi = plan["q_inst"]
+    gkey = np.where(qi >= 0, plan["inst_key"][np.maximum(qi, 0)], np.uint64(0)).astype(np.uint64)
+    assert np.array_equal(gkey, ref["inst_key"])
+    assert np.array_equal(np.where(qi >= 0, np.diff(plan["inst_off"])[np.maximum(qi, 0)], 0), ref["inst_n"])
+    off, pidx = plan["inst_off"], plan["point_idx"]
+    for i in rng.choice(len(plan["inst_key"]), min(150, len(plan["inst_key"])), replace=False):
+        assert np.array_equal(np.sort(pidx[off[i]:off[i + 1]]), np.sort(surf.instance(int(plan["inst_key"][i]))))
+    # variance on, sample only: same instances, same bits for d; variance against the oracle
+    vs = {k: v.cpu().numpy() for k, v in m.query(qs, grad=True, var=True).items()}
+    assert np.array_equal(vs["d"].view(np.uint8), d.view(np.uint8))
+    assert np.array_equal(vs["status"], s)
+    fin = ok & np.isfinite(ref["var"]) & (ref["var"] > 0)
+    rel = np.abs(vs["var"][fin] - ref["var"][fin]) / ref["var"][fin]
+    bound = 2.0 * np.abs(d[fin] - ref["d"][fin]) / np.maximum(ref["d"][fin], 1e-3) * 1.5 + 2e-3
+    print("headline map variance relative error: median %.2e, max %.2e" % (np.median(rel), rel.max()))
+    assert np.all(rel <= bound)
+
+
 def test_patch_sweep_full_size_sampled(api, orc):
     """200,000 instances (N log-uniform in [4, 1024]), 512 queries each, in one call;
     150 sampled instances checked with all their queries."""

@@ -69,6 +69,7 @@ def test_node_choice_and_leaf_cap_brute_force(orc):
     S = orc.Surface(pts, P)
     q = rng.uniform(-1.0, 1.8, (60, 3)).astype(np.float32)
     r = S.query_smooth(q, n_nodes=Q, lam=100.0, want_var=False)
+    node_keys = S.smooth_nodes(q, n_nodes=Q)
     leaves = {}
     for i, p in enumerate(pts):
         leaves.setdefault(_leaf(p), []).append(i)
@@ -87,6 +88,9 @@ def test_node_choice_and_leaf_cap_brute_force(orc):
         cands.sort()
         nodes = [c[2] for c in cands[:Q]]
         assert r["n_nodes"][i] == len(nodes)
+        # the node keys the oracle reports, nearest first, 0 past the last
+        want = [c[1] for c in cands[:Q]] + [0] * (Q - len(nodes))
+        assert [int(k) for k in node_keys[i]] == want
         ds, gs, ok = [], [], []
         for F in nodes:
             ids = leaves[F]
@@ -94,6 +98,7 @@ def test_node_choice_and_leaf_cap_brute_force(orc):
             if len(ids) > cap:
                 dd = [(float(np.sum((pts[j].astype(np.float64) - cen) ** 2)), j) for j in ids]
                 ids = sorted(j for _, j in sorted(dd)[:cap])
+            assert S.leaf_capped(int(orc.pack_key(np.array(F))), cap).tolist() == sorted(ids)
             rr = orc.gp_single(pts[ids].astype(np.float64), q[i:i + 1].astype(np.float64), want_var=False)
             if rr.status[0] == 0:
                 ds.append(rr.d[0])

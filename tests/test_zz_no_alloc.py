@@ -74,3 +74,6 @@ def test_static_batch_refuses_oversize():
     rc, _ = _call_static(lib, L, params, np.zeros(70000, np.int64), np.zeros((1, 3), np.float32),
                          np.zeros(70000, np.int64), np.zeros((1, 3), np.float32))
     assert rc == -1 and b"instances exceed" in lib.vgp_last_error()
+    # a negative first offset is refused before any point is read
+    rc, _ = _call_static(lib, L, params, [-5, 3], np.zeros((3, 3), np.float32), [0, 1], np.zeros((1, 3), np.float32))
+    assert rc == -1 and b"negative, decreasing" in lib.vgp_last_error()
