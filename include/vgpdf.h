@@ -173,6 +173,11 @@ typedef struct {
     int32_t reserved;
     int64_t graph_replays;        /* VGP_LAUNCH_GRAPH: executable-graph launches on this map ... */
     int64_t graph_instantiations; /* ... and graph instantiations (the rest were updates in place) */
+    /* with params.profile (CUDA events on the call's stream, 0 otherwise): */
+    double t_bin_ms;        /* the voxelise / bin kernel of build_frame or set_surface (S1) */
+    double t_gather_ms;     /* the neighbourhood gather kernel of a G-GPDF query (S3) */
+    double t_fuse_ms;       /* the fusion kernels of the latest vgp_fuse (S9) */
+    int64_t n_candidates;   /* candidate points the gather scanned, summed over instances */
 } vgp_stats;
 
 /* Fill *p with the defaults listed above. */

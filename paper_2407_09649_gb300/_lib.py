@@ -34,7 +34,9 @@ class VgpStats(C.Structure):
                 ("t_solve_ms", C.c_double), ("t_bucket_ms", C.c_double * 5),
                 ("cfg_threads", C.c_int32 * 5), ("cfg_per_sm", C.c_int32 * 5), ("grid_leaves", C.c_int64), ("grid_capacity_leaves", C.c_int64),
                 ("cfg_stage_panel", C.c_int32), ("reserved", C.c_int32),
-                ("graph_replays", C.c_int64), ("graph_instantiations", C.c_int64)]
+                ("graph_replays", C.c_int64), ("graph_instantiations", C.c_int64),
+                ("t_bin_ms", C.c_double), ("t_gather_ms", C.c_double), ("t_fuse_ms", C.c_double),
+                ("n_candidates", C.c_int64)]
 
 
 # (name, restype, argtypes)

@@ -126,6 +126,34 @@ struct vgp_map {
     vgp_stats stats{};
     SolveConfig cfg;  // launch shape per size bucket (vgp_autotune)
     GraphCache gcache;  // VGP_LAUNCH_GRAPH: capture stream and executable graphs
+    cudaEvent_t ph0 = nullptr, ph1 = nullptr;  // profile: events around one phase's kernels
+};
+
+// Profile mode (params.profile = 1): CUDA events on the call's stream around the kernels of
+// one phase (bin, gather, fuse); stop() waits for the end event and returns the phase's
+// device time in ms.  Without profiling it records nothing and returns 0.
+struct PhaseTimer {
+    vgp_map* m;
+    cudaStream_t st;
+    bool on;
+    PhaseTimer(vgp_map* mm, cudaStream_t s) : m(mm), st(s), on(mm->prm.profile != 0) {
+        if (on && !m->ph0 &&
+            (cudaEventCreate(&m->ph0) != cudaSuccess || cudaEventCreate(&m->ph1) != cudaSuccess)) {
+            cudaGetLastError();
+            on = false;
+        }
+        if (on) cudaEventRecord(m->ph0, st);
+    }
+    double stop() {
+        if (!on) return 0.0;
+        float ms = 0.f;
+        if (cudaEventRecord(m->ph1, st) != cudaSuccess || cudaEventSynchronize(m->ph1) != cudaSuccess ||
+            cudaEventElapsedTime(&ms, m->ph0, m->ph1) != cudaSuccess) {
+            cudaGetLastError();
+            return 0.0;
+        }
+        return ms;
+    }
 };
 
 struct vgp_frame {
@@ -333,6 +361,8 @@ int vgp_destroy(vgp_map* m) {
     cudaFree(m->ps_tmp);
     cudaFree(m->mc_tab);
     graph_cache_destroy(m->gcache);
+    if (m->ph0) cudaEventDestroy(m->ph0);
+    if (m->ph1) cudaEventDestroy(m->ph1);
     delete m;
     return VGP_OK;
 }
@@ -379,7 +409,9 @@ int vgp_build_frame_props(vgp_map* m, const float* pts, const float* props, int6
     ft.keys = fkeys;
     CUDA_TRY(cudaMemsetAsync(fkeys, 0xFF, sizeof(uint64_t) * Cf, st));
     CUDA_TRY(cudaMemsetAsync(fmasks, 0, sizeof(unsigned long long) * Cf * 8, st));
+    PhaseTimer pbin(m, st);
     frame_voxelise(pts, n, P, ft, fmasks, m->dev_words + 1, m->dev_words, st);
+    S.t_bin_ms = pbin.stop();
     collect_table(ft, fslot2leaf, flist, flkeys, m->dev_words + 2, Cf, m->dev_words, st);
     TRY(read_words(m, st));
     TRY(check_err(m, "vgp_build_frame"));
@@ -742,6 +774,7 @@ int vgp_fuse(vgp_map* m, vgp_frame* f, vgp_stream stream) {
     CUDA_TRY(cudaMemsetAsync(m->dev_words, 0, sizeof(int) * 3, st));
     TRY(grid_reserve(m, f->ntest / 512 + 1, st));
     CUDA_TRY(cudaMemcpyAsync(m->dev_words + 3, &m->g_leaves, sizeof(int), cudaMemcpyHostToDevice, st));
+    PhaseTimer pfuse(m, st);
     fuse_clear_flags(m->g_flags, m->g_leaves, st);
     fuse_insert(f->tkey, f->d, f->v, f->status, f->ntest, m->prm.fusion, m->g, m->g_slot2pool, m->dev_words, st);
     const PropGrid pg = prop_grid(m);
@@ -754,8 +787,10 @@ int vgp_fuse(vgp_map* m, vgp_frame* f, vgp_stream stream) {
     fuse_alloc(m->g_slot2pool, m->g, m->dev_words + 3, m->pool_cap, m->g_known, m->g_flags, m->dev_words, pg, st);
     fuse_update(f->tkey, f->d, f->v, f->status, f->ntest, m->prm.fusion, m->g, m->g_slot2pool, m->g_known, m->g_D,
                 m->g_V, m->g_flags, pin, pg, st);
+    const double t_fuse = pfuse.stop();
     TRY(read_words(m, st));
     TRY(check_err(m, "vgp_fuse"));
+    m->stats.t_fuse_ms = t_fuse;
     CUDA_TRY(cudaGetLastError());
     m->g_leaves = m->host_words[3];
     m->stats.grid_leaves = m->g_leaves;
@@ -928,12 +963,15 @@ int vgp_set_surface(vgp_map* m, const float* pts, int64_t n, vgp_stream stream) 
     ARENA(slot_cnt, int32_t, kTmp1, Cs);
     ARENA(list, int32_t, kTmp2, Cs);
     CUDA_TRY(cudaMemsetAsync(slot_cnt, 0, sizeof(int32_t) * Cs, st));
+    PhaseTimer pbin(m, st);
     surface_bin(m->s_pts, n, P, m->s_tab, pt_slot, slot_cnt, m->dev_words + 1, m->dev_words, st);
+    const double t_bin = pbin.stop();
     collect_table(m->s_tab, m->s_slot2leaf, list, nullptr, m->dev_words + 2, Cs, m->dev_words, st);
     TRY(read_words(m, st));
     TRY(check_err(m, "vgp_set_surface"));
     const int nl = m->host_words[2];
     m->stats = vgp_stats{};
+    m->stats.t_bin_ms = t_bin;
     m->stats.n_points = m->host_words[1];
     m->stats.n_leaves = nl;
     if (nl + 1 > m->s_off_cap) {
@@ -1203,6 +1241,8 @@ struct QueryPlan {
     int64_t T = 0;
     uint64_t* ikeys = nullptr;   // centre leaf key of each instance
     int32_t* q_inst = nullptr;   // instance of each query (< 0: none)
+    double t_gather_ms = 0;      // profile: the gather kernel
+    int64_t n_cand = 0;          // profile: candidate points the gather scanned
     int64_t* inst_off = nullptr;
     double* Xl = nullptr;
     float* Xf = nullptr;
@@ -1292,8 +1332,16 @@ static int plan_queries(vgp_map* m, const float* q, int64_t n, double* d, double
     ARENA(Xf, float, kTmp12, 3 * T);
     ARENA(gidx, int64_t, kTmp13, T);
     ARENA(centre, double, kTmp14, 3 * (int64_t)ni);
+    if (m->prm.profile) {  // candidate count of the gather, for its algorithmic bytes
+        std::vector<int64_t> hc(ni);
+        if (ni) CUDA_TRY(cudaMemcpyAsync(hc.data(), ncand, sizeof(int64_t) * ni, cudaMemcpyDeviceToHost, st));
+        CUDA_TRY(cudaStreamSynchronize(st));
+        for (int i = 0; i < ni; ++i) Q.n_cand += hc[i];
+    }
+    PhaseTimer pgat(m, st);
     inst_gather(ikeys, ni, m->s_tab, m->s_slot2leaf, m->s_off, m->s_idx, m->s_pts, ncand, inst_off, P, Xl, Xf, gidx,
                 centre, st);
+    Q.t_gather_ms = pgat.stop();
     // route queries to instances
     ARENA(q_inst, int32_t, kTmp15, n);
     ARENA(inst_qcnt, int64_t, kTmp16, ni + 1);
@@ -1446,6 +1494,8 @@ int vgp_query_distance_gradient(vgp_map* m, const float* q, int64_t n, double* d
     S.n_train = Q.T;
     S.n_queries = n;
     S.n_groups = Q.ng;
+    S.t_gather_ms = Q.t_gather_ms;
+    S.n_candidates = Q.n_cand;
     for (int i = 0; i < 5; ++i) S.bucket_count[i] = ss.bucket_count[i];
     S.sum_n3 = ss.sum_n3;
     S.sum_n2 = ss.sum_n2;

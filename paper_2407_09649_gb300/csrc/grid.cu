@@ -783,14 +783,46 @@ __global__ void k_surface_scatter(const int32_t* pt_slot, int64_t n, const int32
     idx[off[l] + r] = (int32_t)i;
 }
 
-// Sort each leaf's point indices ascending (bitonic in shared memory, up to 4096 points;
-// longer leaves keep their scatter order, which only changes summation order).
+// Sort n > 4096 point indices a[0 .. n) ascending in place in global memory, one CTA: a
+// bitonic network whose compare-exchanges all put the smaller value first (each merge of size
+// k starts by comparing the mirrored positions i and i ^ (k - 1)), so the padding to a power
+// of two is virtual: a partner at or beyond n holds +infinity and never moves.
+__device__ void sort_long_segment(int32_t* a, int64_t n) {
+    int64_t m = 1;
+    while (m < n) m <<= 1;
+    const int64_t half = m >> 1;
+    for (int64_t k = 2; k <= m; k <<= 1) {
+        for (int64_t j = k >> 1; j > 0; j >>= 1) {
+            for (int64_t p = threadIdx.x; p < half; p += blockDim.x) {
+                const int64_t i = (p / j) * 2 * j + (p % j);
+                const int64_t q = j == (k >> 1) ? i ^ (k - 1) : i + j;
+                if (q < n) {
+                    const int32_t x = a[i], y = a[q];
+                    if (x > y) {
+                        a[i] = y;
+                        a[q] = x;
+                    }
+                }
+            }
+            __syncthreads();
+        }
+    }
+}
+
+// Sort each leaf's point indices ascending (bitonic in shared memory up to 4096 points, in
+// global memory above), so that the order of every leaf's list, and hence the order of the
+// points in every GP instance, does not depend on the order of the scatter's atomics.
 __global__ void k_sort_segments(const int64_t* off, int nl, int32_t* idx) {
     __shared__ int32_t buf[4096];
     const int l = blockIdx.x;
     const int64_t b = off[l];
-    const int n = (int)(off[l + 1] - b);
-    if (n <= 1 || n > 4096) return;
+    const int64_t nn = off[l + 1] - b;
+    if (nn <= 1) return;
+    if (nn > 4096) {
+        sort_long_segment(idx + b, nn);
+        return;
+    }
+    const int n = (int)nn;
     int m = 1;
     while (m < n) m <<= 1;
     for (int i = threadIdx.x; i < m; i += blockDim.x) buf[i] = i < n ? idx[b + i] : 0x7fffffff;

@@ -512,31 +512,42 @@ def test_graph_launch_mode_matches_direct(vg, emulate):
         assert b[5] > 0  # the G-GPDF query solved instances with N > 256
 
 
-def test_emulated_results_repeatable(vg):
-    """The emulated factorisation (emulate_fp64 = 1) is deterministic: on the sphere surface
-    with 20k queries (the case where a graph-mode difference was once seen), two direct calls,
-    a call on a subset of the queries (other instances in flight, other CTAs, other workspace
-    slots) and a graph-mode call all give bit-identical distances, gradients, variances and
-    statuses."""
+def test_results_repeatable_across_calls_maps_and_launch_modes(vg, orc):
+    """Results depend on nothing but the inputs: on the sphere surface with 20k queries, whose
+    densest leaves hold more than 4096 points (their point lists are sorted in global memory
+    by the surface binning, so every instance lists its points in index order), two calls of
+    one map, a call on a subset of the queries, a second map with its own surface binning and
+    a graph-mode map give bit-identical distances, gradients, variances and statuses, with the
+    emulated FP64-accurate updates and without."""
     rng = np.random.default_rng(8)
     u = rng.normal(size=(150000, 3))
     surf = (1.3 * u / np.linalg.norm(u, axis=1, keepdims=True)).astype(np.float32)
     q = (surf[rng.integers(0, len(surf), 20000)] * rng.uniform(0.6, 1.4, (20000, 1))).astype(np.float32)
+    assert np.unique(orc.leaf_key_of_points(surf, 0.1), return_counts=True)[1].max() > 4096
     qt = torch.from_numpy(q).cuda()
     st = torch.from_numpy(surf).cuda()
+    keys = ("d", "grad", "var", "status")
     for precision in ("mixed", "fp64"):
-        m = vg.Map(precision=precision, emulate_fp64=1)
-        m.set_surface(st)
-        runs = [{k: v.cpu().numpy() for k, v in m.query(qt, grad=True, var=True).items()} for _ in range(2)]
-        assert m.stats()["bucket_count"][4] > 50
-        sub = {k: v.cpu().numpy() for k, v in m.query(qt[7000:12000], grad=True, var=True).items()}
-        mg = vg.Map(precision=precision, emulate_fp64=1, launch="graph")
-        mg.set_surface(st)
-        runs.append({k: v.cpu().numpy() for k, v in mg.query(qt, grad=True, var=True).items()})
-        for k in ("d", "grad", "var", "status"):
-            for r in runs[1:]:
-                assert np.array_equal(r[k].view(np.uint8), runs[0][k].view(np.uint8)), (precision, k)
-            assert np.array_equal(sub[k].view(np.uint8), runs[0][k][7000:12000].view(np.uint8)), (precision, k)
+        for emu in (1, 0):
+            def run(m, qq=qt):
+                return {k: v.cpu().numpy() for k, v in m.query(qq, grad=True, var=True).items()}
+            m = vg.Map(precision=precision, emulate_fp64=emu)
+            m.set_surface(st)
+            ref = run(m)
+            assert m.stats()["bucket_count"][4] > 50
+            other = {"second call": run(m)}
+            sub = run(m, qt[7000:12000])
+            m2 = vg.Map(precision=precision, emulate_fp64=emu)
+            m2.set_surface(st)
+            other["second map"] = run(m2)
+            mg = vg.Map(precision=precision, emulate_fp64=emu, launch="graph")
+            mg.set_surface(st)
+            other["graph mode"] = run(mg)
+            for name, r in other.items():
+                for k in keys:
+                    assert np.array_equal(r[k].view(np.uint8), ref[k].view(np.uint8)), (precision, emu, name, k)
+            for k in keys:
+                assert np.array_equal(sub[k].view(np.uint8), ref[k][7000:12000].view(np.uint8)), (precision, emu, k)
 
 
 @pytest.mark.parametrize("precision", ["fp64", "mixed"])
