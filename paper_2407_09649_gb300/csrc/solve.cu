@@ -92,13 +92,67 @@ struct Shared {
                     // distance alpha and its FP32 copies, which that mode does not use
     double* Tblk;   // [kEB][64] inverses of the diagonal tiles of the current block
     double* Wsc;    // [warps][64] per-warp tile scratch (layout changes between mma operands)
+    unsigned char* stage;  // emulated kernel: slice operands of the tensor-core updates (aliases
+                           // X .. alf_lo, which the factorisation does not use; reloaded after it)
 };
 
-constexpr int kEmuSmemDoubles = 8 * 64 + 8 * 64;  // Tblk + Wsc for the 8 warps of an emulated CTA
+// Emulated trailing updates on the tensor cores (tcgen05): an output tile is kBandT row tiles
+// (128 rows, the MMA's M) by kColT row tiles (32 columns, its N) of the trailing matrix; the
+// slices of one 16-column half of the block are staged for the band (A) and the column tile (B).
+constexpr int kBandT = 16;
+constexpr int kColT = 4;
+constexpr int kSliceTileBytes = 7 * 2 * 128;  // one row tile, one K half: 7 slices x 2 core matrices
+// staging: the band's slices of both K halves (A), and two buffers of the column tile's (B)
+constexpr int kStageA = 2 * kBandT * kSliceTileBytes;
+constexpr int kStageB = 2 * kColT * kSliceTileBytes;
+constexpr int kStageBytes = kStageA + 2 * kStageB;
+constexpr int kEmuTmemCols = 8 * 8 * kColT;    // 8 slice groups x 32 FP32 columns
+constexpr int kEmuCtasPerSm = 512 / kEmuTmemCols;  // CTAs whose tensor memory fits one SM
+
+__host__ __device__ __forceinline__ size_t align128(size_t x) { return (x + 127) & ~(size_t)127; }
+__host__ __device__ __forceinline__ size_t emu_fixed_bytes(int npad) {
+    return align128((size_t)(npad + 256 + kEB * 64 + 8 * 64) * sizeof(double));  // invd, T256, Tblk, Wsc
+}
+__host__ __device__ __forceinline__ size_t emu_alias_bytes(int npad, int nprop, bool lattice) {
+    const size_t b = (size_t)5 * npad * sizeof(double) + (size_t)5 * npad * sizeof(float) +
+                     (lattice ? (size_t)npad * sizeof(int) : 0) + (size_t)(nprop > 2 ? nprop - 2 : 0) * npad * sizeof(double);
+    return b > (size_t)kStageBytes ? b : (size_t)kStageBytes;
+}
+
+// Emulated kernel: invd, the exp table, the block's tile inverses and the warp scratch first, then
+// (128-byte aligned) the staging buffer of the tensor-core updates, which X, alpha, z, Xf, alf,
+// alf_lo, xi and the property weights alias.
+__device__ Shared carve_emu(double* sm, int npad, double* ws_a, int nprop, bool lattice) {
+    Shared s;
+    s.invd = sm;
+    s.T256 = s.invd + npad;
+    s.Tblk = s.T256 + 256;
+    s.Wsc = s.Tblk + kEB * 64;
+    s.Tinv = nullptr;
+    s.w = nullptr;
+    s.panel = nullptr;
+    s.A = ws_a;
+    s.stage = reinterpret_cast<unsigned char*>(sm) + emu_fixed_bytes(npad);
+    s.X = reinterpret_cast<double*>(s.stage);
+    s.alpha = s.X + 3 * npad;
+    s.z = s.alpha + npad;
+    s.Xf = reinterpret_cast<float*>(s.z + npad);
+    s.alf = s.Xf + 3 * npad;
+    s.alf_lo = s.alf + npad;
+    s.xi = lattice ? reinterpret_cast<int*>(s.alf_lo + npad) : nullptr;
+    double* extra = reinterpret_cast<double*>(reinterpret_cast<int*>(s.alf_lo + npad) + (lattice ? npad : 0));
+    s.pa[0] = s.alpha;
+    s.pa[1] = reinterpret_cast<double*>(s.alf);
+    s.pa[2] = nprop > 2 ? extra : nullptr;
+    s.pa[3] = nprop > 3 ? extra + npad : nullptr;
+    return s;
+}
 
 __device__ Shared carve(double* sm, int npad, int a_in_smem, double* ws_a, int nprop, int stage_panel,
                         bool lattice, bool with_w, bool emu = false) {
+    if (emu) return carve_emu(sm, npad, ws_a, nprop, lattice);
     Shared s;
+    s.stage = nullptr;
     s.X = sm;
     s.alpha = s.X + 3 * npad;
     s.invd = s.alpha + npad;
@@ -107,9 +161,8 @@ __device__ Shared carve(double* sm, int npad, int a_in_smem, double* ws_a, int n
     s.Tinv = s.z + (with_w ? 2 : 1) * npad;
     s.T256 = s.Tinv + 64;
     double* end = s.T256 + 256;
-    s.Tblk = emu ? end : nullptr;
-    s.Wsc = emu ? end + 8 * 64 : nullptr;
-    if (emu) end += kEmuSmemDoubles;
+    s.Tblk = nullptr;
+    s.Wsc = nullptr;
     if (a_in_smem) {
         s.A = end;
         end += n_tiles(npad / 8) * 64;
@@ -134,7 +187,8 @@ __device__ Shared carve(double* sm, int npad, int a_in_smem, double* ws_a, int n
 
 __host__ size_t smem_bytes(int npad, int a_in_smem, int nprop, int stage_panel, bool lattice, bool with_w = false,
                           bool emu = false) {
-    size_t d = (size_t)(with_w ? 7 : 6) * npad + 64 + 256 + (emu ? kEmuSmemDoubles : 0) +
+    if (emu) return emu_fixed_bytes(npad) + emu_alias_bytes(npad, nprop, lattice);
+    size_t d = (size_t)(with_w ? 7 : 6) * npad + 64 + 256 +
                (a_in_smem ? (size_t)n_tiles(npad / 8) * 64 : (stage_panel ? (size_t)(npad / 8) * 64 : 0));
     return d * sizeof(double) + (size_t)5 * npad * sizeof(float) + (lattice ? (size_t)npad * sizeof(int) : 0) +
            (size_t)std::max(nprop - 2, 0) * npad * sizeof(double);
@@ -370,21 +424,13 @@ __device__ __forceinline__ double scaled_int(long long w, int e) {
                                             (m & 0xFFFFFFFFFFFFFull)));
 }
 
-// D += A B on the bf16 tensor path (m16n8k16, FP32 accumulation)
-__device__ __forceinline__ void mma_bf16(float* d, const uint32_t* a, const uint32_t* b) {
-    asm volatile(
-        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
-        "{%0,%1,%2,%3};\n"
-        : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
-        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
-}
-
 // Balanced base-256 digits of row g of an 8-row tile over one block (the FP64 values
 // x[0 .. 2 kEB - 1] held by the four lanes t of the row: columns 8 j + 2t and 8 j + 2t + 1 in
-// x[2j], x[2j + 1]), written as bf16 pairs in mma fragment order to F ([slice][16-column step]
-// [lane] uint2), and the row scale 2^(em - 1021) to *scale (lane t = 0).  The digit scheme is
-// described at factor_emulated.
-__device__ __forceinline__ void slice_row(const double (&x)[2 * kEB], uint2* F, double* scale) {
+// x[2j], x[2j + 1]), written as bf16 pairs to F[kh] (the tile's slices of the block's columns
+// 16 kh .. 16 kh + 15) in the tensor cores' K-major layout: [slice][core matrix of 8 columns]
+// [row][8 bf16], 16 bytes per row and 128 per core matrix; and the row scale 2^(em - 1021) to
+// *scale (lane t = 0).  The digit scheme is described at factor_emulated.
+__device__ __forceinline__ void slice_row(const double (&x)[2 * kEB], uint32_t* F0, uint32_t* F1, double* scale) {
     const int lane = threadIdx.x & 31;
     int em = 0;
 #pragma unroll
@@ -393,6 +439,7 @@ __device__ __forceinline__ void slice_row(const double (&x)[2 * kEB], uint2* F, 
     em = max(em, __shfl_xor_sync(0xffffffffu, em, 2));
 #pragma unroll
     for (int kk = 0; kk < kEK; ++kk) {
+        uint32_t* F = kk ? F1 : F0;
         unsigned long long Yb[4];
         bool negx[4];
 #pragma unroll
@@ -419,7 +466,9 @@ __device__ __forceinline__ void slice_row(const double (&x)[2 * kEB], uint2* F, 
                 if (negx[i]) qv = -qv;
                 h16[i] = __float_as_uint((float)qv) >> 16;  // exact: |qv| <= 2^7
             }
-            F[(ss * kEK + kk) * 32 + lane] = make_uint2(h16[0] | (h16[1] << 16), h16[2] | (h16[3] << 16));
+            // lane = 4 g + t: row g, columns 2t, 2t + 1 of the core matrices of columns 0-7 and 8-15
+            F[ss * 64 + lane] = h16[0] | (h16[1] << 16);
+            F[ss * 64 + 32 + lane] = h16[2] | (h16[3] << 16);
         }
     }
     if ((lane & 3) == 0) *scale = em > 0 ? __longlong_as_double((long long)(em + 2) << 52) : 0.0;
@@ -431,7 +480,8 @@ __device__ __forceinline__ void slice_row(const double (&x)[2 * kEB], uint2* F, 
 // scratch tile W turns each result from the accumulator into the operand layout.  The
 // results are stored to A and sliced for the trailing update (F, scale: this tile's slices
 // and row scales).
-__device__ void block_rows(double* A, int it, int K0, const double* Tblk, double* W, uint2* F, double* scale) {
+__device__ void block_rows(double* A, int it, int K0, const double* Tblk, double* W, uint32_t* F0, uint32_t* F1,
+                           double* scale) {
     const int lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
     double* R = A + tix(it, K0);  // tiles (it, K0 .. K0 + kEB - 1), contiguous
     double x[2 * kEB];            // accumulator layout: tile j holds columns 2t, 2t + 1 of row g
@@ -472,15 +522,205 @@ __device__ void block_rows(double* A, int it, int K0, const double* Tblk, double
             __syncwarp();
         }
     }
-    slice_row(x, F, scale + g);
+    slice_row(x, F0, F1, scale + g);
 }
 
-// Per-CTA workspace of the emulated factorisation: the slices of the rows below the current
-// block ([row tile][7 slices][kEK steps][lane] uint2), npad row scales, then the inverses of all
-// diagonal tiles ([npad / 8][64] doubles).
+// Per-CTA workspace of the emulated factorisation: for each of the block's two 16-column halves
+// the slices of the rows below the current block ([row tile][7 slices][2 core matrices], 1792
+// bytes per row tile), npad row scales, then the inverses of all diagonal tiles ([npad / 8][64]
+// doubles).
+__device__ __forceinline__ unsigned char* emu_ws(const SolveCtx& c) { return c.ws_e + (int64_t)blockIdx.x * c.ws_e_stride; }
+__device__ __forceinline__ int64_t emu_half_bytes(int npad) { return (int64_t)(npad / 8) * kSliceTileBytes; }
 __device__ __forceinline__ double* emu_tile_inverses(const SolveCtx& c) {
-    const uint2* sl = reinterpret_cast<const uint2*>(c.ws_e + (int64_t)blockIdx.x * c.ws_e_stride);
-    return const_cast<double*>(reinterpret_cast<const double*>(sl + (int64_t)(c.npad / 8) * 7 * kEK * 32)) + c.npad;
+    return reinterpret_cast<double*>(emu_ws(c) + 2 * emu_half_bytes(c.npad)) + c.npad;
+}
+
+// ---- tensor-core (tcgen05) helpers for the emulated updates --------------------------------
+__device__ __forceinline__ uint32_t smem_addr(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+// Shared-memory matrix descriptor, K-major without swizzle: core matrices of 8 rows x 16 bytes,
+// the next along K lbo bytes on, the next along M or N sbo bytes on.
+__device__ __forceinline__ uint64_t umma_desc(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
+    return (uint64_t)((saddr >> 4) & 0x3FFF) | ((uint64_t)((lbo >> 4) & 0x3FFF) << 16) |
+           ((uint64_t)((sbo >> 4) & 0x3FFF) << 32) | (1ull << 46);
+}
+
+// Instruction descriptor of kind::f16: bf16 A and B (K-major), FP32 D, M = 128, N = 8 kColT.
+constexpr uint32_t kUmmaIdesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(8 * kColT / 8) << 17) |
+                                ((uint32_t)(128 / 16) << 24);
+
+__device__ __forceinline__ void umma_bf16(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t accumulate) {
+    asm volatile("{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+                 " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}"
+                 ::"r"(d_tmem), "l"(a), "l"(b), "r"(kUmmaIdesc), "r"(accumulate));
+}
+
+__device__ __forceinline__ void bulk_load(void* dst, const void* src, uint32_t bytes, uint32_t bar) {
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+                 ::"r"(smem_addr(dst)), "l"(src), "r"(bytes), "r"(bar) : "memory");
+}
+
+// Wait for the completion of phase `parity` of an mbarrier, at most kWaitLimit polls; the
+// result is the same on every thread of the CTA (false: the wait gave up somewhere).
+constexpr int kWaitLimit = 1 << 22;
+__device__ __forceinline__ bool bar_wait(uint32_t bar, uint32_t parity) {
+    uint32_t done = 0;
+    for (int it = 0; it < kWaitLimit && !done; ++it)
+        asm volatile("{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+                     " selp.u32 %0, 1, 0, p;\n}"
+                     : "=r"(done) : "r"(bar), "r"(parity) : "memory");
+    return __syncthreads_and((int)done) != 0;
+}
+
+// Tensor memory and barriers of an emulated CTA.
+struct EmuTc {
+    uint32_t tmem;       // base of kEmuTmemCols columns: slice group g at columns 8 kColT g
+    uint32_t bar_ld;     // completion of the staging copies
+    uint32_t bar_mma;    // completion of the MMAs
+    uint32_t ph_ld, ph_mma;
+    bool dead;           // a bounded wait gave up: take no more work
+};
+
+__device__ __forceinline__ void tmem_ld4(uint32_t taddr, uint32_t (&v)[4]) {
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x4.b32 {%0,%1,%2,%3}, [%4];"
+                 : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]) : "r"(taddr) : "memory");
+}
+__device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
+
+// A bounded wait gave up: record it; the CTA stops taking work.
+__device__ __forceinline__ bool emu_fail(const SolveCtx& c, EmuTc& tc) {
+    if (threadIdx.x == 0) atomicOr(c.err, kErrTimeout);
+    tc.dead = true;
+    return false;
+}
+
+// Trailing update C -= P P^T of the M = Nt - K1 row tiles below the block that ends at K1, on
+// the tensor cores.  P's rows are cut into seven digit slices (see factor_emulated), and every
+// slice group G_g = sum_{s+t=g} P_s P_t^T is accumulated exactly in FP32 in tensor memory.
+// Output tiles of kBandT row tiles (128 rows) by kColT row tiles (32 columns) cover the lower
+// triangle, band by band.  Bulk copies stage the band's slices (A, both 16-column halves of the
+// block) once per band and each column tile's slices (B) in one of two buffers, the next tile's
+// while the current one computes.  One thread issues the 68 slice products of a tile (34 slice
+// pairs x 2 halves) into the 8 group accumulators; all 8 warps then read their rows (lane
+// quadrant warp % 4) and columns (half warp / 4) of the groups, pack each element's groups into
+// one integer and subtract it as an FP64 value.
+__device__ bool trailing_update_tc(const SolveCtx& c, double* A, int Nt, int K1, const unsigned char* E,
+                                   int64_t KH, const double* sr, unsigned char* stage, EmuTc& tc) {
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int M = Nt - K1;
+    const uint32_t aA = smem_addr(stage), aB = aA + kStageA;
+    const int q = warp & 3, h = warp >> 2;  // lane quadrant (rows 32 q ..) and column half
+    const int row = 32 * q + lane, rb = row >> 3, rr = row & 7;
+    for (int b0 = 0; b0 < M; b0 += kBandT) {
+        const int nb = min(kBandT, M - b0);
+        const bool rvalid = rb < nb;
+        const int rt = K1 + b0 + rb;
+        const int er = rvalid ? (int)(__double_as_longlong(sr[8 * (b0 + rb) + rr]) >> 52) : 0;
+        const int n_tiles = (b0 + nb + kColT - 1) / kColT;  // column tiles reaching the band's last row tile
+        if (tid == 0) {  // the band's A and the first column tile's B (buffer 0)
+            const int nc = min(kColT, M);
+            asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(tc.bar_ld),
+                         "r"((uint32_t)(2 * (nb + nc) * kSliceTileBytes))
+                         : "memory");
+            for (int kh = 0; kh < 2; ++kh) {
+                const unsigned char* H = E + kh * KH;
+                bulk_load(stage + kh * kBandT * kSliceTileBytes, H + (int64_t)b0 * kSliceTileBytes,
+                          (uint32_t)nb * kSliceTileBytes, tc.bar_ld);
+                bulk_load(stage + kStageA + kh * kColT * kSliceTileBytes, H, (uint32_t)nc * kSliceTileBytes, tc.bar_ld);
+            }
+        }
+        for (int jt = 0; jt < n_tiles; ++jt) {
+            const int c0 = jt * kColT, nc = min(kColT, M - c0);
+            const uint32_t bufB = aB + (uint32_t)((jt & 1) * kStageB);
+            if (!bar_wait(tc.bar_ld, tc.ph_ld)) return emu_fail(c, tc);
+            tc.ph_ld ^= 1;
+            if (tid == 0) {
+                asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+#pragma unroll
+                for (int kh = 0; kh < 2; ++kh)
+#pragma unroll
+                    for (int ss = 0; ss < 7; ++ss)
+#pragma unroll
+                        for (int tt = 0; tt < 7 && ss + tt < 8; ++tt) {
+                            const int gq = ss + tt;
+                            umma_bf16(tc.tmem + gq * 8 * kColT,
+                                      umma_desc(aA + kh * kBandT * kSliceTileBytes + ss * 256, 128, kSliceTileBytes),
+                                      umma_desc(bufB + kh * kColT * kSliceTileBytes + tt * 256, 128, kSliceTileBytes),
+                                      // the first product of a group (pair (0, g), or (1, 6)
+                                      // for g = 7) overwrites the accumulator
+                                      (kh == 0 && (ss == 0 || (ss == 1 && gq == 7))) ? 0u : 1u);
+                        }
+                asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                                 tc.bar_mma)
+                             : "memory");
+                if (jt + 1 < n_tiles) {  // the next column tile's B into the other buffer
+                    const int c1 = c0 + kColT, n1 = min(kColT, M - c1);
+                    unsigned char* dst = stage + kStageA + ((jt + 1) & 1) * kStageB;
+                    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(tc.bar_ld),
+                                 "r"((uint32_t)(2 * n1 * kSliceTileBytes))
+                                 : "memory");
+                    for (int kh = 0; kh < 2; ++kh)
+                        bulk_load(dst + kh * kColT * kSliceTileBytes, E + kh * KH + (int64_t)c1 * kSliceTileBytes,
+                                  (uint32_t)n1 * kSliceTileBytes, tc.bar_ld);
+                }
+            }
+            // while the MMAs run: this thread's 16 entries of C (row `row`, the 8 columns of each
+            // of its two column tiles) and the column scales, all loads issued at once
+            double cv[2][8];
+            int ec[2][8];
+            bool ok[2];
+#pragma unroll
+            for (int j = 0; j < 2; ++j) {
+                const int cb = 2 * h + j, ct = K1 + c0 + cb;
+                ok[j] = rvalid && cb < nc && ct <= rt;
+                const double* C = A + tix(ok[j] ? rt : K1, ok[j] ? ct : K1);
+                const double* scl = sr + 8 * (ok[j] ? c0 + cb : 0);
+#pragma unroll
+                for (int cc = 0; cc < 8; ++cc) {
+                    cv[j][cc] = ok[j] ? C[te(rr, cc)] : 0.0;
+                    ec[j][cc] = (int)(__double_as_longlong(scl[cc]) >> 52);
+                }
+            }
+            if (!bar_wait(tc.bar_mma, tc.ph_mma)) return emu_fail(c, tc);
+            tc.ph_mma ^= 1;
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+#pragma unroll
+            for (int j = 0; j < 2; ++j) {  // the thread's two column tiles of the output tile
+                const int cb = 2 * h + j;
+#pragma unroll
+                for (int p = 0; p < 2; ++p) {  // four columns at a time
+                    uint32_t v[8][4];
+#pragma unroll
+                    for (int gq = 0; gq < 8; ++gq)
+                        tmem_ld4(tc.tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(gq * 8 * kColT + 8 * cb + 4 * p), v[gq]);
+                    tmem_wait_ld();
+#pragma unroll
+                    for (int e = 0; e < 4; ++e) {
+                        const int cc = 4 * p + e;
+                        // each group read from the bits of G + 1.5 * 2^23 (exact: |G| < 2^22)
+                        long long gq8[8];
+#pragma unroll
+                        for (int gq = 0; gq < 8; ++gq) gq8[gq] = __float_as_int(__uint_as_float(v[gq][e]) + 12582912.0f);
+                        constexpr long long kOffBits = 0x4B400000ll * 0x01010101ll;
+                        const long long hi = gq8[0] * (1ll << 24) + gq8[1] * (1ll << 16) + gq8[2] * 256 + gq8[3] - kOffBits;
+                        const long long lo = gq8[4] * (1ll << 24) + gq8[5] * (1ll << 16) + gq8[6] * 256 + gq8[7] - kOffBits;
+                        cv[j][cc] -= scaled_int(hi * (1ll << 16) + ((lo + (1ll << 15)) >> 16), er + ec[j][cc] - 1079);
+                    }
+                }
+            }
+#pragma unroll
+            for (int j = 0; j < 2; ++j)
+                if (ok[j]) {
+                    double* C = A + tix(rt, K1 + c0 + 2 * h + j);
+#pragma unroll
+                    for (int cc = 0; cc < 8; ++cc) C[te(rr, cc)] = cv[j][cc];
+                }
+            // every thread's reads of the accumulators are done before the next tile's MMAs
+            asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+            __syncthreads();
+        }
+    }
+    return true;
 }
 
 // Right-looking Cholesky of a global-memory instance in blocks of W = 8 kEB columns, with
@@ -499,22 +739,17 @@ __device__ __forceinline__ double* emu_tile_inverses(const SolveCtx& c) {
 // and joined as w = 2^16 hi + round(lo / 2^16), below 2^63 because every group stays below
 // 2^22 with W = 32: the rounding of lo is below 2^-57 of the scale 2^(e_r + e_c - 2042).  The
 // scaled w is built as an FP64 value on the integer pipe (scaled_int) and subtracted: one
-// FP64 operation per updated entry.  With W = 32 every partial group sum stays below 2^22,
-// so the accumulators start at 1.5 * 2^23, where FP32 holds every integer, and the group is
-// read from the accumulator's bits (no float-to-integer conversion).
-// Within a block the diagonal block is factorised as in the plain loop (8x8 tiles, FP64 tensor
-// path); the rows below it are solved one row tile per warp (block_rows).
-__device__ bool factor_emulated(const SolveCtx& c, const Shared& s, double* A, int Nt, int* s_fail) {
+// FP64 operation per updated entry.  The slice products run on the tensor cores
+// (trailing_update_tc); within a block the diagonal block is factorised as in the plain loop
+// (8x8 tiles, FP64 tensor path) and the rows below it are solved one row tile per warp
+// (block_rows), which also writes their slices.
+__device__ bool factor_emulated(const SolveCtx& c, const Shared& s, double* A, int Nt, int* s_fail, EmuTc& tc) {
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarps = blockDim.x >> 5;
     const int g = lane >> 2, t = lane & 3;
-    // per CTA: the slices in mma fragment order, [row tile][slice][16-column step kk][lane]
-    // [2 x u32] (lane = 4 g + t holds columns 16 kk + 2t, +1 and 16 kk + 8 + 2t, +1 of row g
-    // of the tile), so that every A or B fragment is one coalesced 8-byte load per lane; then
-    // npad row scales
-    uint2* sl = reinterpret_cast<uint2*>(c.ws_e + (int64_t)blockIdx.x * c.ws_e_stride);
-    constexpr int kTS = 7 * kEK * 32;  // uint2 per row tile
-    double* sr = reinterpret_cast<double*>(sl + (int64_t)(c.npad / 8) * kTS);
-    double* Tall = emu_tile_inverses(c);  // inverses of all diagonal tiles, for the solves
+    unsigned char* E = emu_ws(c);
+    const int64_t KH = emu_half_bytes(c.npad);
+    double* sr = reinterpret_cast<double*>(E + 2 * KH);  // row scales of the rows below the block
+    double* Tall = emu_tile_inverses(c);                  // inverses of all diagonal tiles, for the solves
     for (int K0 = 0; K0 < Nt; K0 += kEB) {
         const int K1 = min(K0 + kEB, Nt);
         // the diagonal block: tiles (it, jt), K0 <= jt <= it < K1, right-looking by 8 columns
@@ -547,83 +782,23 @@ __device__ bool factor_emulated(const SolveCtx& c, const Shared& s, double* A, i
             __syncthreads();
         }
         if (K1 >= Nt) break;
-        // the rows below: one warp per row tile solves its eight tiles against the diagonal
-        // block and writes their slices and row scales
+        // the rows below: one warp per row tile solves its four tiles against the diagonal
+        // block and writes their slices (both column halves) and row scales
         for (int it = K1 + warp; it < Nt; it += nwarps)
-            block_rows(A, it, K0, s.Tblk, s.Wsc + 64 * warp, sl + (int64_t)(it - K1) * kTS, sr + 8 * (it - K1));
+            block_rows(A, it, K0, s.Tblk, s.Wsc + 64 * warp,
+                       reinterpret_cast<uint32_t*>(E + (int64_t)(it - K1) * kSliceTileBytes),
+                       reinterpret_cast<uint32_t*>(E + KH + (int64_t)(it - K1) * kSliceTileBytes), sr + 8 * (it - K1));
+        // the slices are read by the copy engine (async proxy)
+        asm volatile("fence.proxy.async;" ::: "memory");
         __syncthreads();
-        // trailing update, warp item = 16 rows (tiles i0, i0 + 1) x 8 columns (tile jt),
-        // K1 <= jt <= i0 + 1; items ordered by row pair bi, with bi (bi + 1) items before bi
-        const int M = Nt - K1, MB = (M + 1) >> 1;
-        const int total = (MB - 1) * MB + min(2 * MB, M);
-        for (int p = warp; p < total; p += nwarps) {
-            int bi = (int)((sqrtf(4.f * (float)p + 1.f) - 1.f) * 0.5f);
-            while (bi > 0 && bi * (bi + 1) > p) --bi;
-            while (bi + 1 < MB && (bi + 1) * (bi + 2) <= p) ++bi;
-            const int jt = K1 + (p - bi * (bi + 1));
-            const int i0 = K1 + 2 * bi, i1 = i0 + 1;
-            const bool has1 = i1 < Nt;
-            const int ra = 16 * bi + g, rb = ra + 8;
-            const uint2* fa = sl + (int64_t)(2 * bi) * kTS + lane;  // row tiles i0, i1
-            const uint2* fb = sl + (int64_t)(jt - K1) * kTS + lane;  // column tile jt
-            static_assert(7 * 8 * kEB * 128 * 128 < (1 << 22), "group sums must stay below 2^22");
-            constexpr float kOff = 12582912.0f;  // 1.5 * 2^23, bits 0x4B400000
-            float acc[8][4];
-#pragma unroll
-            for (int q = 0; q < 8; ++q) acc[q][0] = acc[q][1] = acc[q][2] = acc[q][3] = kOff;
-#pragma unroll
-            for (int kk = 0; kk < kEK; ++kk) {
-                uint32_t bf[7][2];
-#pragma unroll
-                for (int tt = 0; tt < 7; ++tt) {
-                    const uint2 v = fb[(tt * kEK + kk) * 32];
-                    bf[tt][0] = v.x;
-                    bf[tt][1] = v.y;
-                }
-#pragma unroll
-                for (int ss = 0; ss < 7; ++ss) {
-                    const uint2 va = fa[(ss * kEK + kk) * 32];
-                    const uint2 vb = has1 ? fa[kTS + (ss * kEK + kk) * 32] : make_uint2(0u, 0u);
-                    uint32_t af[4];
-                    af[0] = va.x;
-                    af[1] = vb.x;
-                    af[2] = va.y;
-                    af[3] = vb.y;
-#pragma unroll
-                    for (int tt = 0; tt < 7 && tt + ss < 8; ++tt) mma_bf16(acc[ss + tt], af, bf[tt]);
-                }
-            }
-#pragma unroll
-            for (int half = 0; half < 2; ++half) {
-                const int it = half ? i1 : i0;
-                if (it >= Nt || it < jt) continue;  // past the end, or above the diagonal
-                double* C = A + tix(it, jt);
-                // biased exponents of the row scales (0 for a zero row, whose w is 0)
-                const int er = (int)(__double_as_longlong(sr[half ? rb : ra]) >> 52);
-#pragma unroll
-                for (int e = 0; e < 2; ++e) {
-                    const int ai = 2 * half + e, col = 2 * t + e;
-                    const int ec = (int)(__double_as_longlong(sr[8 * (jt - K1) + col]) >> 52);
-                    long long gq[8];  // G + 0x4B400000: the accumulator bits
-#pragma unroll
-                    for (int q = 0; q < 8; ++q) gq[q] = __float_as_int(acc[q][ai]);
-                    constexpr long long kOffBits = 0x4B400000ll * 0x01010101ll;
-                    const long long hi = gq[0] * (1ll << 24) + gq[1] * (1ll << 16) + gq[2] * 256 + gq[3] - kOffBits;
-                    const long long lo = gq[4] * (1ll << 24) + gq[5] * (1ll << 16) + gq[6] * 256 + gq[7] - kOffBits;
-                    // scale 2^(er + ec - 2046) 2^-56 = 2^(eS - 1023)
-                    double* cp = C + te(g, col);
-                    *cp -= scaled_int(hi * (1ll << 16) + ((lo + (1ll << 15)) >> 16), er + ec - 1079);
-                }
-            }
-        }
-        __syncthreads();
+        if (!trailing_update_tc(c, A, Nt, K1, E, KH, sr, s.stage, tc)) return false;
     }
     return true;
 }
 
 // Assemble A, factorise, solve alpha.  Returns false if a pivot was not positive.
 template <bool kProps, bool kEmu = false>
-__device__ bool fit_instance(const SolveCtx& c, const Shared& s, int N, int64_t base) {
+__device__ bool fit_instance(const SolveCtx& c, const Shared& s, int N, int64_t base, EmuTc* tc = nullptr) {
     const int tid = threadIdx.x, nt = blockDim.x;
     const int lane = tid & 31, warp = tid >> 5, nwarps = nt >> 5;
     const int g = lane >> 2, t = lane & 3;
@@ -660,7 +835,19 @@ __device__ bool fit_instance(const SolveCtx& c, const Shared& s, int N, int64_t 
     }
     __syncthreads();
     if (kEmu) {
-        if (!factor_emulated(c, s, A, Nt, &s_fail)) return false;
+        if (!factor_emulated(c, s, A, Nt, &s_fail, *tc)) return false;
+        // the staging of the tensor-core updates overwrote X, Xf and xi: reload them
+        for (int e = tid; e < 3 * N; e += nt) {
+            double v = c.b.Xl[3 * base + e];
+            s.X[e] = v;
+            s.Xf[e] = (float)v;
+        }
+        if (lattice)
+            for (int e = tid; e < N; e += nt) {
+                const char4 q = c.b.Xi[base + e];
+                s.xi[e] = ((int)q.x + 16) | (((int)q.y + 16) << 8) | (((int)q.z + 16) << 16);
+            }
+        __syncthreads();
     } else
     for (int kt = 0; kt < Nt; ++kt) {
         // diagonal tile: 8x8 Cholesky and the inverse of its factor (FP64 pipe)
@@ -1007,14 +1194,39 @@ __device__ __forceinline__ void invalid(EvalOut& r, int status) {
 // The body of the GP solve kernels (see k_solve below).
 template <bool kProps, bool kEmu>
 __device__ __forceinline__ void solve_body(const SolveCtx& c) {
-    extern __shared__ double sm[];
+    extern __shared__ __align__(128) double sm[];
     __shared__ int s_w;
+    __shared__ uint32_t s_tmem;
+    __shared__ __align__(8) uint64_t s_bar[2];
     const int tid = threadIdx.x, nt = blockDim.x;
     double* ws_a = c.a_in_smem ? nullptr : c.ws_a + (int64_t)blockIdx.x * c.ws_a_stride;
     Shared s = carve(sm, c.npad, c.a_in_smem, ws_a, c.b.nprop, c.stage_panel, c.b.Xi != nullptr, false, kEmu);
     double* V = c.ws_v ? c.ws_v + (int64_t)blockIdx.x * c.ws_v_stride + tid : nullptr;
     const bool lattice = c.b.Xi != nullptr;
     for (int j = tid; j < 256; j += nt) s.T256[j] = c.P.exp_tab[j];
+    EmuTc tc{};
+    if (kEmu) {
+        // tensor memory for the 8 slice-group accumulators (held until the CTA exits) and the
+        // barriers of the staging copies and of the MMAs
+        if ((tid >> 5) == 0) {
+            asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_addr(&s_tmem)),
+                         "r"(kEmuTmemCols)
+                         : "memory");
+            asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+        }
+        if (tid == 0) {
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(&s_bar[0])) : "memory");
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(&s_bar[1])) : "memory");
+            asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        }
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+        __syncthreads();
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        tc.tmem = s_tmem;
+        tc.bar_ld = smem_addr(&s_bar[0]);
+        tc.bar_mma = smem_addr(&s_bar[1]);
+    }
     for (;;) {
         if (tid == 0) s_w = atomicAdd(c.counter, 1);
         __syncthreads();
@@ -1027,7 +1239,7 @@ __device__ __forceinline__ void solve_body(const SolveCtx& c) {
         const int64_t base = c.b.inst_off[I];
         const int N = (int)(c.b.inst_off[I + 1] - base);
         const int64_t q0 = c.b.q_off[I], q1 = c.b.q_off[I + 1];
-        const bool ok = N > 0 && fit_instance<kProps, kEmu>(c, s, N, base);
+        const bool ok = N > 0 && fit_instance<kProps, kEmu>(c, s, N, base, &tc);
         if (kProps) {
             // property mode: means and variance (Eq. 6, variance read as for Eq. 2)
             const int np = c.b.nprop;
@@ -1045,8 +1257,9 @@ __device__ __forceinline__ void solve_body(const SolveCtx& c) {
                 for (int ch = 0; ch < np; ++ch) c.b.pc[qid * np + ch] = cm[ch];
                 c.b.pw[qid] = w;
             }
-            if (!ok && N > 0 && tid == 0) atomicOr(c.err, kErrFactor);
+            if (!ok && N > 0 && tid == 0 && !tc.dead) atomicOr(c.err, kErrFactor);
             __syncthreads();
+            if (kEmu && tc.dead) break;
             continue;
         }
         if (c.b.alpha_out)
@@ -1070,8 +1283,20 @@ __device__ __forceinline__ void solve_body(const SolveCtx& c) {
             }
             write_out(c.b, qid, r);
         }
-        if (!ok && N > 0 && tid == 0) atomicOr(c.err, kErrFactor);
+        if (!ok && N > 0 && tid == 0 && !tc.dead) atomicOr(c.err, kErrFactor);
         __syncthreads();
+        if (kEmu && tc.dead) break;
+    }
+    if (kEmu) {
+        if (tc.dead) {  // let copies or MMAs still in flight finish (bounded) before releasing
+            bar_wait(tc.bar_ld, tc.ph_ld);
+            bar_wait(tc.bar_mma, tc.ph_mma);
+        }
+        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+        __syncthreads();
+        if ((tid >> 5) == 0)
+            asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tc.tmem), "r"(kEmuTmemCols)
+                         : "memory");
     }
 }
 
@@ -1284,6 +1509,38 @@ SolveKernel pick_solve(bool props, bool emu) {
 // seven bf16 slices of a block's columns, the row scale, and one row of diagonal-tile inverses
 constexpr int64_t kEmuBytesPerRow = 7 * 8 * kEB * 2 + 8 + 64;
 
+// The emulated kernel's shared memory (about 100 KB at N = 1024) fits twice per SM only in the
+// largest shared-memory configuration; ask for it (a preference, so a failure is harmless).
+void set_emu_carveout(SolveKernel k) {
+    if (cudaFuncSetAttribute(k, cudaFuncAttributePreferredSharedMemoryCarveout, (int)cudaSharedmemCarveoutMaxShared) !=
+        cudaSuccess)
+        cudaGetLastError();
+}
+
+// Resident CTAs per SM of the emulated kernel.  The occupancy calculator reports one CTA per SM
+// for any kernel that allocates tensor memory, while the SM runs as many as their registers,
+// shared memory and tensor memory allow (each CTA holds kEmuTmemCols of the 512 columns), so
+// the bound is computed from those resources.
+int emu_ctas_per_sm(SolveKernel k, int threads, size_t shm) {
+    cudaFuncAttributes fa{};
+    int dev = 0, regs_sm = 65536, smem_sm = 0, thr_sm = 2048;
+    if (cudaFuncGetAttributes(&fa, k) != cudaSuccess || cudaGetDevice(&dev) != cudaSuccess) {
+        cudaGetLastError();
+        return 1;
+    }
+    cudaDeviceGetAttribute(&regs_sm, cudaDevAttrMaxRegistersPerMultiprocessor, dev);
+    cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
+    cudaDeviceGetAttribute(&thr_sm, cudaDevAttrMaxThreadsPerMultiProcessor, dev);
+    const int warps = (threads + 31) / 32;
+    const int regs_cta = warps * ((fa.numRegs * 32 + 255) & ~255);  // allocated per warp in units of 256
+    const size_t smem_cta = shm + fa.sharedSizeBytes + 1024;        // 1 KB reserved per CTA
+    int n = kEmuCtasPerSm;
+    n = std::min(n, regs_cta > 0 ? regs_sm / regs_cta : n);
+    n = std::min(n, (int)(smem_sm / std::max<size_t>(smem_cta, 1)));
+    n = std::min(n, thr_sm / std::max(threads, 1));
+    return std::max(n, 1);
+}
+
 }  // namespace
 
 void graph_cache_destroy(GraphCache& gc) {
@@ -1354,6 +1611,7 @@ int solve_batch_graph(const SolveBatch& b, const DevParams& P, int* err_dev, cud
     // launch it, set before any occupancy query or captured launch
     for (int i = 0; i < 5; ++i) {
         if (!sh[i].live) continue;
+        if (sh[i].emu) set_emu_carveout(sh[i].kern);
         size_t shm_max = 0;
         for (int j = 0; j < 5; ++j)
             if (sh[j].live && sh[j].kern == sh[i].kern) shm_max = std::max(shm_max, sh[j].shm);
@@ -1365,9 +1623,13 @@ int solve_batch_graph(const SolveBatch& b, const DevParams& P, int* err_dev, cud
         Shape& s = sh[i];
         if (!s.live) continue;
         int per_sm = 0;
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, s.kern, s.threads, s.shm);
-        per_sm = std::max(per_sm, 1);
-        if (cfg->per_sm[i] > 0 && !s.emu) per_sm = std::min(per_sm, cfg->per_sm[i]);
+        if (s.emu) {
+            per_sm = emu_ctas_per_sm(s.kern, s.threads, s.shm);
+        } else {
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, s.kern, s.threads, s.shm);
+            per_sm = std::max(per_sm, 1);
+            if (cfg->per_sm[i] > 0) per_sm = std::min(per_sm, cfg->per_sm[i]);
+        }
         s.grid = (int)std::min<int64_t>(n, (int64_t)n_sm * per_sm);
         if (!s.smem_a) ws_a_need = std::max<int64_t>(ws_a_need, n_tiles(s.npad / 8) * 64 * s.grid);
         if (b.want_var) ws_v_need = std::max<int64_t>(ws_v_need, (int64_t)s.npad * s.threads * s.grid);
@@ -1624,10 +1886,15 @@ int solve_batch(const SolveBatch& b, const DevParams& P, int* err_dev, cudaStrea
             smem_bytes(c.npad, c.a_in_smem, bw ? 0 : b.nprop, c.stage_panel, b.Xi != nullptr, bw != nullptr, emu);
         auto kern = bw ? k_backward : pick_solve(b.nprop > 0, emu);
         cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm);
+        if (emu) set_emu_carveout(kern);
         int per_sm = 0;
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, threads, shm);
-        per_sm = std::max(per_sm, 1);
-        if (cfg->per_sm[bi] > 0 && !emu) per_sm = std::min(per_sm, cfg->per_sm[bi]);  // emulated: occupancy limit
+        if (emu) {
+            per_sm = emu_ctas_per_sm(kern, threads, shm);
+        } else {
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, threads, shm);
+            per_sm = std::max(per_sm, 1);
+            if (cfg->per_sm[bi] > 0) per_sm = std::min(per_sm, cfg->per_sm[bi]);
+        }
         const int grid = (int)std::min<int64_t>(cnt, (int64_t)n_sm * per_sm);
         c.ws_a_stride = c.a_in_smem ? 0 : n_tiles(c.npad / 8) * 64;
         c.ws_a = c.a_in_smem ? nullptr : (double*)ar.get(Arena::kWs0, sizeof(double) * c.ws_a_stride * grid, st);
