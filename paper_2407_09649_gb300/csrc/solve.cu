@@ -72,6 +72,8 @@ struct SolveCtx {
     uint8_t* ws_e;         // per-CTA bf16 slices and row scales (emulated trailing updates)
     int64_t ws_e_stride;
     BackwardBatch bw;
+    int qmax = 0;          // emulated kernel with variance: query rows appended to A (0: none)
+    int nrow = 0;          // emulated kernel: rows of the workspace matrices (npad + qmax)
 };
 
 struct Shared {
@@ -94,6 +96,7 @@ struct Shared {
     double* Wsc;    // [warps][64] per-warp tile scratch (layout changes between mma operands)
     unsigned char* stage;  // emulated kernel: slice operands of the tensor-core updates (aliases
                            // X .. alf_lo, which the factorisation does not use; reloaded after it)
+    double* qxl;           // emulated kernel: [kBorderQ][3] local coordinates of appended queries
 };
 
 // Emulated trailing updates on the tensor cores (tcgen05): an output tile is kBandT row tiles
@@ -107,15 +110,22 @@ constexpr int kStageA = 2 * kBandT * kSliceTileBytes;
 constexpr int kStageB = 2 * kColT * kSliceTileBytes;
 constexpr int kStageBytes = kStageA + 2 * kStageB;
 constexpr int kEmuTmemCols = 8 * 8 * kColT;    // 8 slice groups x 32 FP32 columns
+// Latent variance in the emulated kernel: up to kBorderQ queries of an instance append their
+// kernel vectors to A as rows, so the factorisation itself yields 1 - |L^-1 k|^2 (see
+// fit_instance); an instance with more queries is factorised once per chunk of kBorderQ.
+constexpr int kBorderQ = 256;
 constexpr int kEmuCtasPerSm = 512 / kEmuTmemCols;  // CTAs whose tensor memory fits one SM
 
 __host__ __device__ __forceinline__ size_t align128(size_t x) { return (x + 127) & ~(size_t)127; }
 __host__ __device__ __forceinline__ size_t emu_fixed_bytes(int npad) {
     return align128((size_t)(npad + 256 + kEB * 64 + 8 * 64) * sizeof(double));  // invd, T256, Tblk, Wsc
 }
+__host__ __device__ __forceinline__ size_t emu_point_bytes(int npad, int nprop, bool lattice) {
+    return (size_t)5 * npad * sizeof(double) + (size_t)5 * npad * sizeof(float) +
+           (lattice ? (size_t)npad * sizeof(int) : 0) + (size_t)(nprop > 2 ? nprop - 2 : 0) * npad * sizeof(double);
+}
 __host__ __device__ __forceinline__ size_t emu_alias_bytes(int npad, int nprop, bool lattice) {
-    const size_t b = (size_t)5 * npad * sizeof(double) + (size_t)5 * npad * sizeof(float) +
-                     (lattice ? (size_t)npad * sizeof(int) : 0) + (size_t)(nprop > 2 ? nprop - 2 : 0) * npad * sizeof(double);
+    const size_t b = emu_point_bytes(npad, nprop, lattice) + (size_t)kBorderQ * 3 * sizeof(double);
     return b > (size_t)kStageBytes ? b : (size_t)kStageBytes;
 }
 
@@ -145,6 +155,7 @@ __device__ Shared carve_emu(double* sm, int npad, double* ws_a, int nprop, bool 
     s.pa[1] = reinterpret_cast<double*>(s.alf);
     s.pa[2] = nprop > 2 ? extra : nullptr;
     s.pa[3] = nprop > 3 ? extra + npad : nullptr;
+    s.qxl = reinterpret_cast<double*>(s.stage + emu_point_bytes(npad, nprop, lattice));
     return s;
 }
 
@@ -153,6 +164,7 @@ __device__ Shared carve(double* sm, int npad, int a_in_smem, double* ws_a, int n
     if (emu) return carve_emu(sm, npad, ws_a, nprop, lattice);
     Shared s;
     s.stage = nullptr;
+    s.qxl = nullptr;
     s.X = sm;
     s.alpha = s.X + 3 * npad;
     s.invd = s.alpha + npad;
@@ -531,8 +543,9 @@ __device__ void block_rows(double* A, int it, int K0, const double* Tblk, double
 // doubles).
 __device__ __forceinline__ unsigned char* emu_ws(const SolveCtx& c) { return c.ws_e + (int64_t)blockIdx.x * c.ws_e_stride; }
 __device__ __forceinline__ int64_t emu_half_bytes(int npad) { return (int64_t)(npad / 8) * kSliceTileBytes; }
+__device__ __forceinline__ int emu_rows(const SolveCtx& c) { return c.nrow > 0 ? c.nrow : c.npad; }
 __device__ __forceinline__ double* emu_tile_inverses(const SolveCtx& c) {
-    return reinterpret_cast<double*>(emu_ws(c) + 2 * emu_half_bytes(c.npad)) + c.npad;
+    return reinterpret_cast<double*>(emu_ws(c) + 2 * emu_half_bytes(emu_rows(c))) + emu_rows(c);
 }
 
 // ---- tensor-core (tcgen05) helpers for the emulated updates --------------------------------
@@ -604,10 +617,13 @@ __device__ __forceinline__ bool emu_fail(const SolveCtx& c, EmuTc& tc) {
 // pairs x 2 halves) into the 8 group accumulators; all 8 warps then read their rows (lane
 // quadrant warp % 4) and columns (half warp / 4) of the groups, pack each element's groups into
 // one integer and subtract it as an FP64 value.
-__device__ bool trailing_update_tc(const SolveCtx& c, double* A, int Nt, int K1, const unsigned char* E,
+// With appended query rows (tiles Ntr .. Nt - 1, see fit_instance) only the diagonal tiles of
+// the query-by-query block are needed: its other column tiles are skipped.
+__device__ bool trailing_update_tc(const SolveCtx& c, double* A, int Nt, int Ntr, int K1, const unsigned char* E,
                                    int64_t KH, const double* sr, unsigned char* stage, EmuTc& tc) {
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int M = Nt - K1;
+    const int jr = (max(Ntr - K1, 0) + kColT - 1) / kColT;  // column tiles of the matrix itself
     const uint32_t aA = smem_addr(stage), aB = aA + kStageA;
     const int q = warp & 3, h = warp >> 2;  // lane quadrant (rows 32 q ..) and column half
     const int row = 32 * q + lane, rb = row >> 3, rr = row & 7;
@@ -617,8 +633,13 @@ __device__ bool trailing_update_tc(const SolveCtx& c, double* A, int Nt, int K1,
         const int rt = K1 + b0 + rb;
         const int er = rvalid ? (int)(__double_as_longlong(sr[8 * (b0 + rb) + rr]) >> 52) : 0;
         const int n_tiles = (b0 + nb + kColT - 1) / kColT;  // column tiles reaching the band's last row tile
+        // column tiles of appended query rows: only those that meet the band's rows
+        const int qstart = max(jr, b0 / kColT);
+        auto next_tile = [&](int j) { return j + 1 < jr ? j + 1 : max(j + 1, qstart); };
+        const int first = jr > 0 ? 0 : qstart;
+        if (first >= n_tiles) continue;
         if (tid == 0) {  // the band's A and the first column tile's B (buffer 0)
-            const int nc = min(kColT, M);
+            const int nc = min(kColT, M - first * kColT);
             asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(tc.bar_ld),
                          "r"((uint32_t)(2 * (nb + nc) * kSliceTileBytes))
                          : "memory");
@@ -626,12 +647,13 @@ __device__ bool trailing_update_tc(const SolveCtx& c, double* A, int Nt, int K1,
                 const unsigned char* H = E + kh * KH;
                 bulk_load(stage + kh * kBandT * kSliceTileBytes, H + (int64_t)b0 * kSliceTileBytes,
                           (uint32_t)nb * kSliceTileBytes, tc.bar_ld);
-                bulk_load(stage + kStageA + kh * kColT * kSliceTileBytes, H, (uint32_t)nc * kSliceTileBytes, tc.bar_ld);
+                bulk_load(stage + kStageA + kh * kColT * kSliceTileBytes, H + (int64_t)first * kColT * kSliceTileBytes,
+                          (uint32_t)nc * kSliceTileBytes, tc.bar_ld);
             }
         }
-        for (int jt = 0; jt < n_tiles; ++jt) {
+        for (int jt = first, kb = 0; jt < n_tiles; jt = next_tile(jt), ++kb) {
             const int c0 = jt * kColT, nc = min(kColT, M - c0);
-            const uint32_t bufB = aB + (uint32_t)((jt & 1) * kStageB);
+            const uint32_t bufB = aB + (uint32_t)((kb & 1) * kStageB);
             if (!bar_wait(tc.bar_ld, tc.ph_ld)) return emu_fail(c, tc);
             tc.ph_ld ^= 1;
             if (tid == 0) {
@@ -653,9 +675,9 @@ __device__ bool trailing_update_tc(const SolveCtx& c, double* A, int Nt, int K1,
                 asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
                                  tc.bar_mma)
                              : "memory");
-                if (jt + 1 < n_tiles) {  // the next column tile's B into the other buffer
-                    const int c1 = c0 + kColT, n1 = min(kColT, M - c1);
-                    unsigned char* dst = stage + kStageA + ((jt + 1) & 1) * kStageB;
+                if (next_tile(jt) < n_tiles) {  // the next column tile's B into the other buffer
+                    const int c1 = next_tile(jt) * kColT, n1 = min(kColT, M - c1);
+                    unsigned char* dst = stage + kStageA + ((kb + 1) & 1) * kStageB;
                     asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(tc.bar_ld),
                                  "r"((uint32_t)(2 * n1 * kSliceTileBytes))
                                  : "memory");
@@ -672,7 +694,7 @@ __device__ bool trailing_update_tc(const SolveCtx& c, double* A, int Nt, int K1,
 #pragma unroll
             for (int j = 0; j < 2; ++j) {
                 const int cb = 2 * h + j, ct = K1 + c0 + cb;
-                ok[j] = rvalid && cb < nc && ct <= rt;
+                ok[j] = rvalid && cb < nc && ct <= rt && (ct < Ntr || ct == rt);
                 const double* C = A + tix(ok[j] ? rt : K1, ok[j] ? ct : K1);
                 const double* scl = sr + 8 * (ok[j] ? c0 + cb : 0);
 #pragma unroll
@@ -743,15 +765,18 @@ __device__ bool trailing_update_tc(const SolveCtx& c, double* A, int Nt, int K1,
 // (trailing_update_tc); within a block the diagonal block is factorised as in the plain loop
 // (8x8 tiles, FP64 tensor path) and the rows below it are solved one row tile per warp
 // (block_rows), which also writes their slices.
-__device__ bool factor_emulated(const SolveCtx& c, const Shared& s, double* A, int Nt, int* s_fail, EmuTc& tc) {
+// Nt row tiles, of which the first Ntr are factorised (Nt > Ntr: appended query rows, whose
+// rows below are solved and whose diagonal tiles are updated, but not factorised).
+__device__ bool factor_emulated(const SolveCtx& c, const Shared& s, double* A, int Nt, int Ntr, int* s_fail,
+                                EmuTc& tc) {
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarps = blockDim.x >> 5;
     const int g = lane >> 2, t = lane & 3;
     unsigned char* E = emu_ws(c);
-    const int64_t KH = emu_half_bytes(c.npad);
+    const int64_t KH = emu_half_bytes(emu_rows(c));
     double* sr = reinterpret_cast<double*>(E + 2 * KH);  // row scales of the rows below the block
     double* Tall = emu_tile_inverses(c);                  // inverses of all diagonal tiles, for the solves
-    for (int K0 = 0; K0 < Nt; K0 += kEB) {
-        const int K1 = min(K0 + kEB, Nt);
+    for (int K0 = 0; K0 < Ntr; K0 += kEB) {
+        const int K1 = min(K0 + kEB, Ntr);
         // the diagonal block: tiles (it, jt), K0 <= jt <= it < K1, right-looking by 8 columns
         for (int kt = K0; kt < K1; ++kt) {
             double* Ti = s.Tblk + 64 * (kt - K0);
@@ -791,19 +816,31 @@ __device__ bool factor_emulated(const SolveCtx& c, const Shared& s, double* A, i
         // the slices are read by the copy engine (async proxy)
         asm volatile("fence.proxy.async;" ::: "memory");
         __syncthreads();
-        if (!trailing_update_tc(c, A, Nt, K1, E, KH, sr, s.stage, tc)) return false;
+        if (!trailing_update_tc(c, A, Nt, Ntr, K1, E, KH, sr, s.stage, tc)) return false;
     }
     return true;
 }
 
 // Assemble A, factorise, solve alpha.  Returns false if a pivot was not positive.
+// Local coordinates of the query at position p (id qid) of instance I (defined below).
+__device__ __forceinline__ void query_local(const SolveCtx& c, int I, int64_t p, int64_t qid, double xl[3],
+                                            int* qi = nullptr);
+
+// Latent variance by bordering (emulated kernel, nq > 0 queries of instance I from position q0):
+// the matrix is padded to Nr = 32 ceil(N / 32) rows and the kernel vectors k_a of the queries are
+// appended as rows Nr + a, with k(x*, x*) = 1 on the diagonal.  Factorising only the first Nr
+// columns turns row Nr + a into v_a = L^-1 k_a and leaves the Schur complement, whose diagonal
+// entry is 1 - |v_a|^2 = u_a (Eq. 2).  Each appended row's arithmetic involves only that row and
+// the instance's own rows, so u_a does not depend on the other queries.
 template <bool kProps, bool kEmu = false>
-__device__ bool fit_instance(const SolveCtx& c, const Shared& s, int N, int64_t base, EmuTc* tc = nullptr) {
+__device__ bool fit_instance(const SolveCtx& c, const Shared& s, int N, int64_t base, EmuTc* tc = nullptr, int nq = 0,
+                             int64_t q0 = 0, int I = 0) {
     const int tid = threadIdx.x, nt = blockDim.x;
     const int lane = tid & 31, warp = tid >> 5, nwarps = nt >> 5;
     const int g = lane >> 2, t = lane & 3;
     __shared__ int s_fail;
-    const int Np = (N + 7) & ~7, Nt = Np >> 3;
+    const int Np = nq > 0 ? (N + 31) & ~31 : (N + 7) & ~7, Nt = Np >> 3;  // the instance's rows (Nr)
+    const int Ntq = Nt + (nq + 7) / 8;                                   // with the appended rows
     const bool lattice = c.b.Xi != nullptr;
     for (int e = tid; e < 3 * N; e += nt) {
         double v = c.b.Xl[3 * base + e];
@@ -815,18 +852,42 @@ __device__ bool fit_instance(const SolveCtx& c, const Shared& s, int N, int64_t 
             const char4 q = c.b.Xi[base + e];
             s.xi[e] = ((int)q.x + 16) | (((int)q.y + 16) << 8) | (((int)q.z + 16) << 16);
         }
+    if (nq > 0)  // local coordinates of the appended queries (NaN: not finite, row left zero)
+        for (int a = tid; a < nq; a += nt) {
+            const int64_t p = q0 + a;
+            const int64_t qid = c.b.qidx ? c.b.qidx[p] : p;
+            double xl[3];
+            query_local(c, I, p, qid, xl);
+            const bool fin = isfinite(xl[0]) && isfinite(xl[1]) && isfinite(xl[2]);
+            for (int k = 0; k < 3; ++k) s.qxl[3 * a + k] = fin ? xl[k] : NAN;
+        }
     if (tid == 0) s_fail = 0;
     __syncthreads();
     double* A = s.A;
     // A = K + sigma^2 I in 8x8 tiles (Sec. III-A kernel, Eq. 1 noise term); padding rows and
-    // columns are the identity so the padded factor is block-diagonal.
-    const int64_t ntl = n_tiles(Nt);
+    // columns are the identity so the padded factor is block-diagonal.  Appended query rows:
+    // the query's kernel values (FP64, as in latent_var), 1 on the diagonal, and only the
+    // diagonal tiles of the query-by-query block.
+    const int64_t ntl = n_tiles(Ntq);
     for (int64_t tl = warp; tl < ntl; tl += nwarps) {
         const int it = tri_row((int)tl), jt = (int)tl - it * (it + 1) / 2;
+        if (jt >= Nt && jt != it) continue;
         for (int e = lane; e < 64; e += 32) {
             const int i = 8 * it + (e >> 3), j = 8 * jt + (e & 7);
             double v;
-            if (i >= N || j >= N) v = (i == j) ? 1.0 : 0.0;
+            if (i >= Np) {  // appended query row a = i - Np
+                const int a = i - Np;
+                if (j >= Np || a >= nq) {
+                    v = (i == j) ? 1.0 : 0.0;
+                } else if (j >= N || isnan(s.qxl[3 * a])) {
+                    v = 0.0;
+                } else {
+                    const double dx = s.X[3 * j] - s.qxl[3 * a], dy = s.X[3 * j + 1] - s.qxl[3 * a + 1],
+                                 dz = s.X[3 * j + 2] - s.qxl[3 * a + 2];
+                    const double y = -(dx * dx + dy * dy + dz * dz) * c.P.inv2l2;
+                    v = c.P.precision == VGP_MIXED ? exp_neg(y, s.T256) : exp(y);
+                }
+            } else if (i >= N || j >= N) v = (i == j) ? 1.0 : 0.0;
             else if (j > i) v = 0.0;
             else if (j == i) v = 1.0 + c.P.s2;
             else v = kval_pair(c.P, s, lattice, i, j);
@@ -835,7 +896,7 @@ __device__ bool fit_instance(const SolveCtx& c, const Shared& s, int N, int64_t 
     }
     __syncthreads();
     if (kEmu) {
-        if (!factor_emulated(c, s, A, Nt, &s_fail, *tc)) return false;
+        if (!factor_emulated(c, s, A, Ntq, Nt, &s_fail, *tc)) return false;
         // the staging of the tensor-core updates overwrote X, Xf and xi: reload them
         for (int e = tid; e < 3 * N; e += nt) {
             double v = c.b.Xl[3 * base + e];
@@ -959,26 +1020,30 @@ __device__ bool fit_instance(const SolveCtx& c, const Shared& s, int N, int64_t 
         __syncthreads();
     }
     if (s_fail) return false;
+    // The solves use the instance's own 8-row tiles only: the leading block of the factor is the
+    // factor of the leading block, so rows padded to 32 for appended queries change no bit of
+    // alpha (the solves' work split depends on the tile count).
+    const int Ns = (N + 7) & ~7, Nts = Ns >> 3;
     if (kProps) {
         // property weights alpha_c = A^-1 y_c, one right-hand side per channel (Eq. 6)
         for (int ch = 0; ch < c.b.nprop; ++ch) {
-            for (int i = tid; i < Np; i += nt) s.z[i] = i < N ? c.b.yprop[(base + i) * c.b.nprop + ch] : 0.0;
+            for (int i = tid; i < Ns; i += nt) s.z[i] = i < N ? c.b.yprop[(base + i) * c.b.nprop + ch] : 0.0;
             __syncthreads();
             if (kEmu)
-                chol_solve_inv(s, A, Nt, s.pa[ch], emu_tile_inverses(c));
+                chol_solve_inv(s, A, Nts, s.pa[ch], emu_tile_inverses(c));
             else
-                chol_solve(s, A, Nt, s.pa[ch]);
+                chol_solve(s, A, Nts, s.pa[ch]);
         }
         return true;
     }
     // alpha = A^-1 1 (Eq. 1)
-    for (int i = tid; i < Np; i += nt) s.z[i] = i < N ? 1.0 : 0.0;
+    for (int i = tid; i < Ns; i += nt) s.z[i] = i < N ? 1.0 : 0.0;
     __syncthreads();
     if (kEmu)
-        chol_solve_inv(s, A, Nt, s.alpha, emu_tile_inverses(c));
+        chol_solve_inv(s, A, Nts, s.alpha, emu_tile_inverses(c));
     else
-        chol_solve(s, A, Nt, s.alpha);
-    for (int j = tid; j < Np; j += nt) {
+        chol_solve(s, A, Nts, s.alpha);
+    for (int j = tid; j < Ns; j += nt) {
         const float hi = (float)s.alpha[j];
         s.alf[j] = hi;
         s.alf_lo[j] = (float)(s.alpha[j] - (double)hi);
@@ -1035,7 +1100,7 @@ __device__ __forceinline__ void write_out(const SolveBatch& b, int64_t qid, cons
 }
 
 __device__ __forceinline__ void query_local(const SolveCtx& c, int I, int64_t p, int64_t qid, double xl[3],
-                                            int* qi = nullptr) {
+                                            int* qi) {
     double xg[3];
     if (c.b.qkey) {
         int i, j, k;
@@ -1239,8 +1304,8 @@ __device__ __forceinline__ void solve_body(const SolveCtx& c) {
         const int64_t base = c.b.inst_off[I];
         const int N = (int)(c.b.inst_off[I + 1] - base);
         const int64_t q0 = c.b.q_off[I], q1 = c.b.q_off[I + 1];
-        const bool ok = N > 0 && fit_instance<kProps, kEmu>(c, s, N, base, &tc);
         if (kProps) {
+            const bool ok = N > 0 && fit_instance<kProps, kEmu>(c, s, N, base, &tc);
             // property mode: means and variance (Eq. 6, variance read as for Eq. 2)
             const int np = c.b.nprop;
             for (int64_t p = q0 + tid; p < q1; p += nt) {
@@ -1262,29 +1327,51 @@ __device__ __forceinline__ void solve_body(const SolveCtx& c) {
             if (kEmu && tc.dead) break;
             continue;
         }
-        if (c.b.alpha_out)
-            for (int j = tid; j < N; j += nt) c.b.alpha_out[base + j] = ok ? s.alpha[j] : NAN;
-        for (int64_t p = q0 + tid; p < q1; p += nt) {
-            const int64_t qid = c.b.qidx ? c.b.qidx[p] : p;
-            EvalOut r;
-            if (!ok) {
-                invalid(r, N > 0 ? VGP_ST_FACTOR_FAIL : VGP_ST_NO_SUPPORT);
-            } else {
-                double xl[3], lo, gro[3];
-                int qi = 0;
-                query_local(c, I, p, qid, xl, &qi);
-                if (!(isfinite(xl[0]) && isfinite(xl[1]) && isfinite(xl[2]))) {
-                    invalid(r, VGP_ST_BAD_INPUT);
+        // Variance by bordering (see fit_instance): the instance's queries are appended to its
+        // matrix in chunks of at most qmax, one factorisation per chunk.  Every chunk repeats
+        // the same arithmetic on the instance's own rows, and a query's row involves only
+        // itself, so every result is independent of the chunking and of the other queries.
+        const bool border = kEmu && c.b.want_var && !lattice && c.qmax > 0;
+        const int Ntr = ((N + 31) & ~31) >> 3;  // first appended row tile
+        for (int64_t cq0 = q0;;) {
+            const int64_t cq1 = border ? min(q1, cq0 + (int64_t)c.qmax) : q1;
+            const bool ok = N > 0 && fit_instance<kProps, kEmu>(c, s, N, base, &tc, border ? (int)(cq1 - cq0) : 0,
+                                                                 cq0, I);
+            if (c.b.alpha_out && cq0 == q0)
+                for (int j = tid; j < N; j += nt) c.b.alpha_out[base + j] = ok ? s.alpha[j] : NAN;
+            const int64_t ce = ok ? cq1 : q1;  // a failed factorisation answers all remaining queries
+            for (int64_t p = cq0 + tid; p < ce; p += nt) {
+                const int64_t qid = c.b.qidx ? c.b.qidx[p] : p;
+                EvalOut r;
+                if (!ok) {
+                    invalid(r, N > 0 ? VGP_ST_FACTOR_FAIL : VGP_ST_NO_SUPPORT);
                 } else {
-                    latent_mean(c.P, s, N, lattice, qi, xl, lo, gro);
-                    const double u = c.b.want_var ? latent_var(c.P, s, N, lattice, qi, xl, V, nt) : 0.0;
-                    revert(c.P, lo, gro, u, c.b.want_var != 0, r);
+                    double xl[3], lo, gro[3];
+                    int qi = 0;
+                    query_local(c, I, p, qid, xl, &qi);
+                    if (!(isfinite(xl[0]) && isfinite(xl[1]) && isfinite(xl[2]))) {
+                        invalid(r, VGP_ST_BAD_INPUT);
+                    } else {
+                        latent_mean(c.P, s, N, lattice, qi, xl, lo, gro);
+                        double u = 0.0;
+                        if (c.b.want_var) {
+                            if (border) {  // the Schur complement's diagonal entry, clamped at 0
+                                const int a = (int)(p - cq0), ta = Ntr + (a >> 3);
+                                u = fmax(0.0, s.A[tix(ta, ta) + te(a & 7, a & 7)]);
+                            } else {
+                                u = latent_var(c.P, s, N, lattice, qi, xl, V, nt);
+                            }
+                        }
+                        revert(c.P, lo, gro, u, c.b.want_var != 0, r);
+                    }
                 }
+                write_out(c.b, qid, r);
             }
-            write_out(c.b, qid, r);
+            if (!ok && N > 0 && tid == 0 && !tc.dead) atomicOr(c.err, kErrFactor);
+            __syncthreads();
+            cq0 = ce;
+            if ((kEmu && tc.dead) || cq0 >= q1) break;
         }
-        if (!ok && N > 0 && tid == 0 && !tc.dead) atomicOr(c.err, kErrFactor);
-        __syncthreads();
         if (kEmu && tc.dead) break;
     }
     if (kEmu) {
@@ -1509,6 +1596,18 @@ SolveKernel pick_solve(bool props, bool emu) {
 // seven bf16 slices of a block's columns, the row scale, and one row of diagonal-tile inverses
 constexpr int64_t kEmuBytesPerRow = 7 * 8 * kEB * 2 + 8 + 64;
 
+// Emulated launch with the latent variance: the queries of an instance (up to kBorderQ) are
+// appended to its matrix, which is padded to a multiple of 32 rows (see fit_instance); the
+// workspaces hold npad + kBorderQ rows.  Otherwise npad rows.
+void emu_rows_for(bool emu, const SolveBatch& b, int& npad, int& qmax, int& nrow) {
+    qmax = 0;
+    if (emu && b.want_var && b.nprop == 0 && !b.Xi) {
+        npad = (npad + 31) & ~31;
+        qmax = kBorderQ;
+    }
+    nrow = npad + qmax;
+}
+
 // The emulated kernel's shared memory (about 100 KB at N = 1024) fits twice per SM only in the
 // largest shared-memory configuration; ask for it (a preference, so a failure is harmless).
 void set_emu_carveout(SolveKernel k) {
@@ -1591,7 +1690,7 @@ int solve_batch_graph(const SolveBatch& b, const DevParams& P, int* err_dev, cud
     const int maxn = std::min(std::max(b.max_n, 1), 1024);
     const int lo[5] = {225, 129, 65, 33, 0}, hi[5] = {1024, 224, 128, 64, 32};
     struct Shape {
-        int npad, smem_a, stage, threads, grid;
+        int npad, smem_a, stage, threads, grid, qmax, nrow;
         size_t shm;
         bool live, emu;
         SolveKernel kern;
@@ -1602,6 +1701,7 @@ int solve_batch_graph(const SolveBatch& b, const DevParams& P, int* err_dev, cud
         s.npad = std::max((std::min(hi[i], maxn) + 7) & ~7, 8);
         s.smem_a = i > 0;
         s.emu = !s.smem_a && P.emulate;
+        emu_rows_for(s.emu, b, s.npad, s.qmax, s.nrow);
         s.stage = s.smem_a ? 1 : (s.emu ? 0 : cfg->stage_panel);
         s.threads = s.emu ? kEmuThreads : cfg->threads[i];
         s.shm = smem_bytes(s.npad, s.smem_a, b.nprop, s.stage, b.Xi != nullptr, false, s.emu);
@@ -1631,9 +1731,9 @@ int solve_batch_graph(const SolveBatch& b, const DevParams& P, int* err_dev, cud
             if (cfg->per_sm[i] > 0) per_sm = std::min(per_sm, cfg->per_sm[i]);
         }
         s.grid = (int)std::min<int64_t>(n, (int64_t)n_sm * per_sm);
-        if (!s.smem_a) ws_a_need = std::max<int64_t>(ws_a_need, n_tiles(s.npad / 8) * 64 * s.grid);
+        if (!s.smem_a) ws_a_need = std::max<int64_t>(ws_a_need, n_tiles(s.nrow / 8) * 64 * s.grid);
         if (b.want_var) ws_v_need = std::max<int64_t>(ws_v_need, (int64_t)s.npad * s.threads * s.grid);
-        if (s.emu) ws_e_need = std::max<int64_t>(ws_e_need, (int64_t)s.npad * kEmuBytesPerRow * s.grid);
+        if (s.emu) ws_e_need = std::max<int64_t>(ws_e_need, (int64_t)s.nrow * kEmuBytesPerRow * s.grid);
     }
     // every buffer exists before the capture starts (allocation is not captured)
     int* hist = (int*)ar.get(Arena::kHist, sizeof(int) * 2 * 1025, st);
@@ -1673,11 +1773,13 @@ int solve_batch_graph(const SolveBatch& b, const DevParams& P, int* err_dev, cud
         c.npad = s.npad;
         c.a_in_smem = s.smem_a;
         c.stage_panel = s.stage;
-        c.ws_a_stride = s.smem_a ? 0 : n_tiles(s.npad / 8) * 64;
+        c.qmax = s.qmax;
+        c.nrow = s.nrow;
+        c.ws_a_stride = s.smem_a ? 0 : n_tiles(s.nrow / 8) * 64;
         c.ws_a = s.smem_a ? nullptr : ws_a;
         c.ws_v_stride = (int64_t)s.npad * s.threads;
         c.ws_v = ws_v;
-        c.ws_e_stride = s.emu ? (int64_t)s.npad * kEmuBytesPerRow : 0;
+        c.ws_e_stride = s.emu ? (int64_t)s.nrow * kEmuBytesPerRow : 0;
         c.ws_e = s.emu ? ws_e : nullptr;
         s.kern<<<s.grid, s.threads, s.shm, gs>>>(c);
         note_launch();
@@ -1785,10 +1887,12 @@ int solve_batch(const SolveBatch& b, const DevParams& P, int* err_dev, cudaStrea
     cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev);
     if (launch == VGP_LAUNCH_PER_INSTANCE && !bw) {
         // the plain comparison form: one launch per instance, in instance order, one CTA each
-        // workspaces sized for the largest instance (N <= 1024, at most 512 threads)
+        // workspaces sized for the largest instance (N <= 1024, at most 512 threads, appended
+        // query rows of the emulated kernel)
+        constexpr int kRowsMax = 1024 + kBorderQ;
         int* ctr = (int*)ar.get(Arena::kCounters, sizeof(int) * n, st);
-        uint8_t* ws_e = P.emulate ? (uint8_t*)ar.get(Arena::kWs3, 1024 * kEmuBytesPerRow, st) : nullptr;
-        double* ws_a = (double*)ar.get(Arena::kWs0, sizeof(double) * n_tiles(128) * 64, st);
+        uint8_t* ws_e = P.emulate ? (uint8_t*)ar.get(Arena::kWs3, kRowsMax * kEmuBytesPerRow, st) : nullptr;
+        double* ws_a = (double*)ar.get(Arena::kWs0, sizeof(double) * n_tiles(kRowsMax / 8) * 64, st);
         double* ws_v = b.want_var ? (double*)ar.get(Arena::kWs1, sizeof(double) * 1024 * 512, st) : nullptr;
         if (!ctr || !ws_a || (P.emulate && !ws_e) || (b.want_var && !ws_v)) {
             if (profile) {
@@ -1818,14 +1922,15 @@ int solve_batch(const SolveBatch& b, const DevParams& P, int* err_dev, cudaStrea
             c.npad = std::max((N + 7) & ~7, 8);
             c.a_in_smem = c.npad <= 224;
             const bool emu = !c.a_in_smem && P.emulate;
+            emu_rows_for(emu, b, c.npad, c.qmax, c.nrow);
             c.stage_panel = emu ? 0 : 1;
             const int threads = emu ? kEmuThreads : c.npad <= 32 ? 64 : c.npad <= 64 ? 128 : c.npad <= 128 ? 256 : 512;
             const size_t shm = smem_bytes(c.npad, c.a_in_smem, b.nprop, c.stage_panel, b.Xi != nullptr, false, emu);
             auto ks = pick_solve(b.nprop > 0, emu);
-            c.ws_e_stride = emu ? (int64_t)c.npad * kEmuBytesPerRow : 0;
+            c.ws_e_stride = emu ? (int64_t)c.nrow * kEmuBytesPerRow : 0;
             c.ws_e = emu ? ws_e : nullptr;
             cudaFuncSetAttribute(ks, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm);
-            c.ws_a_stride = c.a_in_smem ? 0 : n_tiles(c.npad / 8) * 64;
+            c.ws_a_stride = c.a_in_smem ? 0 : n_tiles(c.nrow / 8) * 64;
             c.ws_a = c.a_in_smem ? nullptr : ws_a;
             c.ws_v_stride = (int64_t)c.npad * threads;
             c.ws_v = ws_v;
@@ -1879,6 +1984,7 @@ int solve_batch(const SolveBatch& b, const DevParams& P, int* err_dev, cudaStrea
         c.npad = std::max((nmax + 7) & ~7, 8);
         c.a_in_smem = bk.smem_a;
         const bool emu = !bw && !bk.smem_a && P.emulate;
+        emu_rows_for(emu, b, c.npad, c.qmax, c.nrow);
         const int threads = emu ? kEmuThreads : bk.threads;
         c.stage_panel = bk.smem_a ? 1 : (emu ? 0 : cfg->stage_panel);
         if (bw) c.bw = *bw;
@@ -1896,11 +2002,11 @@ int solve_batch(const SolveBatch& b, const DevParams& P, int* err_dev, cudaStrea
             if (cfg->per_sm[bi] > 0) per_sm = std::min(per_sm, cfg->per_sm[bi]);
         }
         const int grid = (int)std::min<int64_t>(cnt, (int64_t)n_sm * per_sm);
-        c.ws_a_stride = c.a_in_smem ? 0 : n_tiles(c.npad / 8) * 64;
+        c.ws_a_stride = c.a_in_smem ? 0 : n_tiles(c.nrow / 8) * 64;
         c.ws_a = c.a_in_smem ? nullptr : (double*)ar.get(Arena::kWs0, sizeof(double) * c.ws_a_stride * grid, st);
         c.ws_v_stride = (int64_t)c.npad * threads;
         c.ws_v = (b.want_var && !bw) ? (double*)ar.get(Arena::kWs1, sizeof(double) * c.ws_v_stride * grid, st) : nullptr;
-        c.ws_e_stride = emu ? (int64_t)c.npad * kEmuBytesPerRow : 0;
+        c.ws_e_stride = emu ? (int64_t)c.nrow * kEmuBytesPerRow : 0;
         c.ws_e = emu ? (uint8_t*)ar.get(Arena::kWs3, c.ws_e_stride * grid, st) : nullptr;
         if ((!c.a_in_smem && !c.ws_a) || (b.want_var && !bw && !c.ws_v) || (emu && !c.ws_e)) {
             if (profile) {

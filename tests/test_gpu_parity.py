@@ -273,6 +273,60 @@ def test_gp_batch_parity(vg, orc, precision):
         assert np.abs(d[mid] - ref.d[mid]).max() <= D_TOL_MIXED
 
 
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_bordered_variance_chunks(vg, orc, precision):
+    """Latent variance of N > 224 instances with the emulated updates: the instance's queries are
+    appended to its matrix as rows, at most 256 per factorisation, and u is read from the Schur
+    complement's diagonal (Eq. 2).  Instances with 1, 255, 256, 257 and 700 queries (one to
+    three chunks), a non-finite query inside a chunk and queries far from the points (u near 1):
+    the variance agrees with the oracle (FP64 contract) and with the per-query triangular solve
+    of the FP64 tensor path, and each query's bits do not depend on the other queries (the
+    last 100 queries alone, in reverse order, give the same bits)."""
+    rng = np.random.default_rng(31)
+    sizes = [225, 250, 600, 1000, 1024]
+    nqs = [1, 255, 256, 257, 700]
+    Xs, Qs = [], []
+    for N, nq in zip(sizes, nqs):
+        c = rng.uniform(-20, 20, 3)
+        Xs.append(c + rng.uniform(-0.05, 0.05, (N, 3)) * np.sqrt(N))
+        q = c + rng.uniform(-1, 1, (nq, 3))
+        if nq > 100:
+            q[7] = np.nan
+            q[11] = c + 40.0  # no kernel value above underflow: u = 1
+        Qs.append(q)
+    X = np.vstack(Xs).astype(np.float32)
+    Q = np.vstack(Qs).astype(np.float32)
+    io = np.concatenate([[0], np.cumsum(sizes)])
+    qo = np.concatenate([[0], np.cumsum(nqs)])
+    ref = orc.gp_batch(io, X.astype(np.float64), qo, Q.astype(np.float64), orc.params())
+    out = {}
+    for emu in (1, 0):
+        m = vg.Map(precision=precision, emulate_fp64=emu)
+        out[emu] = {k: v.cpu().numpy() for k, v in m.gp_batch(io, X, qo, Q, var=True).items()}
+        assert sum(m.stats()["bucket_count"][3:]) == len(sizes)  # N > 224: the emulated kernel
+    d, v, s = out[1]["d"], out[1]["var"], out[1]["status"]
+    assert np.array_equal(s, ref.status)
+    assert s[qo[3] + 7] == 3 and s[qo[4] + 7] == 3  # bad input
+    ok = ref.status == 0
+    fin = ok & np.isfinite(ref.var) & (ref.var > 0)
+    assert fin.sum() > 1000
+    if precision == "fp64":
+        np.testing.assert_allclose(v[fin], ref.var[fin], rtol=1e-5, atol=1e-12)
+        # the per-query solve (FP64 tensor path) to rounding
+        np.testing.assert_allclose(v[fin], out[0]["var"][fin], rtol=1e-8, atol=0)
+    else:
+        bound = 2.0 * np.abs(d[fin] - ref.d[fin]) / np.maximum(ref.d[fin], 1e-3) * 1.5 + 2e-3
+        assert np.all(np.abs(v[fin] - ref.var[fin]) / ref.var[fin] <= bound)
+    # the last instance's last 100 queries alone, reversed: the same bits per query
+    sub = Q[qo[4]:qo[5]][-100:][::-1].copy()
+    m = vg.Map(precision=precision, emulate_fp64=1)
+    r2 = {k: v.cpu().numpy()
+          for k, v in m.gp_batch(np.array([0, sizes[4]]), X[io[4]:io[5]], np.array([0, 100]), sub, var=True).items()}
+    for k in ("d", "grad", "var", "status"):
+        a = np.ascontiguousarray(out[1][k][qo[5] - 100:qo[5]][::-1])
+        assert np.array_equal(np.ascontiguousarray(r2[k]).view(np.uint8), a.view(np.uint8)), k
+
+
 def test_gp_batch_rejects_oversize(vg):
     from paper_2407_09649_gb300 import _lib
     m = vg.Map()
