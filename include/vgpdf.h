@@ -531,6 +531,16 @@ int vgp_get_stats(const vgp_map* m, vgp_stats* out);
  */
 int vgp_debug_exp_neg(const vgp_map* m, const double* y_dev, double* out_dev, int64_t n, vgp_stream stream);
 
+/*
+ * Diagnostic: out_dev[i] = round(k 2^61), k = exp(-|a_i - b_i|^2 / (2 l^2)), as the emulated
+ * factorisation (emulate_fp64 = 1) assembles its mixed-precision kernel matrix (Sec. III-A
+ * kernel) from the FP32 world coordinates a_i = xa_dev[3i..3i+2], b_i = xb_dev[3i..3i+2]:
+ * float-pair arithmetic on the FP32 pipe, error below 2^-45 k (1 + y) + 2 units of 2^-61
+ * (y = |a - b|^2 / (2 l^2)); 0 where k < 2^-62.  Device arrays; n pairs; stream-ordered.
+ */
+int vgp_debug_kernel_fix(const vgp_map* m, const float* xa_dev, const float* xb_dev, int64_t n, int64_t* out_dev,
+                         vgp_stream stream);
+
 /* Number of CUDA kernels this library has launched in the process so far (diagnostic). */
 int64_t vgp_launch_count(void);
 

@@ -77,6 +77,7 @@ SIGNATURES = [
     ("vgp_sync", _i32, [_vp]),
     ("vgp_launch_count", C.c_int64, []),
     ("vgp_debug_exp_neg", _i32, [_vp, _vp, _vp, _i64, _vp]),
+    ("vgp_debug_kernel_fix", _i32, [_vp, _vp, _vp, _i64, _vp, _vp]),
     ("vgp_debug_query_plan", _i32, [_vp, _vp, _i64, _vp, C.POINTER(C.c_int64), C.POINTER(C.c_int64), _vp, _vp, _vp,
                                     _vp]),
     ("vgp_debug_smooth_plan", _i32, [_vp, _vp, _i64, C.c_int32, _vp, C.POINTER(C.c_int64), C.POINTER(C.c_int64),

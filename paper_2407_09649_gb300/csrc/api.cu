@@ -198,6 +198,8 @@ static DevParams expand(const vgp_params& p) {
     P.log_floor = -(p.d_max * p.d_max) / (2.0 * P.l2);
     P.d_var_floor = p.d_var_floor;
     P.inv2l2_log2e = (float)(1.4426950408889634 / (2.0 * P.l2));
+    P.inv2l2_hi = (float)P.inv2l2;
+    P.inv2l2_lo = (float)(P.inv2l2 - (double)P.inv2l2_hi);
     P.cap_leaf = p.max_pts_leaf;
     P.cap_group = p.max_pts_group;
     P.n_props = p.n_props;
@@ -1792,6 +1794,14 @@ extern "C" int vgp_debug_exp_neg(const vgp_map* m, const double* y, double* out,
     k_exp_probe<<<(unsigned)((n + 255) / 256), 256, 0, (cudaStream_t)stream>>>(y, out, n, m->P.exp_tab);
     note_launch();
     CUDA_TRY(cudaGetLastError());
+    return VGP_OK;
+}
+
+extern "C" int vgp_debug_kernel_fix(const vgp_map* m, const float* xa, const float* xb, int64_t n, int64_t* out,
+                                    vgp_stream stream) {
+    if (!m || n < 0 || (n > 0 && (!xa || !xb || !out))) return fail(VGP_ERR_ARG, "vgp_debug_kernel_fix: bad argument");
+    if (debug_kernel_fix(m->P, xa, xb, n, (long long*)out, (cudaStream_t)stream) != 0)
+        return fail(VGP_ERR_CUDA, "vgp_debug_kernel_fix: launch failed");
     return VGP_OK;
 }
 

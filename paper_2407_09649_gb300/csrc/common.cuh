@@ -35,6 +35,7 @@ struct DevParams {
     double log_floor;   // -d_max^2 / (2 l^2)
     double d_var_floor;
     float inv2l2_log2e; // log2(e) / (2 l^2), for exp2f of the FP32 path
+    float inv2l2_hi, inv2l2_lo;  // 1 / (2 l^2) as a float pair (hi + lo), for the float-pair kernel values
     float vs_f;         // voxel size in FP32
     int cap_leaf, cap_group, search_r, fusion, precision, n_props;
     int emulate;        // Cholesky trailing updates of N > 224 instances on the bf16 tensor cores

@@ -122,6 +122,10 @@ int solve_batch(const SolveBatch& b, const DevParams& P, int* err_dev, cudaStrea
 void set_last_error(const char* msg);
 
 // k_solve with caller-provided scratch and no allocation (see noalloc.cu); 0 on success.
+// Diagnostic: the emulated kernel's mixed-precision kernel values round(k 2^61) of n pairs of
+// FP32 world coordinates (device arrays [n][3]); 0 or -1 on a launch error.
+int debug_kernel_fix(const DevParams& P, const float* xa, const float* xb, int64_t n, long long* out,
+                     cudaStream_t st);
 int solve_launch_static(const SolveBatch& b, const DevParams& P, int* err_dev, int npad, int threads, int max_grid,
                         int* counter, const int32_t* order, double* ws_v, cudaStream_t st);
 

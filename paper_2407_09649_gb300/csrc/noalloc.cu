@@ -184,6 +184,8 @@ extern "C" int vgp_gp_batch_static(const vgp_params* p, int64_t n_inst, const in
     P.log_floor = -(p->d_max * p->d_max) / (2.0 * P.l2);
     P.d_var_floor = p->d_var_floor;
     P.inv2l2_log2e = (float)(1.4426950408889634 / (2.0 * P.l2));
+    P.inv2l2_hi = (float)P.inv2l2;
+    P.inv2l2_lo = (float)(P.inv2l2 - (double)P.inv2l2_hi);
     P.vs_f = (float)p->voxel_size;
     P.precision = p->precision;
     P.exp_tab = (const double*)(base + kOffTab);

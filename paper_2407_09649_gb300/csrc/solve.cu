@@ -97,6 +97,9 @@ struct Shared {
     unsigned char* stage;  // emulated kernel: slice operands of the tensor-core updates (aliases
                            // X .. alf_lo, which the factorisation does not use; reloaded after it)
     double* qxl;           // emulated kernel: [kBorderQ][3] local coordinates of appended queries
+    float* qw;             // emulated kernel: [kBorderQ][3] world coordinates of appended queries (FP32)
+    float* Xw;             // emulated kernel: [npad][3] world coordinates of the points (FP32, exact)
+    float2* Tff;           // emulated kernel: 2^(j/256), j = 0..255, as float pairs
 };
 
 // Emulated trailing updates on the tensor cores (tcgen05): an output tile is kBandT row tiles
@@ -118,14 +121,17 @@ constexpr int kEmuCtasPerSm = 512 / kEmuTmemCols;  // CTAs whose tensor memory f
 
 __host__ __device__ __forceinline__ size_t align128(size_t x) { return (x + 127) & ~(size_t)127; }
 __host__ __device__ __forceinline__ size_t emu_fixed_bytes(int npad) {
-    return align128((size_t)(npad + 256 + kEB * 64 + 8 * 64) * sizeof(double));  // invd, T256, Tblk, Wsc
+    // invd, T256, Tblk, Wsc, Tff
+    return align128((size_t)(npad + 256 + kEB * 64 + 8 * 64 + 256) * sizeof(double));
 }
 __host__ __device__ __forceinline__ size_t emu_point_bytes(int npad, int nprop, bool lattice) {
     return (size_t)5 * npad * sizeof(double) + (size_t)5 * npad * sizeof(float) +
            (lattice ? (size_t)npad * sizeof(int) : 0) + (size_t)(nprop > 2 ? nprop - 2 : 0) * npad * sizeof(double);
 }
+// the points (also as FP32 world coordinates) and the appended queries (both forms)
 __host__ __device__ __forceinline__ size_t emu_alias_bytes(int npad, int nprop, bool lattice) {
-    const size_t b = emu_point_bytes(npad, nprop, lattice) + (size_t)kBorderQ * 3 * sizeof(double);
+    const size_t b = emu_point_bytes(npad, nprop, lattice) + (size_t)3 * npad * sizeof(float) +
+                     (size_t)kBorderQ * (3 * sizeof(double) + 3 * sizeof(float));
     return b > (size_t)kStageBytes ? b : (size_t)kStageBytes;
 }
 
@@ -155,7 +161,10 @@ __device__ Shared carve_emu(double* sm, int npad, double* ws_a, int nprop, bool 
     s.pa[1] = reinterpret_cast<double*>(s.alf);
     s.pa[2] = nprop > 2 ? extra : nullptr;
     s.pa[3] = nprop > 3 ? extra + npad : nullptr;
-    s.qxl = reinterpret_cast<double*>(s.stage + emu_point_bytes(npad, nprop, lattice));
+    s.Xw = reinterpret_cast<float*>(s.stage + emu_point_bytes(npad, nprop, lattice));
+    s.qxl = reinterpret_cast<double*>(s.Xw + 3 * npad);
+    s.qw = reinterpret_cast<float*>(s.qxl + 3 * kBorderQ);
+    s.Tff = reinterpret_cast<float2*>(s.Wsc + 8 * 64);
     return s;
 }
 
@@ -165,6 +174,9 @@ __device__ Shared carve(double* sm, int npad, int a_in_smem, double* ws_a, int n
     Shared s;
     s.stage = nullptr;
     s.qxl = nullptr;
+    s.qw = nullptr;
+    s.Xw = nullptr;
+    s.Tff = nullptr;
     s.X = sm;
     s.alpha = s.X + 3 * npad;
     s.invd = s.alpha + npad;
@@ -218,6 +230,117 @@ __device__ __forceinline__ double kval_pair(const DevParams& P, const Shared& s,
     double dx = s.X[3 * i] - s.X[3 * j], dy = s.X[3 * i + 1] - s.X[3 * j + 1], dz = s.X[3 * i + 2] - s.X[3 * j + 2];
     const double y = -(dx * dx + dy * dy + dz * dz) * P.inv2l2;
     return P.precision == VGP_MIXED ? exp_neg(y, s.T256) : exp(y);
+}
+
+// ---- the emulated kernel's matrix in fixed point -------------------------------------------
+// Until its column block is reached, an entry of the emulated factorisation is held as the
+// integer round(v 2^61) (|v| <= 1 + sigma^2: every entry of K + sigma^2 I and of its Schur
+// complements is bounded by the largest diagonal entry).  The trailing updates then subtract
+// integers (one shift and one 64-bit subtraction per entry) and the block's columns are
+// turned into FP64 once, when the block is factorised.  Resolution 2^-61, far below the
+// updates' own rounding (2^-55 of the row maxima).
+constexpr int kFixBits = 61;
+__device__ __forceinline__ long long fix_of_double(double v) { return __double2ll_rn(v * 0x1p61); }
+__device__ __forceinline__ double double_of_fix(long long f) { return __ll2double_rn(f) * 0x1p-61; }
+
+// round(x 2^e) of a float x, |x| 2^e < 2^62, on the integer pipe (ties away from zero; 0 for
+// subnormal x).
+__device__ __forceinline__ long long fix_of_float(float x, int e) {
+    const unsigned b = __float_as_uint(x);
+    const int ex = (int)((b >> 23) & 255);
+    if (ex == 0) return 0;
+    const long long mant = (long long)((b & 0x7FFFFFu) | 0x800000u);
+    const int sh = ex - 150 + e;  // |x| = mant 2^(ex - 150)
+    long long v;
+    if (sh >= 0)
+        v = mant << sh;
+    else if (sh >= -25)
+        v = ((mant >> (-sh - 1)) + 1) >> 1;
+    else
+        v = 0;
+    return (b >> 31) ? -v : v;
+}
+
+// Float pairs: a value is hi + lo, |lo| near 2^-24 |hi| at most.  Knuth's two-sum and the
+// FMA product error are error-free; every operation is an _rn intrinsic, so nothing is
+// contracted or reassociated.
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+    s = __fadd_rn(a, b);
+    const float bv = __fsub_rn(s, a);
+    e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bv)), __fsub_rn(b, bv));
+}
+
+// ln2/256 = kL0 + kL1 + kL2 (kL0 with 10 significant bits, so n kL0 is exact for n < 2^14;
+// the three parts hold 58 bits) and 256/ln2.
+constexpr float kL0 = 0x1.63p-9f, kL1 = -0x1.bd0106p-21f, kL2 = 0x1.cf79acp-48f;
+constexpr float kInvL = 369.32993046757464f;
+
+// k = exp(-|a - b|^2 / (2 l^2)) in the fixed point above, on the FP32 and integer pipes (the
+// mixed-precision entries of the emulated kernel; the FP64 pipe is the scarce unit of the
+// factorisation).  a, b: FP32 world coordinates (the inputs' own values), so each difference
+// is exactly a float pair (two-sum) and |a - b|^2 is carried as a float pair renormalised
+// after every axis;
+//   y = |a - b|^2 / (2 l^2) as a float pair;
+//   e^-y = 2^-(n/256) e^r with n = round(256 y / ln2) and r = n ln2/256 - y, |r| <= ln2/512
+//   (Tang's table-driven reduction, as exp_neg), r as a normalised float pair, e^r from its
+//   Taylor terms to r^4 (the next term is below 2^-54), 2^(i/256) from the float-pair table;
+//   the float-pair result scaled by 2^(61 - m) into a 64-bit integer.
+// The error stays below 2^-45 k (1 + y) + 2 units of 2^-61, about 2^-47 at most in k, at the
+// level of the Cholesky's own backward error; 0 where y > 43.5 (k < 2^-62).
+__device__ __forceinline__ long long kfix_ff(const float a[3], const float b[3], float ch, float cl,
+                                             const float2* tab) {
+    float S = 0.f, E = 0.f;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        float dh, dl;
+        two_sum(a[k], -b[k], dh, dl);  // a - b = dh + dl exactly
+        const float p = __fmul_rn(dh, dh), pe = __fmaf_rn(dh, dh, -p);
+        float t, te;
+        two_sum(S, p, t, te);
+        // (dh + dl)^2 = p + pe + dl (2 dh + dl); then renormalise (S, E)
+        E = __fadd_rn(E, __fadd_rn(te, __fmaf_rn(dl, __fmaf_rn(2.f, dh, dl), pe)));
+        S = __fadd_rn(t, E);
+        E = __fsub_rn(E, __fsub_rn(S, t));
+    }
+    const float yh = __fmul_rn(S, ch);
+    const float yl = __fadd_rn(__fmaf_rn(S, ch, -yh), __fmaf_rn(S, cl, __fmul_rn(E, ch)));
+    if (!(yh <= 43.5f)) return 0;
+    const float n = rintf(__fmul_rn(yh, kInvL));
+    const int ni = (int)n;
+    // r = (n kL0 - yh) + n kL1 - yl + n kL2, the large parts summed error-free
+    float a0, ae, b0, be, rh, ce;
+    two_sum(__fmul_rn(n, kL0), -yh, a0, ae);
+    const float p2 = __fmul_rn(n, kL1), p2e = __fmaf_rn(n, kL1, -p2);
+    two_sum(a0, p2, b0, be);
+    two_sum(b0, -yl, rh, ce);
+    const float rl = __fadd_rn(__fadd_rn(__fadd_rn(ae, be), ce), __fmaf_rn(n, kL2, p2e));
+    // e^r - 1 = rh + rh^2/2 + [rl + rh rl + rh^3/6 + rh^4/24 + (rh^2 error)/2]
+    const float q = __fmul_rn(rh, rh), qe = __fmaf_rn(rh, rh, -q);
+    const float c34 = __fmul_rn(__fmul_rn(q, rh), __fmaf_rn(rh, 1.f / 24.f, 1.f / 6.f));
+    const float small = __fadd_rn(__fmaf_rn(0.5f, qe, rl), __fmaf_rn(rh, rl, c34));
+    float u, ue, eh, e4;
+    two_sum(rh, __fmul_rn(0.5f, q), u, ue);
+    two_sum(1.f, u, eh, e4);
+    const float el = __fadd_rn(e4, __fadd_rn(ue, small));
+    // 2^(-n/256) = 2^-m 2^(i/256) with m = ceil(n / 256) and i = (-n) mod 256
+    const int j = ni & 255, m = (ni >> 8) + (j != 0);
+    const float2 T = tab[(256 - j) & 255];
+    const float vh = __fmul_rn(T.x, eh);
+    const float vl = __fadd_rn(__fmaf_rn(T.x, eh, -vh), __fmaf_rn(T.x, el, __fmul_rn(T.y, eh)));
+    return fix_of_float(vh, kFixBits - m) + fix_of_float(vl, kFixBits - m);
+}
+
+// Entry (i, j), i > j, of K in the fixed point: float pairs in mixed precision, the FP64 value
+// (as kval_pair) rounded to the fixed point in FP64 precision and on the lattice.
+__device__ __forceinline__ long long kfix_pair(const DevParams& P, const Shared& s, bool lattice, int i, int j) {
+    if (lattice || P.precision != VGP_MIXED) return fix_of_double(kval_pair(P, s, lattice, i, j));
+    return kfix_ff(s.Xw + 3 * i, s.Xw + 3 * j, P.inv2l2_hi, P.inv2l2_lo, s.Tff);
+}
+
+// The float pair (hi, lo) of an FP64 value.
+__device__ __forceinline__ void split_pair(double v, float& hi, float& lo) {
+    hi = (float)v;
+    lo = (float)(v - (double)hi);
 }
 
 // Solve (L L^T) x = rhs in place on s.z (x written to out), L tile-packed; rows >= N of rhs
@@ -411,29 +534,12 @@ __device__ void panel_column(double* A, int kt, int it_end, const double* Ti) {
     }
 }
 
-// w 2^(e - 1023) as an FP64 value for a 64-bit integer w, |w| < 2^62, and a biased exponent e,
-// built on the integer pipe: the leading bit of |w| gives the exponent, the significand is
-// rounded to 53 bits (ties away from zero).  0 when w = 0 or the result would not be normal
-// (below 2^-1022, far under any entry it is added to).
-__device__ __forceinline__ double scaled_int(long long w, int e) {
-    if (w == 0) return 0.0;
-    const unsigned long long a = (unsigned long long)(w < 0 ? -w : w);
-    const int p = 63 - __clzll((long long)a);  // |w| in [2^p, 2^(p+1))
-    int E = p + e;
-    unsigned long long m;
-    if (p > 52) {
-        const int sh = p - 52;
-        m = (a + (1ull << (sh - 1))) >> sh;
-        if (m >> 53) {
-            m >>= 1;
-            ++E;
-        }
-    } else {
-        m = a << (52 - p);
-    }
-    if (E <= 0) return 0.0;
-    return __longlong_as_double((long long)(((unsigned long long)(w < 0) << 63) | ((unsigned long long)E << 52) |
-                                            (m & 0xFFFFFFFFFFFFFull)));
+// w 2^sh rounded to an integer (ties up) for a 64-bit integer w: a slice-product update in
+// the fixed point of the trailing matrix.  No overflow: |w| 2^sh is bounded by the entry bound.
+__device__ __forceinline__ long long fix_shift(long long w, int sh) {
+    if (sh >= 0) return w << sh;
+    if (sh < -63) return 0;
+    return ((w >> (-sh - 1)) + 1) >> 1;
 }
 
 // Balanced base-256 digits of row g of an 8-row tile over one block (the FP64 values
@@ -688,7 +794,7 @@ __device__ bool trailing_update_tc(const SolveCtx& c, double* A, int Nt, int Ntr
             }
             // while the MMAs run: this thread's 16 entries of C (row `row`, the 8 columns of each
             // of its two column tiles) and the column scales, all loads issued at once
-            double cv[2][8];
+            long long cv[2][8];
             int ec[2][8];
             bool ok[2];
 #pragma unroll
@@ -699,7 +805,7 @@ __device__ bool trailing_update_tc(const SolveCtx& c, double* A, int Nt, int Ntr
                 const double* scl = sr + 8 * (ok[j] ? c0 + cb : 0);
 #pragma unroll
                 for (int cc = 0; cc < 8; ++cc) {
-                    cv[j][cc] = ok[j] ? C[te(rr, cc)] : 0.0;
+                    cv[j][cc] = ok[j] ? __double_as_longlong(C[te(rr, cc)]) : 0;
                     ec[j][cc] = (int)(__double_as_longlong(scl[cc]) >> 52);
                 }
             }
@@ -726,7 +832,9 @@ __device__ bool trailing_update_tc(const SolveCtx& c, double* A, int Nt, int Ntr
                         constexpr long long kOffBits = 0x4B400000ll * 0x01010101ll;
                         const long long hi = gq8[0] * (1ll << 24) + gq8[1] * (1ll << 16) + gq8[2] * 256 + gq8[3] - kOffBits;
                         const long long lo = gq8[4] * (1ll << 24) + gq8[5] * (1ll << 16) + gq8[6] * 256 + gq8[7] - kOffBits;
-                        cv[j][cc] -= scaled_int(hi * (1ll << 16) + ((lo + (1ll << 15)) >> 16), er + ec[j][cc] - 1079);
+                        // the update is w 2^(er + ec - 2102), in units of 2^-kFixBits
+                        cv[j][cc] -= fix_shift(hi * (1ll << 16) + ((lo + (1ll << 15)) >> 16),
+                                               er + ec[j][cc] - (2102 - kFixBits));
                     }
                 }
             }
@@ -735,7 +843,7 @@ __device__ bool trailing_update_tc(const SolveCtx& c, double* A, int Nt, int Ntr
                 if (ok[j]) {
                     double* C = A + tix(rt, K1 + c0 + 2 * h + j);
 #pragma unroll
-                    for (int cc = 0; cc < 8; ++cc) C[te(rr, cc)] = cv[j][cc];
+                    for (int cc = 0; cc < 8; ++cc) C[te(rr, cc)] = __longlong_as_double(cv[j][cc]);
                 }
             // every thread's reads of the accumulators are done before the next tile's MMAs
             asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
@@ -760,8 +868,10 @@ __device__ bool trailing_update_tc(const SolveCtx& c, double* A, int Nt, int Ntr
 // The groups are packed exactly into two 64-bit integers, hi (g = 2..5) and lo (g = 6..9),
 // and joined as w = 2^16 hi + round(lo / 2^16), below 2^63 because every group stays below
 // 2^22 with W = 32: the rounding of lo is below 2^-57 of the scale 2^(e_r + e_c - 2042).  The
-// scaled w is built as an FP64 value on the integer pipe (scaled_int) and subtracted: one
-// FP64 operation per updated entry.  The slice products run on the tensor cores
+// trailing matrix is held in the fixed point of kFixBits (assembled so by fit_instance): w is
+// shifted to it and subtracted as an integer, so an updated entry costs no FP64 operation,
+// and each block's columns are turned into FP64 when the block is reached.  The slice
+// products run on the tensor cores
 // (trailing_update_tc); within a block the diagonal block is factorised as in the plain loop
 // (8x8 tiles, FP64 tensor path) and the rows below it are solved one row tile per warp
 // (block_rows), which also writes their slices.
@@ -777,6 +887,19 @@ __device__ bool factor_emulated(const SolveCtx& c, const Shared& s, double* A, i
     double* Tall = emu_tile_inverses(c);                  // inverses of all diagonal tiles, for the solves
     for (int K0 = 0; K0 < Ntr; K0 += kEB) {
         const int K1 = min(K0 + kEB, Ntr);
+        // the block's columns (tiles (it, jt), K0 <= jt < K1, jt <= it) from the fixed point of
+        // the trailing matrix to FP64
+        {
+            const int nb = K1 - K0;
+            const int64_t ne = (int64_t)(Nt - K0) * nb * 64;
+            for (int64_t x = tid; x < ne; x += blockDim.x) {
+                const int p = (int)(x >> 6), it = K0 + p / nb, jt = K0 + p % nb;
+                if (jt > it) continue;
+                double* v = A + tix(it, jt) + (x & 63);
+                *v = double_of_fix(__double_as_longlong(*v));
+            }
+            __syncthreads();
+        }
         // the diagonal block: tiles (it, jt), K0 <= jt <= it < K1, right-looking by 8 columns
         for (int kt = K0; kt < K1; ++kt) {
             double* Ti = s.Tblk + 64 * (kt - K0);
@@ -846,6 +969,9 @@ __device__ bool fit_instance(const SolveCtx& c, const Shared& s, int N, int64_t 
         double v = c.b.Xl[3 * base + e];
         s.X[e] = v;
         s.Xf[e] = (float)v;
+        // the point's own FP32 world coordinate, recovered exactly (the FP64 local value
+        // differs from it by the centre up to a rounding far below half an FP32 ulp)
+        if (kEmu) s.Xw[e] = (float)(v + (c.b.centre ? c.b.centre[3 * (int64_t)I + e % 3] : 0.0));
     }
     if (lattice)
         for (int e = tid; e < N; e += nt) {
@@ -859,16 +985,47 @@ __device__ bool fit_instance(const SolveCtx& c, const Shared& s, int N, int64_t 
             double xl[3];
             query_local(c, I, p, qid, xl);
             const bool fin = isfinite(xl[0]) && isfinite(xl[1]) && isfinite(xl[2]);
-            for (int k = 0; k < 3; ++k) s.qxl[3 * a + k] = fin ? xl[k] : NAN;
+            for (int k = 0; k < 3; ++k) {
+                s.qxl[3 * a + k] = fin ? xl[k] : NAN;
+                s.qw[3 * a + k] = fin ? (float)(xl[k] + (c.b.centre ? c.b.centre[3 * (int64_t)I + k] : 0.0)) : 0.f;
+            }
         }
     if (tid == 0) s_fail = 0;
     __syncthreads();
     double* A = s.A;
     // A = K + sigma^2 I in 8x8 tiles (Sec. III-A kernel, Eq. 1 noise term); padding rows and
-    // columns are the identity so the padded factor is block-diagonal.  Appended query rows:
-    // the query's kernel values (FP64, as in latent_var), 1 on the diagonal, and only the
-    // diagonal tiles of the query-by-query block.
+    // columns are the identity so the padded factor is block-diagonal.  The emulated kernel
+    // writes the fixed point of kfix_pair (appended query rows: the query's kernel values, 1
+    // on the diagonal, and only the diagonal tiles of the query-by-query block).
     const int64_t ntl = n_tiles(Ntq);
+    if (kEmu)
+        for (int64_t tl = warp; tl < ntl; tl += nwarps) {
+            const int it = tri_row((int)tl), jt = (int)tl - it * (it + 1) / 2;
+            if (jt >= Nt && jt != it) continue;
+            for (int e = lane; e < 64; e += 32) {
+                const int i = 8 * it + (e >> 3), j = 8 * jt + (e & 7);
+                long long v;
+                if (i >= Np) {  // appended query row a = i - Np
+                    const int a = i - Np;
+                    if (j >= Np || a >= nq) {
+                        v = (i == j) ? (1ll << kFixBits) : 0;
+                    } else if (j >= N || isnan(s.qxl[3 * a])) {
+                        v = 0;
+                    } else if (c.P.precision == VGP_MIXED) {
+                        v = kfix_ff(s.qw + 3 * a, s.Xw + 3 * j, c.P.inv2l2_hi, c.P.inv2l2_lo, s.Tff);
+                    } else {
+                        const double dx = s.X[3 * j] - s.qxl[3 * a], dy = s.X[3 * j + 1] - s.qxl[3 * a + 1],
+                                     dz = s.X[3 * j + 2] - s.qxl[3 * a + 2];
+                        v = fix_of_double(exp(-(dx * dx + dy * dy + dz * dz) * c.P.inv2l2));
+                    }
+                } else if (i >= N || j >= N) v = (i == j) ? (1ll << kFixBits) : 0;
+                else if (j > i) v = 0;
+                else if (j == i) v = fix_of_double(1.0 + c.P.s2);  // s2: sigma_prop^2 for properties
+                else v = kfix_pair(c.P, s, lattice, i, j);
+                A[tl * 64 + te(e >> 3, e & 7)] = __longlong_as_double(v);
+            }
+        }
+    else
     for (int64_t tl = warp; tl < ntl; tl += nwarps) {
         const int it = tri_row((int)tl), jt = (int)tl - it * (it + 1) / 2;
         if (jt >= Nt && jt != it) continue;
@@ -1269,6 +1426,12 @@ __device__ __forceinline__ void solve_body(const SolveCtx& c) {
     double* V = c.ws_v ? c.ws_v + (int64_t)blockIdx.x * c.ws_v_stride + tid : nullptr;
     const bool lattice = c.b.Xi != nullptr;
     for (int j = tid; j < 256; j += nt) s.T256[j] = c.P.exp_tab[j];
+    if (kEmu)
+        for (int j = tid; j < 256; j += nt) {
+            float h, l;
+            split_pair(c.P.exp_tab[j], h, l);
+            s.Tff[j] = make_float2(h, l);
+        }
     EmuTc tc{};
     if (kEmu) {
         // tensor memory for the 8 slice-group accumulators (held until the CTA exits) and the
@@ -1305,7 +1468,7 @@ __device__ __forceinline__ void solve_body(const SolveCtx& c) {
         const int N = (int)(c.b.inst_off[I + 1] - base);
         const int64_t q0 = c.b.q_off[I], q1 = c.b.q_off[I + 1];
         if (kProps) {
-            const bool ok = N > 0 && fit_instance<kProps, kEmu>(c, s, N, base, &tc);
+            const bool ok = N > 0 && fit_instance<kProps, kEmu>(c, s, N, base, &tc, 0, q0, I);
             // property mode: means and variance (Eq. 6, variance read as for Eq. 2)
             const int np = c.b.nprop;
             for (int64_t p = q0 + tid; p < q1; p += nt) {
@@ -1357,7 +1520,7 @@ __device__ __forceinline__ void solve_body(const SolveCtx& c) {
                         if (c.b.want_var) {
                             if (border) {  // the Schur complement's diagonal entry, clamped at 0
                                 const int a = (int)(p - cq0), ta = Ntr + (a >> 3);
-                                u = fmax(0.0, s.A[tix(ta, ta) + te(a & 7, a & 7)]);
+                                u = fmax(0.0, double_of_fix(__double_as_longlong(s.A[tix(ta, ta) + te(a & 7, a & 7)])));
                             } else {
                                 u = latent_var(c.P, s, N, lattice, qi, xl, V, nt);
                             }
@@ -2045,6 +2208,33 @@ int solve_batch(const SolveBatch& b, const DevParams& P, int* err_dev, cudaStrea
         cudaEventDestroy(ev1);
     }
     return 0;
+}
+
+namespace {
+// One pair of FP32 world coordinates per thread: the emulated kernel's mixed-precision kernel
+// value in the fixed point.
+__global__ void k_kfix_probe(const float* xa, const float* xb, long long* out, int64_t n, DevParams P) {
+    __shared__ float2 tab[256];
+    for (int j = threadIdx.x; j < 256; j += blockDim.x) {
+        float h, l;
+        split_pair(P.exp_tab[j], h, l);
+        tab[j] = make_float2(h, l);
+    }
+    __syncthreads();
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const float a[3] = {xa[3 * i], xa[3 * i + 1], xa[3 * i + 2]};
+    const float b[3] = {xb[3 * i], xb[3 * i + 1], xb[3 * i + 2]};
+    out[i] = kfix_ff(a, b, P.inv2l2_hi, P.inv2l2_lo, tab);
+}
+}  // namespace
+
+int debug_kernel_fix(const DevParams& P, const float* xa, const float* xb, int64_t n, long long* out,
+                     cudaStream_t st) {
+    if (n <= 0) return 0;
+    k_kfix_probe<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(xa, xb, out, n, P);
+    note_launch();
+    return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }
 
 }  // namespace vgp

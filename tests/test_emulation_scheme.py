@@ -182,3 +182,160 @@ def test_an_eight_7_bit_slice_cut_is_less_accurate():
             new.append(float(abs(Fraction(emulated_update(0.0, p[i], p[j])[0]) - exact)) / bound)
             old.append(float(abs(Fraction(old_update(0.0, p[i], p[j])) - exact)) / bound)
     assert max(new) < max(old)
+
+
+# ---- the fixed point of the trailing matrix ---------------------------------------------
+# The kernel holds the not yet factorised part of A as integers round(v 2^61) (every entry of
+# K + sigma^2 I and of its Schur complements lies within the largest diagonal entry, about 1)
+# and subtracts each slice-product update w 2^(e_i + e_j - 2098) shifted to that scale.
+
+FIX = 61
+
+
+def fix_shift(w, sh):
+    """w 2^sh rounded to an integer, ties up (the kernel's shift of an update)."""
+    if sh >= 0:
+        return w << sh
+    if sh < -63:
+        return 0
+    return ((w >> (-sh - 1)) + 1) >> 1
+
+
+def fixed_update(cfix, pi, pj):
+    ei, di = slice_row(pi)
+    ej, dj = slice_row(pj)
+    G = {g: 0 for g in range(2, 10)}
+    for s in range(7):
+        for t in range(7):
+            g = s + t + 2
+            if g <= 9:
+                G[g] += sum(di[k][s] * dj[k][t] for k in range(W))
+    hi = G[2] * 2**24 + G[3] * 2**16 + G[4] * 256 + G[5]
+    lo = G[6] * 2**24 + G[7] * 2**16 + G[8] * 256 + G[9]
+    w = hi * 2**16 + ((lo + 2**15) >> 16)
+    upd = fix_shift(w, ei + ej - 2098 + FIX)
+    assert abs(upd) < 2**63 and abs(cfix - upd) < 2**63  # no 64-bit overflow
+    return cfix - upd
+
+
+def _factor_rows(rng, n):
+    """Rows of a Cholesky factor's panel: unit-bounded rows, magnitudes over several orders."""
+    p = rng.normal(size=(n, W)) * np.exp(rng.normal(size=(n, 1)) * 2)
+    p /= np.maximum(1.0, np.linalg.norm(p, axis=1, keepdims=True))
+    p[rng.random(p.shape) < 0.05] = 0.0
+    return p
+
+
+@pytest.mark.parametrize("seed", [5, 6])
+def test_fixed_point_update_error_is_that_of_plain_fp64(seed):
+    """C in [-1, 1] held as round(C 2^61), rows of norm <= 1: the fixed-point update stays within
+    a few u of the exact value relative to |C| + sum |P_i||P_j| (as the FP64 update), plus the
+    fixed point's half unit 2^-62; the diagonal case (i = j, C_ii - |P_i|^2 > 0) included."""
+    rng = np.random.default_rng(seed)
+    n = 6
+    p = _factor_rows(rng, n)
+    C = rng.uniform(-1, 1, (n, n))
+    u = 2.0**-53
+    worst = 0.0
+    for i in range(n):
+        for j in range(n):
+            c = float(C[i, j]) if i != j else 1.0 + 1e-4
+            cfix = round(Fraction(c) * 2**FIX)
+            got = Fraction(fixed_update(cfix, p[i], p[j]), 2**FIX)
+            exact = Fraction(c) - sum(Fraction(float(p[i, k])) * Fraction(float(p[j, k])) for k in range(W))
+            bound = abs(c) + float(np.abs(p[i]) @ np.abs(p[j]))
+            err = float(abs(got - exact))
+            assert err <= 4 * u * bound + 2.0 ** -61, (i, j, err / (u * bound))
+            worst = max(worst, err / (u * bound))
+    assert worst > 0  # the check is not vacuous
+
+
+# ---- float-pair kernel values ----------------------------------------------------------
+# Model of the kernel's mixed-precision entries exp(-|a - b|^2 / (2 l^2)) in float-pair
+# arithmetic on FP32 world coordinates, operation for operation in numpy float32 (an FMA as
+# the float64 product plus the addend, rounded once to float32: exact wherever the kernel
+# relies on an FMA being error-free).
+
+f32 = np.float32
+
+
+def _fma(a, b, c):
+    a, b, c = np.broadcast_arrays(np.asarray(a, f32), np.asarray(b, f32), np.asarray(c, f32))
+    return (a.astype(np.float64) * b.astype(np.float64) + c.astype(np.float64)).astype(f32)
+
+
+def _two_sum(a, b):
+    s = (a + b).astype(f32)
+    bv = (s - a).astype(f32)
+    return s, ((a - (s - bv)).astype(f32) + (b - bv)).astype(f32)
+
+
+def kernel_fix_model(a, b, inv2l2):
+    kL0, kL1, kL2 = f32(float.fromhex("0x1.63p-9")), f32(float.fromhex("-0x1.bd0106p-21")), f32(float.fromhex("0x1.cf79acp-48"))
+    ch = f32(inv2l2)
+    cl = f32(inv2l2 - float(ch))
+    tab = np.array([2.0 ** (j / 256) for j in range(256)])
+    Th = tab.astype(f32)
+    Tl = (tab - Th.astype(np.float64)).astype(f32)
+    S = np.zeros(len(a), f32)
+    E = np.zeros(len(a), f32)
+    for k in range(3):
+        dh, dl = _two_sum(a[:, k], -b[:, k])
+        p = (dh * dh).astype(f32)
+        pe = _fma(dh, dh, -p)
+        t, te = _two_sum(S, p)
+        E = (E + (te + _fma(dl, _fma(2, dh, dl), pe)).astype(f32)).astype(f32)
+        S = (t + E).astype(f32)
+        E = (E - (S - t).astype(f32)).astype(f32)
+    yh = (S * ch).astype(f32)
+    yl = (_fma(S, ch, -yh) + _fma(S, cl, (E * ch).astype(f32))).astype(f32)
+    n = np.rint((yh * f32(369.32993046757464)).astype(f32)).astype(f32)
+    a0, ae = _two_sum((n * kL0).astype(f32), -yh)
+    p2 = (n * kL1).astype(f32)
+    b0, be = _two_sum(a0, p2)
+    rh, ce = _two_sum(b0, -yl)
+    rl = (((ae + be).astype(f32) + ce).astype(f32) + _fma(n, kL2, _fma(n, kL1, -p2))).astype(f32)
+    q = (rh * rh).astype(f32)
+    qe = _fma(rh, rh, -q)
+    c34 = ((q * rh).astype(f32) * _fma(rh, f32(1 / 24), f32(1 / 6))).astype(f32)
+    small = (_fma(0.5, qe, rl) + _fma(rh, rl, c34)).astype(f32)
+    u, ue = _two_sum(rh, (f32(0.5) * q).astype(f32))
+    eh, e4 = _two_sum(np.ones_like(u), u)
+    el = (e4 + (ue + small).astype(f32)).astype(f32)
+    ni = n.astype(np.int64)
+    j = ni & 255
+    m = (ni >> 8) + (j != 0)
+    th, tl = Th[(256 - j) & 255], Tl[(256 - j) & 255]
+    vh = (th * eh).astype(f32)
+    vl = (_fma(th, eh, -vh) + _fma(th, el, (tl * eh).astype(f32))).astype(f32)
+    # vh 2^(61 - m) is exact in binary; vl's part rounds to the integer grid
+    out = np.array([round(Fraction(float(x)) * 2 ** (FIX - int(mm))) + round(Fraction(float(z)) * 2 ** (FIX - int(mm)))
+                    for x, z, mm in zip(vh, vl, m)], dtype=object)
+    return np.where(yh <= 43.5, out, 0)
+
+
+def test_float_pair_kernel_value_model():
+    """The float-pair kernel value, modelled operation for operation, against the exact value
+    (FP32 world coordinates 100 m from the origin, l = 0.3): error below 2^-45 k (1 + y) + 2
+    units of 2^-61 and below 2^-46 absolute; coincident points give 2^61 exactly."""
+    rng = np.random.default_rng(7)
+    n = 4000
+    a = (np.array([103.7, -45.3, 12.9]) + rng.uniform(-1.5, 1.5, (n, 3))).astype(f32)
+    d = rng.normal(size=(n, 3))
+    d /= np.linalg.norm(d, axis=1, keepdims=True)
+    r = np.concatenate([rng.uniform(0, 2.0, n // 2), rng.uniform(0, 0.3, n // 4), 10.0 ** rng.uniform(-6, -1, n // 4)])
+    b = (a + d * r[:, None]).astype(f32)
+    b[:10] = a[:10]
+    inv2l2 = 1.0 / (2 * 0.3 * 0.3)
+    got = kernel_fix_model(a, b, inv2l2)
+    assert all(v == 2**FIX for v in got[:10])
+    worst = 0.0
+    for i in range(n):
+        r2 = sum((Fraction(float(a[i, k])) - Fraction(float(b[i, k]))) ** 2 for k in range(3))
+        y = float(r2 * Fraction(inv2l2))
+        exact = np.exp(-np.longdouble(y)) * np.longdouble(2.0) ** FIX
+        err = abs(np.longdouble(int(got[i])) - exact)
+        assert err <= exact * (1 + y) * np.longdouble(2.0) ** -45 + 2, i
+        assert err <= 2.0 ** (FIX - 46)
+        worst = max(worst, float(err / (exact * (1 + y) + 1)))
+    assert worst > 0

@@ -400,6 +400,47 @@ def test_table_exp_matches_libm(vg):
     assert r.cpu().tolist() == [0.0, 0.0]
 
 
+def test_float_pair_kernel_values(vg):
+    """Mixed-precision kernel values of the emulated factorisation (float-pair arithmetic on the
+    FP32 pipe, fixed point round(k 2^61)) against exp(-r^2 / (2 l^2)) in extended precision, for
+    FP32 world coordinates 100 m from the origin and distances from 0 to beyond the fixed
+    point's range: error below 2^-45 k (1 + y) + 2 units (y = r^2 / (2 l^2)), 2^-46 at most in
+    absolute terms, exact 2^61 for coincident points, 0 where k < 2^-63, symmetric bit for bit."""
+    import ctypes as C
+    from paper_2407_09649_gb300 import _lib
+    m = vg.Map(precision="mixed", emulate_fp64=1)
+    rng = np.random.default_rng(3)
+    n = 400000
+    xa = (np.array([103.7, -45.3, 12.9]) + rng.uniform(-1.5, 1.5, (n, 3))).astype(np.float32)
+    dirs = rng.normal(size=(n, 3))
+    dirs /= np.linalg.norm(dirs, axis=1, keepdims=True)
+    r = np.concatenate([rng.uniform(0, 2.0, n // 2), rng.uniform(0, 0.3, n // 4), 10.0 ** rng.uniform(-6, -1, n // 4)])
+    xb = (xa + dirs * r[:, None]).astype(np.float32)
+    xb[:100] = xa[:100]  # coincident
+    st = C.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+    def run(a, b):
+        ta, tb = torch.from_numpy(np.ascontiguousarray(a)).cuda(), torch.from_numpy(np.ascontiguousarray(b)).cuda()
+        out = torch.empty(len(a), dtype=torch.int64, device="cuda")
+        _lib.check(_lib.load().vgp_debug_kernel_fix(m._h, C.c_void_p(ta.data_ptr()), C.c_void_p(tb.data_ptr()),
+                                                    len(a), C.c_void_p(out.data_ptr()), st))
+        return out.cpu().numpy()
+
+    got = run(xa, xb)
+    assert np.array_equal(got, run(xb, xa))  # symmetric
+    assert np.all(got[:100] == 2**61)
+    L = np.longdouble
+    y = np.sum((xa.astype(L) - xb.astype(L)) ** 2, axis=1) / (2 * L(0.3) * L(0.3))
+    exact = np.exp(-y) * L(2.0) ** 61
+    err = np.abs(got.astype(L) - exact)
+    assert np.all(err <= exact * (1 + y) * L(2.0) ** -45 + 2), float(np.max((err - 2) / (exact * (1 + y))))
+    assert float(err.max()) <= 2.0 ** (61 - 46)
+    assert np.all(got[exact < 0.125] == 0)
+    big = exact > 2.0 ** 51
+    print("kernel-value error relative to k (median, max over k > 2^-10):", float(np.median(err[big] / exact[big])),
+          float(np.max(err[big] / exact[big])))
+
+
 # ----------------------------------------------------------------------------------
 # G-GPDF as blended per-leaf GPs (Eq. 10)
 # ----------------------------------------------------------------------------------
