@@ -237,11 +237,15 @@ __device__ __forceinline__ double kval_pair(const DevParams& P, const Shared& s,
 // integer round(v 2^61) (|v| <= 1 + sigma^2: every entry of K + sigma^2 I and of its Schur
 // complements is bounded by the largest diagonal entry).  The trailing updates then subtract
 // integers (one shift and one 64-bit subtraction per entry) and the block's columns are
-// turned into FP64 once, when the block is factorised.  Resolution 2^-61, far below the
+// turned into FP64 once, by the update that completes them.  Resolution 2^-61, far below the
 // updates' own rounding (2^-55 of the row maxima).
 constexpr int kFixBits = 61;
 __device__ __forceinline__ long long fix_of_double(double v) { return __double2ll_rn(v * 0x1p61); }
-__device__ __forceinline__ double double_of_fix(long long f) { return __ll2double_rn(f) * 0x1p-61; }
+// f 2^-61 as FP64: the conversion, then the exponent lowered by 61 on the integer pipe
+// (|f| >= 1 keeps the result normal)
+__device__ __forceinline__ double double_of_fix(long long f) {
+    return f == 0 ? 0.0 : __longlong_as_double(__double_as_longlong(__ll2double_rn(f)) - (61ll << 52));
+}
 
 // round(x 2^e) of a float x, |x| 2^e < 2^62, on the integer pipe (ties away from zero; 0 for
 // subnormal x).
@@ -730,6 +734,7 @@ __device__ bool trailing_update_tc(const SolveCtx& c, double* A, int Nt, int Ntr
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int M = Nt - K1;
     const int jr = (max(Ntr - K1, 0) + kColT - 1) / kColT;  // column tiles of the matrix itself
+    const int next1 = min(K1 + kEB, Ntr);                     // end of the next block's columns
     const uint32_t aA = smem_addr(stage), aB = aA + kStageA;
     const int q = warp & 3, h = warp >> 2;  // lane quadrant (rows 32 q ..) and column half
     const int row = 32 * q + lane, rb = row >> 3, rr = row & 7;
@@ -838,12 +843,20 @@ __device__ bool trailing_update_tc(const SolveCtx& c, double* A, int Nt, int Ntr
                     }
                 }
             }
+            // the next block's columns are final after this update: stored as FP64 (see
+            // factor_emulated), the rest in the fixed point
 #pragma unroll
             for (int j = 0; j < 2; ++j)
                 if (ok[j]) {
-                    double* C = A + tix(rt, K1 + c0 + 2 * h + j);
+                    const int ct = K1 + c0 + 2 * h + j;
+                    double* C = A + tix(rt, ct);
+                    if (ct < next1) {
 #pragma unroll
-                    for (int cc = 0; cc < 8; ++cc) C[te(rr, cc)] = __longlong_as_double(cv[j][cc]);
+                        for (int cc = 0; cc < 8; ++cc) C[te(rr, cc)] = double_of_fix(cv[j][cc]);
+                    } else {
+#pragma unroll
+                        for (int cc = 0; cc < 8; ++cc) C[te(rr, cc)] = __longlong_as_double(cv[j][cc]);
+                    }
                 }
             // every thread's reads of the accumulators are done before the next tile's MMAs
             asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
@@ -870,7 +883,7 @@ __device__ bool trailing_update_tc(const SolveCtx& c, double* A, int Nt, int Ntr
 // 2^22 with W = 32: the rounding of lo is below 2^-57 of the scale 2^(e_r + e_c - 2042).  The
 // trailing matrix is held in the fixed point of kFixBits (assembled so by fit_instance): w is
 // shifted to it and subtracted as an integer, so an updated entry costs no FP64 operation,
-// and each block's columns are turned into FP64 when the block is reached.  The slice
+// and each block's columns are stored as FP64 by the update that completes them.  The slice
 // products run on the tensor cores
 // (trailing_update_tc); within a block the diagonal block is factorised as in the plain loop
 // (8x8 tiles, FP64 tensor path) and the rows below it are solved one row tile per warp
@@ -887,9 +900,10 @@ __device__ bool factor_emulated(const SolveCtx& c, const Shared& s, double* A, i
     double* Tall = emu_tile_inverses(c);                  // inverses of all diagonal tiles, for the solves
     for (int K0 = 0; K0 < Ntr; K0 += kEB) {
         const int K1 = min(K0 + kEB, Ntr);
-        // the block's columns (tiles (it, jt), K0 <= jt < K1, jt <= it) from the fixed point of
-        // the trailing matrix to FP64
-        {
+        // the first block's columns (tiles (it, jt), jt < K1, jt <= it) from the fixed point of
+        // the assembly to FP64; later blocks' columns are stored as FP64 by the trailing update
+        // that completes them
+        if (K0 == 0) {
             const int nb = K1 - K0;
             const int64_t ne = (int64_t)(Nt - K0) * nb * 64;
             for (int64_t x = tid; x < ne; x += blockDim.x) {
