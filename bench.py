@@ -37,14 +37,12 @@ UNIT = "queries/s"
 WORKLOAD = "city G-GPDF: 2M surface pts, 10M queries (70% free space, 30% <=0.5 m from surface), 27-leaf cap 1024"
 
 # DRAM bytes (read + write) of the N > 224 solve launch (k_solve_emu) of one full 10M-query
-# step: 690.4 GB measured by one ncu capture of the current kernel on the 100k-query city case,
-# scaled by the ratio of the two launches' algorithmic work (sum of N^3/3 + 2 N^2: 2.854e12
-# against 1.851e12 flop; the previous kernel's small and full-size traffic had the same ratio,
-# 1.55).  The four smaller launches (3 % of the solve time) are not included.  None when the
-# kernel has changed since.
-K_SOLVE_TRAFFIC = 1.0644e12
+# step, from an ncu capture of the current kernel on the 100k-query city case scaled by the
+# ratio of the two launches' algorithmic work (sum of N^3/3 + 2 N^2).  None until the current
+# kernel has been captured.
+K_SOLVE_TRAFFIC = None
 K_SOLVE_TRAFFIC_SOURCE = ("ncu dram__bytes_read.sum + dram__bytes_write.sum of the N > 224 launch (k_solve_emu) on "
-                          "the 100k-query city case, scaled to the full step by its algorithmic work (x1.542); "
+                          "the 100k-query city case, scaled to the full step by its algorithmic work; "
                           "smaller buckets not included")
 
 # Algorithmic DRAM bytes of the HBM-bound steps (what each step must move at least):

@@ -19,7 +19,7 @@ public:
         kScan0, kScan1, kScan2, kHist, kOrder, kTmp0, kTmp1, kTmp2, kTmp3, kTmp4, kTmp5, kTmp6,
         kTmp7, kTmp8, kTmp9, kTmp10, kTmp11, kTmp12, kTmp13, kTmp14, kTmp15, kTmp16, kTmp17,
         kWs0, kWs1, kWs2, kWs3, kBw0, kBw1, kPair0, kPair1, kPair2, kPair3, kPair4, kPair5, kPair6, kPair7,
-        kCounters, kNumSlots
+        kChunks, kCounters, kNumSlots
     };
     void* get(Slot s, size_t bytes, cudaStream_t st);
     void release_all(cudaStream_t st);
@@ -121,11 +121,12 @@ int solve_batch(const SolveBatch& b, const DevParams& P, int* err_dev, cudaStrea
 // Set the thread-local message returned by vgp_last_error().
 void set_last_error(const char* msg);
 
-// k_solve with caller-provided scratch and no allocation (see noalloc.cu); 0 on success.
 // Diagnostic: the emulated kernel's mixed-precision kernel values round(k 2^61) of n pairs of
 // FP32 world coordinates (device arrays [n][3]); 0 or -1 on a launch error.
 int debug_kernel_fix(const DevParams& P, const float* xa, const float* xb, int64_t n, long long* out,
                      cudaStream_t st);
+
+// k_solve with caller-provided scratch and no allocation (see noalloc.cu); 0 on success.
 int solve_launch_static(const SolveBatch& b, const DevParams& P, int* err_dev, int npad, int threads, int max_grid,
                         int* counter, const int32_t* order, double* ws_v, cudaStream_t st);
 

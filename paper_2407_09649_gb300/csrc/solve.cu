@@ -72,6 +72,9 @@ struct SolveCtx {
     uint8_t* ws_e;         // per-CTA bf16 slices and row scales (emulated trailing updates)
     int64_t ws_e_stride;
     BackwardBatch bw;
+    const int* chunk_off = nullptr;  // work items (see k_chunk_plan): chunk offsets over the order;
+                                     // nullptr: one work item per instance
+    const int* chunk_q = nullptr;    // queries of a work item for this launch (0: all of them)
     int qmax = 0;          // emulated kernel with variance: query rows appended to A (0: none)
     int nrow = 0;          // emulated kernel: rows of the workspace matrices (npad + qmax)
 };
@@ -1431,7 +1434,7 @@ __device__ __forceinline__ void invalid(EvalOut& r, int status) {
 template <bool kProps, bool kEmu>
 __device__ __forceinline__ void solve_body(const SolveCtx& c) {
     extern __shared__ __align__(128) double sm[];
-    __shared__ int s_w;
+    __shared__ int s_item[2];
     __shared__ uint32_t s_tmem;
     __shared__ __align__(8) uint64_t s_bar[2];
     const int tid = threadIdx.x, nt = blockDim.x;
@@ -1469,18 +1472,47 @@ __device__ __forceinline__ void solve_body(const SolveCtx& c) {
         tc.bar_ld = smem_addr(&s_bar[0]);
         tc.bar_mma = smem_addr(&s_bar[1]);
     }
-    for (;;) {
-        if (tid == 0) s_w = atomicAdd(c.counter, 1);
+    for (bool first = true;; first = false) {
+        // the next work item: an instance, or one chunk of its queries (the instance is fitted
+        // again for every chunk, so the queries of a large instance spread over the GPU).  CTA i
+        // takes item i first (the CTAs of a launch are spread over the SMs in index order, so a
+        // grid larger than the work stays balanced), then items from the counter.
+        if (tid == 0) {
+            const int w = first ? (int)blockIdx.x : (int)gridDim.x + atomicAdd(c.counter, 1);
+            // graph mode: this bucket's count and share of the order, planned on the device
+            const int nb = c.plan ? c.plan[c.bucket] : c.n_work;
+            const int ob = c.plan ? c.plan[5 + c.bucket] : 0;
+            int k = w, ci = 0, nw = nb;
+            if (c.chunk_off) {
+                const int* cof = c.chunk_off + ob;  // direct launches pass the bucket's offset
+                nw = cof[nb] - cof[0];
+                if (w < nw) {  // the last instance whose first chunk is at or before w
+                    const int t = cof[0] + w;
+                    int lo = 0, hi = nb - 1;
+                    while (lo < hi) {
+                        const int mid = (lo + hi + 1) >> 1;
+                        if (cof[mid] <= t)
+                            lo = mid;
+                        else
+                            hi = mid - 1;
+                    }
+                    k = lo;
+                    ci = t - cof[lo];
+                }
+            }
+            s_item[0] = w < nw ? (c.order ? c.order[ob + k] : c.inst_base + k) : -1;
+            s_item[1] = ci;
+        }
         __syncthreads();
-        const int w = s_w;
+        const int I = s_item[0], ci = s_item[1];
         __syncthreads();
-        // graph mode: this bucket's count and share of the order, planned on the device (read
-        // per work item rather than held in registers across the loop)
-        if (w >= (c.plan ? c.plan[c.bucket] : c.n_work)) break;
-        const int I = c.order ? c.order[(c.plan ? c.plan[5 + c.bucket] : 0) + w] : c.inst_base + w;
+        if (I < 0) break;
         const int64_t base = c.b.inst_off[I];
         const int N = (int)(c.b.inst_off[I + 1] - base);
-        const int64_t q0 = c.b.q_off[I], q1 = c.b.q_off[I + 1];
+        const int64_t qa = c.b.q_off[I], qb = c.b.q_off[I + 1];
+        const int qch = c.chunk_q ? *c.chunk_q : 0;
+        const int64_t q0 = qch > 0 ? min(qb, qa + (int64_t)ci * qch) : qa;
+        const int64_t q1 = qch > 0 ? min(qb, q0 + qch) : qb;
         if (kProps) {
             const bool ok = N > 0 && fit_instance<kProps, kEmu>(c, s, N, base, &tc, 0, q0, I);
             // property mode: means and variance (Eq. 6, variance read as for Eq. 2)
@@ -1514,7 +1546,7 @@ __device__ __forceinline__ void solve_body(const SolveCtx& c) {
             const int64_t cq1 = border ? min(q1, cq0 + (int64_t)c.qmax) : q1;
             const bool ok = N > 0 && fit_instance<kProps, kEmu>(c, s, N, base, &tc, border ? (int)(cq1 - cq0) : 0,
                                                                  cq0, I);
-            if (c.b.alpha_out && cq0 == q0)
+            if (c.b.alpha_out && ci == 0 && cq0 == q0)
                 for (int j = tid; j < N; j += nt) c.b.alpha_out[base + j] = ok ? s.alpha[j] : NAN;
             const int64_t ce = ok ? cq1 : q1;  // a failed factorisation answers all remaining queries
             for (int64_t p = cq0 + tid; p < ce; p += nt) {
@@ -1678,6 +1710,15 @@ __global__ void k_hist_n(const int64_t* inst_off, int64_t n, int* hist) {
     atomicAdd(&hist[min(N, 1024)], 1);
 }
 
+// Queries of each size bucket (N > 224, > 128, > 64, > 32, the rest), for the chunk planning.
+__global__ void k_bucket_queries(const int64_t* inst_off, const int64_t* q_off, int64_t n, unsigned long long* qsum) {
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const int64_t N = inst_off[i + 1] - inst_off[i];
+    const int bk = N > 224 ? 0 : N > 128 ? 1 : N > 64 ? 2 : N > 32 ? 3 : 4;
+    atomicAdd(&qsum[bk], (unsigned long long)(q_off[i + 1] - q_off[i]));
+}
+
 // order[] sorted by increasing N via the prefix of the histogram
 __global__ void k_order_n(const int64_t* inst_off, int64_t n, int* cursor, int32_t* order) {
     int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
@@ -1707,6 +1748,101 @@ __global__ void k_plan_buckets(const int* hist, int* cursor, int* plan) {
         plan[5 + b] = off;
         off += cnt;
     }
+}
+
+// Work items of the solve launches: where the evaluation is heavy (variance, surface
+// properties), a bucket with few instances is split into chunks of qc queries (chunk_size) so
+// that its queries spread over the GPU; each chunk fits its instance again.  cap[b] > 0
+// bounds qc (the rows a bordered factorisation appends).  chunk_q[b] receives qc (0: no
+// split; taken from a.qc when the host decided); chunk_off[k]
+// the number of work items of the order before instance k, chunk_off[n] the total.  The
+// buckets are contiguous in the order: from the device plan in graph mode, else from a.
+struct ChunkPlanArgs {
+    int off[5], cnt[5], slots[5], cap[5];
+    int heavy;
+    int decided, qc[5];  // decided: the chunk sizes qc were chosen on the host (same rule)
+};
+constexpr int kMinChunk = 64, kMinChunksPer = 8;
+// Queries per work item of a bucket of cnt instances with tq queries in all, launched on slots
+// CTAs; cap > 0 bounds it; 0: no bound (one work item per instance).  A bucket that holds at
+// most half as many instances as CTAs is split into chunks of ceil(tq / slots) queries, at
+// least kMinChunk, when that gives its instances kMinChunksPer chunks on average: for fewer,
+// fitting each chunk again costs more than the spread gains.
+__host__ __device__ inline int chunk_size(bool heavy, int cnt, int slots, int cap, long long tq) {
+    int qc = cap;
+    if (heavy && cnt > 0 && 2 * (long long)cnt <= slots) {
+        long long want = (tq + slots - 1) / slots;
+        if (want < kMinChunk) want = kMinChunk;
+        if (tq >= (long long)kMinChunksPer * want * cnt) {
+            if (qc > 0 && qc < want) want = qc;
+            qc = (int)(want < INT32_MAX ? want : INT32_MAX);
+        }
+    }
+    return qc;
+}
+__global__ void k_chunk_plan(const int32_t* order, int n, const int64_t* inst_off, const int64_t* q_off,
+                             const int* plan, ChunkPlanArgs a, int* chunk_q, int* chunk_off) {
+    __shared__ long long wq[32];
+    __shared__ int wsum[32];
+    __shared__ int carry, s_qc;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarp = blockDim.x >> 5;
+    if (tid == 0) carry = 0;
+    for (int bk = 0; bk < 5; ++bk) {
+        const int off = plan ? plan[5 + bk] : a.off[bk], cnt = plan ? plan[bk] : a.cnt[bk];
+        // the bucket's queries
+        long long q = 0;
+        for (int k = tid; k < cnt; k += blockDim.x) {
+            const int I = order[off + k];
+            q += q_off[I + 1] - q_off[I];
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) q += __shfl_xor_sync(0xffffffffu, q, o);
+        if (lane == 0) wq[warp] = q;
+        __syncthreads();
+        if (tid == 0) {
+            long long tq = 0;
+            for (int w = 0; w < nwarp; ++w) tq += wq[w];
+            int qc = a.decided ? a.qc[bk] : chunk_size(a.heavy != 0, cnt, a.slots[bk], a.cap[bk], tq);
+            chunk_q[bk] = qc;
+            s_qc = qc;
+        }
+        __syncthreads();
+        const int qc = s_qc;
+        // exclusive scan of the chunk counts, continuing the running total
+        for (int b0 = 0; b0 < cnt; b0 += blockDim.x) {
+            const int k = b0 + tid;
+            int v = 0;
+            if (k < cnt) {
+                const int I = order[off + k];
+                const int64_t nq = q_off[I + 1] - q_off[I];
+                v = qc > 0 ? (int)max((int64_t)1, (nq + qc - 1) / qc) : 1;
+            }
+            int x = v;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int y = __shfl_up_sync(0xffffffffu, x, o);
+                if (lane >= o) x += y;
+            }
+            if (lane == 31) wsum[warp] = x;
+            __syncthreads();
+            if (warp == 0) {
+                int t = lane < nwarp ? wsum[lane] : 0;
+#pragma unroll
+                for (int o = 1; o < 32; o <<= 1) {
+                    const int y = __shfl_up_sync(0xffffffffu, t, o);
+                    if (lane >= o) t += y;
+                }
+                wsum[lane] = t;
+            }
+            __syncthreads();
+            const int excl = carry + (warp > 0 ? wsum[warp - 1] : 0) + x - v;
+            if (k < cnt) chunk_off[off + k] = excl;
+            __syncthreads();
+            if (tid == blockDim.x - 1) carry = excl + v;
+            __syncthreads();
+        }
+    }
+    if (tid == 0) chunk_off[n] = carry;
 }
 
 __global__ void k_reverse_i32(const int32_t* in, int32_t* out, int n) {
@@ -1772,6 +1908,15 @@ SolveKernel pick_solve(bool props, bool emu) {
 
 // seven bf16 slices of a block's columns, the row scale, and one row of diagonal-tile inverses
 constexpr int64_t kEmuBytesPerRow = 7 * 8 * kEB * 2 + 8 + 64;
+
+// Chunk planning of a solve (see k_chunk_plan): heavy evaluation, and the bordered emulated
+// bucket's bound (kBorderQ queries appended at a time).  False when no launch splits.
+bool chunk_args(const SolveBatch& b, const DevParams& P, bool bw, ChunkPlanArgs& a) {
+    a = ChunkPlanArgs{};
+    a.heavy = !bw && (b.want_var || b.nprop > 0);
+    a.cap[0] = (!bw && P.emulate && b.want_var && b.nprop == 0 && !b.Xi) ? kBorderQ : 0;
+    return a.heavy != 0;
+}
 
 // Emulated launch with the latent variance: the queries of an instance (up to kBorderQ) are
 // appended to its matrix, which is padded to a multiple of 32 rows (see fit_instance); the
@@ -1895,6 +2040,8 @@ int solve_batch_graph(const SolveBatch& b, const DevParams& P, int* err_dev, cud
         if (cudaFuncSetAttribute(sh[i].kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm_max) != cudaSuccess)
             return -1;
     }
+    ChunkPlanArgs ca;
+    const bool chunks = chunk_args(b, P, false, ca);
     int64_t ws_a_need = 0, ws_v_need = 0, ws_e_need = 0;
     for (int i = 0; i < 5; ++i) {
         Shape& s = sh[i];
@@ -1908,6 +2055,7 @@ int solve_batch_graph(const SolveBatch& b, const DevParams& P, int* err_dev, cud
             if (cfg->per_sm[i] > 0) per_sm = std::min(per_sm, cfg->per_sm[i]);
         }
         s.grid = (int)std::min<int64_t>(n, (int64_t)n_sm * per_sm);
+        ca.slots[i] = s.grid;
         if (!s.smem_a) ws_a_need = std::max<int64_t>(ws_a_need, n_tiles(s.nrow / 8) * 64 * s.grid);
         if (b.want_var) ws_v_need = std::max<int64_t>(ws_v_need, (int64_t)s.npad * s.threads * s.grid);
         if (s.emu) ws_e_need = std::max<int64_t>(ws_e_need, (int64_t)s.nrow * kEmuBytesPerRow * s.grid);
@@ -1919,8 +2067,11 @@ int solve_batch_graph(const SolveBatch& b, const DevParams& P, int* err_dev, cud
     double* ws_a = ws_a_need ? (double*)ar.get(Arena::kWs0, sizeof(double) * ws_a_need, st) : nullptr;
     double* ws_v = ws_v_need ? (double*)ar.get(Arena::kWs1, sizeof(double) * ws_v_need, st) : nullptr;
     uint8_t* ws_e = ws_e_need ? (uint8_t*)ar.get(Arena::kWs3, ws_e_need, st) : nullptr;
-    if (!hist || !order || !counters || (ws_a_need && !ws_a) || (ws_v_need && !ws_v) || (ws_e_need && !ws_e))
+    int* chunk_off = chunks ? (int*)ar.get(Arena::kChunks, sizeof(int) * (n + 1 + 5), st) : nullptr;
+    if (!hist || !order || !counters || (ws_a_need && !ws_a) || (ws_v_need && !ws_v) || (ws_e_need && !ws_e) ||
+        (chunks && !chunk_off))
         return alloc_failed(err_dev, st);
+    int* chunk_q = chunk_off ? chunk_off + n + 1 : nullptr;
     int* cursor = hist + 1025;
     int* plan = counters + 5;
     cudaStream_t gs = gc->gs;
@@ -1934,10 +2085,16 @@ int solve_batch_graph(const SolveBatch& b, const DevParams& P, int* err_dev, cud
     note_launch();
     k_order_n<<<(unsigned)((n + T - 1) / T), T, 0, gs>>>(b.inst_off, n, cursor, order);
     note_launch();
+    if (chunk_off) {
+        k_chunk_plan<<<1, 1024, 0, gs>>>(order, (int)n, b.inst_off, b.q_off, plan, ca, chunk_q, chunk_off);
+        note_launch();
+    }
     for (int i = 0; i < 5; ++i) {
         const Shape& s = sh[i];
         if (!s.live) continue;
         SolveCtx c;
+        c.chunk_off = chunk_off;
+        c.chunk_q = chunk_q ? chunk_q + i : nullptr;
         c.b = b;
         c.P = P;
         c.err = err_dev;
@@ -2024,16 +2181,26 @@ int solve_batch(const SolveBatch& b, const DevParams& P, int* err_dev, cudaStrea
         }
         return 0;
     }
-    // size histogram and decreasing-size order
-    int* hist = (int*)ar.get(Arena::kHist, sizeof(int) * 2 * 1025, st);
+    // size histogram (and, for chunk planning, each bucket's queries) and decreasing-size order
+    ChunkPlanArgs ca;
+    const bool heavy = chunk_args(b, P, bw != nullptr, ca);
+    int* hist = (int*)ar.get(Arena::kHist, sizeof(int) * 2 * 1025 + sizeof(unsigned long long) * 5, st);
     if (!hist) return alloc_failed(err_dev, st);
     int* cursor = hist + 1025;
+    unsigned long long* qsum = reinterpret_cast<unsigned long long*>(hist + 2 * 1025);
     cudaMemsetAsync(hist, 0, sizeof(int) * 1025, st);
     const int T = 256;
     k_hist_n<<<(unsigned)((n + T - 1) / T), T, 0, st>>>(b.inst_off, n, hist);
     note_launch();
+    unsigned long long hq[5] = {0, 0, 0, 0, 0};
+    if (heavy) {
+        cudaMemsetAsync(qsum, 0, sizeof(hq), st);
+        k_bucket_queries<<<(unsigned)((n + T - 1) / T), T, 0, st>>>(b.inst_off, b.q_off, n, qsum);
+        note_launch();
+    }
     std::vector<int> h(1025);
     cudaMemcpyAsync(h.data(), hist, sizeof(int) * 1025, cudaMemcpyDeviceToHost, st);
+    if (heavy) cudaMemcpyAsync(hq, qsum, sizeof(hq), cudaMemcpyDeviceToHost, st);
     cudaStreamSynchronize(st);
     std::vector<int> start(1026, 0);
     for (int i = 0; i < 1025; ++i) start[i + 1] = start[i] + h[i];
@@ -2046,6 +2213,8 @@ int solve_batch(const SolveBatch& b, const DevParams& P, int* err_dev, cudaStrea
     k_reverse_i32<<<(unsigned)((n + T - 1) / T), T, 0, st>>>(order_inc, order, (int)n);
     note_launch();
     add_stats(stats, h);
+    int* chunk_off = nullptr;
+    int* chunk_q = nullptr;
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
     if (profile) {
         cudaEventCreate(&ev0);
@@ -2125,8 +2294,71 @@ int solve_batch(const SolveBatch& b, const DevParams& P, int* err_dev, cudaStrea
         }
         return 0;
     }
+    // a bucket's launch: shapes, kernel and resident CTAs per SM
+    struct Launch {
+        int npad, qmax, nrow, threads, stage, per_sm;
+        size_t shm;
+        bool emu;
+        SolveKernel kern;
+    };
+    auto bucket_nmax = [&](int i, int& cnt) {
+        int nmax = 0;
+        cnt = 0;
+        for (int N = buckets[i].lo; N <= buckets[i].hi; ++N) {
+            cnt += h[N];
+            if (h[N]) nmax = N;
+        }
+        return nmax;
+    };
+    auto bucket_launch = [&](int i, int nmax) {
+        const Bucket& bk = buckets[i];
+        Launch L;
+        L.npad = std::max((nmax + 7) & ~7, 8);
+        L.emu = !bw && !bk.smem_a && P.emulate;
+        emu_rows_for(L.emu, b, L.npad, L.qmax, L.nrow);
+        L.threads = L.emu ? kEmuThreads : bk.threads;
+        L.stage = bk.smem_a ? 1 : (L.emu ? 0 : cfg->stage_panel);
+        L.shm = smem_bytes(L.npad, bk.smem_a, bw ? 0 : b.nprop, L.stage, b.Xi != nullptr, bw != nullptr, L.emu);
+        L.kern = bw ? k_backward : pick_solve(b.nprop > 0, L.emu);
+        cudaFuncSetAttribute(L.kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.shm);
+        if (L.emu) set_emu_carveout(L.kern);
+        L.per_sm = 0;
+        if (L.emu) {
+            L.per_sm = emu_ctas_per_sm(L.kern, L.threads, L.shm);
+        } else {
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&L.per_sm, L.kern, L.threads, L.shm);
+            L.per_sm = std::max(L.per_sm, 1);
+            if (cfg->per_sm[i] > 0) L.per_sm = std::min(L.per_sm, cfg->per_sm[i]);
+        }
+        return L;
+    };
     int* counters = (int*)ar.get(Arena::kCounters, sizeof(int) * 8, st);
-    if (!counters) {
+    bool chunks = false;
+    if (heavy) {
+        // the buckets' ranges of the order, their resident CTAs (as the launches below) and
+        // chunk sizes; work items are planned only where some bucket has more than its instances
+        int off = 0;
+        for (int i = 0; i < 5; ++i) {
+            int cnt = 0;
+            const int nmax = bucket_nmax(i, cnt);
+            ca.off[i] = off;
+            ca.cnt[i] = cnt;
+            off += cnt;
+            ca.slots[i] = cnt > 0 ? n_sm * bucket_launch(i, nmax).per_sm : 0;
+            ca.qc[i] = chunk_size(true, cnt, ca.slots[i], ca.cap[i], (long long)hq[i]);
+            chunks = chunks || (cnt > 0 && ca.qc[i] > 0);
+        }
+        ca.decided = 1;
+    }
+    if (chunks) {
+        chunk_off = (int*)ar.get(Arena::kChunks, sizeof(int) * (n + 1 + 5), st);
+        if (chunk_off) {
+            chunk_q = chunk_off + n + 1;
+            k_chunk_plan<<<1, 1024, 0, st>>>(order, (int)n, b.inst_off, b.q_off, nullptr, ca, chunk_q, chunk_off);
+            note_launch();
+        }
+    }
+    if (!counters || (chunks && !chunk_off)) {
         if (profile) {
             cudaEventDestroy(ev0);
             cudaEventDestroy(ev1);
@@ -2137,11 +2369,8 @@ int solve_batch(const SolveBatch& b, const DevParams& P, int* err_dev, cudaStrea
     int done = 0;  // instances already assigned (from the large end)
     int bi = 0;
     for (const Bucket& bk : buckets) {
-        int cnt = 0, nmax = 0;
-        for (int N = bk.lo; N <= bk.hi; ++N) {
-            cnt += h[N];
-            if (h[N]) nmax = N;
-        }
+        int cnt = 0;
+        const int nmax = bucket_nmax(bi, cnt);
         if (cnt == 0) {
             ++bi;
             continue;
@@ -2158,27 +2387,23 @@ int solve_batch(const SolveBatch& b, const DevParams& P, int* err_dev, cudaStrea
         c.order = order + done;
         c.inst_base = 0;
         c.n_work = cnt;
-        c.npad = std::max((nmax + 7) & ~7, 8);
+        c.chunk_off = chunk_off ? chunk_off + done : nullptr;
+        c.chunk_q = chunk_q ? chunk_q + bi : nullptr;
+        const Launch L = bucket_launch(bi, nmax);
+        c.npad = L.npad;
+        c.qmax = L.qmax;
+        c.nrow = L.nrow;
         c.a_in_smem = bk.smem_a;
-        const bool emu = !bw && !bk.smem_a && P.emulate;
-        emu_rows_for(emu, b, c.npad, c.qmax, c.nrow);
-        const int threads = emu ? kEmuThreads : bk.threads;
-        c.stage_panel = bk.smem_a ? 1 : (emu ? 0 : cfg->stage_panel);
+        const bool emu = L.emu;
+        const int threads = L.threads;
+        c.stage_panel = L.stage;
         if (bw) c.bw = *bw;
-        const size_t shm =
-            smem_bytes(c.npad, c.a_in_smem, bw ? 0 : b.nprop, c.stage_panel, b.Xi != nullptr, bw != nullptr, emu);
-        auto kern = bw ? k_backward : pick_solve(b.nprop > 0, emu);
-        cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm);
-        if (emu) set_emu_carveout(kern);
-        int per_sm = 0;
-        if (emu) {
-            per_sm = emu_ctas_per_sm(kern, threads, shm);
-        } else {
-            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, threads, shm);
-            per_sm = std::max(per_sm, 1);
-            if (cfg->per_sm[bi] > 0) per_sm = std::min(per_sm, cfg->per_sm[bi]);
-        }
-        const int grid = (int)std::min<int64_t>(cnt, (int64_t)n_sm * per_sm);
+        const size_t shm = L.shm;
+        auto kern = L.kern;
+        const int per_sm = L.per_sm;
+        // a split bucket keeps every resident CTA busy; otherwise one CTA per instance at most
+        const bool split = chunk_off && ca.qc[bi] > 0;
+        const int grid = (int)std::min<int64_t>(split ? INT32_MAX : cnt, (int64_t)n_sm * per_sm);
         c.ws_a_stride = c.a_in_smem ? 0 : n_tiles(c.nrow / 8) * 64;
         c.ws_a = c.a_in_smem ? nullptr : (double*)ar.get(Arena::kWs0, sizeof(double) * c.ws_a_stride * grid, st);
         c.ws_v_stride = (int64_t)c.npad * threads;

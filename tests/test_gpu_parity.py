@@ -327,6 +327,40 @@ def test_bordered_variance_chunks(vg, orc, precision):
         assert np.array_equal(np.ascontiguousarray(r2[k]).view(np.uint8), a.view(np.uint8)), k
 
 
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_chunked_queries_bit_identical(vg, orc, precision):
+    """Few instances with many queries (3000 each, N from 20 to 400): the launch splits each
+    instance's queries into chunks that fit the instance again, so that the queries spread over
+    the GPU.  Every query's distance, gradient, variance and status are bit-identical to the
+    same query answered with 40 queries per instance (not split), and agree with the oracle."""
+    rng = np.random.default_rng(41)
+    sizes = [20, 60, 100, 180, 400]
+    nq = 3000
+    Xs, Qs = [], []
+    for N in sizes:
+        c = rng.uniform(-20, 20, 3)
+        Xs.append(c + rng.uniform(-0.05, 0.05, (N, 3)) * np.sqrt(N))
+        Qs.append(c + rng.uniform(-1, 1, (nq, 3)))
+    X = np.vstack(Xs).astype(np.float32)
+    Q = np.vstack(Qs).astype(np.float32)
+    io = np.concatenate([[0], np.cumsum(sizes)])
+    qo = np.arange(len(sizes) + 1) * nq
+    m = vg.Map(precision=precision, emulate_fp64=1)
+    full = {k: v.cpu().numpy() for k, v in m.gp_batch(io, X, qo, Q, var=True).items()}
+    pick = np.concatenate([i * nq + np.sort(rng.choice(nq, 40, replace=False)) for i in range(len(sizes))])
+    sub = {k: v.cpu().numpy() for k, v in m.gp_batch(io, X, np.arange(len(sizes) + 1) * 40, Q[pick], var=True).items()}
+    for k in ("d", "grad", "var", "status"):
+        assert np.array_equal(np.ascontiguousarray(full[k][pick]).view(np.uint8), np.ascontiguousarray(sub[k]).view(np.uint8)), k
+    ref = orc.gp_batch(io, X.astype(np.float64), np.arange(len(sizes) + 1) * 40, Q[pick].astype(np.float64), orc.params())
+    assert np.array_equal(sub["status"], ref.status)
+    ok = (ref.status == 0) & (ref.d > 2e-3) & (ref.d < 9.0)
+    assert ok.sum() > 100
+    assert np.abs(sub["d"][ok] - ref.d[ok]).max() <= (D_TOL if precision == "fp64" else D_TOL_MIXED)
+    fin = ok & np.isfinite(ref.var) & (ref.var > 0)
+    if precision == "fp64":
+        np.testing.assert_allclose(sub["var"][fin], ref.var[fin], rtol=1e-5, atol=1e-12)
+
+
 def test_gp_batch_rejects_oversize(vg):
     from paper_2407_09649_gb300 import _lib
     m = vg.Map()
