@@ -37,10 +37,11 @@ UNIT = "queries/s"
 WORKLOAD = "city G-GPDF: 2M surface pts, 10M queries (70% free space, 30% <=0.5 m from surface), 27-leaf cap 1024"
 
 # DRAM bytes (read + write) of the N > 224 solve launch (k_solve_emu) of one full 10M-query
-# step, from an ncu capture of the current kernel on the 100k-query city case scaled by the
-# ratio of the two launches' algorithmic work (sum of N^3/3 + 2 N^2).  None until the current
-# kernel has been captured.
-K_SOLVE_TRAFFIC = None
+# step: 710.0 GB from an ncu capture of the current kernel on the 100k-query city case, scaled
+# by the ratio of the two launches' algorithmic work (sum of N^3/3 + 2 N^2: 2.854e12 against
+# 1.851e12 flop, x1.542; an earlier kernel's small and full-size captures had that ratio).
+# None when the kernel has changed since.
+K_SOLVE_TRAFFIC = 1.0948e12
 K_SOLVE_TRAFFIC_SOURCE = ("ncu dram__bytes_read.sum + dram__bytes_write.sum of the N > 224 launch (k_solve_emu) on "
                           "the 100k-query city case, scaled to the full step by its algorithmic work; "
                           "smaller buckets not included")
@@ -154,21 +155,23 @@ def _emu_mma_table():
     """bf16 tensor flops of the emulated factorisation of one instance, by N (0..1024).
 
     The factorisation runs in blocks of 4 tiles (32 columns); after each block but the last,
-    the M = Nt - K1 row tiles below it take a trailing update in warp items of 16 rows x 8
-    columns ((MB - 1) MB + min(2 MB, M) items, MB = ceil(M / 2)), each 2 steps x 34 slice
-    products of mma.sync m16n8k16 (2 * 16 * 8 * 16 flops each)."""
+    the M = Nt - K1 row tiles below it take a trailing update in bands of 16 row tiles (128
+    rows); a band meets ceil((b0 + nb) / 4) column tiles of 32 columns (b0: the band's first
+    row tile, nb its row tiles), and each (band, column tile) output is 2 steps x 34 slice
+    products of tcgen05.mma kind::f16 M = 128, N = 32, K = 16 (2 * 128 * 32 * 16 flops each)."""
     tab = np.zeros(1025)
     for N in range(1, 1025):
         Nt = (N + 7) // 8
-        items = 0
+        mmas = 0
         for K0 in range(0, Nt, 4):
             K1 = min(K0 + 4, Nt)
             if K1 >= Nt:
                 break
             M = Nt - K1
-            MB = (M + 1) // 2
-            items += (MB - 1) * MB + min(2 * MB, M)
-        tab[N] = items * 2 * 34 * (2 * 16 * 8 * 16)
+            for b0 in range(0, M, 16):
+                nb = min(16, M - b0)
+                mmas += ((b0 + nb + 3) // 4) * 2 * 34
+        tab[N] = mmas * (2 * 128 * 32 * 16)
     return tab
 
 
@@ -361,8 +364,9 @@ def solve_roofline(prof, fp64_peak, bf16_peak):
                           "frac": bf16_achieved / bf16_peak if bf16_achieved else None,
                           "peak_source": "of measured: MEASURED_PEAKS bf16_tflops (cuBLAS burst)",
                           "kernel_ms": prof["emu_ms"], "bf16_flop": bf16_flop,
-                          "flop_def": ("mma.sync m16n8k16 slice products issued: per 32-column block "
-                                       "((MB-1) MB + min(2 MB, M)) warp items x 2 steps x 34 products x 4096 flop")}}
+                          "flop_def": ("tcgen05.mma kind::f16 128x32x16 slice products issued: per 32-column "
+                                       "block, per band of 128 rows, ceil(rows reached / 32) column tiles x 2 steps "
+                                       "x 34 products x 131072 flop")}}
 
 
 def hbm_lines(prof, fuse_prof, peak):
