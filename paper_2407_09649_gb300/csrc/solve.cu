@@ -99,8 +99,8 @@ struct Shared {
     double* Wsc;    // [warps][64] per-warp tile scratch (layout changes between mma operands)
     unsigned char* stage;  // emulated kernel: slice operands of the tensor-core updates (aliases
                            // X .. alf_lo, which the factorisation does not use; reloaded after it)
-    double* qxl;           // emulated kernel: [kBorderQ][3] local coordinates of appended queries
-    float* qw;             // emulated kernel: [kBorderQ][3] world coordinates of appended queries (FP32)
+    float* qw;             // emulated kernel: [kBorderQ][3] world coordinates of appended queries (FP32;
+                           // NaN: not finite)
     float* Xw;             // emulated kernel: [npad][3] world coordinates of the points (FP32, exact)
     float2* Tff;           // emulated kernel: 2^(j/256), j = 0..255, as float pairs
 };
@@ -119,7 +119,10 @@ constexpr int kEmuTmemCols = 8 * 8 * kColT;    // 8 slice groups x 32 FP32 colum
 // Latent variance in the emulated kernel: up to kBorderQ queries of an instance append their
 // kernel vectors to A as rows, so the factorisation itself yields 1 - |L^-1 k|^2 (see
 // fit_instance); an instance with more queries is factorised once per chunk of kBorderQ.
-constexpr int kBorderQ = 256;
+// Instances gather the queries of several query leaves (those that fall back to a shared
+// leaf), so the bound is set high: a factorisation costs about N^3/6 products against
+// N^2/2 per appended row.
+constexpr int kBorderQ = 1024;
 constexpr int kEmuCtasPerSm = 512 / kEmuTmemCols;  // CTAs whose tensor memory fits one SM
 
 __host__ __device__ __forceinline__ size_t align128(size_t x) { return (x + 127) & ~(size_t)127; }
@@ -134,7 +137,7 @@ __host__ __device__ __forceinline__ size_t emu_point_bytes(int npad, int nprop, 
 // the points (also as FP32 world coordinates) and the appended queries (both forms)
 __host__ __device__ __forceinline__ size_t emu_alias_bytes(int npad, int nprop, bool lattice) {
     const size_t b = emu_point_bytes(npad, nprop, lattice) + (size_t)3 * npad * sizeof(float) +
-                     (size_t)kBorderQ * (3 * sizeof(double) + 3 * sizeof(float));
+                     (size_t)kBorderQ * 3 * sizeof(float);
     return b > (size_t)kStageBytes ? b : (size_t)kStageBytes;
 }
 
@@ -165,8 +168,7 @@ __device__ Shared carve_emu(double* sm, int npad, double* ws_a, int nprop, bool 
     s.pa[2] = nprop > 2 ? extra : nullptr;
     s.pa[3] = nprop > 3 ? extra + npad : nullptr;
     s.Xw = reinterpret_cast<float*>(s.stage + emu_point_bytes(npad, nprop, lattice));
-    s.qxl = reinterpret_cast<double*>(s.Xw + 3 * npad);
-    s.qw = reinterpret_cast<float*>(s.qxl + 3 * kBorderQ);
+    s.qw = s.Xw + 3 * npad;
     s.Tff = reinterpret_cast<float2*>(s.Wsc + 8 * 64);
     return s;
 }
@@ -176,7 +178,6 @@ __device__ Shared carve(double* sm, int npad, int a_in_smem, double* ws_a, int n
     if (emu) return carve_emu(sm, npad, ws_a, nprop, lattice);
     Shared s;
     s.stage = nullptr;
-    s.qxl = nullptr;
     s.qw = nullptr;
     s.Xw = nullptr;
     s.Tff = nullptr;
@@ -823,6 +824,10 @@ __device__ bool trailing_update_tc(const SolveCtx& c, double* A, int Nt, int Ntr
 #pragma unroll
             for (int j = 0; j < 2; ++j) {  // the thread's two column tiles of the output tile
                 const int cb = 2 * h + j;
+                // a warp none of whose rows is updated in this column tile (rows past the band,
+                // above the diagonal, or of the query block away from its diagonal) skips it;
+                // the test is warp-uniform, as the collective tcgen05.ld needs
+                if (!__any_sync(0xffffffffu, ok[j])) continue;
 #pragma unroll
                 for (int p = 0; p < 2; ++p) {  // four columns at a time
                     uint32_t v[8][4];
@@ -1003,8 +1008,7 @@ __device__ bool fit_instance(const SolveCtx& c, const Shared& s, int N, int64_t 
             query_local(c, I, p, qid, xl);
             const bool fin = isfinite(xl[0]) && isfinite(xl[1]) && isfinite(xl[2]);
             for (int k = 0; k < 3; ++k) {
-                s.qxl[3 * a + k] = fin ? xl[k] : NAN;
-                s.qw[3 * a + k] = fin ? (float)(xl[k] + (c.b.centre ? c.b.centre[3 * (int64_t)I + k] : 0.0)) : 0.f;
+                s.qw[3 * a + k] = fin ? (float)(xl[k] + (c.b.centre ? c.b.centre[3 * (int64_t)I + k] : 0.0)) : NAN;
             }
         }
     if (tid == 0) s_fail = 0;
@@ -1026,14 +1030,19 @@ __device__ bool fit_instance(const SolveCtx& c, const Shared& s, int N, int64_t 
                     const int a = i - Np;
                     if (j >= Np || a >= nq) {
                         v = (i == j) ? (1ll << kFixBits) : 0;
-                    } else if (j >= N || isnan(s.qxl[3 * a])) {
+                    } else if (j >= N || isnan(s.qw[3 * a])) {
                         v = 0;
                     } else if (c.P.precision == VGP_MIXED) {
                         v = kfix_ff(s.qw + 3 * a, s.Xw + 3 * j, c.P.inv2l2_hi, c.P.inv2l2_lo, s.Tff);
                     } else {
-                        const double dx = s.X[3 * j] - s.qxl[3 * a], dy = s.X[3 * j + 1] - s.qxl[3 * a + 1],
-                                     dz = s.X[3 * j + 2] - s.qxl[3 * a + 2];
-                        v = fix_of_double(exp(-(dx * dx + dy * dy + dz * dz) * c.P.inv2l2));
+                        // the query's FP64 local coordinates, formed as query_local forms them
+                        double r2 = 0.0;
+                        for (int k = 0; k < 3; ++k) {
+                            const double cen = c.b.centre ? c.b.centre[3 * (int64_t)I + k] : 0.0;
+                            const double d = s.X[3 * j + k] - ((double)s.qw[3 * a + k] - cen);
+                            r2 += d * d;
+                        }
+                        v = fix_of_double(exp(-r2 * c.P.inv2l2));
                     }
                 } else if (i >= N || j >= N) v = (i == j) ? (1ll << kFixBits) : 0;
                 else if (j > i) v = 0;
@@ -1049,19 +1058,7 @@ __device__ bool fit_instance(const SolveCtx& c, const Shared& s, int N, int64_t 
         for (int e = lane; e < 64; e += 32) {
             const int i = 8 * it + (e >> 3), j = 8 * jt + (e & 7);
             double v;
-            if (i >= Np) {  // appended query row a = i - Np
-                const int a = i - Np;
-                if (j >= Np || a >= nq) {
-                    v = (i == j) ? 1.0 : 0.0;
-                } else if (j >= N || isnan(s.qxl[3 * a])) {
-                    v = 0.0;
-                } else {
-                    const double dx = s.X[3 * j] - s.qxl[3 * a], dy = s.X[3 * j + 1] - s.qxl[3 * a + 1],
-                                 dz = s.X[3 * j + 2] - s.qxl[3 * a + 2];
-                    const double y = -(dx * dx + dy * dy + dz * dz) * c.P.inv2l2;
-                    v = c.P.precision == VGP_MIXED ? exp_neg(y, s.T256) : exp(y);
-                }
-            } else if (i >= N || j >= N) v = (i == j) ? 1.0 : 0.0;
+            if (i >= N || j >= N) v = (i == j) ? 1.0 : 0.0;  // (no appended rows here)
             else if (j > i) v = 0.0;
             else if (j == i) v = 1.0 + c.P.s2;
             else v = kval_pair(c.P, s, lattice, i, j);
