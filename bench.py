@@ -190,7 +190,7 @@ def run_ours(args):
     S = torch.from_numpy(S_h).to(dev)
     Q = torch.from_numpy(Q_h).to(dev)
     nq = Q.shape[0]
-    # emulate_fp64=1: the trailing Cholesky updates of the N > 224 instances run as exact
+    # emulate_fp64=1: the trailing Cholesky updates of the N > 64 instances run as exact
     # integer-slice products on the bf16 tensor cores, recombined to FP64 accuracy; profile off
     m = Map(precision="mixed", emulate_fp64=1)
     out = {"d": torch.empty(nq, dtype=torch.float64, device=dev),
@@ -276,10 +276,11 @@ def run_ours(args):
             "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32+f64+bf16", "data": "synthetic (seeded city scene)",
             "config": {"workload": WORKLOAD, "n_surface": int(S.shape[0]), "n_queries": int(nq),
-                       "precision": ("mixed: FP32 kernel values, mean and gradient; FP64 K entries, panels, "
-                                     "diagonal blocks, solves and reverting; the Cholesky trailing updates of "
-                                     "N > 224 instances as exact bf16 slice products on the tensor cores "
-                                     "(FP32 accumulation, integer recombination, FP64 application)"),
+                       "precision": ("mixed: FP32 kernel values, mean and gradient; FP64 panels, diagonal "
+                                     "blocks, solves and reverting; for N > 64 instances float-pair K entries "
+                                     "(FP32 pipe) and the Cholesky trailing updates as exact bf16 slice "
+                                     "products on the tensor cores (FP32 accumulation, integer recombination "
+                                     "into a 2^-61 fixed-point trailing matrix); FP64 K entries below"),
                        "variance": False, "l2": "inputs+outputs (~460 MB) larger than L2",
                        "instrumentation": "none in the timed steps (kernel times from a separate profile pass)",
                        "parallelism": f"replicas x{ws}" if ws > 1 else "single GPU",
@@ -322,7 +323,7 @@ def instrumented_pass(Map, S, Q, out, tuned, steps):
         acc["bin_ms"] += sb["t_bin_ms"]
         acc["points"] += sb["n_points"]
         acc["solve_ms"] += sq["t_solve_ms"]
-        acc["emu_ms"] += sq["t_bucket_ms"][0]
+        acc["emu_ms"] += sum(sq["t_bucket_ms"][:3])  # the emulated launches: N > 64
         acc["gather_ms"] += sq["t_gather_ms"]
         acc["cand"] += sq["n_candidates"]
         acc["train"] += sq["n_train"]
@@ -339,18 +340,18 @@ def instrumented_pass(Map, S, Q, out, tuned, steps):
 
 
 def solve_roofline(prof, fp64_peak, bf16_peak):
-    """The dominant kernel: the GP solve launches (k_solve_emu for N > 224, k_solve below).
+    """The dominant kernel: the GP solve launches (k_solve_emu for N > 64, k_solve below).
     FP64-equivalent Cholesky work over the solve time against the FP64 tensor peak, and the
     bf16 slice products actually issued by k_solve_emu over its own time against the bf16
     peak."""
     N = prof["N"]
     flop = prof["sum_n3"] / 3.0 + 2.0 * prof["sum_n2"]
     achieved = flop / (prof["solve_ms"] / 1e3) / 1e12
-    big = N[N > 224].astype(np.int64)
+    big = N[N > 64].astype(np.int64)
     bf16_flop = float(_emu_mma_table()[big].sum())
     bf16_achieved = bf16_flop / (prof["emu_ms"] / 1e3) / 1e12 if prof["emu_ms"] > 0 else None
-    return {"kernel": ("k_solve_emu (N > 224: FP64-accurate Cholesky, trailing updates as bf16 slice products) + "
-                       "k_solve (N <= 224: FP64 tile Cholesky on mma.sync f64); alpha, fused eval"),
+    return {"kernel": ("k_solve_emu (N > 64: FP64-accurate Cholesky, trailing updates as bf16 slice products) + "
+                       "k_solve (N <= 64: FP64 tile Cholesky on mma.sync f64); alpha, fused eval"),
             "bound": "tensor", "dtype": "fp64 (FP64-equivalent work)", "achieved": achieved, "peak": fp64_peak,
             "unit": "TFLOP/s", "frac": achieved / fp64_peak,
             "frac_note": ("achieved counts the FP64 Cholesky flops the method needs; the emulated updates run "

@@ -109,15 +109,19 @@ enum {
  *                    report their time in vgp_stats.t_solve_ms (adds one stream sync per call).
  *   normal_steps     K in [0, 16] (default 3): with a sensor origin, vgp_build_frame also tests
  *                    the voxels round(s + k n), k = +-1..+-K, along each surface voxel's normal.
- *   emulate_fp64     1: instances with N > 224 (A in global memory) are factorised in blocks of
+ *   emulate_fp64     1: instances with N > 64 (A in global memory) are factorised in blocks of
  *                    32 columns whose trailing updates run on the bf16 tensor cores to FP64
  *                    accuracy: each row of the block is cut into seven balanced base-256 digit
  *                    slices (55 bits under a power-of-two row scale), the slice products
  *                    accumulate exactly in FP32, and each update is packed exactly into an
- *                    integer and applied as an FP64 value (error of the order of the FP64
- *                    rounding of the update).  Same results up to rounding; 0 keeps every
+ *                    integer and added to the not yet factorised matrix, held as 64-bit
+ *                    integers round(v 2^61) (error of the order of the FP64 rounding of the
+ *                    update).  In mixed precision their K entries are float-pair values (error
+ *                    below 2^-45 k (1 + r^2 / 2l^2)), and off-lattice distance instances take
+ *                    the latent variance from the Schur complement of the matrix with up to
+ *                    1024 query rows appended.  Same results up to rounding; 0 keeps every
  *                    update on the FP64 tensor path.  Uses a per-CTA workspace of about
- *                    0.5 KB per matrix row.
+ *                    0.5 KB per matrix row and 8 bytes per lower-triangle entry.
  *   launch           VGP_LAUNCH_BATCHED (default): all GP instances of a call run in a few
  *                    persistent launches, one per size bucket, largest first.
  *                    VGP_LAUNCH_PER_INSTANCE: one kernel launch per instance, in instance
