@@ -100,7 +100,8 @@ struct Shared {
     unsigned char* stage;  // emulated kernel: slice operands of the tensor-core updates (aliases
                            // X .. alf_lo, which the factorisation does not use; reloaded after it)
     float* qw;             // emulated kernel: [kBorderQ][3] world coordinates of appended queries (FP32;
-                           // NaN: not finite)
+                           // NaN: not finite); lattice instances: [0] the lattice code's bits, [1] NaN
+                           // when not finite
     float* Xw;             // emulated kernel: [npad][3] world coordinates of the points (FP32, exact)
     float2* Tff;           // emulated kernel: 2^(j/256), j = 0..255, as float pairs
 };
@@ -1005,10 +1006,15 @@ __device__ bool fit_instance(const SolveCtx& c, const Shared& s, int N, int64_t 
             const int64_t p = q0 + a;
             const int64_t qid = c.b.qidx ? c.b.qidx[p] : p;
             double xl[3];
-            query_local(c, I, p, qid, xl);
+            int qi = 0;
+            query_local(c, I, p, qid, xl, &qi);
             const bool fin = isfinite(xl[0]) && isfinite(xl[1]) && isfinite(xl[2]);
-            for (int k = 0; k < 3; ++k) {
-                s.qw[3 * a + k] = fin ? (float)(xl[k] + (c.b.centre ? c.b.centre[3 * (int64_t)I + k] : 0.0)) : NAN;
+            if (lattice) {  // the lattice code (its bits: a tiny float, never NaN); [1]: finite flag
+                s.qw[3 * a] = __int_as_float(qi);
+                s.qw[3 * a + 1] = fin ? 0.f : NAN;
+            } else {
+                for (int k = 0; k < 3; ++k)
+                    s.qw[3 * a + k] = fin ? (float)(xl[k] + (c.b.centre ? c.b.centre[3 * (int64_t)I + k] : 0.0)) : NAN;
             }
         }
     if (tid == 0) s_fail = 0;
@@ -1030,8 +1036,10 @@ __device__ bool fit_instance(const SolveCtx& c, const Shared& s, int N, int64_t 
                     const int a = i - Np;
                     if (j >= Np || a >= nq) {
                         v = (i == j) ? (1ll << kFixBits) : 0;
-                    } else if (j >= N || isnan(s.qw[3 * a])) {
+                    } else if (j >= N || isnan(s.qw[3 * a + 1])) {
                         v = 0;
+                    } else if (lattice) {
+                        v = fix_of_double(c.P.lat_tab[lat_m(s.xi[j], __float_as_int(s.qw[3 * a]))]);
                     } else if (c.P.precision == VGP_MIXED) {
                         v = kfix_ff(s.qw + 3 * a, s.Xw + 3 * j, c.P.inv2l2_hi, c.P.inv2l2_lo, s.Tff);
                     } else {
@@ -1537,7 +1545,7 @@ __device__ __forceinline__ void solve_body(const SolveCtx& c) {
         // matrix in chunks of at most qmax, one factorisation per chunk.  Every chunk repeats
         // the same arithmetic on the instance's own rows, and a query's row involves only
         // itself, so every result is independent of the chunking and of the other queries.
-        const bool border = kEmu && c.b.want_var && !lattice && c.qmax > 0;
+        const bool border = kEmu && c.b.want_var && c.qmax > 0;
         const int Ntr = ((N + 31) & ~31) >> 3;  // first appended row tile
         for (int64_t cq0 = q0;;) {
             const int64_t cq1 = border ? min(q1, cq0 + (int64_t)c.qmax) : q1;
@@ -1911,7 +1919,7 @@ constexpr int64_t kEmuBytesPerRow = 7 * 8 * kEB * 2 + 8 + 64;
 bool chunk_args(const SolveBatch& b, const DevParams& P, bool bw, ChunkPlanArgs& a) {
     a = ChunkPlanArgs{};
     a.heavy = !bw && (b.want_var || b.nprop > 0);
-    a.cap[0] = (!bw && P.emulate && b.want_var && b.nprop == 0 && !b.Xi) ? kBorderQ : 0;
+    a.cap[0] = (!bw && P.emulate && b.want_var && b.nprop == 0) ? kBorderQ : 0;
     a.cap[1] = a.cap[2] = a.cap[0];  // the emulated buckets
     return a.heavy != 0;
 }
@@ -1921,7 +1929,7 @@ bool chunk_args(const SolveBatch& b, const DevParams& P, bool bw, ChunkPlanArgs&
 // workspaces hold npad + kBorderQ rows.  Otherwise npad rows.
 void emu_rows_for(bool emu, const SolveBatch& b, int& npad, int& qmax, int& nrow) {
     qmax = 0;
-    if (emu && b.want_var && b.nprop == 0 && !b.Xi) {
+    if (emu && b.want_var && b.nprop == 0) {
         npad = (npad + 31) & ~31;
         qmax = kBorderQ;
     }

@@ -724,3 +724,9 @@ def test_emulated_trailing_updates(vg, orc, precision):
     assert np.array_equal(fr[0]["keys"], fr[1]["keys"]) and np.array_equal(fr[0]["status"], fr[1]["status"])
     ok = fr[0]["status"] == 0
     assert np.abs(fr[0]["d"][ok] - fr[1]["d"][ok]).max() <= (1e-7 if precision == "fp64" else 1e-5)
+    # the testing voxels' variance: per-voxel solve (plain) against the bordered factorisation
+    # of the lattice instances (emulated)
+    fin = ok & np.isfinite(fr[0]["v"]) & (fr[0]["v"] > 0)
+    rel = np.abs(fr[1]["v"][fin] - fr[0]["v"][fin]) / fr[0]["v"][fin]
+    assert fin.sum() > 1000 and np.median(rel) <= 1e-6
+    assert rel.max() <= (1e-5 if precision == "fp64" else 1e-2)
