@@ -190,7 +190,7 @@ def run_ours(args):
     S = torch.from_numpy(S_h).to(dev)
     Q = torch.from_numpy(Q_h).to(dev)
     nq = Q.shape[0]
-    # emulate_fp64=1: the trailing Cholesky updates of the N > 64 instances run as exact
+    # emulate_fp64=1: the trailing Cholesky updates of the N > 32 instances run as exact
     # integer-slice products on the bf16 tensor cores, recombined to FP64 accuracy; profile off
     m = Map(precision="mixed", emulate_fp64=1)
     out = {"d": torch.empty(nq, dtype=torch.float64, device=dev),
@@ -277,7 +277,7 @@ def run_ours(args):
             "vs_baseline": None, "dtype": "f32+f64+bf16", "data": "synthetic (seeded city scene)",
             "config": {"workload": WORKLOAD, "n_surface": int(S.shape[0]), "n_queries": int(nq),
                        "precision": ("mixed: FP32 kernel values, mean and gradient; FP64 panels, diagonal "
-                                     "blocks, solves and reverting; for N > 64 instances float-pair K entries "
+                                     "blocks, solves and reverting; for N > 32 instances float-pair K entries "
                                      "(FP32 pipe) and the Cholesky trailing updates as exact bf16 slice "
                                      "products on the tensor cores (FP32 accumulation, integer recombination "
                                      "into a 2^-61 fixed-point trailing matrix); FP64 K entries below"),
@@ -323,7 +323,7 @@ def instrumented_pass(Map, S, Q, out, tuned, steps):
         acc["bin_ms"] += sb["t_bin_ms"]
         acc["points"] += sb["n_points"]
         acc["solve_ms"] += sq["t_solve_ms"]
-        acc["emu_ms"] += sum(sq["t_bucket_ms"][:3])  # the emulated launches: N > 64
+        acc["emu_ms"] += sum(sq["t_bucket_ms"][:4])  # the emulated launches: N > 32
         acc["gather_ms"] += sq["t_gather_ms"]
         acc["cand"] += sq["n_candidates"]
         acc["train"] += sq["n_train"]
@@ -340,18 +340,18 @@ def instrumented_pass(Map, S, Q, out, tuned, steps):
 
 
 def solve_roofline(prof, fp64_peak, bf16_peak):
-    """The dominant kernel: the GP solve launches (k_solve_emu for N > 64, k_solve below).
+    """The dominant kernel: the GP solve launches (k_solve_emu for N > 32, k_solve below).
     FP64-equivalent Cholesky work over the solve time against the FP64 tensor peak, and the
     bf16 slice products actually issued by k_solve_emu over its own time against the bf16
     peak."""
     N = prof["N"]
     flop = prof["sum_n3"] / 3.0 + 2.0 * prof["sum_n2"]
     achieved = flop / (prof["solve_ms"] / 1e3) / 1e12
-    big = N[N > 64].astype(np.int64)
+    big = N[N > 32].astype(np.int64)
     bf16_flop = float(_emu_mma_table()[big].sum())
     bf16_achieved = bf16_flop / (prof["emu_ms"] / 1e3) / 1e12 if prof["emu_ms"] > 0 else None
-    return {"kernel": ("k_solve_emu (N > 64: FP64-accurate Cholesky, trailing updates as bf16 slice products) + "
-                       "k_solve (N <= 64: FP64 tile Cholesky on mma.sync f64); alpha, fused eval"),
+    return {"kernel": ("k_solve_emu (N > 32: FP64-accurate Cholesky, trailing updates as bf16 slice products) + "
+                       "k_solve (N <= 32: FP64 tile Cholesky on mma.sync f64); alpha, fused eval"),
             "bound": "tensor", "dtype": "fp64 (FP64-equivalent work)", "achieved": achieved, "peak": fp64_peak,
             "unit": "TFLOP/s", "frac": achieved / fp64_peak,
             "frac_note": ("achieved counts the FP64 Cholesky flops the method needs; the emulated updates run "
@@ -497,7 +497,8 @@ def sphere_plane_lines(args):
     pt = torch.from_numpy(pts).cuda()
     qt = torch.from_numpy(q).cuda()
     res = {}
-    for name, kw in (("fp64", dict(precision="fp64")), ("mixed", dict(precision="mixed")),
+    # mixed: with the emulated updates (instances above 32 points), as the headline map
+    for name, kw in (("fp64", dict(precision="fp64")), ("mixed", dict(precision="mixed", emulate_fp64=1)),
                      ("per_instance_fp64", dict(precision="fp64", launch="per_instance"))):
         m = Map(**kw)
         nvox = {}
@@ -555,7 +556,7 @@ def room_lines(args):
         return a.elapsed_time(b) / 1e3, nvox
 
     for prec in ("mixed", "fp64"):
-        # mixed: with the emulated updates (instances above 64 points), as the headline map
+        # mixed: with the emulated updates (instances above 32 points), as the headline map
         mr = Map(precision=prec, max_pts_leaf=512, emulate_fp64=int(prec == "mixed"))
         mr.fuse(mr.build_frame(frames[0]))
         sec, nvox = run_frames(mr, False)
@@ -588,7 +589,7 @@ def room_lines(args):
     sec, nvox = run_frames(mr, True)
     out["lgpdf_room_raycast"] = {"voxels_per_s": nvox / sec, "frames": len(frames),
                                  "ms_per_frame": 1e3 * sec / len(frames),
-                                 "testing_voxels_per_frame": nvox / len(frames), "precision": "mixed, emulated updates above 64 points"}
+                                 "testing_voxels_per_frame": nvox / len(frames), "precision": "mixed, emulated updates above 32 points"}
     mr.close()
     # the fusion kernels alone (profile mode), dilated testing sets of all frames
     mf = Map(precision="mixed", max_pts_leaf=512, profile=1)
@@ -622,7 +623,7 @@ def room_lines(args):
     out["room_mapping_step"] = {"ms_per_frame": 1e3 * sec / len(frames), "frames": len(frames),
                                 "training_points": int(mp.surface_points().shape[0]),
                                 "mesh_ms": a.elapsed_time(b), "mesh_triangles": int(mesh["triangles"][0].shape[0]),
-                                "zero_crossings": int(mesh["crossings"][0].shape[0]), "precision": "mixed, emulated updates above 64 points"}
+                                "zero_crossings": int(mesh["crossings"][0].shape[0]), "precision": "mixed, emulated updates above 32 points"}
     surf = mp.surface_points()
     mp.close()
     # the same mapping step with three colour channels per point (Eq. 6 properties, fused)
@@ -638,7 +639,7 @@ def room_lines(args):
     b.record()
     torch.cuda.synchronize()
     out["room_mapping_step_rgb"] = {"ms_per_frame": a.elapsed_time(b) / len(frames), "frames": len(frames),
-                                    "n_props": 3, "precision": "mixed, emulated updates above 64 points"}
+                                    "n_props": 3, "precision": "mixed, emulated updates above 32 points"}
     mc.close()
     # the same mapping step with every GP solve replayed as a CUDA graph (VGP_LAUNCH_GRAPH)
     mg = Map(precision="mixed", max_pts_leaf=512, launch="graph", emulate_fp64=1)
@@ -655,7 +656,7 @@ def room_lines(args):
     out["room_mapping_step_graph"] = {"ms_per_frame": a.elapsed_time(b) / len(frames), "frames": len(frames),
                                       "graph_replays": int(gst["graph_replays"]),
                                       "graph_instantiations": int(gst["graph_instantiations"]),
-                                      "precision": "mixed, emulated updates above 64 points"}
+                                      "precision": "mixed, emulated updates above 32 points"}
     mg.close()
     # differentiation: loss = sum softplus(0.5 m - d) over 256 x 64 waypoints on the room map
     # (the G-GPDF training set the mapping step kept), forward + backward through autograd

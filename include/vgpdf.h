@@ -109,7 +109,7 @@ enum {
  *                    report their time in vgp_stats.t_solve_ms (adds one stream sync per call).
  *   normal_steps     K in [0, 16] (default 3): with a sensor origin, vgp_build_frame also tests
  *                    the voxels round(s + k n), k = +-1..+-K, along each surface voxel's normal.
- *   emulate_fp64     1: instances with N > 64 (A in global memory) are factorised in blocks of
+ *   emulate_fp64     1: instances with N > 32 (A in global memory) are factorised in blocks of
  *                    32 columns whose trailing updates run on the bf16 tensor cores to FP64
  *                    accuracy: each row of the block is cut into seven balanced base-256 digit
  *                    slices (55 bits under a power-of-two row scale), the slice products

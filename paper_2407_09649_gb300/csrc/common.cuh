@@ -38,7 +38,7 @@ struct DevParams {
     float inv2l2_hi, inv2l2_lo;  // 1 / (2 l^2) as a float pair (hi + lo), for the float-pair kernel values
     float vs_f;         // voxel size in FP32
     int cap_leaf, cap_group, search_r, fusion, precision, n_props;
-    int emulate;        // Cholesky trailing updates of N > 64 instances on the bf16 tensor cores
+    int emulate;        // Cholesky trailing updates of N > 32 instances on the bf16 tensor cores
     double s2p;         // sigma_prop^2 (surface-property GP, Eq. 6)
     const double* exp_tab;   // 2^(j/256), j = 0..255 (FP64), for exp_neg
     const double* lat_tab;   // exp(-m vs^2 / (2 l^2)), m = 0..kLatticeTable-1 (FP64)

@@ -71,7 +71,7 @@ struct BackwardBatch {
 // Launch shape of the five size buckets of solve_batch (N > 224 with A in global memory,
 // then N <= 224, 128, 64, 32 with A in shared memory): threads per CTA and the cap on
 // resident CTAs per SM (0: as many as fit).  Chosen by vgp_autotune or the defaults.  With
-// emulate_fp64 the buckets above 64 points run the emulated kernel, whose shape is fixed.
+// emulate_fp64 the buckets above 32 points run the emulated kernel, whose shape is fixed.
 struct SolveConfig {
     int threads[5] = {512, 512, 256, 128, 64};
     int per_sm[5] = {1, 0, 0, 0, 0};

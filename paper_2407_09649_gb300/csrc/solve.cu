@@ -1602,7 +1602,7 @@ __device__ __forceinline__ void solve_body(const SolveCtx& c) {
 }
 
 // kProps: surface-property mode (Eq. 6); the emulated kernels run the trailing updates of
-// N > 64 instances on the bf16 tensor cores (256 threads, two CTAs per SM).  Separate
+// N > 32 instances on the bf16 tensor cores (256 threads, two CTAs per SM).  Separate
 // kernels, so that the plain distance kernel keeps its register budget.
 template <bool kProps>
 __global__ void k_solve(SolveCtx c) {
@@ -1920,7 +1920,7 @@ bool chunk_args(const SolveBatch& b, const DevParams& P, bool bw, ChunkPlanArgs&
     a = ChunkPlanArgs{};
     a.heavy = !bw && (b.want_var || b.nprop > 0);
     a.cap[0] = (!bw && P.emulate && b.want_var && b.nprop == 0) ? kBorderQ : 0;
-    a.cap[1] = a.cap[2] = a.cap[0];  // the emulated buckets
+    a.cap[1] = a.cap[2] = a.cap[3] = a.cap[0];  // the emulated buckets
     return a.heavy != 0;
 }
 
@@ -2027,7 +2027,7 @@ int solve_batch_graph(const SolveBatch& b, const DevParams& P, int* err_dev, cud
         Shape& s = sh[i];
         s.live = maxn >= lo[i];
         s.npad = std::max((std::min(hi[i], maxn) + 7) & ~7, 8);
-        s.smem_a = i > (P.emulate ? 2 : 0);  // emulated: the buckets above 64 points
+        s.smem_a = i > (P.emulate ? 3 : 0);  // emulated: the buckets above 32 points
         s.emu = !s.smem_a && P.emulate;
         emu_rows_for(s.emu, b, s.npad, s.qmax, s.nrow);
         s.stage = s.smem_a ? 1 : (s.emu ? 0 : cfg->stage_panel);
@@ -2231,11 +2231,11 @@ int solve_batch(const SolveBatch& b, const DevParams& P, int* err_dev, cudaStrea
     struct Bucket {
         int lo, hi, smem_a, threads;
     };
-    // with the emulated updates every bucket above 64 points runs the emulated kernel (A in
-    // global memory): two 32-column blocks or fewer leave it little to gain below
+    // with the emulated updates every bucket above 32 points runs the emulated kernel (A in
+    // global memory): a single 32-column block leaves it nothing to gain below
     const int emu_mid = P.emulate && !bw ? 0 : 1;
     const Bucket buckets[] = {{225, 1024, 0, cfg->threads[0]}, {129, 224, emu_mid, cfg->threads[1]},
-                              {65, 128, emu_mid, cfg->threads[2]}, {33, 64, 1, cfg->threads[3]},
+                              {65, 128, emu_mid, cfg->threads[2]}, {33, 64, emu_mid, cfg->threads[3]},
                               {0, 32, 1, cfg->threads[4]}};
     int dev = 0, n_sm = 0;
     cudaGetDevice(&dev);
