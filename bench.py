@@ -37,11 +37,11 @@ UNIT = "queries/s"
 WORKLOAD = "city G-GPDF: 2M surface pts, 10M queries (70% free space, 30% <=0.5 m from surface), 27-leaf cap 1024"
 
 # DRAM bytes (read + write) of the N > 224 solve launch (k_solve_emu) of one full 10M-query
-# step: 710.0 GB from an ncu capture of the current kernel on the 100k-query city case, scaled
+# step: 708.2 GB from an ncu capture of the current kernel on the 100k-query city case, scaled
 # by the ratio of the two launches' algorithmic work (sum of N^3/3 + 2 N^2: 2.854e12 against
 # 1.851e12 flop, x1.542; an earlier kernel's small and full-size captures had that ratio).
 # None when the kernel has changed since.
-K_SOLVE_TRAFFIC = 1.0948e12
+K_SOLVE_TRAFFIC = 1.0921e12
 K_SOLVE_TRAFFIC_SOURCE = ("ncu dram__bytes_read.sum + dram__bytes_write.sum of the N > 224 launch (k_solve_emu) on "
                           "the 100k-query city case, scaled to the full step by its algorithmic work; "
                           "smaller buckets not included")
