@@ -332,7 +332,8 @@ def test_chunked_queries_bit_identical(vg, orc, precision):
     """Few instances with many queries (3000 each, N from 20 to 400): the launch splits each
     instance's queries into chunks that fit the instance again, so that the queries spread over
     the GPU.  Every query's distance, gradient, variance and status are bit-identical to the
-    same query answered with 40 queries per instance (not split), and agree with the oracle."""
+    same query answered with 40 queries per instance (not split) and to graph launches (which
+    plan the chunks on the device), and agree with the oracle."""
     rng = np.random.default_rng(41)
     sizes = [20, 60, 100, 180, 400]
     nq = 3000
@@ -351,6 +352,11 @@ def test_chunked_queries_bit_identical(vg, orc, precision):
     sub = {k: v.cpu().numpy() for k, v in m.gp_batch(io, X, np.arange(len(sizes) + 1) * 40, Q[pick], var=True).items()}
     for k in ("d", "grad", "var", "status"):
         assert np.array_equal(np.ascontiguousarray(full[k][pick]).view(np.uint8), np.ascontiguousarray(sub[k]).view(np.uint8)), k
+    # graph launches plan the chunks on the device: the same bits
+    mg = vg.Map(precision=precision, emulate_fp64=1, launch="graph")
+    gr = {k: v.cpu().numpy() for k, v in mg.gp_batch(io, X, qo, Q, var=True).items()}
+    for k in ("d", "grad", "var", "status"):
+        assert np.array_equal(np.ascontiguousarray(gr[k]).view(np.uint8), np.ascontiguousarray(full[k]).view(np.uint8)), k
     ref = orc.gp_batch(io, X.astype(np.float64), np.arange(len(sizes) + 1) * 40, Q[pick].astype(np.float64), orc.params())
     assert np.array_equal(sub["status"], ref.status)
     ok = (ref.status == 0) & (ref.d > 2e-3) & (ref.d < 9.0)
