@@ -264,8 +264,11 @@ def run_ours(args):
     cpu = None
     err = None
     if rank == 0 and not args.no_cpu:
+        # the CPU-baseline leg: the oracle's G-GPDF sample, the error against it, and its frame
         cpu = cpu_baseline(S_h, Q_h, args.cpu_sample, args.cpu_sample_1t)
         err = error_vs_oracle(S_h, Q_h, m, args.cpu_sample)
+        if "lgpdf_sphere_plane" in extra:
+            extra["lgpdf_sphere_plane"]["oracle"] = oracle_frame_baseline()
 
     if rank == 0:
         pk = _peaks()
@@ -486,10 +489,9 @@ def city_lines(S, Q, args):
 def sphere_plane_lines(args):
     """The plain FP64 single frame (20k points on a sphere of radius 2 m and the plane z = -1,
     cap 64 per leaf): L-GPDF build + fuse in testing voxels per second, FP64 and mixed, the
-    per-instance FP64 form, the 10k queries, and the FP64 oracle on the same frame (one thread
-    and all host cores)."""
+    per-instance FP64 form and the 10k queries (the FP64 oracle on the same frame is timed by
+    the CPU-baseline leg, oracle_frame_baseline)."""
     import torch
-    import oracle
     from paper_2407_09649_gb300 import scenes
     from paper_2407_09649_gb300.api import Map
     pts = scenes.sphere_plane_frame(0)
@@ -514,16 +516,6 @@ def sphere_plane_lines(args):
         res[name] = {"voxels_per_s": nvox["n"] / t, "ms_per_frame": 1e3 * t, "testing_voxels": nvox["n"],
                      "queries_per_s": len(q) / tq, "leaf_gps": m.stats()["n_instances"]}
         m.close()
-    oracle.build()
-    cores = os.cpu_count() or 1
-    orc = {}
-    for th in (1, cores):
-        oracle.set_threads(th)
-        t0 = time.perf_counter()
-        f = oracle.frame(pts, oracle.params())
-        dt = time.perf_counter() - t0
-        orc[f"threads_{oracle.get_threads()}"] = {"voxels_per_s": len(f.test_key) / dt, "seconds": dt}
-    res["oracle"] = orc
     res["workload"] = ("sphere r=2 m + plane z=-1, 20k points, sigma 0.01 m noise, voxel 0.1 m, cap 64 per leaf; "
                        "testing voxels = all voxels of occupied leaves and their 26 neighbours; 10k uniform queries")
     return {"lgpdf_sphere_plane": res}
@@ -720,6 +712,24 @@ def sweep_lines(args):
                                                 "batched_mixed_same_queries_per_s": sQ.shape[0] / tb,
                                                 "speedup_batched_mixed": tp / tb}
     return out
+
+
+def oracle_frame_baseline():
+    """CPU-baseline leg: the FP64 oracle's L-GPDF frame of the sphere + plane scene (testing
+    voxels per second, one thread and all host cores)."""
+    import oracle
+    from paper_2407_09649_gb300 import scenes
+    pts = scenes.sphere_plane_frame(0)
+    oracle.build()
+    cores = os.cpu_count() or 1
+    orc = {}
+    for th in (1, cores):
+        oracle.set_threads(th)
+        t0 = time.perf_counter()
+        f = oracle.frame(pts, oracle.params())
+        dt = time.perf_counter() - t0
+        orc[f"threads_{oracle.get_threads()}"] = {"voxels_per_s": len(f.test_key) / dt, "seconds": dt}
+    return orc
 
 
 def cpu_baseline(S_h, Q_h, n_sample, n_sample_1t):
