@@ -339,3 +339,44 @@ def test_float_pair_kernel_value_model():
         assert err <= 2.0 ** (FIX - 46)
         worst = max(worst, float(err / (exact * (1 + y) + 1)))
     assert worst > 0
+
+
+# ---- bordered variance (Eq. 2 as a Schur complement) ------------------------------------
+
+def _partial_cholesky(M, n):
+    """Right-looking Cholesky of the first n columns of the symmetric matrix M (lower part);
+    the trailing block is left as the Schur complement."""
+    M = M.copy()
+    for k in range(n):
+        M[k, k] = np.sqrt(M[k, k])
+        M[k + 1:, k] /= M[k, k]
+        M[k + 1:, k + 1:] -= np.outer(M[k + 1:, k], M[k + 1:, k])
+    return M
+
+
+def test_bordered_factorisation_gives_the_latent_variance():
+    """Appending the queries' kernel vectors to K + sigma^2 I as rows (1 on their diagonal) and
+    factorising only the instance's columns leaves u = 1 - k^T (K + sigma^2 I)^-1 k on the
+    appended diagonal (the latent variance, Eq. 2 read as the posterior); the rows below become
+    (L^-1 k)^T; a query's value does not depend on the other appended rows; and the leading
+    block is the factor of K + sigma^2 I alone."""
+    rng = np.random.default_rng(17)
+    N, nq, l2, s2 = 40, 9, 0.09, 1e-4
+    X = rng.uniform(-0.5, 0.5, (N, 3))
+    Qp = np.vstack([rng.uniform(-0.8, 0.8, (nq - 1, 3)), [[30.0, 30.0, 30.0]]])  # last: far away
+    kern = lambda a, b: np.exp(-((a[:, None, :] - b[None, :, :]) ** 2).sum(-1) / (2 * l2))
+    A = kern(X, X) + s2 * np.eye(N)
+    Ks = kern(Qp, X)
+    M = np.block([[A, Ks.T], [Ks, np.eye(nq)]])
+    F = _partial_cholesky(M, N)
+    u_border = np.diag(F[N:, N:])
+    u_direct = 1.0 - np.einsum("ij,ij->i", Ks, np.linalg.solve(A, Ks.T).T)
+    np.testing.assert_allclose(u_border, u_direct, rtol=1e-9, atol=1e-12)
+    assert abs(u_border[-1] - 1.0) < 1e-12  # no support: the prior variance
+    L = np.linalg.cholesky(A)
+    np.testing.assert_allclose(np.tril(F[:N, :N]), L, rtol=1e-12, atol=1e-12)
+    np.testing.assert_allclose(F[N:, :N], np.linalg.solve(L, Ks.T).T, rtol=1e-9, atol=1e-12)
+    # one query alone gives the same value
+    for a in (0, 4):
+        Ma = np.block([[A, Ks[a:a + 1].T], [Ks[a:a + 1], np.ones((1, 1))]])
+        assert abs(_partial_cholesky(Ma, N)[N, N] - u_border[a]) <= 1e-12
