@@ -137,7 +137,7 @@ __host__ __device__ __forceinline__ size_t emu_point_bytes(int npad, int nprop, 
 }
 // the points (also as FP32 world coordinates) and the appended queries (both forms)
 __host__ __device__ __forceinline__ size_t emu_alias_bytes(int npad, int nprop, bool lattice) {
-    const size_t b = emu_point_bytes(npad, nprop, lattice) + (size_t)3 * npad * sizeof(float) +
+    const size_t b = emu_point_bytes(npad, nprop, lattice) + (lattice ? 0 : (size_t)3 * npad * sizeof(float)) +
                      (size_t)kBorderQ * 3 * sizeof(float);
     return b > (size_t)kStageBytes ? b : (size_t)kStageBytes;
 }
@@ -168,8 +168,10 @@ __device__ Shared carve_emu(double* sm, int npad, double* ws_a, int nprop, bool 
     s.pa[1] = reinterpret_cast<double*>(s.alf);
     s.pa[2] = nprop > 2 ? extra : nullptr;
     s.pa[3] = nprop > 3 ? extra + npad : nullptr;
-    s.Xw = reinterpret_cast<float*>(s.stage + emu_point_bytes(npad, nprop, lattice));
-    s.qw = s.Xw + 3 * npad;
+    // world coordinates of the points off the lattice only (lattice values come from tables)
+    float* after = reinterpret_cast<float*>(s.stage + emu_point_bytes(npad, nprop, lattice));
+    s.Xw = lattice ? nullptr : after;
+    s.qw = lattice ? after : after + 3 * npad;
     s.Tff = reinterpret_cast<float2*>(s.Wsc + 8 * 64);
     return s;
 }
@@ -994,7 +996,7 @@ __device__ bool fit_instance(const SolveCtx& c, const Shared& s, int N, int64_t 
         s.Xf[e] = (float)v;
         // the point's own FP32 world coordinate, recovered exactly (the FP64 local value
         // differs from it by the centre up to a rounding far below half an FP32 ulp)
-        if (kEmu) s.Xw[e] = (float)(v + (c.b.centre ? c.b.centre[3 * (int64_t)I + e % 3] : 0.0));
+        if (kEmu && !lattice) s.Xw[e] = (float)(v + (c.b.centre ? c.b.centre[3 * (int64_t)I + e % 3] : 0.0));
     }
     if (lattice)
         for (int e = tid; e < N; e += nt) {
@@ -1519,7 +1521,11 @@ __device__ __forceinline__ void solve_body(const SolveCtx& c) {
         const int64_t q0 = qch > 0 ? min(qb, qa + (int64_t)ci * qch) : qa;
         const int64_t q1 = qch > 0 ? min(qb, q0 + qch) : qb;
         if (kProps) {
-            const bool ok = N > 0 && fit_instance<kProps, kEmu>(c, s, N, base, &tc, 0, q0, I);
+            // the variance by bordering too (see below) when the work item's queries fit the
+            // appended rows: the property GP's own matrix, noise sigma_c^2
+            const bool pb = kEmu && c.qmax > 0 && q1 - q0 <= c.qmax;
+            const bool ok = N > 0 && fit_instance<kProps, kEmu>(c, s, N, base, &tc, pb ? (int)(q1 - q0) : 0, q0, I);
+            const int Ntr = ((N + 31) & ~31) >> 3;
             // property mode: means and variance (Eq. 6, variance read as for Eq. 2)
             const int np = c.b.nprop;
             for (int64_t p = q0 + tid; p < q1; p += nt) {
@@ -1530,7 +1536,12 @@ __device__ __forceinline__ void solve_body(const SolveCtx& c) {
                     query_local(c, I, p, qid, xl, &qi);
                     if (isfinite(xl[0]) && isfinite(xl[1]) && isfinite(xl[2])) {
                         property_mean(c.P, s, N, np, lattice, qi, xl, cm);
-                        w = latent_var(c.P, s, N, lattice, qi, xl, V, nt);
+                        if (pb) {
+                            const int a = (int)(p - q0), ta = Ntr + (a >> 3);
+                            w = fmax(0.0, double_of_fix(__double_as_longlong(s.A[tix(ta, ta) + te(a & 7, a & 7)])));
+                        } else {
+                            w = latent_var(c.P, s, N, lattice, qi, xl, V, nt);
+                        }
                     }
                 }
                 for (int ch = 0; ch < np; ++ch) c.b.pc[qid * np + ch] = cm[ch];
@@ -1919,7 +1930,7 @@ constexpr int64_t kEmuBytesPerRow = 7 * 8 * kEB * 2 + 8 + 64;
 bool chunk_args(const SolveBatch& b, const DevParams& P, bool bw, ChunkPlanArgs& a) {
     a = ChunkPlanArgs{};
     a.heavy = !bw && (b.want_var || b.nprop > 0);
-    a.cap[0] = (!bw && P.emulate && b.want_var && b.nprop == 0) ? kBorderQ : 0;
+    a.cap[0] = (!bw && P.emulate && b.want_var) ? kBorderQ : 0;
     a.cap[1] = a.cap[2] = a.cap[3] = a.cap[0];  // the emulated buckets
     return a.heavy != 0;
 }
@@ -1929,7 +1940,7 @@ bool chunk_args(const SolveBatch& b, const DevParams& P, bool bw, ChunkPlanArgs&
 // workspaces hold npad + kBorderQ rows.  Otherwise npad rows.
 void emu_rows_for(bool emu, const SolveBatch& b, int& npad, int& qmax, int& nrow) {
     qmax = 0;
-    if (emu && b.want_var && b.nprop == 0) {
+    if (emu && b.want_var) {
         npad = (npad + 31) & ~31;
         qmax = kBorderQ;
     }
